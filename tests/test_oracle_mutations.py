@@ -1,0 +1,97 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and require a pin to catch each.
+
+This shows the pins in tests/oracle_checks.py are discriminating: a dropped
+term, a wrong normaliser, swapped weights, a transposed factor or a wrong
+statistic each make at least one of them fail.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import erx_oracle as eo
+from tests import oracle_checks as oc
+
+
+def _stats_over_p(z):
+    p = z.shape[0]
+    mu = z.sum(axis=0) / p
+    r = z - mu
+    return mu, (r.T @ r) / p
+
+
+def _ema_swapped(mu, k, mu_hat, k_hat, alpha):
+    return alpha * mu + (1 - alpha) * mu_hat, alpha * k + (1 - alpha) * k_hat
+
+
+def _chol_no_ridge(k, ridge):
+    return np.linalg.cholesky(k)
+
+
+def _solve_transposed(z, mu, lower):
+    m = scipy.linalg.solve_triangular(lower.T, (z - mu).T, lower=False)
+    return np.sqrt(np.sum(m * m, axis=0))
+
+
+def _normalise_ddof1(delta):
+    return (delta - delta.mean()) / delta.std(ddof=1)
+
+
+def _stats_uncentred(z):
+    p = z.shape[0]
+    mu = z.sum(axis=0) / p
+    return mu, (z.T @ z) / (p - 1)
+
+
+MUTATIONS = {
+    "cov_over_p": ("line_stats", _stats_over_p),
+    "ema_weights_swapped": ("ema_update", _ema_swapped),
+    "ridge_dropped": ("cholesky_ridge", _chol_no_ridge),
+    "factor_transposed": ("mahalanobis", _solve_transposed),
+    "normalise_ddof1": ("normalise", _normalise_ddof1),
+    "cov_uncentred": ("line_stats", _stats_uncentred),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_mutation_is_caught(name, monkeypatch):
+    attr, bad = MUTATIONS[name]
+    monkeypatch.setattr(eo, attr, bad)
+    failed = []
+    for check, (fn, tol) in oc.ALL_CHECKS.items():
+        try:
+            err = fn()
+        except (np.linalg.LinAlgError, ValueError, FloatingPointError):
+            err = math.inf
+        if not (err <= tol):
+            failed.append(check)
+    assert failed, f"mutation {name} passed every pin"
+
+
+def test_init_from_zero_is_caught(monkeypatch):
+    orig = eo.ERXOracle._update
+
+    def bad(self, mu_hat, k_hat):
+        if self.t == 0:
+            self.mu, self.k = eo.ema_update(np.zeros_like(mu_hat), np.zeros_like(k_hat),
+                                            mu_hat, k_hat, self.alpha)
+        else:
+            orig(self, mu_hat, k_hat)
+
+    monkeypatch.setattr(eo.ERXOracle, "_update", bad)
+    errs = {k: fn() for k, (fn, tol) in oc.ALL_CHECKS.items()}
+    assert any(errs[k] > oc.ALL_CHECKS[k][1] for k in errs)
+
+
+def test_order_swap_is_caught(monkeypatch):
+    orig_init = eo.ERXOracle.__init__
+
+    def swapped(self, *a, **kw):
+        orig_init(self, *a, **kw)
+        self.order = ("score_then_update" if self.order == "update_then_score"
+                      else "update_then_score")
+
+    monkeypatch.setattr(eo.ERXOracle, "__init__", swapped)
+    errs = {k: fn() for k, (fn, tol) in oc.ALL_CHECKS.items()}
+    assert any(errs[k] > oc.ALL_CHECKS[k][1] for k in errs)
