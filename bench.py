@@ -1,0 +1,371 @@
+"""Benchmark of the ERX per-line step on one GB300 (or N replicas).
+
+Workload (the paper's largest band count): 20000 lines x 640 px x 108 bands,
+uint16 12-bit digital numbers, scenes switching every 2000 lines, 0.2 %
+anomalies in 3 x 3 clusters (synthetic, seeded), FP64 form, all 108 bands
+(no projection), alpha 0.1, ridge 1e-5, 99-line warm-up.  One step is one
+pass of the whole line step over the whole cube from a fresh state; the cube
+(2.76 GB) is resident in HBM and larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LINES, WIDTH, BANDS, BITS = 20000, 640, 108, 12
+METRIC = "ERX lines/s, 640 px x 108 bands u16, FP64 form (p50/p99 line latency alongside)"
+UNIT = "lines/s"
+# FP64 pipe of GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2070 MHz (the
+# nominal 1.25 TFLOP/s FP64 rate over 152 SMs at the maximum SM clock).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+IMAD_PEAK_GOPS = 152 * 64 * 2.070        # 32-bit integer multiply-add, per second (G)
+
+
+def _gen_worker(args):
+    name, shape, t0, n, cfg_kw = args
+    from multiprocessing import shared_memory
+
+    import numpy as np
+
+    import synth
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        arr = np.ndarray(shape, dtype=np.uint16, buffer=shm.buf)
+        synth.gen_lines(synth.dn_c2(**cfg_kw), t0, n, out=arr[t0:t0 + n])
+    finally:
+        shm.close()
+    return n
+
+
+def make_cube(n_lines: int, seed: int = 0, workers: int | None = None):
+    """The seeded C2-style cube, generated in parallel by spawned processes."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+
+    import numpy as np
+    shape = (n_lines, WIDTH, BANDS)
+    nbytes = int(np.prod(shape)) * 2
+    workers = workers or min(16, len(os.sched_getaffinity(0)))
+    shm = shared_memory.SharedMemory(create=True, size=nbytes)
+    try:
+        step = max(1, math.ceil(n_lines / (workers * 4)))
+        jobs = [(shm.name, shape, t0, min(step, n_lines - t0),
+                 {"seed": seed, "width": WIDTH, "bands": BANDS})
+                for t0 in range(0, n_lines, step)]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(workers) as pool:
+            pool.map(_gen_worker, jobs)
+        out = np.ndarray(shape, dtype=np.uint16, buffer=shm.buf).copy()
+    finally:
+        shm.close()
+        shm.unlink()
+    return out
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(sample_lines: int, one_thread: bool = False):
+    """Time the FP64 CPU oracle on the first `sample_lines` lines, in a fresh
+    process with the BLAS thread count set to the usable cores."""
+    cores = 1 if one_thread else len(os.sched_getaffinity(0))
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    code = (
+        "import sys, time, json; sys.path.insert(0, %r)\n"
+        "import synth, oracle\n"
+        "cube = synth.gen_lines(synth.dn_c2(width=%d, bands=%d), 0, %d)\n"
+        "t = time.perf_counter(); oracle.run_cube(cube); dt = time.perf_counter() - t\n"
+        "print(json.dumps({'lines': %d, 'seconds': dt}))\n"
+    ) % (ROOT, WIDTH, BANDS, sample_lines, sample_lines)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed: " + r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": res["lines"] / res["seconds"], "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"first {sample_lines} lines of the {LINES}-line workload, "
+                      f"{WIDTH} px x {BANDS} bands u16, FP64 NumPy oracle"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    sample = args.ref_lines
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(sample)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sample / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"C2: {LINES} lines x {WIDTH} px x {BANDS} bands u16 12-bit",
+                       "sample_lines_per_step": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": cb["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2408_14947_gb300 as erx
+    from paper_2408_14947_gb300 import Detector, _build
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    _build.build()
+    erx.load_library()
+    dev = torch.device("cuda", local)
+
+    t_gen = time.perf_counter()
+    cube = make_cube(LINES, seed=rank)
+    gen_s = time.perf_counter() - t_gen
+    x = torch.from_numpy(cube.view(np.int16)).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def detector(**kw):
+        return Detector(BANDS, WIDTH, in_dtype="u16", in_bits=BITS, stream=stream, **kw)
+
+    det = detector(form="fp64")
+    out = (torch.empty((LINES, WIDTH), dtype=torch.float64, device=dev),
+           torch.empty((LINES, WIDTH), dtype=torch.float64, device=dev),
+           torch.empty((LINES, WIDTH), dtype=torch.uint8, device=dev),
+           torch.empty((LINES,), dtype=torch.uint8, device=dev))
+
+    def step(d, o):
+        d.reset()
+        d.push(x, o)
+
+    for _ in range(args.warmup):
+        step(det, out)
+    det.sync()
+    det.profile(True)
+    det.profile_read(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step(det, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    det.sync()
+    ms_total = e0.elapsed_time(e1)
+    prof = det.profile_read(reset=True)
+    det.profile(False)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = LINES * world / (ms_step / 1000.0)
+    launches = sum(v[2] for v in prof.values())
+
+    # roofline of the dominant kernel: the FP64 score kernel (d(d+1)/2 + d DFMA per pixel)
+    d = BANDS
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms_dom, n_dom, _ = prof[dom]
+    blocks = max(1, n_dom // args.steps)
+    lines_per_launch = LINES / blocks
+    flops = {
+        "solve_fp64": 2.0 * WIDTH * (d * (d + 1) / 2 + d),
+        "chol_inv": 2.0 * (d ** 3 / 3.0),
+        "stats_int": 2.0 * WIDTH * d * d,
+    }
+    per_line = flops.get(dom, 0.0)
+    achieved = per_line * lines_per_launch / (ms_dom / n_dom / 1000.0) / 1e9 if n_dom else 0.0
+    if dom == "stats_int":
+        peak, unit, bound = IMAD_PEAK_GOPS * 2, "GOP/s", "alu"
+    else:
+        peak, unit, bound = FP64_PEAK_GFLOPS, "GFLOP/s", "alu"
+    roof = {"bound": bound, "pipe": "fp64" if dom != "stats_int" else "int32", "kernel": dom,
+            "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": None, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2070 MHz"}
+    kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[2] / args.steps,
+                   "share": v[0] / max(1e-9, sum(w[0] for w in prof.values()))}
+               for k, v in prof.items() if v[2]}
+
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+              "data": "synthetic",
+              "config": {"workload": f"C2: {LINES} lines x {WIDTH} px x {BANDS} bands u16 "
+                                     f"12-bit, scenes of 2000 lines, 0.2% 3x3 anomalies",
+                         "form": "fp64", "projection": "none (d = 108)", "alpha": 0.1,
+                         "block_lines": det.cfg.block_lines or "auto",
+                         "l2": "inputs (2.76 GB) larger than L2; no flush",
+                         "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                         "gen_seconds": round(gen_s, 1)},
+              "gpu_launches": launches, "roofline": roof, "kernels": kernels,
+              "clocks": clk.summary()}
+
+    if rank == 0 and not args.quick:
+        # p50 / p99 latency of one line pushed alone (stream mode), after warm-up
+        lat = []
+        det.reset()
+        one = tuple(o[:1] for o in out)
+        for i in range(200):
+            det.push(x[i:i + 1], one)
+        det.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.latency_lines)]
+        for i, (a, b) in enumerate(ev):
+            j = 200 + i % (LINES - 200)
+            a.record(stream)
+            det.push(x[j:j + 1], one)
+            b.record(stream)
+        torch.cuda.synchronize()
+        lat = sorted(a.elapsed_time(b) for a, b in ev)
+        result["latency_ms"] = {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * len(lat))],
+                                "lines": len(lat), "mode": "one line per push"}
+
+        # other forms on the same cube, same step definition
+        forms = {}
+        for name, kw in (("fp32", {"form": "fp32"}),
+                         ("fp64_srp5", {"form": "fp64", "proj": "srp", "proj_dim": 5}),
+                         ("fp32_srp5", {"form": "fp32", "proj": "srp", "proj_dim": 5})):
+            dd = detector(**kw)
+            sdt = torch.float64 if kw["form"] == "fp64" else torch.float32
+            oo = (torch.empty((LINES, WIDTH), dtype=sdt, device=dev),
+                  torch.empty((LINES, WIDTH), dtype=sdt, device=dev), out[2], out[3])
+            step(dd, oo)
+            dd.sync()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(2):
+                step(dd, oo)
+            b.record(stream)
+            torch.cuda.synchronize()
+            dd.sync()
+            forms[name] = {"lines_per_s": LINES * 2 / (a.elapsed_time(b) / 1000.0)}
+            dd.close()
+        result["forms"] = forms
+
+        # end to end through the public host-buffer call: pinned input, results to host
+        xh = torch.from_numpy(cube.view(np.int16)).pin_memory()
+        oh = (torch.empty((LINES, WIDTH), dtype=torch.float64).pin_memory(),
+              torch.empty((LINES, WIDTH), dtype=torch.float64).pin_memory(),
+              torch.empty((LINES, WIDTH), dtype=torch.uint8).pin_memory(),
+              torch.empty((LINES,), dtype=torch.uint8).pin_memory())
+        det.reset()
+        det.push_host(xh, oh)
+        ts = []
+        for _ in range(max(1, min(args.steps, 3))):
+            det.reset()
+            t0 = time.perf_counter()
+            det.push_host(xh, oh)
+            ts.append(time.perf_counter() - t0)
+        h2d = cube.nbytes
+        d2h = sum(o.numel() * o.element_size() for o in oh)
+        result["e2e"] = {"value": LINES / statistics.median(ts), "unit": UNIT,
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        result["cpu_baseline"] = cpu_baseline(args.cpu_lines)
+    elif rank == 0:
+        result["e2e"] = None
+        result["cpu_baseline"] = None
+    det.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-lines", type=int, default=3000)
+    ap.add_argument("--ref-lines", type=int, default=1000)
+    ap.add_argument("--latency-lines", type=int, default=5000)
+    ap.add_argument("--quick", action="store_true", help="skip latency, forms, e2e, baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

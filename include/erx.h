@@ -1,0 +1,183 @@
+/*
+ * erx.h - C ABI of the GB300 (sm_103a) ERX per-line engine.
+ *
+ * ERX (Garske et al., "ERX: A fast real-time anomaly detection algorithm for
+ * hyperspectral line scanning", Sec. III) scores every pixel of each incoming
+ * line of a line-scan cube by its Mahalanobis distance to an exponentially
+ * moving background mean and covariance, then normalises the scores per line.
+ * One call of erx_push_lines runs, for every line t it is given:
+ *
+ *   S1 project     Z_t = X_t W  (sparse random projection, Sec. III-B), or Z_t = X_t
+ *   S2 line stats  mu_hat_t = mean of the pixels, K_hat_t = 1/(p-1) centred scatter (Sec. III-C)
+ *   S3 EMA         mu_t = (1-a) mu_{t-1} + a mu_hat_t, K_t likewise; t = 0 starts from line 0 (Sec. III-C)
+ *   S4 factor      L_t L_t^T = K_t + ridge I (Sec. III-D)
+ *   S5 score       L_t m_i = z_i - mu_t, delta_i = sqrt(m_i . m_i) (Sec. III-D)
+ *   S6 normalise   delta_N,i = (delta_i - mean) / std (population std), mask = delta_N >= tau (Sec. III-E)
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers owned by the caller; they must
+ *    stay valid until the work enqueued on the context's stream has finished.
+ *    Pointers named *_host are host pointers.
+ *  - All work is enqueued on the CUDA stream given to erx_create and the call
+ *    returns after enqueueing (erx_push_lines) unless stated otherwise.
+ *  - Errors found on the device (a non-positive or non-finite pivot, an input
+ *    value above the declared bit depth) are deferred: they are reported by
+ *    erx_sync or by the next call on the context.
+ *  - ERX_EINVAL leaves the context unchanged.  After ERX_ECUDA the context is
+ *    failed and only erx_destroy may be called.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *  - No C++ exception crosses this interface.
+ */
+#ifndef ERX_H
+#define ERX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct erx_ctx erx_ctx;
+
+typedef enum {
+  ERX_OK = 0,
+  ERX_EINVAL = 1,       /* invalid argument; nothing was done */
+  ERX_ENOMEM = 2,       /* device or host allocation failed */
+  ERX_ECUDA = 3,        /* a CUDA call failed; the context is failed */
+  ERX_ENOTPD = 4,       /* K_t + ridge I was not positive definite at some line */
+  ERX_ERANGE = 5,       /* an integer input sample exceeded 2^in_bits - 1 */
+  ERX_ESTATE = 6,       /* call not valid in the context's current state */
+  ERX_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} erx_status;
+
+/* projection (Sec. III-B) */
+enum { ERX_PROJ_NONE = 0, ERX_PROJ_SRP = 1 };
+/* order of update and scoring (Sec. III-C/III-D: the paper scores with mu_t, L_t) */
+enum { ERX_UPDATE_THEN_SCORE = 0, ERX_SCORE_THEN_UPDATE = 1 };
+/* input sample type, lines laid out [pixel][band] (band-interleaved-by-pixel) */
+enum { ERX_U16 = 0, ERX_F32 = 1, ERX_F64 = 2 };
+/* arithmetic form of S2 and S5; S3 and S4 are FP64 in every form */
+enum { ERX_FORM_FP64 = 0, ERX_FORM_FP32 = 1 };
+
+typedef struct {
+  int32_t bands;        /* b >= 1 */
+  int32_t width;        /* p >= 2 pixels per line (K_hat needs p - 1 > 0) */
+  double momentum;      /* alpha in (0, 1]; paper default 0.1 (Sec. III-C) */
+  int32_t proj;         /* ERX_PROJ_NONE (d = b) or ERX_PROJ_SRP */
+  int32_t proj_dim;     /* d for SRP, 1 <= d <= b; paper default 5 (Sec. III-B) */
+  uint64_t seed;        /* seed of the SRP matrix when srp_weights is NULL */
+  double ridge;         /* added to the diagonal at factorisation only; 1e-5 (Sec. III-D) */
+  int32_t warmup_lines; /* lines flagged not-detecting at the start; 99 (Sec. IV-B) */
+  int32_t order;        /* ERX_UPDATE_THEN_SCORE (paper) or ERX_SCORE_THEN_UPDATE */
+  int32_t in_dtype;     /* ERX_U16, ERX_F32 or ERX_F64 */
+  int32_t in_bits;      /* for ERX_U16: samples are < 2^in_bits (1..16); else ignored */
+  int32_t form;         /* ERX_FORM_FP64 or ERX_FORM_FP32 */
+  double threshold;     /* tau_N for the mask (Sec. III-E) */
+  int32_t block_lines;  /* lines processed per internal block; 0 = automatic */
+  const double* srp_weights; /* optional b x d row-major host matrix replacing the drawn SRP */
+} erx_config;
+
+/* Fill *cfg with the paper's defaults for a b-band, p-pixel line:
+ * alpha 0.1, no projection, ridge 1e-5, warm-up 99, update-then-score,
+ * ERX_F32 input, FP64 form, threshold 3.0, SRP d = 5 when proj is set. */
+void erx_config_default(erx_config* cfg, int32_t bands, int32_t width);
+
+/* Create a context.  cuda_stream is a cudaStream_t (NULL: the legacy default
+ * stream).  Allocates the FP64 state (mu: d, K: d x d) and per-block scratch
+ * on the current device.  Limits: d <= 224 (the factor of K_t + ridge I is
+ * held in one SM's shared memory), p <= 1 << 20.  Returns ERX_EINVAL on a bad
+ * config, ERX_EUNSUPPORTED beyond the limits, ERX_ENOMEM / ERX_ECUDA on
+ * allocation failure. */
+erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out);
+
+/* Process n_lines consecutive lines, in order, continuing the context's stream
+ * of lines.  lines_dev: n_lines lines, line j at lines_dev + j*line_stride_bytes,
+ * each p x b samples of in_dtype, row-major [pixel][band]; line_stride_bytes
+ * = 0 means p*b*sizeof(sample).  Outputs (device, caller-owned, row-major
+ * [line][pixel]):
+ *   delta_dev       delta (Sec. III-D); double for ERX_FORM_FP64, float otherwise
+ *   delta_norm_dev  delta_N (Sec. III-E), same type as delta; may be NULL
+ *   mask_dev        uint8 delta_N >= threshold; may be NULL
+ *   detecting_dev   uint8 per line, 1 once the warm-up lines have passed; may be NULL
+ * Asynchronous on the context's stream. */
+erx_status erx_push_lines(erx_ctx* ctx, const void* lines_dev, int64_t n_lines,
+                          int64_t line_stride_bytes, void* delta_dev, void* delta_norm_dev,
+                          uint8_t* mask_dev, uint8_t* detecting_dev);
+
+/* As erx_push_lines, with every buffer in HOST memory (pageable or pinned).
+ * Lines are staged to the device in blocks through library-owned pinned and
+ * device buffers, the copies overlapping the compute of the previous block.
+ * Synchronous: returns when the results are in the host buffers. */
+erx_status erx_push_lines_host(erx_ctx* ctx, const void* lines_host, int64_t n_lines,
+                               int64_t line_stride_bytes, void* delta_host,
+                               void* delta_norm_host, uint8_t* mask_host,
+                               uint8_t* detecting_host);
+
+/* Wait for the context's stream and report deferred device errors
+ * (ERX_ENOTPD, ERX_ERANGE) raised since the last erx_sync.  *bad_line (may be
+ * NULL) receives the global index of the first offending line or -1. */
+erx_status erx_sync(erx_ctx* ctx, int64_t* bad_line);
+
+/* Forget every line seen: the next line pushed is line 0 again. */
+erx_status erx_reset(erx_ctx* ctx);
+
+/* Copy the state out (host pointers): *t = lines seen, mu (d), K (d x d
+ * row-major, symmetric).  Synchronises the context's stream. */
+erx_status erx_get_state(erx_ctx* ctx, int64_t* t, double* mu_host, double* K_host);
+
+/* Replace the state (host pointers): t lines seen, mu (d), K (d x d, the
+ * lower triangle is used).  t = 0 makes the next line initialise the state. */
+erx_status erx_set_state(erx_ctx* ctx, int64_t t, const double* mu_host, const double* K_host);
+
+/* Projected dimension d of the context (b without projection). */
+int32_t erx_dim(const erx_ctx* ctx);
+
+/* Copy the context's b x d projection matrix (row-major) to w_host. */
+erx_status erx_get_projection(const erx_ctx* ctx, double* w_host);
+
+/* Draw the b x d SRP matrix of Sec. III-B (host only, no GPU needed): entry
+ * (i, j) is sqrt(sqrt(b)/d) times +1, -1 or 0 with probabilities
+ * 1/(2 sqrt b), 1/(2 sqrt b), 1 - 1/sqrt b, decided by output k = i*d + j of
+ * SplitMix64 (Steele, Lea and Flood, 2014) seeded with seed: u = (z >> 11)
+ * 2^-53, +1 if u < 1/(2s), -1 if u < 1/s. */
+erx_status erx_srp_weights(int32_t bands, int32_t dim, uint64_t seed, double* w_host);
+
+/* Kernels of the line step, for erx_profile_read. */
+enum {
+  ERX_K_PROJECT = 0,    /* S1 sparse projection */
+  ERX_K_STATS_INT = 1,  /* S2 exact integer sums (u16, no projection) */
+  ERX_K_MEAN = 2,       /* S2 line means */
+  ERX_K_STATS_FP = 3,   /* S2 centred scatter, floating point */
+  ERX_K_EMA = 4,        /* S3 EMA scan */
+  ERX_K_CHOL = 5,       /* S4 Cholesky and inverse */
+  ERX_K_SOLVE_FP64 = 6, /* S5 scores, FP64 */
+  ERX_K_SOLVE_FP32 = 7, /* S5 scores, FP32 */
+  ERX_K_NORMALISE = 8,  /* S6 normalisation */
+  ERX_K_COUNT = 9
+};
+
+/* Per-kernel timing.  While enabled (on != 0), every kernel the context
+ * launches is bracketed by two CUDA events recorded on the context's stream.
+ * Launch counts are kept whether or not timing is enabled. */
+erx_status erx_profile_enable(erx_ctx* ctx, int32_t on);
+
+/* Totals since the last call with reset != 0: *launches kernel launches of
+ * kind `kernel` (ERX_K_*) and, for launches made while timing was enabled,
+ * *total_ms their summed device time.  Synchronises the context's stream. */
+erx_status erx_profile_read(erx_ctx* ctx, int32_t kernel, int32_t reset, double* total_ms,
+                            int64_t* timed_launches, int64_t* launches);
+
+/* Static name of kernel kind `kernel`, or NULL. */
+const char* erx_kernel_name(int32_t kernel);
+
+/* Release the context and everything it allocated.  NULL is a no-op. */
+erx_status erx_destroy(erx_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* erx_status_str(erx_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ERX_H */

@@ -1,0 +1,652 @@
+// Host engine and C ABI of the ERX per-line step (include/erx.h).
+//
+// A context owns the FP64 background state (mu: d, K: packed lower d x d) and
+// the scratch for one block of T lines.  erx_push_lines cuts the caller's
+// lines into blocks and, per block, enqueues on the context's stream:
+//   [S1 project] -> S2 stats -> S3 EMA scan -> S4 chol + inverse -> S5 scores -> S6 normalise
+// The per-line statistics of a block are independent, so S2, S4 and S5 run
+// all T lines at once; only S3 is sequential in t, as a d^2-wide scan.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/erx.h"
+#include "erx_internal.cuh"
+
+using namespace erx;
+
+struct erx_ctx {
+  erx_config cfg{};
+  int B = 0, W = 0, d = 0, T = 0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool int_stats = false;
+  bool fp64 = true;
+  bool failed = false;
+  int64_t t = 0;
+  std::vector<double> w_host;   // b x d projection (empty without projection)
+  // device buffers
+  double* mu_state = nullptr;
+  double* K_state = nullptr;
+  double* mu_t = nullptr;
+  double* K_t = nullptr;
+  double* Linv = nullptr;
+  float* Linv32 = nullptr;
+  uint64_t* S1i = nullptr;
+  uint64_t* S2i = nullptr;
+  double* mu_hat = nullptr;
+  double* shift = nullptr;
+  double* S2f = nullptr;
+  void* Z = nullptr;
+  int* colptr = nullptr;
+  int* rows = nullptr;
+  double* vals = nullptr;
+  unsigned long long* err = nullptr;
+  // host staging for erx_push_lines_host
+  void* h_in[2] = {nullptr, nullptr};
+  void* d_in[2] = {nullptr, nullptr};
+  void* h_out = nullptr;
+  void* d_out = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr};
+  cudaEvent_t ev_used[2] = {nullptr, nullptr};
+  std::vector<void*> allocs;
+  // per-kernel launch counts and event-bracketed timing
+  bool profiling = false;
+  int64_t launches[ERX_K_COUNT] = {};
+  int64_t timed[ERX_K_COUNT] = {};
+  double total_ms[ERX_K_COUNT] = {};
+  struct Pending { int k; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> spare_events;
+};
+
+namespace {
+
+size_t elem_size(int dt) { return dt == ERX_U16 ? 2 : dt == ERX_F32 ? 4 : 8; }
+
+template <typename T>
+erx_status dalloc(erx_ctx* c, T** p, size_t n) {
+  void* q = nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc(&q, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return ERX_ENOMEM;
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return ERX_OK;
+}
+
+void free_all(erx_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  for (int i = 0; i < 2; ++i) {
+    if (c->h_in[i]) cudaFreeHost(c->h_in[i]);
+    if (c->ev_in[i]) cudaEventDestroy(c->ev_in[i]);
+    if (c->ev_used[i]) cudaEventDestroy(c->ev_used[i]);
+  }
+  if (c->h_out) cudaFreeHost(c->h_out);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  for (auto& p : c->pending) cudaEventDestroy(p.a), cudaEventDestroy(p.b);
+  for (auto e : c->spare_events) cudaEventDestroy(e);
+  c->pending.clear();
+  c->spare_events.clear();
+}
+
+cudaEvent_t take_event(erx_ctx* c) {
+  if (!c->spare_events.empty()) {
+    cudaEvent_t e = c->spare_events.back();
+    c->spare_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel launch: counts it and, when profiling, records events around it.
+struct KernelScope {
+  erx_ctx* c;
+  int k;
+  cudaEvent_t a = nullptr;
+  KernelScope(erx_ctx* c_, int k_) : c(c_), k(k_) {
+    c->launches[k]++;
+    if (c->profiling) {
+      a = take_event(c);
+      if (a) cudaEventRecord(a, c->stream);
+    }
+  }
+  ~KernelScope() {
+    if (a) {
+      cudaEvent_t b = take_event(c);
+      if (b) {
+        cudaEventRecord(b, c->stream);
+        c->pending.push_back({k, a, b});
+      } else {
+        c->spare_events.push_back(a);
+      }
+    }
+  }
+};
+
+void resolve_pending(erx_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->total_ms[p.k] += ms;
+      c->timed[p.k]++;
+    }
+    c->spare_events.push_back(p.a);
+    c->spare_events.push_back(p.b);
+  }
+  c->pending.clear();
+  cudaGetLastError();
+}
+
+uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+erx_status check_cuda(erx_ctx* c, cudaError_t e) {
+  if (e == cudaSuccess) return ERX_OK;
+  if (c) c->failed = true;
+  return ERX_ECUDA;
+}
+
+erx_status validate(const erx_config* cfg) {
+  if (!cfg) return ERX_EINVAL;
+  if (cfg->bands < 1 || cfg->width < 2) return ERX_EINVAL;
+  if (!(cfg->momentum > 0.0 && cfg->momentum <= 1.0)) return ERX_EINVAL;
+  if (!(cfg->ridge >= 0.0) || !std::isfinite(cfg->ridge)) return ERX_EINVAL;
+  if (cfg->proj != ERX_PROJ_NONE && cfg->proj != ERX_PROJ_SRP) return ERX_EINVAL;
+  if (cfg->proj == ERX_PROJ_SRP && (cfg->proj_dim < 1 || cfg->proj_dim > cfg->bands))
+    return ERX_EINVAL;
+  if (cfg->order != ERX_UPDATE_THEN_SCORE && cfg->order != ERX_SCORE_THEN_UPDATE)
+    return ERX_EINVAL;
+  if (cfg->in_dtype < ERX_U16 || cfg->in_dtype > ERX_F64) return ERX_EINVAL;
+  if (cfg->in_dtype == ERX_U16 && (cfg->in_bits < 1 || cfg->in_bits > 16)) return ERX_EINVAL;
+  if (cfg->form != ERX_FORM_FP64 && cfg->form != ERX_FORM_FP32) return ERX_EINVAL;
+  if (cfg->block_lines < 0 || cfg->warmup_lines < 0) return ERX_EINVAL;
+  const int d = cfg->proj == ERX_PROJ_SRP ? cfg->proj_dim : cfg->bands;
+  if (d > kMaxDim || cfg->width > (1 << 20) || cfg->bands > 65536) return ERX_EUNSUPPORTED;
+  return ERX_OK;
+}
+
+// Enqueue the whole step for `n` lines at `x` (device), outputs at line offset 0 of the given
+// pointers.
+erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems, void* delta,
+                     void* dn, uint8_t* mask, uint8_t* det) {
+  const int T = (int)n, W = c->W, d = c->d, B = c->B;
+  const int in_t = c->cfg.in_dtype;
+  cudaStream_t st = c->stream;
+  const void* zsrc = x;
+  int ztype = in_t;
+  int64_t zstride = stride_elems;
+  int ps = B;
+  if (!c->w_host.empty()) {
+    KernelScope ks(c, ERX_K_PROJECT);
+    launch_project(in_t, x, stride_elems, B, W, d, T, c->colptr, c->rows, c->vals, c->fp64,
+                   c->Z, st);
+    zsrc = c->Z;
+    ztype = c->fp64 ? ERX_F64 : ERX_F32;
+    zstride = (int64_t)W * d;
+    ps = d;
+  }
+  if (c->int_stats) {
+    KernelScope ks(c, ERX_K_STATS_INT);
+    launch_stats_int((const uint16_t*)x, stride_elems, W, d, (1u << c->cfg.in_bits) - 1u, T,
+                     c->S1i, c->S2i, c->err, c->t, st);
+  } else {
+    {
+      KernelScope ks(c, ERX_K_MEAN);
+      launch_mean(ztype, zsrc, zstride, ps, W, d, T, !c->fp64, c->mu_hat, c->shift, st);
+    }
+    KernelScope ks(c, ERX_K_STATS_FP);
+    launch_stats_fp(ztype, c->fp64, zsrc, zstride, ps, W, d, T, c->shift, c->S2f, st);
+  }
+  {
+    KernelScope ks(c, ERX_K_EMA);
+    launch_ema_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W,
+                  c->cfg.momentum, c->t, c->cfg.order, c->mu_state, c->K_state, c->mu_t, c->K_t,
+                  st);
+  }
+  {
+    KernelScope ks(c, ERX_K_CHOL);
+    launch_chol_inv(c->K_t, d, T, c->cfg.ridge, c->Linv, c->fp64 ? nullptr : c->Linv32, c->err,
+                    c->t, st);
+  }
+  if (c->fp64) {
+    KernelScope ks(c, ERX_K_SOLVE_FP64);
+    launch_solve_fp64(ztype, zsrc, zstride, ps, W, d, T, c->mu_t, c->Linv, (double*)delta, st);
+  } else {
+    KernelScope ks(c, ERX_K_SOLVE_FP32);
+    launch_solve_fp32(ztype, zsrc, zstride, ps, W, d, T, c->mu_t, c->Linv32, (float*)delta, st);
+  }
+  {
+    KernelScope ks(c, ERX_K_NORMALISE);
+    launch_normalise(c->fp64, delta, W, T, c->cfg.threshold, c->t, c->cfg.warmup_lines, dn,
+                     mask, det, st);
+  }
+  c->t += n;
+  return check_cuda(c, cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+void erx_config_default(erx_config* cfg, int32_t bands, int32_t width) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->bands = bands;
+  cfg->width = width;
+  cfg->momentum = 0.1;
+  cfg->proj = ERX_PROJ_NONE;
+  cfg->proj_dim = 5;
+  cfg->seed = 0;
+  cfg->ridge = 1e-5;
+  cfg->warmup_lines = 99;
+  cfg->order = ERX_UPDATE_THEN_SCORE;
+  cfg->in_dtype = ERX_F32;
+  cfg->in_bits = 16;
+  cfg->form = ERX_FORM_FP64;
+  cfg->threshold = 3.0;
+  cfg->block_lines = 0;
+  cfg->srp_weights = nullptr;
+}
+
+erx_status erx_srp_weights(int32_t bands, int32_t dim, uint64_t seed, double* w) {
+  if (bands < 1 || dim < 1 || !w) return ERX_EINVAL;
+  const double s = std::sqrt((double)bands);
+  const double p_half = 1.0 / (2.0 * s), p_nz = 1.0 / s;
+  const double mag = std::sqrt(s) / std::sqrt((double)dim);
+  for (int64_t i = 0; i < bands; ++i)
+    for (int64_t j = 0; j < dim; ++j) {
+      const uint64_t z = splitmix64_at(seed, (uint64_t)(i * dim + j));
+      const double u = (double)(z >> 11) * 0x1.0p-53;
+      w[i * dim + j] = u < p_half ? mag : (u < p_nz ? -mag : 0.0);
+    }
+  return ERX_OK;
+}
+
+erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
+  if (!out) return ERX_EINVAL;
+  *out = nullptr;
+  erx_status s = validate(cfg);
+  if (s != ERX_OK) return s;
+  erx_ctx* c = new (std::nothrow) erx_ctx();
+  if (!c) return ERX_ENOMEM;
+  c->cfg = *cfg;
+  c->cfg.srp_weights = nullptr;
+  c->B = cfg->bands;
+  c->W = cfg->width;
+  c->d = cfg->proj == ERX_PROJ_SRP ? cfg->proj_dim : cfg->bands;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->fp64 = cfg->form == ERX_FORM_FP64;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return ERX_ECUDA;
+  }
+  const int B = c->B, W = c->W, d = c->d;
+  if (cfg->proj == ERX_PROJ_SRP) {
+    c->w_host.resize((size_t)B * d);
+    if (cfg->srp_weights)
+      std::memcpy(c->w_host.data(), cfg->srp_weights, sizeof(double) * B * d);
+    else
+      erx_srp_weights(B, d, cfg->seed, c->w_host.data());
+  }
+  // exact integer statistics: u16 samples, no projection, and p^2 maxv^2 < 2^62
+  const double maxv = std::ldexp(1.0, cfg->in_bits) - 1.0;
+  c->int_stats = cfg->in_dtype == ERX_U16 && cfg->proj == ERX_PROJ_NONE &&
+                 (double)W * maxv < 2.1e9;
+  // block size: keep the per-block scratch near 256 MiB
+  const int64_t P = packed_size(d);
+  size_t per_line = (size_t)P * 8 * 2 + (size_t)d * 8 * 4 + (size_t)d * d * 8 +
+                    (c->fp64 ? 0 : (size_t)P * 4) + (c->w_host.empty() ? 0 : (size_t)W * d * 8);
+  int T = cfg->block_lines > 0 ? cfg->block_lines
+                               : (int)std::max<size_t>(1, (256ull << 20) / per_line);
+  T = std::min(T, 4096);
+  c->T = T;
+  if (configure_factor_kernels() != cudaSuccess || configure_solve_kernels() != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return ERX_ECUDA;
+  }
+  s = ERX_OK;
+#define ERX_A(p, n) \
+  if (s == ERX_OK) s = dalloc(c, &c->p, (size_t)(n))
+  ERX_A(mu_state, d);
+  ERX_A(K_state, P);
+  ERX_A(mu_t, (size_t)T * d);
+  ERX_A(K_t, (size_t)T * P);
+  ERX_A(Linv, (size_t)T * P);
+  if (!c->fp64) ERX_A(Linv32, (size_t)T * P);
+  if (c->int_stats) {
+    ERX_A(S1i, (size_t)T * d);
+    ERX_A(S2i, (size_t)T * d * d);
+  } else {
+    ERX_A(mu_hat, (size_t)T * d);
+    ERX_A(shift, (size_t)T * d);
+    ERX_A(S2f, (size_t)T * d * d);
+  }
+  ERX_A(err, kErrSlots);
+#undef ERX_A
+  if (s == ERX_OK && !c->w_host.empty()) {
+    std::vector<int> cp(d + 1, 0), rw;
+    std::vector<double> vl;
+    for (int j = 0; j < d; ++j) {
+      for (int i = 0; i < B; ++i) {
+        const double v = c->w_host[(size_t)i * d + j];
+        if (v != 0.0) rw.push_back(i), vl.push_back(v);
+      }
+      cp[j + 1] = (int)rw.size();
+    }
+    s = dalloc(c, &c->colptr, cp.size());
+    if (s == ERX_OK) s = dalloc(c, &c->rows, std::max<size_t>(1, rw.size()));
+    if (s == ERX_OK) s = dalloc(c, &c->vals, std::max<size_t>(1, vl.size()));
+    void* zp = nullptr;
+    if (s == ERX_OK) {
+      s = c->fp64 ? dalloc(c, (double**)&zp, (size_t)T * W * d)
+                  : dalloc(c, (float**)&zp, (size_t)T * W * d);
+      c->Z = zp;
+    }
+    if (s == ERX_OK) {
+      cudaMemcpy(c->colptr, cp.data(), cp.size() * sizeof(int), cudaMemcpyHostToDevice);
+      if (!rw.empty()) {
+        cudaMemcpy(c->rows, rw.data(), rw.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->vals, vl.data(), vl.size() * sizeof(double), cudaMemcpyHostToDevice);
+      }
+    }
+  }
+  if (s == ERX_OK) {
+    if (cudaMemset(c->mu_state, 0, sizeof(double) * d) != cudaSuccess ||
+        cudaMemset(c->K_state, 0, sizeof(double) * P) != cudaSuccess ||
+        cudaMemset(c->err, 0xff, sizeof(unsigned long long) * kErrSlots) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      s = ERX_ECUDA;
+  }
+  if (s != ERX_OK) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return ERX_OK;
+}
+
+erx_status erx_push_lines(erx_ctx* c, const void* lines, int64_t n, int64_t stride_bytes,
+                          void* delta, void* dn, uint8_t* mask, uint8_t* det) {
+  if (!c) return ERX_EINVAL;
+  if (c->failed) return ERX_ECUDA;
+  if (n < 0 || (n > 0 && (!lines || !delta))) return ERX_EINVAL;
+  const size_t es = elem_size(c->cfg.in_dtype);
+  const int64_t line_elems = (int64_t)c->W * c->B;
+  if (stride_bytes == 0) stride_bytes = line_elems * (int64_t)es;
+  if (stride_bytes < line_elems * (int64_t)es || stride_bytes % (int64_t)es) return ERX_EINVAL;
+  const int64_t stride = stride_bytes / (int64_t)es;
+  const size_t ss = c->fp64 ? 8 : 4;
+  for (int64_t b = 0; b < n; b += c->T) {
+    const int64_t m = std::min<int64_t>(c->T, n - b);
+    const char* x = (const char*)lines + b * stride_bytes;
+    erx_status s = run_block(c, x, m, stride, (char*)delta + (size_t)b * c->W * ss,
+                             dn ? (char*)dn + (size_t)b * c->W * ss : nullptr,
+                             mask ? mask + (size_t)b * c->W : nullptr, det ? det + b : nullptr);
+    if (s != ERX_OK) return s;
+  }
+  return ERX_OK;
+}
+
+erx_status erx_push_lines_host(erx_ctx* c, const void* lines, int64_t n, int64_t stride_bytes,
+                               void* delta, void* dn, uint8_t* mask, uint8_t* det) {
+  if (!c) return ERX_EINVAL;
+  if (c->failed) return ERX_ECUDA;
+  if (n < 0 || (n > 0 && (!lines || !delta))) return ERX_EINVAL;
+  const size_t es = elem_size(c->cfg.in_dtype);
+  const int64_t line_elems = (int64_t)c->W * c->B;
+  const size_t line_bytes = (size_t)line_elems * es;
+  if (stride_bytes == 0) stride_bytes = (int64_t)line_bytes;
+  if (stride_bytes < (int64_t)line_bytes || stride_bytes % (int64_t)es) return ERX_EINVAL;
+  const int T = c->T, W = c->W;
+  const size_t ss = c->fp64 ? 8 : 4;
+  // per line outputs: delta, delta_n (ss each), mask (1); detecting (1) per line
+  const size_t out_line = (size_t)W * (2 * ss + 1) + 1;
+  if (!c->copy_stream) {
+    erx_status s = ERX_OK;
+    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return check_cuda(c, cudaGetLastError());
+    for (int i = 0; i < 2 && s == ERX_OK; ++i) {
+      if (cudaMallocHost(&c->h_in[i], (size_t)T * line_bytes) != cudaSuccess) s = ERX_ENOMEM;
+      if (s == ERX_OK) s = dalloc(c, (char**)&c->d_in[i], (size_t)T * line_bytes);
+      if (s == ERX_OK && (cudaEventCreateWithFlags(&c->ev_in[i], cudaEventDisableTiming) !=
+                              cudaSuccess ||
+                          cudaEventCreateWithFlags(&c->ev_used[i], cudaEventDisableTiming) !=
+                              cudaSuccess))
+        s = ERX_ECUDA;
+    }
+    if (s == ERX_OK && cudaMallocHost(&c->h_out, (size_t)T * out_line) != cudaSuccess)
+      s = ERX_ENOMEM;
+    if (s == ERX_OK) s = dalloc(c, (char**)&c->d_out, (size_t)T * out_line);
+    if (s != ERX_OK) {
+      cudaGetLastError();
+      return s;
+    }
+  }
+  // Input: pinned caller memory is copied directly; pageable memory through h_in.
+  cudaPointerAttributes pa{};
+  const bool pinned = cudaPointerGetAttributes(&pa, lines) == cudaSuccess &&
+                      (pa.type == cudaMemoryTypeHost);
+  cudaGetLastError();
+  const int64_t nb = (n + T - 1) / T;
+  auto stage = [&](int64_t b) -> erx_status {
+    const int slot = (int)(b & 1);
+    const int64_t m = std::min<int64_t>(T, n - b * T);
+    const char* src = (const char*)lines + b * T * stride_bytes;
+    // the slot's previous block must have been consumed by the compute stream
+    if (cudaStreamWaitEvent(c->copy_stream, c->ev_used[slot], 0) != cudaSuccess)
+      return check_cuda(c, cudaGetLastError());
+    if (pinned && stride_bytes == (int64_t)line_bytes) {
+      if (cudaMemcpyAsync(c->d_in[slot], src, (size_t)m * line_bytes, cudaMemcpyHostToDevice,
+                          c->copy_stream) != cudaSuccess)
+        return check_cuda(c, cudaGetLastError());
+    } else {
+      if (cudaEventSynchronize(c->ev_in[slot]) != cudaSuccess)
+        return check_cuda(c, cudaGetLastError());
+      for (int64_t j = 0; j < m; ++j)
+        std::memcpy((char*)c->h_in[slot] + j * line_bytes, src + j * stride_bytes, line_bytes);
+      if (cudaMemcpyAsync(c->d_in[slot], c->h_in[slot], (size_t)m * line_bytes,
+                          cudaMemcpyHostToDevice, c->copy_stream) != cudaSuccess)
+        return check_cuda(c, cudaGetLastError());
+    }
+    if (cudaEventRecord(c->ev_in[slot], c->copy_stream) != cudaSuccess)
+      return check_cuda(c, cudaGetLastError());
+    return ERX_OK;
+  };
+  if (nb > 0) {
+    erx_status s = stage(0);
+    if (s != ERX_OK) return s;
+  }
+  for (int64_t b = 0; b < nb; ++b) {
+    const int slot = (int)(b & 1);
+    const int64_t m = std::min<int64_t>(T, n - b * T);
+    if (b + 1 < nb) {
+      erx_status s = stage(b + 1);
+      if (s != ERX_OK) return s;
+    }
+    if (cudaStreamWaitEvent(c->stream, c->ev_in[slot], 0) != cudaSuccess)
+      return check_cuda(c, cudaGetLastError());
+    char* o = (char*)c->d_out;
+    void* d_delta = o;
+    void* d_dn = o + (size_t)T * W * ss;
+    uint8_t* d_mask = (uint8_t*)(o + (size_t)T * W * ss * 2);
+    uint8_t* d_det = d_mask + (size_t)T * W;
+    erx_status s = run_block(c, c->d_in[slot], m, (int64_t)(line_bytes / es), d_delta,
+                             dn ? d_dn : nullptr, mask ? d_mask : nullptr,
+                             det ? d_det : nullptr);
+    if (s != ERX_OK) return s;
+    if (cudaEventRecord(c->ev_used[slot], c->stream) != cudaSuccess)
+      return check_cuda(c, cudaGetLastError());
+    // results of this block back to the caller
+    const size_t off = (size_t)b * T;
+    cudaError_t e = cudaMemcpyAsync((char*)delta + off * W * ss, d_delta, (size_t)m * W * ss,
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && dn)
+      e = cudaMemcpyAsync((char*)dn + off * W * ss, d_dn, (size_t)m * W * ss,
+                          cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && mask)
+      e = cudaMemcpyAsync(mask + off * W, d_mask, (size_t)m * W, cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (e == cudaSuccess && det)
+      e = cudaMemcpyAsync(det + off, d_det, (size_t)m, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return check_cuda(c, e);
+  }
+  erx_status s = check_cuda(c, cudaStreamSynchronize(c->copy_stream));
+  if (s == ERX_OK) s = check_cuda(c, cudaStreamSynchronize(c->stream));
+  return s;
+}
+
+erx_status erx_sync(erx_ctx* c, int64_t* bad_line) {
+  if (bad_line) *bad_line = -1;
+  if (!c) return ERX_EINVAL;
+  if (c->failed) return ERX_ECUDA;
+  unsigned long long e[kErrSlots];
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaMemcpy(e, c->err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return check_cuda(c, cudaGetLastError());
+  if (cudaMemset(c->err, 0xff, sizeof(e)) != cudaSuccess) return check_cuda(c, cudaGetLastError());
+  if (e[kErrNotPD] != ~0ull) {
+    if (bad_line) *bad_line = (int64_t)e[kErrNotPD];
+    return ERX_ENOTPD;
+  }
+  if (e[kErrRange] != ~0ull) {
+    if (bad_line) *bad_line = (int64_t)e[kErrRange];
+    return ERX_ERANGE;
+  }
+  return ERX_OK;
+}
+
+erx_status erx_reset(erx_ctx* c) {
+  if (!c) return ERX_EINVAL;
+  if (c->failed) return ERX_ECUDA;
+  c->t = 0;
+  return ERX_OK;
+}
+
+erx_status erx_get_state(erx_ctx* c, int64_t* t, double* mu, double* K) {
+  if (!c) return ERX_EINVAL;
+  if (c->failed) return ERX_ECUDA;
+  const int d = c->d;
+  const int64_t P = packed_size(d);
+  std::vector<double> kp((size_t)P);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, cudaGetLastError());
+  if (mu && cudaMemcpy(mu, c->mu_state, sizeof(double) * d, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return check_cuda(c, cudaGetLastError());
+  if (K) {
+    if (cudaMemcpy(kp.data(), c->K_state, sizeof(double) * P, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return check_cuda(c, cudaGetLastError());
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b <= a; ++b) {
+        const double v = kp[(size_t)a * (a + 1) / 2 + b];
+        K[(size_t)a * d + b] = v;
+        K[(size_t)b * d + a] = v;
+      }
+  }
+  if (t) *t = c->t;
+  return ERX_OK;
+}
+
+erx_status erx_set_state(erx_ctx* c, int64_t t, const double* mu, const double* K) {
+  if (!c || t < 0 || (t > 0 && (!mu || !K))) return ERX_EINVAL;
+  if (c->failed) return ERX_ECUDA;
+  const int d = c->d;
+  const int64_t P = packed_size(d);
+  if (t > 0) {
+    std::vector<double> kp((size_t)P);
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b <= a; ++b) kp[(size_t)a * (a + 1) / 2 + b] = K[(size_t)a * d + b];
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+        cudaMemcpy(c->mu_state, mu, sizeof(double) * d, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->K_state, kp.data(), sizeof(double) * P, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      return check_cuda(c, cudaGetLastError());
+  }
+  c->t = t;
+  return ERX_OK;
+}
+
+int32_t erx_dim(const erx_ctx* c) { return c ? c->d : -1; }
+
+erx_status erx_get_projection(const erx_ctx* c, double* w) {
+  if (!c || !w) return ERX_EINVAL;
+  const int B = c->B, d = c->d;
+  if (c->w_host.empty()) {
+    for (int i = 0; i < B; ++i)
+      for (int j = 0; j < d; ++j) w[(size_t)i * d + j] = i == j ? 1.0 : 0.0;
+  } else {
+    std::memcpy(w, c->w_host.data(), sizeof(double) * B * d);
+  }
+  return ERX_OK;
+}
+
+erx_status erx_profile_enable(erx_ctx* c, int32_t on) {
+  if (!c) return ERX_EINVAL;
+  c->profiling = on != 0;
+  return ERX_OK;
+}
+
+erx_status erx_profile_read(erx_ctx* c, int32_t k, int32_t reset, double* total_ms,
+                            int64_t* timed, int64_t* launches) {
+  if (!c || k < 0 || k >= ERX_K_COUNT) return ERX_EINVAL;
+  if (c->failed) return ERX_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, cudaGetLastError());
+  resolve_pending(c);
+  if (total_ms) *total_ms = c->total_ms[k];
+  if (timed) *timed = c->timed[k];
+  if (launches) *launches = c->launches[k];
+  if (reset) {
+    for (int i = 0; i < ERX_K_COUNT; ++i) c->total_ms[i] = 0.0, c->timed[i] = 0, c->launches[i] = 0;
+  }
+  return ERX_OK;
+}
+
+const char* erx_kernel_name(int32_t k) {
+  static const char* names[ERX_K_COUNT] = {"project", "stats_int", "mean", "stats_fp",
+                                           "ema_scan", "chol_inv", "solve_fp64", "solve_fp32",
+                                           "normalise"};
+  return (k >= 0 && k < ERX_K_COUNT) ? names[k] : nullptr;
+}
+
+erx_status erx_destroy(erx_ctx* c) {
+  if (!c) return ERX_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  cudaGetLastError();
+  free_all(c);
+  delete c;
+  return ERX_OK;
+}
+
+const char* erx_status_str(erx_status s) {
+  switch (s) {
+    case ERX_OK: return "ERX_OK";
+    case ERX_EINVAL: return "ERX_EINVAL: invalid argument";
+    case ERX_ENOMEM: return "ERX_ENOMEM: allocation failed";
+    case ERX_ECUDA: return "ERX_ECUDA: CUDA error; context failed";
+    case ERX_ENOTPD: return "ERX_ENOTPD: K_t + ridge I not positive definite";
+    case ERX_ERANGE: return "ERX_ERANGE: input sample above 2^in_bits - 1";
+    case ERX_ESTATE: return "ERX_ESTATE: call not valid in this state";
+    case ERX_EUNSUPPORTED: return "ERX_EUNSUPPORTED: beyond this build's limits";
+  }
+  return "ERX_?: unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Internal declarations shared by the ERX CUDA translation units.
+//
+// Device data layout of one block of T lines (all row-major):
+//   lines      caller's [T][p][b] samples (u16 / f32 / f64), line stride given
+//   Z          [T][p][d] projected pixels when SRP is on (double or float)
+//   S1i, S2i   exact integer sums  sum_i x_i  [T][d]  and  sum_i x_i x_i^T  [T][d][d]
+//   mu_hat     [T][d] line means (double);  shift [T][d] centring shift c
+//   S2f        [T][d][d] sums  sum_i (z_i - c)(z_i - c)^T  (double)
+//   mu_t, K_t  [T][d], [T][P] statistics each line is scored with (P = d(d+1)/2,
+//              packed lower triangle, row j starts at j(j+1)/2)
+//   Linv       [T][P] packed lower L_t^{-1} (double), Linv32 its float copy
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace erx {
+
+constexpr int kMaxDim = 224;   // packed FP64 factor must fit one SM's shared memory
+
+// error slots (unsigned long long, min-reduced line index; ~0ull = none)
+enum { kErrNotPD = 0, kErrRange = 1, kErrSlots = 2 };
+
+__host__ __device__ inline int64_t packed_size(int d) { return (int64_t)d * (d + 1) / 2; }
+
+// Opt the kernels that need it into large dynamic shared memory on the
+// current device (called once per device at context creation).
+cudaError_t configure_factor_kernels();
+cudaError_t configure_solve_kernels();
+
+// ---- launchers (all asynchronous on `st`) -------------------------------
+
+// Exact integer sums for u16 input without projection.  maxv = 2^bits - 1.
+void launch_stats_int(const uint16_t* x, int64_t line_stride, int W, int d, uint32_t maxv,
+                      int T, uint64_t* S1, uint64_t* S2, unsigned long long* err, int64_t t0,
+                      cudaStream_t st);
+
+// Line means (double) and centring shifts c (= mean, or the mean rounded to
+// float when `float_shift`).  in_type: 0 u16, 1 f32, 2 f64.  ps = pixel stride.
+void launch_mean(int in_type, const void* x, int64_t line_stride, int ps, int W, int d, int T,
+                 bool float_shift, double* mu_hat, double* shift, cudaStream_t st);
+
+// Centred scatter sums about `shift`, accumulated in double (fp64=true) or float.
+void launch_stats_fp(int in_type, bool fp64, const void* x, int64_t line_stride, int ps, int W,
+                     int d, int T, const double* shift, double* S2f, cudaStream_t st);
+
+// EMA scan over the T lines of a block: turns line statistics into the
+// statistics each line is scored with and advances the state.
+void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
+                     const double* mu_hat, const double* shift, const double* S2f, int T, int d,
+                     int W, double alpha, int64_t t0, int order, double* mu_state,
+                     double* K_state, double* mu_t, double* K_t, cudaStream_t st);
+
+// Cholesky of K_t + ridge I and its inverse, one CTA per line.
+void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Linv, float* Linv32,
+                     unsigned long long* err, int64_t t0, cudaStream_t st);
+
+// delta_i = || L^{-1} (z_i - mu_t) ||, FP64 arithmetic.
+void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
+                       int T, const double* mu_t, const double* Linv, double* delta,
+                       cudaStream_t st);
+
+// delta_i with FP32 arithmetic (register-tiled SIMT).
+void launch_solve_fp32(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
+                       int T, const double* mu_t, const float* Linv32, float* delta,
+                       cudaStream_t st);
+
+// Per-line normalisation (Sec. III-E), mask and warm-up flags.
+void launch_normalise(bool fp64, const void* delta, int W, int T, double threshold,
+                      int64_t t0, int64_t warmup, void* delta_n, uint8_t* mask,
+                      uint8_t* detecting, cudaStream_t st);
+
+// Sparse projection Z = X W (column lists), output double or float.
+void launch_project(int in_type, const void* x, int64_t line_stride, int B, int W, int d, int T,
+                    const int* colptr, const int* rows, const double* vals, bool out_fp64,
+                    void* z, cudaStream_t st);
+
+}  // namespace erx

@@ -1,0 +1,201 @@
+// S5 (Sec. III-D): delta_i = sqrt(m_i . m_i) with m_i = L_t^{-1} (z_i - mu_t).
+//
+// FP64 form: one thread per pixel.  The pixel's centred vector r_i is staged
+// in shared memory (odd row pitch, so the 8-byte loads of a warp hit distinct
+// bank pairs); row j of the packed L^{-1} is read with warp-uniform loads and
+// m_ij = sum_{k<=j} Linv_jk r_ik is accumulated into four independent
+// chains.  Exactly d(d+1)/2 DFMA per pixel: the kernel is bound by the FP64
+// pipe (2 DFMA/clk/SM on GB300), not by memory.
+//
+// FP32 form: a register-tiled product M = R L^{-T} over the lower triangle.
+// A CTA owns 64 pixels; four warps cover 64 pixels x 32 outputs, each thread
+// a 4 x 4 tile, with R^T staged once (k-major) and each 32-row band of L^{-1}
+// staged k-major, so both operand loads are 16-byte and conflict-free.  The
+// centred samples are formed as (x - mu_hi) - mu_lo with mu split into two
+// floats, which keeps r accurate to float rounding without FP64 work per pixel.
+#include <cmath>
+
+#include "erx_internal.cuh"
+
+namespace erx {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ double to_d(T v) { return (double)v; }
+template <typename T>
+__device__ __forceinline__ float to_f(T v) { return (float)v; }
+
+constexpr int kPixF64 = 64;
+
+template <typename InT>
+__global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
+    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
+    const double* __restrict__ mu_t, const double* __restrict__ Linv, double* __restrict__ delta) {
+  extern __shared__ __align__(16) double r[];
+  const int dp = d | 1;
+  const int t = blockIdx.y;
+  const int i0 = blockIdx.x * kPixF64;
+  const double* mu = mu_t + (int64_t)t * d;
+  const InT* x = X + (int64_t)t * line_stride;
+  for (int e = threadIdx.x; e < kPixF64 * d; e += kPixF64) {
+    const int p = e / d, k = e - p * d, i = i0 + p;
+    r[p * dp + k] = i < W ? to_d(x[(int64_t)i * ps + k]) - mu[k] : 0.0;
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x;
+  if (i >= W) return;
+  const double* L = Linv + (int64_t)t * packed_size(d);
+  const double* rr = r + threadIdx.x * dp;
+  double d2 = 0.0;
+  for (int j = 0; j < d; ++j) {
+    const double* Lj = L + j * (j + 1) / 2;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int k = 0;
+    for (; k + 3 <= j; k += 4) {
+      a0 = fma(__ldg(Lj + k), rr[k], a0);
+      a1 = fma(__ldg(Lj + k + 1), rr[k + 1], a1);
+      a2 = fma(__ldg(Lj + k + 2), rr[k + 2], a2);
+      a3 = fma(__ldg(Lj + k + 3), rr[k + 3], a3);
+    }
+    for (; k <= j; ++k) a0 = fma(__ldg(Lj + k), rr[k], a0);
+    const double m = (a0 + a1) + (a2 + a3);
+    d2 = fma(m, m, d2);
+  }
+  delta[(int64_t)t * W + i] = sqrt(d2);
+}
+
+constexpr int kPixF32 = 64;   // pixels per CTA
+constexpr int kOutB = 32;     // outputs per band of L^{-1}
+
+template <typename InT>
+__global__ void __launch_bounds__(128) solve_fp32_kernel(
+    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
+    const double* __restrict__ mu_t, const float* __restrict__ Linv32, float* __restrict__ delta) {
+  extern __shared__ __align__(16) float smf[];
+  float* rT = smf;                        // [d][kPixF32]
+  float* LT = smf + d * kPixF32;          // [d][kOutB]
+  __shared__ float mu_hi[kMaxDim], mu_lo[kMaxDim];
+  __shared__ float d2w[2][kPixF32];
+  const int t = blockIdx.y;
+  const int i0 = blockIdx.x * kPixF32;
+  const InT* x = X + (int64_t)t * line_stride;
+  for (int k = threadIdx.x; k < d; k += 128) {
+    const double m = mu_t[(int64_t)t * d + k];
+    const float h = (float)m;
+    mu_hi[k] = h;
+    mu_lo[k] = (float)(m - (double)h);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kPixF32 * d; e += 128) {
+    const int p = e / d, k = e - p * d, i = i0 + p;
+    float v = 0.f;
+    if (i < W) v = (to_f(x[(int64_t)i * ps + k]) - mu_hi[k]) - mu_lo[k];
+    rT[k * kPixF32 + p] = v;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ph = warp & 1, oh = warp >> 1;
+  const int lp = lane & 7, lo = lane >> 3;
+  const int pcol = ph * 32 + lp * 4;      // first of this thread's 4 pixels
+  const int ocol = oh * 16 + lo * 4;      // first of its 4 outputs within a band
+  const float* Lg = Linv32 + (int64_t)t * packed_size(d);
+  float d2[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int j0 = 0; j0 < d; j0 += kOutB) {
+    const int kend = min(d, j0 + kOutB);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kend * kOutB; e += 128) {
+      const int k = e / kOutB, jj = e % kOutB, j = j0 + jj;
+      LT[k * kOutB + jj] = (j < d && k <= j) ? Lg[j * (j + 1) / 2 + k] : 0.f;
+    }
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < kend; ++k) {
+      const float4 rv = *reinterpret_cast<const float4*>(rT + k * kPixF32 + pcol);
+      const float4 lv = *reinterpret_cast<const float4*>(LT + k * kOutB + ocol);
+      const float ra[4] = {rv.x, rv.y, rv.z, rv.w};
+      const float la[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ra[a], la[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) d2[a] = fmaf(acc[a][b], acc[a][b], d2[a]);
+  }
+  // reduce over the 4 output groups of a warp (lane bits 3, 4), then the 2 output halves
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    d2[a] += __shfl_xor_sync(0xffffffffu, d2[a], 8);
+    d2[a] += __shfl_xor_sync(0xffffffffu, d2[a], 16);
+  }
+  __syncthreads();
+  if (lo == 0) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) d2w[oh][pcol + a] = d2[a];
+  }
+  __syncthreads();
+  if (threadIdx.x < kPixF32) {
+    const int i = i0 + threadIdx.x;
+    if (i < W) delta[(int64_t)t * W + i] = sqrtf(d2w[0][threadIdx.x] + d2w[1][threadIdx.x]);
+  }
+}
+
+size_t smem_fp64(int d) { return (size_t)kPixF64 * (d | 1) * sizeof(double); }
+size_t smem_fp32(int d) { return (size_t)d * (kPixF32 + kOutB) * sizeof(float); }
+
+}  // namespace
+
+cudaError_t configure_solve_kernels() {
+  cudaError_t e = cudaSuccess;
+  const int m64 = (int)smem_fp64(kMaxDim), m32 = (int)smem_fp32(kMaxDim);
+#define ERX_CFG(K, M) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, M)
+  ERX_CFG(solve_fp64_kernel<uint16_t>, m64);
+  ERX_CFG(solve_fp64_kernel<float>, m64);
+  ERX_CFG(solve_fp64_kernel<double>, m64);
+  ERX_CFG(solve_fp32_kernel<uint16_t>, m32);
+  ERX_CFG(solve_fp32_kernel<float>, m32);
+  ERX_CFG(solve_fp32_kernel<double>, m32);
+#undef ERX_CFG
+  return e;
+}
+
+void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
+                       int T, const double* mu_t, const double* Linv, double* delta,
+                       cudaStream_t st) {
+  dim3 grid((W + kPixF64 - 1) / kPixF64, T);
+  const size_t sm = smem_fp64(d);
+  if (in_type == 0)
+    solve_fp64_kernel<uint16_t><<<grid, kPixF64, sm, st>>>((const uint16_t*)x, line_stride, ps,
+                                                           W, d, mu_t, Linv, delta);
+  else if (in_type == 1)
+    solve_fp64_kernel<float><<<grid, kPixF64, sm, st>>>((const float*)x, line_stride, ps, W, d,
+                                                        mu_t, Linv, delta);
+  else
+    solve_fp64_kernel<double><<<grid, kPixF64, sm, st>>>((const double*)x, line_stride, ps, W,
+                                                         d, mu_t, Linv, delta);
+}
+
+void launch_solve_fp32(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
+                       int T, const double* mu_t, const float* Linv32, float* delta,
+                       cudaStream_t st) {
+  dim3 grid((W + kPixF32 - 1) / kPixF32, T);
+  const size_t sm = smem_fp32(d);
+  if (in_type == 0)
+    solve_fp32_kernel<uint16_t><<<grid, 128, sm, st>>>((const uint16_t*)x, line_stride, ps, W,
+                                                       d, mu_t, Linv32, delta);
+  else if (in_type == 1)
+    solve_fp32_kernel<float><<<grid, 128, sm, st>>>((const float*)x, line_stride, ps, W, d,
+                                                    mu_t, Linv32, delta);
+  else
+    solve_fp32_kernel<double><<<grid, 128, sm, st>>>((const double*)x, line_stride, ps, W, d,
+                                                     mu_t, Linv32, delta);
+}
+
+}  // namespace erx

@@ -1,0 +1,254 @@
+// S2 line statistics (Sec. III-C): line mean and centred scatter matrix.
+//
+// Two routes:
+//  * exact integer sums for u16 samples without projection: sum_i x_i and
+//    sum_i x_i x_i^T accumulated with 32-bit integer multiply-adds (products of
+//    b-bit samples are < 2^(2b); partial sums are widened to 64 bits before
+//    they can wrap), so K_hat = (p S2 - S1 S1^T) / (p (p-1)) is formed later
+//    from exact integers with a single rounding.  On GB300 the integer pipe
+//    issues 64 IMAD/clk/SM against 2 DFMA/clk/SM.
+//  * floating point: a mean pass, then the scatter of (z_i - c) about a shift c
+//    accumulated in double or float; the EMA step corrects for c != mean.
+//
+// Both tile the lower triangle of the d x d output into 64 x 64 blocks, one
+// CTA per (block pair, line); 256 threads each own a 4 x 4 sub-block.
+#include "erx_internal.cuh"
+
+namespace erx {
+namespace {
+
+constexpr int SB = 64;    // output block edge
+constexpr int KCI = 64;   // pixels per shared-memory chunk, integer route
+constexpr int KCF = 32;   // pixels per chunk, floating route
+
+__device__ __forceinline__ void block_pair(int q, int& I, int& J) {
+  int i = 0;
+  while ((i + 1) * (i + 2) / 2 <= q) ++i;
+  I = i;
+  J = q - i * (i + 1) / 2;
+}
+
+template <typename T>
+__device__ __forceinline__ double to_d(T v) { return (double)v; }
+
+__global__ void __launch_bounds__(256) stats_int_kernel(
+    const uint16_t* __restrict__ X, int64_t line_stride, int W, int d, uint32_t maxv,
+    int flush_mask, uint64_t* __restrict__ S1, uint64_t* __restrict__ S2,
+    unsigned long long* __restrict__ err, int64_t t0) {
+  __shared__ __align__(16) uint32_t xa[KCI][SB];
+  __shared__ __align__(16) uint32_t xb[KCI][SB];
+  int I, J;
+  block_pair(blockIdx.x, I, J);
+  const int t = blockIdx.y;
+  const bool diag = (I == J);
+  const uint16_t* x = X + (int64_t)t * line_stride;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int a0 = I * SB, b0 = J * SB;
+  uint32_t acc[4][4];
+  uint64_t tot[4][4];
+  uint64_t s1[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0u, tot[i][j] = 0ull;
+  bool bad = false;
+  const uint32_t(*xbp)[SB] = diag ? xa : xb;
+
+  for (int i0 = 0; i0 < W; i0 += KCI) {
+    for (int e = threadIdx.x; e < KCI * SB; e += 256) {
+      const int p = e / SB, c = e % SB, i = i0 + p;
+      uint32_t va = 0, vb = 0;
+      if (i < W) {
+        if (a0 + c < d) va = x[(int64_t)i * d + a0 + c];
+        if (!diag && b0 + c < d) vb = x[(int64_t)i * d + b0 + c];
+      }
+      bad |= (va > maxv) | (vb > maxv);
+      xa[p][c] = va;
+      if (!diag) xb[p][c] = vb;
+    }
+    __syncthreads();
+    const int kn = min(KCI, W - i0);
+    for (int k = 0; k < kn; ++k) {
+      const uint4 av = *reinterpret_cast<const uint4*>(&xa[k][ty * 4]);
+      const uint4 bv = *reinterpret_cast<const uint4*>(&xbp[k][tx * 4]);
+      const uint32_t a[4] = {av.x, av.y, av.z, av.w};
+      const uint32_t b[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+      if (((k + 1) & flush_mask) == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j], acc[i][j] = 0u;
+      }
+      if (diag && ty == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s1[j] += b[j];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) tot[i][j] += acc[i][j], acc[i][j] = 0u;
+    __syncthreads();
+  }
+  if (bad) atomicMin(&err[kErrRange], (unsigned long long)(t0 + t));
+  uint64_t* s2 = S2 + (int64_t)t * d * d;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty * 4 + i;
+    if (a >= d) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tx * 4 + j;
+      if (b < d) s2[(int64_t)a * d + b] = tot[i][j];
+    }
+  }
+  if (diag && ty == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tx * 4 + j;
+      if (b < d) S1[(int64_t)t * d + b] = s1[j];
+    }
+  }
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(256) mean_kernel(const InT* __restrict__ X, int64_t line_stride,
+                                                   int ps, int W, int d, bool float_shift,
+                                                   double* __restrict__ mu_hat,
+                                                   double* __restrict__ shift) {
+  __shared__ double part[256];
+  const int t = blockIdx.x;
+  const int G = max(1, (int)blockDim.x / d);
+  const int g = threadIdx.x / d, b = threadIdx.x % d;
+  const InT* x = X + (int64_t)t * line_stride;
+  double s = 0.0;
+  if (g < G) {
+    for (int i = g; i < W; i += G) s += to_d(x[(int64_t)i * ps + b]);
+  }
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < d) {
+    double tot = 0.0;
+    for (int q = 0; q < G; ++q) tot += part[q * d + threadIdx.x];
+    const double m = tot / (double)W;
+    mu_hat[(int64_t)t * d + threadIdx.x] = m;
+    shift[(int64_t)t * d + threadIdx.x] = float_shift ? (double)(float)m : m;
+  }
+}
+
+template <typename InT, typename AccT>
+__global__ void __launch_bounds__(256) stats_fp_kernel(const InT* __restrict__ X,
+                                                       int64_t line_stride, int ps, int W, int d,
+                                                       const double* __restrict__ shift,
+                                                       double* __restrict__ S2f) {
+  __shared__ __align__(16) AccT xa[KCF][SB];
+  __shared__ __align__(16) AccT xb[KCF][SB];
+  __shared__ AccT cs[2 * SB];
+  int I, J;
+  block_pair(blockIdx.x, I, J);
+  const int t = blockIdx.y;
+  const bool diag = (I == J);
+  const InT* x = X + (int64_t)t * line_stride;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int a0 = I * SB, b0 = J * SB;
+  if (threadIdx.x < 2 * SB) {
+    const int c = threadIdx.x < SB ? a0 + threadIdx.x : b0 + threadIdx.x - SB;
+    cs[threadIdx.x] = c < d ? (AccT)shift[(int64_t)t * d + c] : (AccT)0;
+  }
+  AccT acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = (AccT)0;
+  const AccT(*xbp)[SB] = diag ? xa : xb;
+  __syncthreads();
+  for (int i0 = 0; i0 < W; i0 += KCF) {
+    for (int e = threadIdx.x; e < KCF * SB; e += 256) {
+      const int p = e / SB, c = e % SB, i = i0 + p;
+      AccT va = 0, vb = 0;
+      if (i < W) {
+        if (a0 + c < d) va = (AccT)x[(int64_t)i * ps + a0 + c] - cs[c];
+        if (!diag && b0 + c < d) vb = (AccT)x[(int64_t)i * ps + b0 + c] - cs[SB + c];
+      }
+      xa[p][c] = va;
+      if (!diag) xb[p][c] = vb;
+    }
+    __syncthreads();
+    const int kn = min(KCF, W - i0);
+    for (int k = 0; k < kn; ++k) {
+      AccT a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = xa[k][ty * 4 + i], b[i] = xbp[k][tx * 4 + i];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* s2 = S2f + (int64_t)t * d * d;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty * 4 + i;
+    if (a >= d) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tx * 4 + j;
+      if (b < d) s2[(int64_t)a * d + b] = (double)acc[i][j];
+    }
+  }
+}
+
+int n_pairs(int d) {
+  const int nb = (d + SB - 1) / SB;
+  return nb * (nb + 1) / 2;
+}
+
+}  // namespace
+
+void launch_stats_int(const uint16_t* x, int64_t line_stride, int W, int d, uint32_t maxv,
+                      int T, uint64_t* S1, uint64_t* S2, unsigned long long* err, int64_t t0,
+                      cudaStream_t st) {
+  // flush 32-bit partial sums every F pixels with F * maxv^2 < 2^32, F a power of 2 <= 64
+  const uint64_t m2 = (uint64_t)maxv * maxv;
+  int f = 64;
+  while (f > 1 && (uint64_t)f * m2 > 0xFFFFFFFFull) f >>= 1;
+  dim3 grid(n_pairs(d), T);
+  stats_int_kernel<<<grid, 256, 0, st>>>(x, line_stride, W, d, maxv, f - 1, S1, S2, err, t0);
+}
+
+void launch_mean(int in_type, const void* x, int64_t line_stride, int ps, int W, int d, int T,
+                 bool float_shift, double* mu_hat, double* shift, cudaStream_t st) {
+  if (in_type == 0)
+    mean_kernel<uint16_t><<<T, 256, 0, st>>>((const uint16_t*)x, line_stride, ps, W, d,
+                                             float_shift, mu_hat, shift);
+  else if (in_type == 1)
+    mean_kernel<float><<<T, 256, 0, st>>>((const float*)x, line_stride, ps, W, d, float_shift,
+                                          mu_hat, shift);
+  else
+    mean_kernel<double><<<T, 256, 0, st>>>((const double*)x, line_stride, ps, W, d, float_shift,
+                                           mu_hat, shift);
+}
+
+void launch_stats_fp(int in_type, bool fp64, const void* x, int64_t line_stride, int ps, int W,
+                     int d, int T, const double* shift, double* S2f, cudaStream_t st) {
+  dim3 grid(n_pairs(d), T);
+#define ERX_SFP(IT, AT) \
+  stats_fp_kernel<IT, AT><<<grid, 256, 0, st>>>((const IT*)x, line_stride, ps, W, d, shift, S2f)
+  if (fp64) {
+    if (in_type == 0) ERX_SFP(uint16_t, double);
+    else if (in_type == 1) ERX_SFP(float, double);
+    else ERX_SFP(double, double);
+  } else {
+    if (in_type == 0) ERX_SFP(uint16_t, float);
+    else if (in_type == 1) ERX_SFP(float, float);
+    else ERX_SFP(double, float);
+  }
+#undef ERX_SFP
+}
+
+}  // namespace erx

@@ -1,0 +1,292 @@
+"""ctypes binding of include/erx.h, function for function, plus a small
+torch-tensor convenience wrapper (``Detector``).
+
+Nothing here computes: every step of the ERX line step runs in liberx.so.  If
+the library has not been built, loading fails loudly; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_PKG, "_lib", "liberx.so")
+
+ERX_OK, ERX_EINVAL, ERX_ENOMEM, ERX_ECUDA, ERX_ENOTPD, ERX_ERANGE, ERX_ESTATE, \
+    ERX_EUNSUPPORTED = range(8)
+ERX_PROJ_NONE, ERX_PROJ_SRP = 0, 1
+ERX_UPDATE_THEN_SCORE, ERX_SCORE_THEN_UPDATE = 0, 1
+ERX_U16, ERX_F32, ERX_F64 = 0, 1, 2
+ERX_FORM_FP64, ERX_FORM_FP32 = 0, 1
+
+_SAMPLE_BYTES = {ERX_U16: 2, ERX_F32: 4, ERX_F64: 8}
+
+
+class ErxConfig(C.Structure):
+    _fields_ = [
+        ("bands", C.c_int32), ("width", C.c_int32), ("momentum", C.c_double),
+        ("proj", C.c_int32), ("proj_dim", C.c_int32), ("seed", C.c_uint64),
+        ("ridge", C.c_double), ("warmup_lines", C.c_int32), ("order", C.c_int32),
+        ("in_dtype", C.c_int32), ("in_bits", C.c_int32), ("form", C.c_int32),
+        ("threshold", C.c_double), ("block_lines", C.c_int32),
+        ("srp_weights", C.POINTER(C.c_double)),
+    ]
+
+
+class ErxError(RuntimeError):
+    def __init__(self, status: int, where: str, bad_line: int = -1):
+        self.status = status
+        self.bad_line = bad_line
+        super().__init__(f"{where}: {erx_status_str(status)}"
+                         + (f" (line {bad_line})" if bad_line >= 0 else ""))
+
+
+_lib = None
+
+
+def load_library() -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(lib_path):
+        raise ImportError(f"ERX CUDA library not built ({lib_path} missing); run "
+                          "__graft_entry__.build() or python -m paper_2408_14947_gb300._build")
+    lib = C.CDLL(lib_path)
+    P, I32, I64, U64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    sig = {
+        "erx_config_default": (None, [C.POINTER(ErxConfig), I32, I32]),
+        "erx_create": (C.c_int, [C.POINTER(ErxConfig), P, C.POINTER(P)]),
+        "erx_push_lines": (C.c_int, [P, P, I64, I64, P, P, P, P]),
+        "erx_push_lines_host": (C.c_int, [P, P, I64, I64, P, P, P, P]),
+        "erx_sync": (C.c_int, [P, C.POINTER(I64)]),
+        "erx_reset": (C.c_int, [P]),
+        "erx_get_state": (C.c_int, [P, C.POINTER(I64), P, P]),
+        "erx_set_state": (C.c_int, [P, I64, P, P]),
+        "erx_dim": (I32, [P]),
+        "erx_get_projection": (C.c_int, [P, P]),
+        "erx_srp_weights": (C.c_int, [I32, I32, U64, P]),
+        "erx_destroy": (C.c_int, [P]),
+        "erx_status_str": (C.c_char_p, [C.c_int]),
+        "erx_profile_enable": (C.c_int, [P, I32]),
+        "erx_profile_read": (C.c_int, [P, I32, I32, C.POINTER(D), C.POINTER(I64),
+                                       C.POINTER(I64)]),
+        "erx_kernel_name": (C.c_char_p, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != ERX_OK:
+        raise ErxError(st, where)
+
+
+def erx_status_str(status: int) -> str:
+    return load_library().erx_status_str(status).decode()
+
+
+def erx_config_default(bands: int, width: int) -> ErxConfig:
+    cfg = ErxConfig()
+    load_library().erx_config_default(C.byref(cfg), bands, width)
+    return cfg
+
+
+def erx_create(cfg: ErxConfig, stream: int = 0) -> int:
+    h = C.c_void_p()
+    _check(load_library().erx_create(C.byref(cfg), C.c_void_p(stream), C.byref(h)), "erx_create")
+    return h.value
+
+
+def erx_push_lines(ctx, lines_ptr, n_lines, stride_bytes, delta_ptr, dn_ptr=0, mask_ptr=0,
+                   det_ptr=0):
+    _check(load_library().erx_push_lines(ctx, lines_ptr, n_lines, stride_bytes, delta_ptr,
+                                         dn_ptr or None, mask_ptr or None, det_ptr or None),
+           "erx_push_lines")
+
+
+def erx_push_lines_host(ctx, lines_ptr, n_lines, stride_bytes, delta_ptr, dn_ptr=0, mask_ptr=0,
+                        det_ptr=0):
+    _check(load_library().erx_push_lines_host(ctx, lines_ptr, n_lines, stride_bytes, delta_ptr,
+                                              dn_ptr or None, mask_ptr or None, det_ptr or None),
+           "erx_push_lines_host")
+
+
+def erx_sync(ctx) -> None:
+    bad = C.c_int64(-1)
+    st = load_library().erx_sync(ctx, C.byref(bad))
+    if st != ERX_OK:
+        raise ErxError(st, "erx_sync", bad.value)
+
+
+def erx_reset(ctx) -> None:
+    _check(load_library().erx_reset(ctx), "erx_reset")
+
+
+def erx_dim(ctx) -> int:
+    return int(load_library().erx_dim(ctx))
+
+
+def erx_get_state(ctx):
+    import numpy as np
+    d = erx_dim(ctx)
+    t = C.c_int64()
+    mu = np.zeros(d)
+    k = np.zeros((d, d))
+    _check(load_library().erx_get_state(ctx, C.byref(t), mu.ctypes.data, k.ctypes.data),
+           "erx_get_state")
+    return t.value, mu, k
+
+
+def erx_set_state(ctx, t, mu, k) -> None:
+    import numpy as np
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    k = np.ascontiguousarray(k, dtype=np.float64)
+    _check(load_library().erx_set_state(ctx, int(t), mu.ctypes.data, k.ctypes.data),
+           "erx_set_state")
+
+
+def erx_get_projection(ctx, bands: int):
+    import numpy as np
+    w = np.zeros((bands, erx_dim(ctx)))
+    _check(load_library().erx_get_projection(ctx, w.ctypes.data), "erx_get_projection")
+    return w
+
+
+def erx_srp_weights(bands: int, dim: int, seed: int):
+    import numpy as np
+    w = np.zeros((bands, dim))
+    _check(load_library().erx_srp_weights(bands, dim, C.c_uint64(seed), w.ctypes.data),
+           "erx_srp_weights")
+    return w
+
+
+ERX_K_COUNT = 9
+
+
+def erx_kernel_name(k: int) -> str:
+    return load_library().erx_kernel_name(k).decode()
+
+
+def erx_profile_enable(ctx, on: bool) -> None:
+    _check(load_library().erx_profile_enable(ctx, 1 if on else 0), "erx_profile_enable")
+
+
+def erx_profile_read(ctx, kernel: int, reset: bool = False):
+    """(total_ms, timed_launches, launches) for one kernel kind."""
+    ms, timed, n = C.c_double(), C.c_int64(), C.c_int64()
+    _check(load_library().erx_profile_read(ctx, kernel, 1 if reset else 0, C.byref(ms),
+                                           C.byref(timed), C.byref(n)), "erx_profile_read")
+    return ms.value, timed.value, n.value
+
+
+def erx_destroy(ctx) -> None:
+    _check(load_library().erx_destroy(ctx), "erx_destroy")
+
+
+class Detector:
+    """One ERX context driven with torch tensors (device memory and streams only).
+
+    ``push(lines)`` takes a CUDA tensor [n][p][b] (uint16 viewed as int16,
+    float32 or float64 samples) and returns (delta, delta_n, mask, detecting)
+    CUDA tensors; every step runs in liberx.so on the tensor's stream.
+    """
+
+    def __init__(self, bands, width, momentum=0.1, proj="none", proj_dim=5, seed=0, ridge=1e-5,
+                 warmup=99, order="update_then_score", in_dtype="f32", in_bits=16,
+                 form="fp64", threshold=3.0, block_lines=0, srp_weights=None, stream=None):
+        import torch
+        self.torch = torch
+        cfg = erx_config_default(bands, width)
+        cfg.momentum = momentum
+        cfg.proj = {"none": ERX_PROJ_NONE, "srp": ERX_PROJ_SRP}[proj]
+        cfg.proj_dim = proj_dim
+        cfg.seed = seed
+        cfg.ridge = ridge
+        cfg.warmup_lines = warmup
+        cfg.order = {"update_then_score": ERX_UPDATE_THEN_SCORE,
+                     "score_then_update": ERX_SCORE_THEN_UPDATE}[order]
+        cfg.in_dtype = {"u16": ERX_U16, "f32": ERX_F32, "f64": ERX_F64}[in_dtype]
+        cfg.in_bits = in_bits
+        cfg.form = {"fp64": ERX_FORM_FP64, "fp32": ERX_FORM_FP32}[form]
+        cfg.threshold = threshold if threshold is not None else math.inf
+        cfg.block_lines = block_lines
+        self._w = None
+        if srp_weights is not None:
+            import numpy as np
+            self._w = np.ascontiguousarray(srp_weights, dtype=np.float64)
+            cfg.proj = ERX_PROJ_SRP
+            cfg.proj_dim = self._w.shape[1]
+            cfg.srp_weights = self._w.ctypes.data_as(C.POINTER(C.c_double))
+        self.cfg = cfg
+        self.bands, self.width = bands, width
+        self.in_dtype = cfg.in_dtype
+        self.score_dtype = torch.float64 if form == "fp64" else torch.float32
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = erx_create(cfg, self.stream.cuda_stream)
+        self.dim = erx_dim(self.ctx)
+
+    def push(self, lines, out=None):
+        torch = self.torch
+        assert lines.is_cuda and lines.dim() == 3 and lines.is_contiguous()
+        n, p, b = lines.shape
+        assert p == self.width and b == self.bands
+        assert lines.element_size() == _SAMPLE_BYTES[self.in_dtype]
+        dev = lines.device
+        if out is None:
+            out = (torch.empty((n, p), dtype=self.score_dtype, device=dev),
+                   torch.empty((n, p), dtype=self.score_dtype, device=dev),
+                   torch.empty((n, p), dtype=torch.uint8, device=dev),
+                   torch.empty((n,), dtype=torch.uint8, device=dev))
+        delta, dn, mask, det = out
+        erx_push_lines(self.ctx, lines.data_ptr(), n, 0, delta.data_ptr(), dn.data_ptr(),
+                       mask.data_ptr(), det.data_ptr())
+        return delta, dn, mask, det
+
+    def push_host(self, lines, out):
+        """lines and the four outputs are host (CPU) tensors; synchronous."""
+        n = lines.shape[0]
+        delta, dn, mask, det = out
+        erx_push_lines_host(self.ctx, lines.data_ptr(), n, 0, delta.data_ptr(), dn.data_ptr(),
+                            mask.data_ptr(), det.data_ptr())
+        return out
+
+    def sync(self):
+        erx_sync(self.ctx)
+
+    def reset(self):
+        erx_reset(self.ctx)
+
+    def state(self):
+        return erx_get_state(self.ctx)
+
+    def set_state(self, t, mu, k):
+        erx_set_state(self.ctx, t, mu, k)
+
+    def projection(self):
+        return erx_get_projection(self.ctx, self.bands)
+
+    def profile(self, on: bool = True):
+        erx_profile_enable(self.ctx, on)
+
+    def profile_read(self, reset: bool = False):
+        """{kernel name: (total_ms, timed_launches, launches)}; reset clears after reading."""
+        out = {erx_kernel_name(k): erx_profile_read(self.ctx, k) for k in range(ERX_K_COUNT)}
+        if reset:
+            erx_profile_read(self.ctx, 0, True)
+        return out
+
+    def close(self):
+        if self.ctx:
+            erx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
