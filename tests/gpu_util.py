@@ -55,4 +55,9 @@ def dn_err(got, ref_delta, ref_dn):
     relative delta error implies."""
     m = ref_delta.mean(axis=1, keepdims=True)
     s = ref_delta.std(axis=1, keepdims=True)
-    return float(np.max(np.abs(got - ref_dn) / (m / s + np.abs(ref_dn))))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        scale = np.where(s > 0, m / np.where(s > 0, s, 1.0), np.inf) + np.abs(ref_dn)
+        e = np.abs(got - ref_dn) / scale
+    # zero-spread lines have delta_N = 0 exactly on both sides
+    e = np.where(np.isfinite(scale), e, np.abs(got - ref_dn))
+    return float(np.max(e))
