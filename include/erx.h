@@ -142,6 +142,43 @@ erx_status erx_get_projection(const erx_ctx* ctx, double* w_host);
  * 2^-53, +1 if u < 1/(2s), -1 if u < 1/s. */
 erx_status erx_srp_weights(int32_t bands, int32_t dim, uint64_t seed, double* w_host);
 
+/* erx_push_lines without any device allocation (the paper has no
+ * counterpart; it serves callers that are not allowed to allocate).
+ *
+ * A context (erx_create) allocates its state and scratch with cudaMalloc.
+ * Some callers cannot do that: a real-time pipeline that must not allocate
+ * once running (an allocation can block or fail at any moment), a host whose
+ * device memory is all owned by its own pool, or a runtime that only lends
+ * out buffers it already holds.  This call needs no context: the caller owns
+ * the background state, and the per-line intermediates live in one fixed
+ * scratch array compiled into the library (about 0.9 MiB, reserved on every
+ * GPU that loads the library until the process exits).  It calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ *  cfg           as for erx_create; proj must be ERX_PROJ_NONE and bands <= 224
+ *                (the fixed scratch is sized for one line at d = 224), width
+ *                <= 2^20; beyond these limits the call returns ERX_EUNSUPPORTED
+ *                and does nothing.  cfg->srp_weights and cfg->block_lines are ignored.
+ *  cuda_stream   cudaStream_t the work runs on (NULL: legacy default stream).
+ *  mu_dev        device, d doubles: background mean, read and updated in place.
+ *  K_dev         device, d(d+1)/2 doubles: background covariance, packed lower
+ *                triangle (row j at offset j(j+1)/2), read and updated in place.
+ *  t_host        host, in: lines seen so far (0: the first line initialises the
+ *                state, whatever mu_dev / K_dev hold); out: advanced by n_lines.
+ *  lines_dev ... detecting_dev   exactly as erx_push_lines.
+ *
+ * Processes the lines one at a time and returns when the GPU work has
+ * finished (synchronises cuda_stream), reporting ERX_ENOTPD / ERX_ERANGE
+ * directly.  The first call on each device looks up the scratch array's
+ * device address and raises the shared-memory limit of the large kernels on
+ * that device; make that first call before any stream capture.  Every call
+ * shares the one scratch array: calls whose GPU work overlaps (from several
+ * streams or host threads) race on it and corrupt each other's results. */
+erx_status erx_push_lines_static(const erx_config* cfg, void* cuda_stream, double* mu_dev,
+                                 double* K_dev, int64_t* t_host, const void* lines_dev,
+                                 int64_t n_lines, int64_t line_stride_bytes, void* delta_dev,
+                                 void* delta_norm_dev, uint8_t* mask_dev, uint8_t* detecting_dev);
+
 /* Kernels of the line step, for erx_profile_read. */
 enum {
   ERX_K_PROJECT = 0,    /* S1 sparse projection */

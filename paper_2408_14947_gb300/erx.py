@@ -72,6 +72,8 @@ def load_library() -> C.CDLL:
         "erx_profile_read": (C.c_int, [P, I32, I32, C.POINTER(D), C.POINTER(I64),
                                        C.POINTER(I64)]),
         "erx_kernel_name": (C.c_char_p, [I32]),
+        "erx_push_lines_static": (C.c_int, [C.POINTER(ErxConfig), P, P, P, C.POINTER(I64), P,
+                                            I64, I64, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -166,6 +168,17 @@ def erx_srp_weights(bands: int, dim: int, seed: int):
 
 
 ERX_K_COUNT = 9
+
+
+def erx_push_lines_static(cfg, stream, mu_ptr, k_ptr, t, lines_ptr, n_lines, stride_bytes,
+                          delta_ptr, dn_ptr=0, mask_ptr=0, det_ptr=0) -> int:
+    """Context-free line step on caller-held state; returns the new line count."""
+    tt = C.c_int64(t)
+    _check(load_library().erx_push_lines_static(C.byref(cfg), C.c_void_p(stream), mu_ptr, k_ptr,
+                                                C.byref(tt), lines_ptr, n_lines, stride_bytes,
+                                                delta_ptr, dn_ptr or None, mask_ptr or None,
+                                                det_ptr or None), "erx_push_lines_static")
+    return tt.value
 
 
 def erx_kernel_name(k: int) -> str:
