@@ -8,7 +8,8 @@
 //   S2f        [T][d][d] sums  sum_i (z_i - c)(z_i - c)^T  (double)
 //   mu_t, K_t  [T][d], [T][P] statistics each line is scored with (P = d(d+1)/2,
 //              packed lower triangle, row j starts at j(j+1)/2)
-//   Linv       [T][P] packed lower L_t^{-1} (double), Linv32 its float copy
+//   Linv       [T][P] blocked factor: packed lower L_t with each 32 x 32 diagonal
+//              block replaced by its inverse (double); Linv32 its float copy
 #pragma once
 
 #include <cstdint>
@@ -17,6 +18,7 @@
 namespace erx {
 
 constexpr int kMaxDim = 224;   // packed FP64 factor must fit one SM's shared memory
+constexpr int kFactorBlock = 32;  // diagonal blocks of the factor are stored inverted
 
 // error slots (unsigned long long, min-reduced line index; ~0ull = none)
 enum { kErrNotPD = 0, kErrRange = 1, kErrSlots = 2 };
@@ -51,11 +53,11 @@ void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      int W, double alpha, int64_t t0, int order, double* mu_state,
                      double* K_state, double* mu_t, double* K_t, cudaStream_t st);
 
-// Cholesky of K_t + ridge I and its inverse, one CTA per line.
+// Cholesky of K_t + ridge I, diagonal blocks inverted, one CTA per line.
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Linv, float* Linv32,
                      unsigned long long* err, int64_t t0, cudaStream_t st);
 
-// delta_i = || L^{-1} (z_i - mu_t) ||, FP64 arithmetic.
+// delta_i = || m_i ||, L m_i = z_i - mu_t solved block by block, FP64 arithmetic.
 void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
                        int T, const double* mu_t, const double* Linv, double* delta,
                        cudaStream_t st);

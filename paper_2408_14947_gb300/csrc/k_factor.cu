@@ -1,15 +1,20 @@
-// S4 (Sec. III-D): L_t = chol(K_t + ridge I) and L_t^{-1}, FP64, one CTA per line.
+// S4 (Sec. III-D): L_t = chol(K_t + ridge I), FP64, one CTA per line.
 //
-// The packed lower triangle (d(d+1)/2 doubles, 197 KiB at d = 224) lives in
-// shared memory for the whole factorisation:
-//   Cholesky, right-looking: for each column j the pivot is checked and
-//   square-rooted, the column below it scaled, and the trailing triangle
-//   updated, A_ik -= l_ij l_kj (one warp per row, lanes along the row).
-//   Inverse, in place, columns right to left: with T = inverse of the
-//   trailing factor already stored, column j of L^{-1} is
-//   -(1/l_jj) T l_col (a lower-triangular mat-vec, one warp per row).
-// A pivot that is not positive and finite records the line in the error slot
-// and poisons the line's scores with NaN.
+// Output format ("blocked factor", packed lower, row j at j(j+1)/2): the
+// entries of L_t, except that each 32 x 32 diagonal block L_JJ is replaced by
+// its inverse D_J = L_JJ^{-1}.  The score kernels then solve L m = r block by
+// block, m_J = D_J (r_J - sum_{K<J} L_JK m_K), which costs the same d(d+1)/2
+// multiply-adds per pixel as a product with a full L^{-1} but needs only the
+// d/32 small inverses (d * 32^2 / 6 DFMA) instead of the full d^3/6.
+//
+// The packed factor (d(d+1)/2 doubles, 197 KiB at d = 224) lives in shared
+// memory.  Right-looking Cholesky: per column j the pivot is checked and
+// square-rooted, the column scaled, and the trailing triangle updated
+// A_ik -= l_ij l_kj with its elements spread evenly over all threads (the FP64
+// pipe is 2 lanes/clk/SM on GB300, so idle lanes of a partial warp cost as
+// much as busy ones).  Each diagonal block is then inverted by one warp, one
+// column per lane, with the block in registers.  A pivot that is not positive
+// and finite records the line in the error slot and poisons its scores (NaN).
 #include <cmath>
 
 #include "erx_internal.cuh"
@@ -18,15 +23,15 @@ namespace erx {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kNB = kFactorBlock;
 
 __device__ __forceinline__ int pidx(int i, int k) { return i * (i + 1) / 2 + k; }
 
-__global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __restrict__ K_t, int d,
-                                                           double ridge,
-                                                           double* __restrict__ Linv,
-                                                           float* __restrict__ Linv32,
-                                                           unsigned long long* __restrict__ err,
-                                                           int64_t t0) {
+__global__ void __launch_bounds__(kThreads) chol_kernel(const double* __restrict__ K_t, int d,
+                                                       double ridge, double* __restrict__ Lf,
+                                                       float* __restrict__ Lf32,
+                                                       unsigned long long* __restrict__ err,
+                                                       int64_t t0) {
   extern __shared__ __align__(16) double sm[];
   const int P = d * (d + 1) / 2;
   double* A = sm;
@@ -39,8 +44,6 @@ __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __rest
   for (int j = threadIdx.x; j < d; j += kThreads) A[pidx(j, j)] += ridge;
   __syncthreads();
 
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kThreads >> 5;
-  // ---- Cholesky
   for (int j = 0; j < d; ++j) {
     if (threadIdx.x == 0) {
       double ajj = A[pidx(j, j)];
@@ -60,32 +63,55 @@ __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __rest
       col[i] = v;
     }
     __syncthreads();
-    for (int i = j + 1 + warp; i < d; i += nw) {
-      const double li = col[i];
-      double* row = A + pidx(i, 0);
-      for (int k = j + 1 + lane; k <= i; k += 32) row[k] = fma(-li, col[k], row[k]);
+    // trailing triangle rows/cols j+1 .. d-1: m(m+1)/2 elements, enumerated evenly
+    const int m = d - 1 - j;
+    const int n = m * (m + 1) / 2;
+    for (int q = threadIdx.x; q < n; q += kThreads) {
+      int r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+      while (r * (r + 1) / 2 > q) --r;
+      while ((r + 1) * (r + 2) / 2 <= q) ++r;
+      const int c = q - r * (r + 1) / 2;
+      const int i = j + 1 + r, k = j + 1 + c;
+      const int p = pidx(i, k);
+      A[p] = fma(-col[i], col[k], A[p]);
     }
     __syncthreads();
   }
-  // ---- inverse of the lower factor, in place
-  for (int j = d - 1; j >= 0; --j) {
-    if (threadIdx.x == 0) A[pidx(j, j)] = 1.0 / A[pidx(j, j)];
-    for (int i = j + 1 + threadIdx.x; i < d; i += kThreads) col[i] = A[pidx(i, j)];
-    __syncthreads();
-    const double djj = A[pidx(j, j)];
-    for (int i = j + 1 + warp; i < d; i += nw) {
-      const double* row = A + pidx(i, 0);
-      double s = 0.0;
-      for (int k = j + 1 + lane; k <= i; k += 32) s = fma(row[k], col[k], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) A[pidx(i, j)] = -djj * s;
+
+  for (int i = threadIdx.x; i < d; i += kThreads) col[i] = 1.0 / A[pidx(i, i)];
+  __syncthreads();
+  // invert each 32 x 32 diagonal block: warp w takes blocks w, w + 8, ...
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nblk = (d + kNB - 1) / kNB;
+  for (int bk = warp; bk < nblk; bk += kThreads / 32) {
+    const int j0 = bk * kNB;
+    const int nb = min(kNB, d - j0);
+    // lane c: column c of the block inverse, x_i for i >= c (x_c = 1 / L_cc)
+    double x[kNB];
+#pragma unroll
+    for (int i = 0; i < kNB; ++i) x[i] = 0.0;
+    const int c = lane;
+#pragma unroll
+    for (int i = 0; i < kNB; ++i) {
+      if (i < nb && i >= c) {
+        double s = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+        for (int k = 0; k < i; ++k)
+          if (k >= c) s = fma(-A[pidx(j0 + i, j0 + k)], x[k], s);
+        x[i] = s * col[j0 + i];
+      }
     }
-    __syncthreads();
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < kNB; ++i)
+      if (i < nb && i >= c) A[pidx(j0 + i, j0 + c)] = x[i];
+    __syncwarp();
   }
-  double* dst = Linv + (int64_t)t * P;
+  __syncthreads();
+  double* dst = Lf + (int64_t)t * P;
   for (int q = threadIdx.x; q < P; q += kThreads) dst[q] = A[q];
-  if (Linv32) {
-    float* d32 = Linv32 + (int64_t)t * P;
+  if (Lf32) {
+    float* d32 = Lf32 + (int64_t)t * P;
     for (int q = threadIdx.x; q < P; q += kThreads) d32[q] = (float)A[q];
   }
 }
@@ -93,14 +119,14 @@ __global__ void __launch_bounds__(kThreads) chol_inv_kernel(const double* __rest
 }  // namespace
 
 cudaError_t configure_factor_kernels() {
-  return cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)((packed_size(kMaxDim) + kMaxDim) * sizeof(double)));
 }
 
-void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Linv, float* Linv32,
+void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, float* Lf32,
                      unsigned long long* err, int64_t t0, cudaStream_t st) {
   const size_t smem = (size_t)(packed_size(d) + d) * sizeof(double);
-  chol_inv_kernel<<<T, kThreads, smem, st>>>(K_t, d, ridge, Linv, Linv32, err, t0);
+  chol_kernel<<<T, kThreads, smem, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
 }
 
 }  // namespace erx

@@ -18,7 +18,13 @@ __device__ __forceinline__ double to_d(T v) { return (double)v; }
 // The recursion is a d^2-wide elementwise scan; the values a line is scored
 // with (after the update, or before it for score-then-update) are written
 // to mu_t / K_t.
-__global__ void __launch_bounds__(256) ema_scan_kernel(
+// The per-line loads do not depend on the recursion, so they are issued
+// kEmaBatch lines ahead of it to keep enough memory requests in flight; the
+// recursion itself stays strictly sequential, so results do not depend on how
+// lines are grouped into blocks.
+constexpr int kEmaBatch = 8;
+
+__global__ void __launch_bounds__(128) ema_scan_kernel(
     bool int_stats, const uint64_t* __restrict__ S1i, const uint64_t* __restrict__ S2i,
     const double* __restrict__ mu_hat, const double* __restrict__ shift,
     const double* __restrict__ S2f, int T, int d, int W, double alpha, int64_t t0, int order,
@@ -29,37 +35,66 @@ __global__ void __launch_bounds__(256) ema_scan_kernel(
   if (q >= P + d) return;
   const double beta = 1.0 - alpha;
   const double Wd = (double)W;
+  const double inv_pp = 1.0 / (Wd * (Wd - 1.0));
+  const double inv_p1 = 1.0 / (Wd - 1.0);
+  const int64_t dd = (int64_t)d * d;
   if (q < P) {
     int a = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
     while ((int64_t)a * (a + 1) / 2 > q) --a;
     while ((int64_t)(a + 1) * (a + 2) / 2 <= q) ++a;
     const int b = (int)(q - (int64_t)a * (a + 1) / 2);
+    const int64_t ab = (int64_t)a * d + b;
     double s = K_state[q];
-    for (int t = 0; t < T; ++t) {
-      double kh;
+    for (int t0b = 0; t0b < T; t0b += kEmaBatch) {
+      double kh[kEmaBatch];
+      const int nb = min(kEmaBatch, T - t0b);
       if (int_stats) {
-        const int64_t s1a = (int64_t)S1i[(int64_t)t * d + a];
-        const int64_t s1b = (int64_t)S1i[(int64_t)t * d + b];
-        const int64_t s2 = (int64_t)S2i[((int64_t)t * d + a) * d + b];
-        const int64_t num = (int64_t)W * s2 - s1a * s1b;
-        kh = (double)num / (Wd * (Wd - 1.0));
+        int64_t s1a[kEmaBatch], s1b[kEmaBatch], s2[kEmaBatch];
+#pragma unroll
+        for (int u = 0; u < kEmaBatch; ++u) {
+          if (u < nb) {
+            const int64_t t = t0b + u;
+            s1a[u] = (int64_t)__ldg(S1i + t * d + a);
+            s1b[u] = (int64_t)__ldg(S1i + t * d + b);
+            s2[u] = (int64_t)__ldg(S2i + t * dd + ab);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kEmaBatch; ++u)
+          if (u < nb) kh[u] = (double)((int64_t)W * s2[u] - s1a[u] * s1b[u]) * inv_pp;
       } else {
-        const double ea = mu_hat[(int64_t)t * d + a] - shift[(int64_t)t * d + a];
-        const double eb = mu_hat[(int64_t)t * d + b] - shift[(int64_t)t * d + b];
-        kh = (S2f[((int64_t)t * d + a) * d + b] - Wd * ea * eb) / (Wd - 1.0);
+        double ea[kEmaBatch], eb[kEmaBatch], sv[kEmaBatch];
+#pragma unroll
+        for (int u = 0; u < kEmaBatch; ++u) {
+          if (u < nb) {
+            const int64_t t = t0b + u;
+            ea[u] = __ldg(mu_hat + t * d + a) - __ldg(shift + t * d + a);
+            eb[u] = __ldg(mu_hat + t * d + b) - __ldg(shift + t * d + b);
+            sv[u] = __ldg(S2f + t * dd + ab);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kEmaBatch; ++u)
+          if (u < nb) kh[u] = (sv[u] - Wd * ea[u] * eb[u]) * inv_p1;
       }
-      const bool first = (t0 + t == 0);
-      const double post = first ? kh : beta * s + alpha * kh;
-      K_t[(int64_t)t * P + q] = (order == 0 || first) ? post : s;
-      s = post;
+#pragma unroll
+      for (int u = 0; u < kEmaBatch; ++u) {
+        if (u < nb) {
+          const int64_t t = t0b + u;
+          const bool first = (t0 + t == 0);
+          const double post = first ? kh[u] : beta * s + alpha * kh[u];
+          K_t[t * P + q] = (order == 0 || first) ? post : s;
+          s = post;
+        }
+      }
     }
     K_state[q] = s;
   } else {
     const int a = (int)(q - P);
     double s = mu_state[a];
     for (int t = 0; t < T; ++t) {
-      const double mh = int_stats ? (double)S1i[(int64_t)t * d + a] / Wd
-                                  : mu_hat[(int64_t)t * d + a];
+      const double mh = int_stats ? (double)__ldg(S1i + (int64_t)t * d + a) / Wd
+                                  : __ldg(mu_hat + (int64_t)t * d + a);
       const bool first = (t0 + t == 0);
       const double post = first ? mh : beta * s + alpha * mh;
       mu_t[(int64_t)t * d + a] = (order == 0 || first) ? post : s;

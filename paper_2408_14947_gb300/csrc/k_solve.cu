@@ -1,18 +1,23 @@
-// S5 (Sec. III-D): delta_i = sqrt(m_i . m_i) with m_i = L_t^{-1} (z_i - mu_t).
+// S5 (Sec. III-D): delta_i = sqrt(m_i . m_i) with L_t m_i = z_i - mu_t.
+//
+// Both forms solve block by block with the blocked factor of k_factor.cu
+// (packed L_t whose 32 x 32 diagonal blocks hold D_J = L_JJ^{-1}):
+//   y_J = r_J - sum_{k < j0} L_Jk m_k,   m_J = D_J y_J,
+// exactly d(d+1)/2 multiply-adds per pixel, as forward substitution.
 //
 // FP64 form: one thread per pixel.  The pixel's centred vector r_i is staged
 // in shared memory (odd row pitch, so the 8-byte loads of a warp hit distinct
-// bank pairs); row j of the packed L^{-1} is read with warp-uniform loads and
-// m_ij = sum_{k<=j} Linv_jk r_ik is accumulated into four independent
-// chains.  Exactly d(d+1)/2 DFMA per pixel: the kernel is bound by the FP64
-// pipe (2 DFMA/clk/SM on GB300), not by memory.
+// bank pairs) and overwritten by m_i block by block; rows of the factor are
+// read with warp-uniform loads; the 32 values y_J of a block sit in
+// registers.  The kernel is bound by the FP64 pipe (2 DFMA/clk/SM on GB300).
 //
-// FP32 form: a register-tiled product M = R L^{-T} over the lower triangle.
-// A CTA owns 64 pixels; four warps cover 64 pixels x 32 outputs, each thread
-// a 4 x 4 tile, with R^T staged once (k-major) and each 32-row band of L^{-1}
-// staged k-major, so both operand loads are 16-byte and conflict-free.  The
-// centred samples are formed as (x - mu_hi) - mu_lo with mu split into two
-// floats, which keeps r accurate to float rounding without FP64 work per pixel.
+// FP32 form: register-tiled over pixels x outputs.  A CTA owns 64 pixels;
+// four warps cover 64 pixels x 32 outputs of a block, each thread a 4 x 4
+// tile; R^T (then M^T) is kept k-major in shared memory and each 32-row band
+// of the factor is staged k-major, so both operand loads are 16-byte and
+// conflict-free.  The centred samples are (x - mu_hi) - mu_lo with mu split
+// into two floats, which keeps r accurate to float rounding without FP64 work
+// per pixel.
 #include <cmath>
 
 #include "erx_internal.cuh"
@@ -26,11 +31,12 @@ template <typename T>
 __device__ __forceinline__ float to_f(T v) { return (float)v; }
 
 constexpr int kPixF64 = 64;
+constexpr int kNB = kFactorBlock;
 
 template <typename InT>
 __global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
     const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
-    const double* __restrict__ mu_t, const double* __restrict__ Linv, double* __restrict__ delta) {
+    const double* __restrict__ mu_t, const double* __restrict__ Lf, double* __restrict__ delta) {
   extern __shared__ __align__(16) double r[];
   const int dp = d | 1;
   const int t = blockIdx.y;
@@ -44,36 +50,56 @@ __global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
   __syncthreads();
   const int i = i0 + threadIdx.x;
   if (i >= W) return;
-  const double* L = Linv + (int64_t)t * packed_size(d);
-  const double* rr = r + threadIdx.x * dp;
+  const double* L = Lf + (int64_t)t * packed_size(d);
+  double* rr = r + threadIdx.x * dp;
   double d2 = 0.0;
-  for (int j = 0; j < d; ++j) {
-    const double* Lj = L + j * (j + 1) / 2;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int k = 0;
-    for (; k + 3 <= j; k += 4) {
-      a0 = fma(__ldg(Lj + k), rr[k], a0);
-      a1 = fma(__ldg(Lj + k + 1), rr[k + 1], a1);
-      a2 = fma(__ldg(Lj + k + 2), rr[k + 2], a2);
-      a3 = fma(__ldg(Lj + k + 3), rr[k + 3], a3);
+  for (int j0 = 0; j0 < d; j0 += kNB) {
+    const int nb = min(kNB, d - j0);
+    double y[kNB];
+#pragma unroll
+    for (int jj = 0; jj < kNB; ++jj) {
+      y[jj] = 0.0;
+      if (jj < nb) {
+        const int j = j0 + jj;
+        const double* Lj = L + j * (j + 1) / 2;
+        double a0 = rr[j], a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int k = 0;
+        for (; k + 4 <= j0; k += 4) {
+          a0 = fma(-__ldg(Lj + k), rr[k], a0);
+          a1 = fma(-__ldg(Lj + k + 1), rr[k + 1], a1);
+          a2 = fma(-__ldg(Lj + k + 2), rr[k + 2], a2);
+          a3 = fma(-__ldg(Lj + k + 3), rr[k + 3], a3);
+        }
+        y[jj] = (j0 > 0) ? (a0 + a1) + (a2 + a3) : a0;
+      }
     }
-    for (; k <= j; ++k) a0 = fma(__ldg(Lj + k), rr[k], a0);
-    const double m = (a0 + a1) + (a2 + a3);
-    d2 = fma(m, m, d2);
+#pragma unroll
+    for (int jj = 0; jj < kNB; ++jj) {
+      if (jj < nb) {
+        const int j = j0 + jj;
+        const double* Dj = L + j * (j + 1) / 2 + j0;
+        double s = 0.0;
+#pragma unroll
+        for (int kk = 0; kk <= jj; ++kk) s = fma(__ldg(Dj + kk), y[kk], s);
+        rr[j] = s;
+        d2 = fma(s, s, d2);
+      }
+    }
   }
   delta[(int64_t)t * W + i] = sqrt(d2);
 }
 
 constexpr int kPixF32 = 64;   // pixels per CTA
-constexpr int kOutB = 32;     // outputs per band of L^{-1}
+constexpr int kOutB = kNB;    // outputs per block of the factor
 
 template <typename InT>
 __global__ void __launch_bounds__(128) solve_fp32_kernel(
     const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
-    const double* __restrict__ mu_t, const float* __restrict__ Linv32, float* __restrict__ delta) {
+    const double* __restrict__ mu_t, const float* __restrict__ Lf32, float* __restrict__ delta) {
   extern __shared__ __align__(16) float smf[];
-  float* rT = smf;                        // [d][kPixF32]
-  float* LT = smf + d * kPixF32;          // [d][kOutB]
+  float* rT = smf;                          // [d][kPixF32]: r, then m, k-major
+  float* LT = smf + d * kPixF32;            // [d][kOutB]: factor band, k-major
+  float* yT = LT + d * kOutB;               // [kOutB][kPixF32]
   __shared__ float mu_hi[kMaxDim], mu_lo[kMaxDim];
   __shared__ float d2w[2][kPixF32];
   const int t = blockIdx.y;
@@ -95,38 +121,68 @@ __global__ void __launch_bounds__(128) solve_fp32_kernel(
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ph = warp & 1, oh = warp >> 1;
   const int lp = lane & 7, lo = lane >> 3;
-  const int pcol = ph * 32 + lp * 4;      // first of this thread's 4 pixels
-  const int ocol = oh * 16 + lo * 4;      // first of its 4 outputs within a band
-  const float* Lg = Linv32 + (int64_t)t * packed_size(d);
+  const int pcol = ph * 32 + lp * 4;        // first of this thread's 4 pixels
+  const int ocol = oh * 16 + lo * 4;        // first of its 4 outputs within a block
+  const float* Lg = Lf32 + (int64_t)t * packed_size(d);
   float d2[4] = {0.f, 0.f, 0.f, 0.f};
   for (int j0 = 0; j0 < d; j0 += kOutB) {
-    const int kend = min(d, j0 + kOutB);
+    const int j1 = min(d, j0 + kOutB);
     __syncthreads();
-    for (int e = threadIdx.x; e < kend * kOutB; e += 128) {
+    for (int e = threadIdx.x; e < j1 * kOutB; e += 128) {
       const int k = e / kOutB, jj = e % kOutB, j = j0 + jj;
       LT[k * kOutB + jj] = (j < d && k <= j) ? Lg[j * (j + 1) / 2 + k] : 0.f;
     }
     __syncthreads();
     float acc[4][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + ocol + b;
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+      for (int a = 0; a < 4; ++a) acc[a][b] = j < d ? rT[j * kPixF32 + pcol + a] : 0.f;
+    }
 #pragma unroll 4
-    for (int k = 0; k < kend; ++k) {
-      const float4 rv = *reinterpret_cast<const float4*>(rT + k * kPixF32 + pcol);
+    for (int k = 0; k < j0; ++k) {
+      const float4 mv = *reinterpret_cast<const float4*>(rT + k * kPixF32 + pcol);
       const float4 lv = *reinterpret_cast<const float4*>(LT + k * kOutB + ocol);
-      const float ra[4] = {rv.x, rv.y, rv.z, rv.w};
+      const float ma[4] = {mv.x, mv.y, mv.z, mv.w};
       const float la[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ra[a], la[b], acc[a][b]);
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(-ma[a], la[b], acc[a][b]);
     }
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) yT[(ocol + b) * kPixF32 + pcol + a] = acc[a][b];
+    __syncthreads();
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) d2[a] = fmaf(acc[a][b], acc[a][b], d2[a]);
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    const int nb = j1 - j0;
+#pragma unroll 4
+    for (int kk = 0; kk < nb; ++kk) {
+      const float4 yv = *reinterpret_cast<const float4*>(yT + kk * kPixF32 + pcol);
+      const float4 lv = *reinterpret_cast<const float4*>(LT + (j0 + kk) * kOutB + ocol);
+      const float ya[4] = {yv.x, yv.y, yv.z, yv.w};
+      const float la[4] = {lv.x, lv.y, lv.z, lv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ya[a], la[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = j0 + ocol + b;
+      if (j < d) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          rT[j * kPixF32 + pcol + a] = acc[a][b];
+          d2[a] = fmaf(acc[a][b], acc[a][b], d2[a]);
+        }
+      }
+    }
   }
   // reduce over the 4 output groups of a warp (lane bits 3, 4), then the 2 output halves
 #pragma unroll
@@ -147,7 +203,9 @@ __global__ void __launch_bounds__(128) solve_fp32_kernel(
 }
 
 size_t smem_fp64(int d) { return (size_t)kPixF64 * (d | 1) * sizeof(double); }
-size_t smem_fp32(int d) { return (size_t)d * (kPixF32 + kOutB) * sizeof(float); }
+size_t smem_fp32(int d) {
+  return ((size_t)d * (kPixF32 + kOutB) + (size_t)kOutB * kPixF32) * sizeof(float);
+}
 
 }  // namespace
 
