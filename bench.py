@@ -249,7 +249,7 @@ def run_ours(args):
     lines_per_launch = LINES / blocks
     flops = {
         "solve_fp64": 2.0 * WIDTH * (d * (d + 1) / 2 + d),
-        "chol_inv": 2.0 * (d ** 3 / 3.0),
+        "chol": d ** 3 / 3.0 + d * 32 * 32 / 3.0,
         "stats_int": 2.0 * WIDTH * d * d,
     }
     per_line = flops.get(dom, 0.0)

@@ -47,7 +47,8 @@ typedef enum {
   ERX_ENOTPD = 4,       /* K_t + ridge I was not positive definite at some line */
   ERX_ERANGE = 5,       /* an integer input sample exceeded 2^in_bits - 1 */
   ERX_ESTATE = 6,       /* call not valid in the context's current state */
-  ERX_EUNSUPPORTED = 7  /* valid request this build does not implement */
+  ERX_EUNSUPPORTED = 7, /* valid request this build does not implement */
+  ERX_ETIMEOUT = 8      /* a bounded wait inside a kernel gave up; results of the call are invalid */
 } erx_status;
 
 /* projection (Sec. III-B) */
@@ -56,6 +57,9 @@ enum { ERX_PROJ_NONE = 0, ERX_PROJ_SRP = 1 };
 enum { ERX_UPDATE_THEN_SCORE = 0, ERX_SCORE_THEN_UPDATE = 1 };
 /* input sample type, lines laid out [pixel][band] (band-interleaved-by-pixel) */
 enum { ERX_U16 = 0, ERX_F32 = 1, ERX_F64 = 2 };
+/* flags: ERX_FLAG_SIMT_STATS keeps S2 off the tensor cores (exact integer
+ * sums by 32-bit integer multiply-adds instead); results are identical */
+enum { ERX_FLAG_SIMT_STATS = 1 };
 /* arithmetic form of S2 and S5; S3 and S4 are FP64 in every form */
 enum { ERX_FORM_FP64 = 0, ERX_FORM_FP32 = 1 };
 
@@ -74,6 +78,7 @@ typedef struct {
   int32_t form;         /* ERX_FORM_FP64 or ERX_FORM_FP32 */
   double threshold;     /* tau_N for the mask (Sec. III-E) */
   int32_t block_lines;  /* lines processed per internal block; 0 = automatic */
+  int32_t flags;        /* ERX_FLAG_* bits */
   const double* srp_weights; /* optional b x d row-major host matrix replacing the drawn SRP */
 } erx_config;
 
@@ -114,7 +119,7 @@ erx_status erx_push_lines_host(erx_ctx* ctx, const void* lines_host, int64_t n_l
                                uint8_t* detecting_host);
 
 /* Wait for the context's stream and report deferred device errors
- * (ERX_ENOTPD, ERX_ERANGE) raised since the last erx_sync.  *bad_line (may be
+ * (ERX_ETIMEOUT, ERX_ENOTPD, ERX_ERANGE) raised since the last erx_sync.  *bad_line (may be
  * NULL) receives the global index of the first offending line or -1. */
 erx_status erx_sync(erx_ctx* ctx, int64_t* bad_line);
 
@@ -190,7 +195,8 @@ enum {
   ERX_K_SOLVE_FP64 = 6, /* S5 scores, FP64 */
   ERX_K_SOLVE_FP32 = 7, /* S5 scores, FP32 */
   ERX_K_NORMALISE = 8,  /* S6 normalisation */
-  ERX_K_COUNT = 9
+  ERX_K_STATS_TC = 9,   /* S2 exact integer sums on the tensor cores */
+  ERX_K_COUNT = 10
 };
 
 /* Per-kernel timing.  While enabled (on != 0), every kernel the context

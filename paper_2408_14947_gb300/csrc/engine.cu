@@ -22,6 +22,8 @@ struct erx_ctx {
   erx_config cfg{};
   int B = 0, W = 0, d = 0, T = 0;
   int device = 0;
+  int n_sm = 1;
+  bool tc_stats = false;
   cudaStream_t stream = nullptr;
   bool int_stats = false;
   bool fp64 = true;
@@ -199,7 +201,11 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
     zstride = (int64_t)W * d;
     ps = d;
   }
-  if (c->int_stats) {
+  if (c->int_stats && c->tc_stats) {
+    KernelScope ks(c, ERX_K_STATS_TC);
+    launch_stats_tc((const uint16_t*)x, stride_elems, W, d, (1u << c->cfg.in_bits) - 1u, T,
+                    c->n_sm, c->S1i, c->S2i, c->err, c->t, st);
+  } else if (c->int_stats) {
     KernelScope ks(c, ERX_K_STATS_INT);
     launch_stats_int((const uint16_t*)x, stride_elems, W, d, (1u << c->cfg.in_bits) - 1u, T,
                      c->S1i, c->S2i, c->err, c->t, st);
@@ -259,6 +265,7 @@ void erx_config_default(erx_config* cfg, int32_t bands, int32_t width) {
   cfg->form = ERX_FORM_FP64;
   cfg->threshold = 3.0;
   cfg->block_lines = 0;
+  cfg->flags = 0;
   cfg->srp_weights = nullptr;
 }
 
@@ -307,6 +314,14 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   const double maxv = std::ldexp(1.0, cfg->in_bits) - 1.0;
   c->int_stats = cfg->in_dtype == ERX_U16 && cfg->proj == ERX_PROJ_NONE &&
                  (double)W * maxv < 2.1e9;
+  c->tc_stats = c->int_stats && !(cfg->flags & ERX_FLAG_SIMT_STATS) &&
+                stats_tc_supported(d, W, cfg->in_bits);
+  if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return ERX_ECUDA;
+  }
   // block size: keep the per-block scratch near 256 MiB
   const int64_t P = packed_size(d);
   size_t per_line = (size_t)P * 8 * 2 + (size_t)d * 8 * 4 + (size_t)d * d * 8 +
@@ -315,7 +330,8 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
                                : (int)std::max<size_t>(1, (256ull << 20) / per_line);
   T = std::min(T, 4096);
   c->T = T;
-  if (configure_factor_kernels() != cudaSuccess || configure_solve_kernels() != cudaSuccess) {
+  if (configure_factor_kernels() != cudaSuccess || configure_solve_kernels() != cudaSuccess ||
+      configure_stats_tc_kernel() != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return ERX_ECUDA;
@@ -522,6 +538,10 @@ erx_status erx_sync(erx_ctx* c, int64_t* bad_line) {
       cudaMemcpy(e, c->err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess)
     return check_cuda(c, cudaGetLastError());
   if (cudaMemset(c->err, 0xff, sizeof(e)) != cudaSuccess) return check_cuda(c, cudaGetLastError());
+  if (e[kErrTimeout] != ~0ull) {
+    if (bad_line) *bad_line = (int64_t)e[kErrTimeout];
+    return ERX_ETIMEOUT;
+  }
   if (e[kErrNotPD] != ~0ull) {
     if (bad_line) *bad_line = (int64_t)e[kErrNotPD];
     return ERX_ENOTPD;
@@ -619,9 +639,10 @@ erx_status erx_profile_read(erx_ctx* c, int32_t k, int32_t reset, double* total_
 }
 
 const char* erx_kernel_name(int32_t k) {
-  static const char* names[ERX_K_COUNT] = {"project", "stats_int", "mean", "stats_fp",
-                                           "ema_scan", "chol_inv", "solve_fp64", "solve_fp32",
-                                           "normalise"};
+  static const char* names[ERX_K_COUNT] = {"project",    "stats_int",  "mean",
+                                           "stats_fp",   "ema_scan",   "chol",
+                                           "solve_fp64", "solve_fp32", "normalise",
+                                           "stats_tc"};
   return (k >= 0 && k < ERX_K_COUNT) ? names[k] : nullptr;
 }
 
@@ -645,6 +666,7 @@ const char* erx_status_str(erx_status s) {
     case ERX_ERANGE: return "ERX_ERANGE: input sample above 2^in_bits - 1";
     case ERX_ESTATE: return "ERX_ESTATE: call not valid in this state";
     case ERX_EUNSUPPORTED: return "ERX_EUNSUPPORTED: beyond this build's limits";
+    case ERX_ETIMEOUT: return "ERX_ETIMEOUT: a bounded wait in a kernel gave up";
   }
   return "ERX_?: unknown status";
 }

@@ -21,7 +21,7 @@ constexpr int kMaxDim = 224;   // packed FP64 factor must fit one SM's shared me
 constexpr int kFactorBlock = 32;  // diagonal blocks of the factor are stored inverted
 
 // error slots (unsigned long long, min-reduced line index; ~0ull = none)
-enum { kErrNotPD = 0, kErrRange = 1, kErrSlots = 2 };
+enum { kErrNotPD = 0, kErrRange = 1, kErrTimeout = 2, kErrSlots = 3 };
 
 __host__ __device__ inline int64_t packed_size(int d) { return (int64_t)d * (d + 1) / 2; }
 
@@ -36,6 +36,14 @@ cudaError_t configure_solve_kernels();
 void launch_stats_int(const uint16_t* x, int64_t line_stride, int W, int d, uint32_t maxv,
                       int T, uint64_t* S1, uint64_t* S2, unsigned long long* err, int64_t t0,
                       cudaStream_t st);
+
+// Exact integer sums on the tensor cores (bf16 6-bit split, FP32 accumulation
+// exact below 2^24): u16 samples < 2^12, no projection, d + 1 <= 128, p <= 2048.
+bool stats_tc_supported(int d, int W, int bits);
+cudaError_t configure_stats_tc_kernel();
+void launch_stats_tc(const uint16_t* x, int64_t line_stride, int W, int d, uint32_t maxv, int T,
+                     int n_sm, uint64_t* S1, uint64_t* S2, unsigned long long* err, int64_t t0,
+                     cudaStream_t st);
 
 // Line means (double) and centring shifts c (= mean, or the mean rounded to
 // float when `float_shift`).  in_type: 0 u16, 1 f32, 2 f64.  ps = pixel stride.

@@ -1,0 +1,208 @@
+// S2 (Sec. III-C) on the tensor cores: exact integer line sums for u16 samples.
+//
+// Each sample (< 2^12) is split as x = 64 h + l with h, l < 64, both exact in
+// bf16.  Then
+//   sum_i x_ia x_ib = 4096 HH_ab + 64 (HL_ab + LH_ab) + LL_ab,
+// where HH = H H^T, HL = H L^T, ... are bf16 products accumulated in FP32 in
+// tensor memory.  Every partial sum is an integer below 2^24 for lines of up
+// to 2048 pixels (products < 2^12, at most 2 * 2048 of them per entry), so
+// the FP32 accumulation is exact and the result equals the integer sums of
+// the IMAD route bit for bit.  An extra band of ones appended to the operand
+// gives sum_i x_ia in the same products (column d).
+//
+// One persistent CTA per SM walks lines; per line, 64-pixel chunks are
+// converted into two bf16 operand tiles (bands x pixels, K-major) in shared
+// memory, double-buffered so that the conversion of chunk c+1 overlaps the
+// MMAs of chunk c; one thread issues 16 tcgen05.mma (M = 128 bands, N = d+1
+// rounded to 16, K = 16 pixels) per chunk into three accumulators
+// (HH | HL+LH | LL, 512 TMEM columns) and commits them to the buffer's
+// mbarrier.  The drain converts the three FP32 accumulators to int64 sums.
+#include "erx_internal.cuh"
+#include "tc_util.cuh"
+
+namespace erx {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kKC = 64;                              // pixels per chunk
+constexpr int kRows = 128;                           // M: bands (+ ones row), padded
+constexpr int kTileBytes = kRows * kKC * 2;          // 16 KiB bf16 tile
+constexpr uint32_t kLBO = 128;                       // next 8 pixels (K core matrix)
+constexpr uint32_t kSBO = (kKC / 8) * 128;           // next 8 bands (M core group)
+constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr uint32_t kColHH = 0, kColMid = 128, kColLL = 256, kTmemCols = 512;
+// more shared memory than two CTAs can hold, so that each SM runs one CTA and
+// no CTA waits in tcgen05.alloc for another's 512 TMEM columns
+constexpr int kSmemBytes = 118 * 1024;
+
+__device__ __forceinline__ uint32_t tile_off(int m, int g) {
+  return (uint32_t)(m >> 3) * kSBO + (uint32_t)g * kLBO + (uint32_t)(m & 7) * 16;
+}
+
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t a, uint32_t b) {
+  // small non-negative integers (< 256) are exact in bf16: value v -> bits of float(v) >> 16
+  const uint32_t fa = __float_as_uint((float)a) >> 16;
+  const uint32_t fb = __float_as_uint((float)b) >> 16;
+  return fa | (fb << 16);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) stats_tc_kernel(
+    const uint16_t* __restrict__ X, int64_t line_stride, int W, int d, uint32_t maxv, int T,
+    uint64_t* __restrict__ S1, uint64_t* __restrict__ S2, unsigned long long* __restrict__ err,
+    int64_t t0) {
+  extern __shared__ __align__(1024) unsigned char sm[];   // [2 buffers][H tile | L tile]
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int np = ((d + 1) + 15) & ~15;                    // N: bands + ones row, mult of 16
+  for (int i = tid; i < 4 * kTileBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, kTmemCols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const uint32_t id = tc::idesc(1, kRows, np);
+  uint32_t issued[2] = {0u, 0u}, done[2] = {0u, 0u};
+  bool timed_out = false;
+  const int nchunk = (W + kKC - 1) / kKC;
+  const int items = (d + 1) * (kKC / 8);
+
+  for (int t = blockIdx.x; t < T && !timed_out; t += gridDim.x) {
+    const uint16_t* x = X + (int64_t)t * line_stride;
+    bool bad = false;
+    for (int c = 0; c < nchunk; ++c) {
+      const int b = c & 1;
+      if (issued[b] != done[b]) {
+        const bool ok = tc::mbar_wait(&mbar[b], done[b] & 1u, kWaitLimit);
+        if (ok) ++done[b];
+        if (__syncthreads_or(!ok)) {
+          timed_out = true;
+          break;
+        }
+      }
+      unsigned char* tH = sm + b * 2 * kTileBytes;
+      unsigned char* tL = tH + kTileBytes;
+      const int i0 = c * kKC;
+      for (int it = tid; it < items; it += kThreads) {
+        const int m = it % (d + 1), g = it / (d + 1);
+        uint32_t hv[4], lv[4];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+          uint32_t v[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int i = i0 + g * 8 + q + u;
+            uint32_t s = 0u;
+            if (i < W) s = (m < d) ? (uint32_t)x[(int64_t)i * d + m] : 1u;
+            bad |= (m < d) && (s > maxv);
+            v[u] = s;
+          }
+          hv[q / 2] = bf16_pair(v[0] >> 6, v[1] >> 6);
+          lv[q / 2] = bf16_pair(v[0] & 63u, v[1] & 63u);
+        }
+        const uint32_t off = tile_off(m, g);
+        *reinterpret_cast<uint4*>(tH + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<uint4*>(tL + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+      }
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+      if (tid == 0) {
+        const uint32_t aH = tc::smem_u32(tH), aL = tc::smem_u32(tL);
+#pragma unroll
+        for (int s = 0; s < kKC / 16; ++s) {
+          const uint32_t ko = (uint32_t)s * 2u * kLBO;
+          const uint64_t dH = tc::desc(aH + ko, kLBO, kSBO);
+          const uint64_t dL = tc::desc(aL + ko, kLBO, kSBO);
+          const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
+          tc::mma_bf16(tmem + kColHH, dH, dH, id, acc);
+          tc::mma_bf16(tmem + kColMid, dH, dL, id, acc);
+          tc::mma_bf16(tmem + kColMid, dL, dH, id, 1u);
+          tc::mma_bf16(tmem + kColLL, dL, dL, id, acc);
+        }
+        tc::commit(&mbar[b]);
+      }
+      ++issued[b];
+    }
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) atomicMin(&err[kErrRange], (unsigned long long)(t0 + t));
+    }
+    if (timed_out) break;
+    for (int b = 0; b < 2; ++b) {
+      if (issued[b] != done[b]) {
+        const bool ok = tc::mbar_wait(&mbar[b], done[b] & 1u, kWaitLimit);
+        if (ok) ++done[b];
+        timed_out |= !ok;
+      }
+    }
+    if (__syncthreads_or(timed_out)) {
+      timed_out = true;
+      break;
+    }
+    tc::fence_after_sync();
+    // drain: warp w reads TMEM lanes 32 (w % 4) .. +31 (band rows), 16-column chunks
+    const int m = 32 * (warp & 3) + lane;
+    uint64_t* s2 = S2 + (int64_t)t * d * d;
+    for (int c0 = (warp >> 2) * 16; c0 < np; c0 += 32) {
+      uint32_t hh[16], md[16], ll[16];
+      const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+      tc::tmem_ld16(lane_base + kColHH, hh);
+      tc::tmem_ld16(lane_base + kColMid, md);
+      tc::tmem_ld16(lane_base + kColLL, ll);
+      tc::tmem_ld_wait();
+      if (m < d) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c0 + j;
+          const uint64_t v = 4096ull * (uint64_t)__uint_as_float(hh[j]) +
+                             64ull * (uint64_t)__uint_as_float(md[j]) +
+                             (uint64_t)__uint_as_float(ll[j]);
+          if (n < d) {
+            if (n <= m) s2[(int64_t)m * d + n] = v;
+          } else if (n == d) {
+            S1[(int64_t)t * d + m] = v;
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
+  if (timed_out && tid == 0) atomicMin(&err[kErrTimeout], (unsigned long long)(t0 + blockIdx.x));
+  // outstanding MMAs (only after a timeout) get one more bounded wait before TMEM is released
+  for (int b = 0; b < 2; ++b)
+    if (issued[b] != done[b]) tc::mbar_wait(&mbar[b], done[b] & 1u, kWaitLimit);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, kTmemCols);
+}
+
+}  // namespace
+
+bool stats_tc_supported(int d, int W, int bits) {
+  return d + 1 <= kRows && W <= 2048 && bits <= 12;
+}
+
+cudaError_t configure_stats_tc_kernel() {
+  return cudaFuncSetAttribute(stats_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kSmemBytes);
+}
+
+void launch_stats_tc(const uint16_t* x, int64_t line_stride, int W, int d, uint32_t maxv, int T,
+                     int n_sm, uint64_t* S1, uint64_t* S2, unsigned long long* err, int64_t t0,
+                     cudaStream_t st) {
+  const int grid = T < n_sm ? T : n_sm;
+  stats_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, line_stride, W, d, maxv, T, S1, S2,
+                                                          err, t0);
+}
+
+}  // namespace erx

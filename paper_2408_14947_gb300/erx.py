@@ -14,7 +14,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_PKG, "_lib", "liberx.so")
 
 ERX_OK, ERX_EINVAL, ERX_ENOMEM, ERX_ECUDA, ERX_ENOTPD, ERX_ERANGE, ERX_ESTATE, \
-    ERX_EUNSUPPORTED = range(8)
+    ERX_EUNSUPPORTED, ERX_ETIMEOUT = range(9)
+ERX_FLAG_SIMT_STATS = 1
 ERX_PROJ_NONE, ERX_PROJ_SRP = 0, 1
 ERX_UPDATE_THEN_SCORE, ERX_SCORE_THEN_UPDATE = 0, 1
 ERX_U16, ERX_F32, ERX_F64 = 0, 1, 2
@@ -29,7 +30,7 @@ class ErxConfig(C.Structure):
         ("proj", C.c_int32), ("proj_dim", C.c_int32), ("seed", C.c_uint64),
         ("ridge", C.c_double), ("warmup_lines", C.c_int32), ("order", C.c_int32),
         ("in_dtype", C.c_int32), ("in_bits", C.c_int32), ("form", C.c_int32),
-        ("threshold", C.c_double), ("block_lines", C.c_int32),
+        ("threshold", C.c_double), ("block_lines", C.c_int32), ("flags", C.c_int32),
         ("srp_weights", C.POINTER(C.c_double)),
     ]
 
@@ -167,7 +168,7 @@ def erx_srp_weights(bands: int, dim: int, seed: int):
     return w
 
 
-ERX_K_COUNT = 9
+ERX_K_COUNT = 10
 
 
 def erx_push_lines_static(cfg, stream, mu_ptr, k_ptr, t, lines_ptr, n_lines, stride_bytes,
@@ -211,7 +212,8 @@ class Detector:
 
     def __init__(self, bands, width, momentum=0.1, proj="none", proj_dim=5, seed=0, ridge=1e-5,
                  warmup=99, order="update_then_score", in_dtype="f32", in_bits=16,
-                 form="fp64", threshold=3.0, block_lines=0, srp_weights=None, stream=None):
+                 form="fp64", threshold=3.0, block_lines=0, srp_weights=None, stream=None,
+                 simt_stats=False):
         import torch
         self.torch = torch
         cfg = erx_config_default(bands, width)
@@ -228,6 +230,7 @@ class Detector:
         cfg.form = {"fp64": ERX_FORM_FP64, "fp32": ERX_FORM_FP32}[form]
         cfg.threshold = threshold if threshold is not None else math.inf
         cfg.block_lines = block_lines
+        cfg.flags = ERX_FLAG_SIMT_STATS if simt_stats else 0
         self._w = None
         if srp_weights is not None:
             import numpy as np

@@ -202,3 +202,35 @@ def test_planted_anomaly_ranking_fp32_matches_fp64():
         same = o == g
         close = np.abs(np.diff(rv, append=-np.inf)) < 1e-3
         assert np.all(same | close | np.roll(close, 1))
+
+
+@pytest.mark.parametrize("width,bands", [(640, 108), (2048, 127), (65, 1), (130, 16), (1, 5)])
+def test_tensor_core_stats_match_integer_route_bitwise(width, bands):
+    """The tcgen05 exact-integer SYRK (bf16 6-bit split, FP32 accumulation in
+    TMEM) gives the same sums as the 32-bit integer route, hence identical
+    scores, state and flags."""
+    if width < 2:
+        pytest.skip("a line needs two pixels")
+    cube = synth.gen_lines(synth.dn_c2(width=width, bands=bands, seed=9), 0, 9)
+    a, da = run_gpu(cube, in_bits=12, warmup=2)
+    b, db = run_gpu(cube, in_bits=12, warmup=2, simt_stats=True)
+    for k in ("delta", "delta_n", "mask", "detecting"):
+        assert np.array_equal(a[k], b[k]), k
+    sa, sb = da.state(), db.state()
+    assert np.array_equal(sa[1], sb[1]) and np.array_equal(sa[2], sb[2])
+    ka = da.profile_read()
+    assert ka["stats_tc"][2] > 0 and ka["stats_int"][2] == 0
+    kb = db.profile_read()
+    assert kb["stats_tc"][2] == 0 and kb["stats_int"][2] > 0
+
+
+def test_tensor_core_stats_range_check():
+    from paper_2408_14947_gb300 import Detector, ErxError, ERX_ERANGE
+    cube = synth.gen_lines(synth.dn_c2(width=100, bands=10), 0, 5)
+    cube[3, 7, 2] = 4096
+    det = Detector(10, 100, in_dtype="u16", in_bits=12)
+    det.push(torch.from_numpy(cube.view(np.int16)).cuda())
+    with pytest.raises(ErxError) as ei:
+        det.sync()
+    assert ei.value.status == ERX_ERANGE and ei.value.bad_line == 3
+    assert det.profile_read()["stats_tc"][2] > 0
