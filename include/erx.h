@@ -60,8 +60,11 @@ enum { ERX_U16 = 0, ERX_F32 = 1, ERX_F64 = 2 };
 /* flags: ERX_FLAG_SIMT_STATS keeps S2 off the tensor cores (exact integer
  * sums by 32-bit integer multiply-adds instead); results are identical */
 enum { ERX_FLAG_SIMT_STATS = 1 };
-/* arithmetic form of S2 and S5; S3 and S4 are FP64 in every form */
-enum { ERX_FORM_FP64 = 0, ERX_FORM_FP32 = 1 };
+/* arithmetic form of S5 (and of S2 for floating input); S3 and S4 are FP64 in
+ * every form, and u16 input without projection always gets exact integer S2.
+ * FP64: FP64 arithmetic.  FP32: FP32 SIMT arithmetic.  TF32 / BF16: tensor-core
+ * MMAs with TF32 / BF16 operands and FP32 accumulation. */
+enum { ERX_FORM_FP64 = 0, ERX_FORM_FP32 = 1, ERX_FORM_TF32 = 2, ERX_FORM_BF16 = 3 };
 
 typedef struct {
   int32_t bands;        /* b >= 1 */
@@ -75,7 +78,7 @@ typedef struct {
   int32_t order;        /* ERX_UPDATE_THEN_SCORE (paper) or ERX_SCORE_THEN_UPDATE */
   int32_t in_dtype;     /* ERX_U16, ERX_F32 or ERX_F64 */
   int32_t in_bits;      /* for ERX_U16: samples are < 2^in_bits (1..16); else ignored */
-  int32_t form;         /* ERX_FORM_FP64 or ERX_FORM_FP32 */
+  int32_t form;         /* ERX_FORM_* */
   double threshold;     /* tau_N for the mask (Sec. III-E) */
   int32_t block_lines;  /* lines processed per internal block; 0 = automatic */
   int32_t flags;        /* ERX_FLAG_* bits */
@@ -100,7 +103,7 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out);
  * each p x b samples of in_dtype, row-major [pixel][band]; line_stride_bytes
  * = 0 means p*b*sizeof(sample).  Outputs (device, caller-owned, row-major
  * [line][pixel]):
- *   delta_dev       delta (Sec. III-D); double for ERX_FORM_FP64, float otherwise
+ *   delta_dev       delta (Sec. III-D); double for ERX_FORM_FP64, float for the other forms
  *   delta_norm_dev  delta_N (Sec. III-E), same type as delta; may be NULL
  *   mask_dev        uint8 delta_N >= threshold; may be NULL
  *   detecting_dev   uint8 per line, 1 once the warm-up lines have passed; may be NULL
@@ -196,7 +199,8 @@ enum {
   ERX_K_SOLVE_FP32 = 7, /* S5 scores, FP32 */
   ERX_K_NORMALISE = 8,  /* S6 normalisation */
   ERX_K_STATS_TC = 9,   /* S2 exact integer sums on the tensor cores */
-  ERX_K_COUNT = 10
+  ERX_K_SOLVE_TC = 10,  /* S5 scores on the tensor cores (TF32 / BF16) */
+  ERX_K_COUNT = 11
 };
 
 /* Per-kernel timing.  While enabled (on != 0), every kernel the context

@@ -174,7 +174,7 @@ erx_status validate(const erx_config* cfg) {
     return ERX_EINVAL;
   if (cfg->in_dtype < ERX_U16 || cfg->in_dtype > ERX_F64) return ERX_EINVAL;
   if (cfg->in_dtype == ERX_U16 && (cfg->in_bits < 1 || cfg->in_bits > 16)) return ERX_EINVAL;
-  if (cfg->form != ERX_FORM_FP64 && cfg->form != ERX_FORM_FP32) return ERX_EINVAL;
+  if (cfg->form < ERX_FORM_FP64 || cfg->form > ERX_FORM_BF16) return ERX_EINVAL;
   if (cfg->block_lines < 0 || cfg->warmup_lines < 0) return ERX_EINVAL;
   const int d = cfg->proj == ERX_PROJ_SRP ? cfg->proj_dim : cfg->bands;
   if (d > kMaxDim || cfg->width > (1 << 20) || cfg->bands > 65536) return ERX_EUNSUPPORTED;
@@ -231,6 +231,10 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
   if (c->fp64) {
     KernelScope ks(c, ERX_K_SOLVE_FP64);
     launch_solve_fp64(ztype, zsrc, zstride, ps, W, d, T, c->mu_t, c->Linv, (double*)delta, st);
+  } else if (c->cfg.form == ERX_FORM_TF32 || c->cfg.form == ERX_FORM_BF16) {
+    KernelScope ks(c, ERX_K_SOLVE_TC);
+    launch_solve_tc(c->cfg.form == ERX_FORM_TF32 ? 2 : 1, ztype, zsrc, zstride, ps, W, d, T,
+                    c->mu_t, c->Linv32, (float*)delta, c->err, c->t, st);
   } else {
     KernelScope ks(c, ERX_K_SOLVE_FP32);
     launch_solve_fp32(ztype, zsrc, zstride, ps, W, d, T, c->mu_t, c->Linv32, (float*)delta, st);
@@ -331,7 +335,7 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   T = std::min(T, 4096);
   c->T = T;
   if (configure_factor_kernels() != cudaSuccess || configure_solve_kernels() != cudaSuccess ||
-      configure_stats_tc_kernel() != cudaSuccess) {
+      configure_stats_tc_kernel() != cudaSuccess || configure_solve_tc_kernels() != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return ERX_ECUDA;
@@ -642,7 +646,7 @@ const char* erx_kernel_name(int32_t k) {
   static const char* names[ERX_K_COUNT] = {"project",    "stats_int",  "mean",
                                            "stats_fp",   "ema_scan",   "chol",
                                            "solve_fp64", "solve_fp32", "normalise",
-                                           "stats_tc"};
+                                           "stats_tc",   "solve_tc"};
   return (k >= 0 && k < ERX_K_COUNT) ? names[k] : nullptr;
 }
 

@@ -75,6 +75,12 @@ void launch_solve_fp32(int in_type, const void* x, int64_t line_stride, int ps, 
                        int T, const double* mu_t, const float* Linv32, float* delta,
                        cudaStream_t st);
 
+// delta_i on the tensor cores: fmt 2 = TF32, 1 = BF16 operands, FP32 accumulation.
+cudaError_t configure_solve_tc_kernels();
+void launch_solve_tc(int fmt, int in_type, const void* x, int64_t line_stride, int ps, int W,
+                     int d, int T, const double* mu_t, const float* Lf32, float* delta,
+                     unsigned long long* err, int64_t t0, cudaStream_t st);
+
 // Per-line normalisation (Sec. III-E), mask and warm-up flags.
 void launch_normalise(bool fp64, const void* delta, int W, int T, double threshold,
                       int64_t t0, int64_t warmup, void* delta_n, uint8_t* mask,

@@ -1,0 +1,273 @@
+// S5 (Sec. III-D) on the tensor cores: TF32 or BF16 operands, FP32 accumulation.
+//
+// A CTA owns 128 pixels of a line (the M = 128 rows of the MMA; pixel p is
+// TMEM lane p) and solves L m = r for all of them block by block with the
+// blocked factor (32 x 32 diagonal blocks stored inverted):
+//   acc1 = M_{<J} L_{J,<J}^T          (K = j0, the m values found so far)
+//   y_J  = r_J - acc1                 (FP32, r_J re-read from the line)
+//   acc2 = y_J D_J^T                  (K = 32)
+//   m_J  = acc2,  delta^2 += |m_J|^2  (FP32), m_J written back as an operand.
+// All operand tiles are K-major, no swizzle, in shared memory; one thread
+// issues the MMAs (M = 128, N = 32) and commits them to an mbarrier that the
+// CTA waits on with a bounded poll.  r is formed as (x - mu_hi) - mu_lo with
+// mu split into two floats.  TF32 operands are rounded to nearest (cvt.rna).
+#include <cuda_bf16.h>
+
+#include "erx_internal.cuh"
+#include "tc_util.cuh"
+
+namespace erx {
+namespace {
+
+constexpr int kPix = 128;
+constexpr int kB = kFactorBlock;     // 32 outputs per block
+constexpr uint32_t kLBO = 128;
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+template <typename T>
+__device__ __forceinline__ float to_f(T v) { return (float)v; }
+
+__device__ __forceinline__ uint32_t tf32_bits(float v) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+
+// 16 bytes of operand data (4 tf32 or 8 bf16 values) from consecutive floats
+template <int FMT>
+__device__ __forceinline__ uint4 pack16(const float* v) {
+  if (FMT == 2) {
+    return make_uint4(tf32_bits(v[0]), tf32_bits(v[1]), tf32_bits(v[2]), tf32_bits(v[3]));
+  } else {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      w[i] = *reinterpret_cast<const uint32_t*>(&b);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// FMT 2: TF32 (4-byte elements, 4 per core row, K = 8 per MMA);
+// FMT 1: BF16 (2-byte elements, 8 per core row, K = 16 per MMA).
+template <typename InT, int FMT>
+__global__ void __launch_bounds__(kPix) solve_tc_kernel(
+    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
+    const double* __restrict__ mu_t, const float* __restrict__ Lf32, float* __restrict__ delta,
+    unsigned long long* __restrict__ err, int64_t t0) {
+  constexpr int E = FMT == 2 ? 4 : 2;     // bytes per element
+  constexpr int CK = 16 / E;              // elements per 16-byte core row
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  __shared__ float mu_hi[kMaxDim], mu_lo[kMaxDim];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int t = blockIdx.y;
+  const int i0 = blockIdx.x * kPix;
+  const int dK = (d + kB - 1) / kB * kB;
+  const uint32_t sboM = (uint32_t)(dK / CK) * 128u;
+  const uint32_t sboY = (uint32_t)(kB / CK) * 128u;
+  unsigned char* Mt = sm;                                  // [128][dK]
+  unsigned char* Lt = Mt + (size_t)kPix * dK * E;          // [32][dK]
+  unsigned char* Yt = Lt + (size_t)kB * dK * E;            // [128][32]
+  auto off = [](int row, int k, uint32_t sbo) -> uint32_t {
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k / CK) * kLBO + (uint32_t)(row & 7) * 16u;
+  };
+  const InT* x = X + (int64_t)t * line_stride;
+  for (int k = tid; k < d; k += kPix) {
+    const double m = mu_t[(int64_t)t * d + k];
+    const float h = (float)m;
+    mu_hi[k] = h;
+    mu_lo[k] = (float)(m - (double)h);
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, 64);
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  // r of this thread's pixel into its row of Mt (zero beyond d or beyond the line)
+  const int p = tid, i = i0 + p;
+  const bool valid = i < W;
+  const InT* xp = x + (int64_t)(valid ? i : 0) * ps;
+  for (int k0 = 0; k0 < dK; k0 += CK) {
+    float v[CK];
+#pragma unroll
+    for (int u = 0; u < CK; ++u) {
+      const int k = k0 + u;
+      v[u] = (valid && k < d) ? (to_f(xp[k]) - mu_hi[k]) - mu_lo[k] : 0.f;
+    }
+    *reinterpret_cast<uint4*>(Mt + off(p, k0, sboM) + (k0 % CK) * E) = pack16<FMT>(v);
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const uint32_t id = tc::idesc(FMT, kPix, kB);
+  const float* Lg = Lf32 + (int64_t)t * packed_size(d);
+  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+  uint32_t phase = 0;
+  bool ok = true;
+  float d2 = 0.f;
+  for (int j0 = 0; j0 < d && ok; j0 += kB) {
+    // stage rows j0..j0+31 of the blocked factor, columns k < j0 + 32
+    const int kcols = j0 + kB;
+    for (int e = tid; e < kB * (kcols / CK); e += kPix) {
+      const int jj = e % kB, kg = e / kB, j = j0 + jj;
+      float v[CK];
+#pragma unroll
+      for (int u = 0; u < CK; ++u) {
+        const int k = kg * CK + u;
+        v[u] = (j < d && k <= j) ? Lg[j * (j + 1) / 2 + k] : 0.f;
+      }
+      *reinterpret_cast<uint4*>(Lt + off(jj, kg * CK, sboM)) = pack16<FMT>(v);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    float y[kB];
+    // r_J of this pixel
+#pragma unroll
+    for (int jj = 0; jj < kB; ++jj) {
+      const int k = j0 + jj;
+      y[jj] = (valid && k < d) ? (to_f(xp[k]) - mu_hi[k]) - mu_lo[k] : 0.f;
+    }
+    if (j0 > 0) {
+      if (tid == 0) {
+        const uint32_t aM = tc::smem_u32(Mt), aL = tc::smem_u32(Lt);
+        for (int kk = 0; kk < j0 / (2 * CK); ++kk) {
+          const uint32_t ko = (uint32_t)kk * 2u * kLBO;
+          const uint64_t da = tc::desc(aM + ko, kLBO, sboM);
+          const uint64_t db = tc::desc(aL + ko, kLBO, sboM);
+          if (FMT == 2) tc::mma_tf32(tmem, da, db, id, kk > 0);
+          else tc::mma_bf16(tmem, da, db, id, kk > 0);
+        }
+        tc::commit(&mbar);
+      }
+      const bool w_ok = tc::mbar_wait(&mbar, phase & 1u, kWaitLimit);
+      if (__syncthreads_or(!w_ok)) {
+        ok = false;
+        break;
+      }
+      ++phase;
+      tc::fence_after_sync();
+      uint32_t a0[16], a1[16];
+      tc::tmem_ld16(lane_base, a0);
+      tc::tmem_ld16(lane_base + 16, a1);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        y[jj] -= __uint_as_float(a0[jj]);
+        y[jj + 16] -= __uint_as_float(a1[jj]);
+      }
+    }
+    // y_J into Yt (row p)
+#pragma unroll
+    for (int k0 = 0; k0 < kB; k0 += CK)
+      *reinterpret_cast<uint4*>(Yt + off(p, k0, sboY)) = pack16<FMT>(y + k0);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t aY = tc::smem_u32(Yt);
+      const uint32_t aD = tc::smem_u32(Lt) + (uint32_t)(j0 / CK) * kLBO;
+      for (int kk = 0; kk < kB / (2 * CK); ++kk) {
+        const uint32_t ko = (uint32_t)kk * 2u * kLBO;
+        const uint64_t da = tc::desc(aY + ko, kLBO, sboY);
+        const uint64_t db = tc::desc(aD + ko, kLBO, sboM);
+        if (FMT == 2) tc::mma_tf32(tmem + 32, da, db, id, kk > 0);
+        else tc::mma_bf16(tmem + 32, da, db, id, kk > 0);
+      }
+      tc::commit(&mbar);
+    }
+    const bool w_ok = tc::mbar_wait(&mbar, phase & 1u, kWaitLimit);
+    if (__syncthreads_or(!w_ok)) {
+      ok = false;
+      break;
+    }
+    ++phase;
+    tc::fence_after_sync();
+    uint32_t m0[16], m1[16];
+    tc::tmem_ld16(lane_base + 32, m0);
+    tc::tmem_ld16(lane_base + 48, m1);
+    tc::tmem_ld_wait();
+    float mv[kB];
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      mv[jj] = __uint_as_float(m0[jj]);
+      mv[jj + 16] = __uint_as_float(m1[jj]);
+    }
+#pragma unroll
+    for (int jj = 0; jj < kB; ++jj)
+      if (j0 + jj < d) d2 = fmaf(mv[jj], mv[jj], d2);
+    // m_J replaces r_J in Mt (read by later blocks); zero beyond d
+#pragma unroll
+    for (int jj = 0; jj < kB; ++jj)
+      if (j0 + jj >= d) mv[jj] = 0.f;
+#pragma unroll
+    for (int k0 = 0; k0 < kB; k0 += CK)
+      *reinterpret_cast<uint4*>(Mt + off(p, j0 + k0, sboM)) = pack16<FMT>(mv + k0);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
+  if (!ok) {
+    // one more bounded wait for the MMAs still in flight before TMEM is released
+    tc::mbar_wait(&mbar, phase & 1u, kWaitLimit);
+    if (tid == 0) atomicMin(&err[kErrTimeout], (unsigned long long)(t0 + t));
+  }
+  if (valid) delta[(int64_t)t * W + i] = ok ? sqrtf(d2) : __int_as_float(0x7fc00000);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 64);
+}
+
+size_t smem_bytes(int d, int fmt) {
+  const int E = fmt == 2 ? 4 : 2;
+  const int dK = (d + kB - 1) / kB * kB;
+  return (size_t)(kPix * dK + kB * dK + kPix * kB) * E;
+}
+
+}  // namespace
+
+cudaError_t configure_solve_tc_kernels() {
+  cudaError_t e = cudaSuccess;
+  const int m2 = (int)smem_bytes(kMaxDim, 2), m1 = (int)smem_bytes(kMaxDim, 1);
+#define ERX_CFG(K, M) \
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, M)
+  ERX_CFG((solve_tc_kernel<uint16_t, 2>), m2);
+  ERX_CFG((solve_tc_kernel<float, 2>), m2);
+  ERX_CFG((solve_tc_kernel<double, 2>), m2);
+  ERX_CFG((solve_tc_kernel<uint16_t, 1>), m1);
+  ERX_CFG((solve_tc_kernel<float, 1>), m1);
+  ERX_CFG((solve_tc_kernel<double, 1>), m1);
+#undef ERX_CFG
+  return e;
+}
+
+void launch_solve_tc(int fmt, int in_type, const void* x, int64_t line_stride, int ps, int W,
+                     int d, int T, const double* mu_t, const float* Lf32, float* delta,
+                     unsigned long long* err, int64_t t0, cudaStream_t st) {
+  dim3 grid((W + kPix - 1) / kPix, T);
+  const size_t sm = smem_bytes(d, fmt);
+#define ERX_L(IT, F)                                                                           \
+  solve_tc_kernel<IT, F><<<grid, kPix, sm, st>>>((const IT*)x, line_stride, ps, W, d, mu_t, \
+                                                 Lf32, delta, err, t0)
+  if (fmt == 2) {
+    if (in_type == 0) ERX_L(uint16_t, 2);
+    else if (in_type == 1) ERX_L(float, 2);
+    else ERX_L(double, 2);
+  } else {
+    if (in_type == 0) ERX_L(uint16_t, 1);
+    else if (in_type == 1) ERX_L(float, 1);
+    else ERX_L(double, 1);
+  }
+#undef ERX_L
+}
+
+}  // namespace erx

@@ -15,7 +15,7 @@ from tests.gpu_util import dn_err, need_gpu, rel_err, run_gpu, torch
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-9, "fp32": 1e-4}
+TOL = {"fp64": 1e-9, "fp32": 1e-4, "tf32": 5e-3, "bf16": 4e-2}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -234,3 +234,25 @@ def test_tensor_core_stats_range_check():
         det.sync()
     assert ei.value.status == ERX_ERANGE and ei.value.bad_line == 3
     assert det.profile_read()["stats_tc"][2] > 0
+
+
+TC_CASES = [
+    ("c2_u16", lambda: synth.gen_lines(synth.dn_c2(width=300, bands=108), 0, 12), {"in_bits": 12}),
+    ("c1_f32", lambda: synth.gen_lines(synth.reflectance_c1(width=200, bands=64), 0, 10), {}),
+    ("c3_k1e3_d224", lambda: synth.gen_lines(synth.cov_c3(1e3, width=260, bands=224), 0, 3), {}),
+    ("ragged_d33", lambda: synth.gen_lines(synth.reflectance_c1(width=129, bands=33), 0, 6), {}),
+    ("srp5", lambda: synth.gen_lines(synth.dn_c2(width=140, bands=108), 0, 8),
+     {"proj": "srp", "proj_dim": 5, "seed": 3}),
+]
+
+
+@pytest.mark.parametrize("form", ["tf32", "bf16"])
+@pytest.mark.parametrize("name,make,kw", TC_CASES, ids=[c[0] for c in TC_CASES])
+def test_tensor_core_forms(name, make, kw, form):
+    cube = make()
+    got, det = run_gpu(cube, form=form, warmup=2, threshold=3.0, **kw)
+    ref = oracle.run_cube(cube, warmup=2, **_oracle_kw(kw, cube))
+    e = rel_err(got["delta"], ref["delta"])
+    print(f"{name} {form}: max rel delta err {e:.3e}")
+    assert e <= TOL[form], f"{name} {form}: {e}"
+    assert det.profile_read()["solve_tc"][2] > 0
