@@ -34,7 +34,7 @@ IMAD_PEAK_GOPS = 152 * 64 * 2.070        # 32-bit integer multiply-add, per seco
 
 
 def _gen_worker(args):
-    name, shape, t0, n, cfg_kw = args
+    name, shape, dtype, t0, n, kind, cfg_kw = args
     from multiprocessing import shared_memory
 
     import numpy as np
@@ -42,32 +42,38 @@ def _gen_worker(args):
     import synth
     shm = shared_memory.SharedMemory(name=name)
     try:
-        arr = np.ndarray(shape, dtype=np.uint16, buffer=shm.buf)
-        synth.gen_lines(synth.dn_c2(**cfg_kw), t0, n, out=arr[t0:t0 + n])
+        arr = np.ndarray(shape, dtype=dtype, buffer=shm.buf)
+        cfg = synth.dn_c2(**cfg_kw) if kind == "c2" else synth.cov_c3(**cfg_kw)
+        synth.gen_lines(cfg, t0, n, out=arr[t0:t0 + n])
     finally:
         shm.close()
     return n
 
 
-def make_cube(n_lines: int, seed: int = 0, workers: int | None = None):
-    """The seeded C2-style cube, generated in parallel by spawned processes."""
+def make_cube(n_lines: int, seed: int = 0, workers: int | None = None, kind: str = "c2",
+              width: int = WIDTH, bands: int = BANDS, kappa: float = 1e3):
+    """A seeded synthetic cube (C2-style u16 DN, or C3-style f32 with condition
+    number kappa), generated in parallel by spawned processes."""
     import multiprocessing as mp
     from multiprocessing import shared_memory
 
     import numpy as np
-    shape = (n_lines, WIDTH, BANDS)
-    nbytes = int(np.prod(shape)) * 2
+    dtype = np.uint16 if kind == "c2" else np.float32
+    shape = (n_lines, width, bands)
+    nbytes = int(np.prod(shape)) * np.dtype(dtype).itemsize
     workers = workers or min(16, len(os.sched_getaffinity(0)))
+    kw = {"seed": seed, "width": width, "bands": bands}
+    if kind != "c2":
+        kw["kappa"] = kappa
     shm = shared_memory.SharedMemory(create=True, size=nbytes)
     try:
         step = max(1, math.ceil(n_lines / (workers * 4)))
-        jobs = [(shm.name, shape, t0, min(step, n_lines - t0),
-                 {"seed": seed, "width": WIDTH, "bands": BANDS})
+        jobs = [(shm.name, shape, dtype, t0, min(step, n_lines - t0), kind, kw)
                 for t0 in range(0, n_lines, step)]
         ctx = mp.get_context("spawn")
         with ctx.Pool(workers) as pool:
             pool.map(_gen_worker, jobs)
-        out = np.ndarray(shape, dtype=np.uint16, buffer=shm.buf).copy()
+        out = np.ndarray(shape, dtype=dtype, buffer=shm.buf).copy()
     finally:
         shm.close()
         shm.unlink()
@@ -175,6 +181,36 @@ def run_reference(args):
                              "sample": cb["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def time_form(make, x, kw, dev, stream, reps: int = 2):
+    """lines/s of one detector configuration over the resident cube x (reset + push
+    per step, one warm-up step), plus its per-kernel split."""
+    import torch
+    n, p, _ = x.shape
+    det = make(**kw)
+    sdt = torch.float64 if kw.get("form", "fp64") == "fp64" else torch.float32
+    out = (torch.empty((n, p), dtype=sdt, device=dev), torch.empty((n, p), dtype=sdt, device=dev),
+           torch.empty((n, p), dtype=torch.uint8, device=dev),
+           torch.empty((n,), dtype=torch.uint8, device=dev))
+    det.reset()
+    det.push(x, out)
+    det.sync()
+    det.profile(True)
+    det.profile_read(reset=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        det.reset()
+        det.push(x, out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    det.sync()
+    prof = det.profile_read(reset=True)
+    det.close()
+    ms = a.elapsed_time(b) / reps
+    return {"lines_per_s": n / (ms / 1000.0), "ms_per_step": ms,
+            "kernels_ms": {k: round(v[0] / reps, 3) for k, v in prof.items() if v[2]}}
 
 
 def run_ours(args):
@@ -301,25 +337,28 @@ def run_ours(args):
 
         # other forms on the same cube, same step definition
         forms = {}
-        for name, kw in (("fp32", {"form": "fp32"}),
+        for name, kw in (("fp32", {"form": "fp32"}), ("tf32", {"form": "tf32"}),
+                         ("bf16", {"form": "bf16"}),
                          ("fp64_srp5", {"form": "fp64", "proj": "srp", "proj_dim": 5}),
                          ("fp32_srp5", {"form": "fp32", "proj": "srp", "proj_dim": 5})):
-            dd = detector(**kw)
-            sdt = torch.float64 if kw["form"] == "fp64" else torch.float32
-            oo = (torch.empty((LINES, WIDTH), dtype=sdt, device=dev),
-                  torch.empty((LINES, WIDTH), dtype=sdt, device=dev), out[2], out[3])
-            step(dd, oo)
-            dd.sync()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(2):
-                step(dd, oo)
-            b.record(stream)
-            torch.cuda.synchronize()
-            dd.sync()
-            forms[name] = {"lines_per_s": LINES * 2 / (a.elapsed_time(b) / 1000.0)}
-            dd.close()
-        result["forms"] = forms
+            forms[name] = time_form(lambda **k: Detector(BANDS, WIDTH, in_dtype="u16",
+                                                         in_bits=BITS, stream=stream, **k),
+                                    x, kw, dev, stream)
+        result["forms_108"] = forms
+
+        # 224 bands (AVIRIS raw band count): 2000 lines x 1024 px f32, kappa 1e3
+        n224 = 2000
+        cube224 = make_cube(n224, seed=1, kind="c3", width=1024, bands=224, kappa=1e3)
+        x224 = torch.from_numpy(cube224).to(dev)
+        del cube224
+        forms224 = {}
+        for name in ("fp64", "fp32", "tf32", "bf16"):
+            forms224[name] = time_form(lambda **k: Detector(224, 1024, in_dtype="f32",
+                                                            stream=stream, **k),
+                                       x224, {"form": name}, dev, stream)
+        result["forms_224"] = {"workload": f"{n224} lines x 1024 px x 224 bands f32, "
+                                           "Gaussian background, kappa 1e3", **forms224}
+        del x224
 
         # end to end through the public host-buffer call: pinned input, results to host
         xh = torch.from_numpy(cube.view(np.int16)).pin_memory()

@@ -47,6 +47,7 @@ struct erx_ctx {
   int* rows = nullptr;
   double* vals = nullptr;
   unsigned long long* err = nullptr;
+  double* ema_scratch = nullptr;
   // host staging for erx_push_lines_host
   void* h_in[2] = {nullptr, nullptr};
   void* d_in[2] = {nullptr, nullptr};
@@ -221,7 +222,7 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
     KernelScope ks(c, ERX_K_EMA);
     launch_ema_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W,
                   c->cfg.momentum, c->t, c->cfg.order, c->mu_state, c->K_state, c->mu_t, c->K_t,
-                  st);
+                  c->ema_scratch, st);
   }
   {
     KernelScope ks(c, ERX_K_CHOL);
@@ -358,6 +359,7 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
     ERX_A(S2f, (size_t)T * d * d);
   }
   ERX_A(err, kErrSlots);
+  if (ema_scratch_doubles(d, T) > 0) ERX_A(ema_scratch, ema_scratch_doubles(d, T));
 #undef ERX_A
   if (s == ERX_OK && !c->w_host.empty()) {
     std::vector<int> cp(d + 1, 0), rw;

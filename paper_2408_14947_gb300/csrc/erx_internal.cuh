@@ -55,11 +55,14 @@ void launch_stats_fp(int in_type, bool fp64, const void* x, int64_t line_stride,
                      int d, int T, const double* shift, double* S2f, cudaStream_t st);
 
 // EMA scan over the T lines of a block: turns line statistics into the
-// statistics each line is scored with and advances the state.
+// statistics each line is scored with and advances the state.  `scratch`
+// holds ema_scratch_doubles(d, T) doubles (NULL: sequential scan).
+size_t ema_scratch_doubles(int d, int T);
 void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      const double* mu_hat, const double* shift, const double* S2f, int T, int d,
                      int W, double alpha, int64_t t0, int order, double* mu_state,
-                     double* K_state, double* mu_t, double* K_t, cudaStream_t st);
+                     double* K_state, double* mu_t, double* K_t, double* scratch,
+                     cudaStream_t st);
 
 // Cholesky of K_t + ridge I, diagonal blocks inverted, one CTA per line.
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Linv, float* Linv32,

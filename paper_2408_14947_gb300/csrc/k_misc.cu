@@ -12,96 +12,141 @@ __device__ __forceinline__ double to_d(T v) { return (double)v; }
 
 // ---- S3: exponential moving averages (Sec. III-C) ------------------------
 //
-// One thread per state element (the P entries of the packed lower triangle
-// of K, then the d entries of mu), walking the T lines of the block in order:
-//   line statistics -> (t == 0 ? init : (1-a) state + a stats) -> state.
-// The recursion is a d^2-wide elementwise scan; the values a line is scored
-// with (after the update, or before it for score-then-update) are written
-// to mu_t / K_t.
-// The per-line loads do not depend on the recursion, so they are issued
-// kEmaBatch lines ahead of it to keep enough memory requests in flight; the
-// recursion itself stays strictly sequential, so results do not depend on how
-// lines are grouped into blocks.
-constexpr int kEmaBatch = 8;
+// Per state element (the P entries of the packed lower triangle of K, then the
+// d entries of mu) the recursion s_t = (1-a) s_{t-1} + a khat_t runs over the
+// T lines of a block; line 0 of the stream sets s_0 = khat_0.  The values a
+// line is scored with (after the update, or before it for score-then-update)
+// go to mu_t / K_t.
+//
+// The recursion is linear, so a block is cut into chunks of kEmaChunk lines:
+//   pass A  each (element, chunk) runs the recursion from 0 over its chunk;
+//   pass B  each element chains the chunk results sequentially:
+//           s_end = (1-a)^len s_start + u_chunk  (or u_chunk if the chunk holds line 0);
+//   pass C  each (element, chunk) reruns its chunk from the carried-in state
+//           and writes the per-line values.
+// Within a chunk the arithmetic is the sequential recursion; across chunk
+// boundaries the carried value is formed in closed form, which differs from
+// the sequential recursion only by rounding.  Blocks of at most kEmaChunk lines
+// run pass C alone on the state (purely sequential).
+constexpr int kEmaChunk = 32;
 
-__global__ void __launch_bounds__(128) ema_scan_kernel(
-    bool int_stats, const uint64_t* __restrict__ S1i, const uint64_t* __restrict__ S2i,
-    const double* __restrict__ mu_hat, const double* __restrict__ shift,
-    const double* __restrict__ S2f, int T, int d, int W, double alpha, int64_t t0, int order,
-    double* __restrict__ mu_state, double* __restrict__ K_state, double* __restrict__ mu_t,
-    double* __restrict__ K_t) {
-  const int64_t P = packed_size(d);
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= P + d) return;
-  const double beta = 1.0 - alpha;
-  const double Wd = (double)W;
-  const double inv_pp = 1.0 / (Wd * (Wd - 1.0));
-  const double inv_p1 = 1.0 / (Wd - 1.0);
-  const int64_t dd = (int64_t)d * d;
-  if (q < P) {
-    int a = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
-    while ((int64_t)a * (a + 1) / 2 > q) --a;
-    while ((int64_t)(a + 1) * (a + 2) / 2 <= q) ++a;
-    const int b = (int)(q - (int64_t)a * (a + 1) / 2);
-    const int64_t ab = (int64_t)a * d + b;
-    double s = K_state[q];
-    for (int t0b = 0; t0b < T; t0b += kEmaBatch) {
-      double kh[kEmaBatch];
-      const int nb = min(kEmaBatch, T - t0b);
-      if (int_stats) {
-        int64_t s1a[kEmaBatch], s1b[kEmaBatch], s2[kEmaBatch];
-#pragma unroll
-        for (int u = 0; u < kEmaBatch; ++u) {
-          if (u < nb) {
-            const int64_t t = t0b + u;
-            s1a[u] = (int64_t)__ldg(S1i + t * d + a);
-            s1b[u] = (int64_t)__ldg(S1i + t * d + b);
-            s2[u] = (int64_t)__ldg(S2i + t * dd + ab);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kEmaBatch; ++u)
-          if (u < nb) kh[u] = (double)((int64_t)W * s2[u] - s1a[u] * s1b[u]) * inv_pp;
-      } else {
-        double ea[kEmaBatch], eb[kEmaBatch], sv[kEmaBatch];
-#pragma unroll
-        for (int u = 0; u < kEmaBatch; ++u) {
-          if (u < nb) {
-            const int64_t t = t0b + u;
-            ea[u] = __ldg(mu_hat + t * d + a) - __ldg(shift + t * d + a);
-            eb[u] = __ldg(mu_hat + t * d + b) - __ldg(shift + t * d + b);
-            sv[u] = __ldg(S2f + t * dd + ab);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kEmaBatch; ++u)
-          if (u < nb) kh[u] = (sv[u] - Wd * ea[u] * eb[u]) * inv_p1;
-      }
-#pragma unroll
-      for (int u = 0; u < kEmaBatch; ++u) {
-        if (u < nb) {
-          const int64_t t = t0b + u;
-          const bool first = (t0 + t == 0);
-          const double post = first ? kh[u] : beta * s + alpha * kh[u];
-          K_t[t * P + q] = (order == 0 || first) ? post : s;
-          s = post;
-        }
-      }
-    }
-    K_state[q] = s;
-  } else {
-    const int a = (int)(q - P);
-    double s = mu_state[a];
-    for (int t = 0; t < T; ++t) {
-      const double mh = int_stats ? (double)__ldg(S1i + (int64_t)t * d + a) / Wd
-                                  : __ldg(mu_hat + (int64_t)t * d + a);
-      const bool first = (t0 + t == 0);
-      const double post = first ? mh : beta * s + alpha * mh;
-      mu_t[(int64_t)t * d + a] = (order == 0 || first) ? post : s;
-      s = post;
-    }
-    mu_state[a] = s;
+struct EmaSrc {
+  bool int_stats;
+  const uint64_t* S1i;
+  const uint64_t* S2i;
+  const double* mu_hat;
+  const double* shift;
+  const double* S2f;
+  int d, W;
+  int64_t P;
+};
+
+// line statistic of element (a, b) (b < 0: the mean of band a) at line t of the block
+__device__ __forceinline__ double ema_stat(const EmaSrc& s, int64_t t, int a, int b) {
+  const double Wd = (double)s.W;
+  if (b < 0) {
+    return s.int_stats ? (double)__ldg(s.S1i + t * s.d + a) / Wd : __ldg(s.mu_hat + t * s.d + a);
   }
+  const int64_t dd = (int64_t)s.d * s.d;
+  const int64_t ab = (int64_t)a * s.d + b;
+  if (s.int_stats) {
+    const int64_t s1a = (int64_t)__ldg(s.S1i + t * s.d + a);
+    const int64_t s1b = (int64_t)__ldg(s.S1i + t * s.d + b);
+    const int64_t s2 = (int64_t)__ldg(s.S2i + t * dd + ab);
+    return (double)((int64_t)s.W * s2 - s1a * s1b) * (1.0 / (Wd * (Wd - 1.0)));
+  }
+  const double ea = __ldg(s.mu_hat + t * s.d + a) - __ldg(s.shift + t * s.d + a);
+  const double eb = __ldg(s.mu_hat + t * s.d + b) - __ldg(s.shift + t * s.d + b);
+  return (__ldg(s.S2f + t * dd + ab) - Wd * ea * eb) * (1.0 / (Wd - 1.0));
+}
+
+__device__ __forceinline__ void ema_element(const EmaSrc& s, int64_t q, int& a, int& b) {
+  if (q >= s.P) {
+    a = (int)(q - s.P);
+    b = -1;
+    return;
+  }
+  int r = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while ((int64_t)r * (r + 1) / 2 > q) --r;
+  while ((int64_t)(r + 1) * (r + 2) / 2 <= q) ++r;
+  a = r;
+  b = (int)(q - (int64_t)r * (r + 1) / 2);
+}
+
+// pass A: chunk-local recursion from zero; E[g][q] = its final value
+__global__ void __launch_bounds__(128) ema_pass_a(EmaSrc s, int T, double alpha, int64_t t0,
+                                                  double* __restrict__ E) {
+  const int64_t n = s.P + s.d;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int g = blockIdx.y;
+  int a, b;
+  ema_element(s, q, a, b);
+  const double beta = 1.0 - alpha;
+  const int tb = g * kEmaChunk, te = min(T, tb + kEmaChunk);
+  double u = 0.0;
+  for (int t = tb; t < te; ++t) {
+    const double kh = ema_stat(s, t, a, b);
+    u = (t0 + t == 0) ? kh : beta * u + alpha * kh;
+  }
+  E[(int64_t)g * n + q] = u;
+}
+
+// pass B: chain chunk results; Cin[g][q] = state entering chunk g
+__global__ void __launch_bounds__(128) ema_pass_b(int64_t n, int T, int G, double alpha,
+                                                  int64_t t0, const double* __restrict__ E,
+                                                  double* __restrict__ Cin,
+                                                  double* __restrict__ Kst,
+                                                  double* __restrict__ must, int64_t P) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const double beta = 1.0 - alpha;
+  double* st = q < P ? Kst + q : must + (q - P);
+  double s = *st;
+  double bp = 1.0;                       // (1-a)^kEmaChunk
+  for (int i = 0; i < kEmaChunk; ++i) bp *= beta;
+  for (int g = 0; g < G; ++g) {
+    Cin[(int64_t)g * n + q] = s;
+    const int tb = g * kEmaChunk, te = min(T, tb + kEmaChunk);
+    const bool has_init = (t0 + tb <= 0) && (t0 + te > 0);
+    double w = bp;
+    if (te - tb != kEmaChunk) {
+      w = 1.0;
+      for (int i = tb; i < te; ++i) w *= beta;
+    }
+    const double e = E[(int64_t)g * n + q];
+    s = has_init ? e : w * s + e;
+  }
+  *st = s;
+}
+
+// pass C: rerun each chunk from its carried-in state, write the per-line values
+__global__ void __launch_bounds__(128) ema_pass_c(EmaSrc s, int T, double alpha, int64_t t0,
+                                                  int order, const double* __restrict__ Cin,
+                                                  double* __restrict__ Kst,
+                                                  double* __restrict__ must,
+                                                  double* __restrict__ mu_t,
+                                                  double* __restrict__ K_t) {
+  const int64_t n = s.P + s.d;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int g = blockIdx.y;
+  int a, b;
+  ema_element(s, q, a, b);
+  const double beta = 1.0 - alpha;
+  double* st = q < s.P ? Kst + q : must + (q - s.P);
+  double v = Cin ? Cin[(int64_t)g * n + q] : *st;
+  const int tb = g * kEmaChunk, te = Cin ? min(T, tb + kEmaChunk) : T;
+  for (int t = tb; t < te; ++t) {
+    const double kh = ema_stat(s, t, a, b);
+    const bool first = (t0 + t == 0);
+    const double post = first ? kh : beta * v + alpha * kh;
+    const double out = (order == 0 || first) ? post : v;
+    if (b < 0) mu_t[(int64_t)t * s.d + a] = out;
+    else K_t[(int64_t)t * s.P + q] = out;
+    v = post;
+  }
+  if (!Cin) *st = v;
 }
 
 // ---- S6: line-by-line normalisation (Sec. III-E) -------------------------
@@ -168,11 +213,28 @@ __global__ void __launch_bounds__(256) project_kernel(const InT* __restrict__ X,
 void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      const double* mu_hat, const double* shift, const double* S2f, int T, int d,
                      int W, double alpha, int64_t t0, int order, double* mu_state,
-                     double* K_state, double* mu_t, double* K_t, cudaStream_t st) {
-  const int64_t n = packed_size(d) + d;
-  const int blocks = (int)((n + 127) / 128);
-  ema_scan_kernel<<<blocks, 128, 0, st>>>(int_stats, S1i, S2i, mu_hat, shift, S2f, T, d, W,
-                                          alpha, t0, order, mu_state, K_state, mu_t, K_t);
+                     double* K_state, double* mu_t, double* K_t, double* scratch,
+                     cudaStream_t st) {
+  EmaSrc s{int_stats, S1i, S2i, mu_hat, shift, S2f, d, W, packed_size(d)};
+  const int64_t n = s.P + d;
+  const unsigned bx = (unsigned)((n + 127) / 128);
+  const int G = (T + kEmaChunk - 1) / kEmaChunk;
+  if (G <= 1 || !scratch) {
+    ema_pass_c<<<dim3(bx, 1), 128, 0, st>>>(s, T, alpha, t0, order, nullptr, K_state, mu_state,
+                                           mu_t, K_t);
+    return;
+  }
+  double* E = scratch;
+  double* Cin = scratch + (int64_t)G * n;
+  ema_pass_a<<<dim3(bx, G), 128, 0, st>>>(s, T, alpha, t0, E);
+  ema_pass_b<<<bx, 128, 0, st>>>(n, T, G, alpha, t0, E, Cin, K_state, mu_state, s.P);
+  ema_pass_c<<<dim3(bx, G), 128, 0, st>>>(s, T, alpha, t0, order, Cin, K_state, mu_state, mu_t,
+                                         K_t);
+}
+
+size_t ema_scratch_doubles(int d, int T) {
+  const int G = (T + kEmaChunk - 1) / kEmaChunk;
+  return G <= 1 ? 0 : (size_t)2 * G * (size_t)(packed_size(d) + d);
 }
 
 void launch_normalise(bool fp64, const void* delta, int W, int T, double threshold, int64_t t0,

@@ -203,6 +203,37 @@ __global__ void __launch_bounds__(256) stats_fp_kernel(const InT* __restrict__ X
   }
 }
 
+// Small d (projected lines, d <= 16): one CTA per line, one thread per entry
+// (a, b) of the lower triangle, walking all pixels; four independent partial
+// sums per thread.  The 64 x 64 tiles above would be nearly all padding here.
+constexpr int kSmallD = 16;
+
+template <typename InT, typename AccT>
+__global__ void __launch_bounds__(256) stats_small_kernel(const InT* __restrict__ X,
+                                                          int64_t line_stride, int ps, int W,
+                                                          int d, const double* __restrict__ shift,
+                                                          double* __restrict__ S2f) {
+  const int t = blockIdx.x;
+  const int P = d * (d + 1) / 2;
+  const int q = threadIdx.x;
+  if (q >= P) return;
+  int a = 0;
+  while ((a + 1) * (a + 2) / 2 <= q) ++a;
+  const int b = q - a * (a + 1) / 2;
+  const InT* x = X + (int64_t)t * line_stride;
+  const AccT ca = (AccT)shift[(int64_t)t * d + a], cb = (AccT)shift[(int64_t)t * d + b];
+  AccT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  int i = 0;
+  for (; i + 4 <= W; i += 4) {
+    s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
+    s1 = fma((AccT)x[(int64_t)(i + 1) * ps + a] - ca, (AccT)x[(int64_t)(i + 1) * ps + b] - cb, s1);
+    s2 = fma((AccT)x[(int64_t)(i + 2) * ps + a] - ca, (AccT)x[(int64_t)(i + 2) * ps + b] - cb, s2);
+    s3 = fma((AccT)x[(int64_t)(i + 3) * ps + a] - ca, (AccT)x[(int64_t)(i + 3) * ps + b] - cb, s3);
+  }
+  for (; i < W; ++i) s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
+  S2f[(int64_t)t * d * d + (int64_t)a * d + b] = (double)((s0 + s1) + (s2 + s3));
+}
+
 int n_pairs(int d) {
   const int nb = (d + SB - 1) / SB;
   return nb * (nb + 1) / 2;
@@ -236,6 +267,21 @@ void launch_mean(int in_type, const void* x, int64_t line_stride, int ps, int W,
 
 void launch_stats_fp(int in_type, bool fp64, const void* x, int64_t line_stride, int ps, int W,
                      int d, int T, const double* shift, double* S2f, cudaStream_t st) {
+  if (d <= kSmallD) {
+#define ERX_SMALL(IT, AT) \
+  stats_small_kernel<IT, AT><<<T, 256, 0, st>>>((const IT*)x, line_stride, ps, W, d, shift, S2f)
+    if (fp64) {
+      if (in_type == 0) ERX_SMALL(uint16_t, double);
+      else if (in_type == 1) ERX_SMALL(float, double);
+      else ERX_SMALL(double, double);
+    } else {
+      if (in_type == 0) ERX_SMALL(uint16_t, float);
+      else if (in_type == 1) ERX_SMALL(float, float);
+      else ERX_SMALL(double, float);
+    }
+#undef ERX_SMALL
+    return;
+  }
   dim3 grid(n_pairs(d), T);
 #define ERX_SFP(IT, AT) \
   stats_fp_kernel<IT, AT><<<grid, 256, 0, st>>>((const IT*)x, line_stride, ps, W, d, shift, S2f)

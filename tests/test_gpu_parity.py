@@ -256,3 +256,21 @@ def test_tensor_core_forms(name, make, kw, form):
     print(f"{name} {form}: max rel delta err {e:.3e}")
     assert e <= TOL[form], f"{name} {form}: {e}"
     assert det.profile_read()["solve_tc"][2] > 0
+
+
+def test_long_block_chunked_ema_matches_line_by_line():
+    """Blocks longer than one EMA chunk (32 lines) chain chunk results in closed
+    form; they agree with line-by-line pushes to rounding and with the oracle."""
+    cube = synth.gen_lines(synth.reflectance_c1(width=70, bands=12), 0, 150)
+    a, da = run_gpu(cube, block_lines=150)
+    b, db = run_gpu(cube, push_sizes=[1] * 150)
+    assert rel_err(a["delta"], b["delta"]) < 1e-12
+    ref = oracle.run_cube(cube)
+    assert rel_err(a["delta"], ref["delta"]) < 1e-9
+    ta, ma, ka = da.state()
+    tb, mb, kb = db.state()
+    assert ta == tb == 150 and rel_err(ka, kb) < 1e-12
+    for order in ("score_then_update",):
+        c, _ = run_gpu(cube, block_lines=150, order=order)
+        refc = oracle.run_cube(cube, order=order)
+        assert rel_err(c["delta"], refc["delta"]) < 1e-9
