@@ -187,6 +187,58 @@ erx_status erx_push_lines_static(const erx_config* cfg, void* cuda_stream, doubl
                                  int64_t n_lines, int64_t line_stride_bytes, void* delta_dev,
                                  void* delta_norm_dev, uint8_t* mask_dev, uint8_t* detecting_dev);
 
+/* ---- Batched form: many independent streams, one line each per step ------
+ *
+ * A batch holds n independent ERX streams, each with its own width, band
+ * count and parameters, and advances every one of them by one line per step.
+ * A step is six phase kernels launched once for the whole batch (line means,
+ * centred scatter, EMA update, FP64 factor, scores, normalisation) with work
+ * lists mapping CTAs to (stream, tile); it is captured once in a CUDA graph and
+ * replayed.  Limits: float32 input, no projection, bands <= 224, one form for
+ * the whole batch. */
+typedef struct erx_batch erx_batch;
+
+/* Create a batch of n streams from cfgs[0..n-1] (all with the same form and
+ * in_dtype ERX_F32, proj ERX_PROJ_NONE).  Allocates per-stream state, one
+ * input line and one output line per stream on the current device. */
+erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream,
+                            erx_batch** out);
+
+/* The batch-owned device buffers of stream i: the input line (width x bands
+ * float, written by the caller or by erx_batch_push) and the scores of the
+ * last step (delta and delta_N: double for ERX_FORM_FP64, float otherwise;
+ * mask: width bytes; detecting: 1 byte).  Any out pointer may be NULL. */
+erx_status erx_batch_buffers(erx_batch* b, int32_t i, float** line_dev, void** delta_dev,
+                             void** delta_norm_dev, uint8_t** mask_dev, uint8_t** detecting_dev);
+
+/* One step: every stream takes one line.  lines_dev: NULL, or a host array of
+ * n device pointers (an entry may be NULL) whose lines are first copied into
+ * the streams' input buffers by one gather kernel.  Asynchronous. */
+erx_status erx_batch_push(erx_batch* b, const float* const* lines_dev);
+
+/* Wait for the batch's stream; report ERX_ENOTPD / ERX_ETIMEOUT raised since
+ * the last call, with the index of the first offending stream. */
+erx_status erx_batch_sync(erx_batch* b, int64_t* bad_stream);
+
+/* State of stream i (host pointers, as erx_get_state).  Synchronises. */
+erx_status erx_batch_get_state(erx_batch* b, int32_t i, int64_t* t, double* mu, double* K);
+
+/* Score kernel chosen for stream i: 0 FP64, 1 FP32 SIMT, 2 TF32 MMA, 3 BF16 MMA. */
+erx_status erx_batch_route(const erx_batch* b, int32_t i, int32_t* route);
+
+/* Autotuner: for every band count in the batch, time each score kernel the
+ * form allows (TF32 form: TF32 MMA or FP32 SIMT; BF16 form: BF16 MMA or FP32
+ * SIMT; FP64 and FP32 forms have one) over that count's streams, `reps` runs
+ * each with CUDA events, keep the fastest and re-capture the step.  Needs one
+ * step pushed before (ERX_ESTATE otherwise); overwrites the last step's scores,
+ * not the state.  cache_path (may be NULL): a JSON object of earlier choices
+ * keyed by device, form, band count and width bucket; hits skip the timing and
+ * new choices are appended. */
+erx_status erx_batch_tune(erx_batch* b, int32_t reps, const char* cache_path);
+
+/* Release the batch.  NULL is a no-op. */
+erx_status erx_batch_destroy(erx_batch* b);
+
 /* Kernels of the line step, for erx_profile_read. */
 enum {
   ERX_K_PROJECT = 0,    /* S1 sparse projection */

@@ -1,0 +1,575 @@
+// Batched form: many independent line streams, with their own widths and band
+// counts, each advanced by one line per step.
+//
+// A step is six phase kernels over the whole batch (line means, centred
+// scatter, EMA update, FP64 factor, scores, normalisation), each launched once
+// for all streams with a work list that maps its CTAs to (stream, tile); the
+// per-stream parameters, including the line count, live in a device table, so
+// the step is captured once in a CUDA graph and replayed.  The score kernel of
+// each band count is chosen by an autotuner that times the candidate kernels
+// on the batch itself.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/erx.h"
+#include "erx_batch.cuh"
+#include "erx_internal.cuh"
+
+using namespace erx;
+
+namespace erx {
+int batch_stats_tiles(int d);
+int batch_solve_tiles(int route, int W);
+void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, int n_items,
+                             int dmax, cudaStream_t st);
+void launch_batch_solve_tc(int fmt, const BStream* S, const BItem* items, int n_items, int dmax,
+                           unsigned long long* err, cudaStream_t st);
+}  // namespace erx
+
+namespace {
+
+__global__ void gather_kernel(const float* const* __restrict__ src, const BStream* __restrict__ S) {
+  const BStream& s = S[blockIdx.y];
+  const float* p = src[blockIdx.y];
+  if (!p) return;
+  float* dst = const_cast<float*>(s.x);
+  const int64_t n = (int64_t)s.W * s.d;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = p[i];
+}
+
+}  // namespace
+
+struct erx_batch {
+  int n = 0;
+  int form = ERX_FORM_FP64;
+  int dmax = 1;
+  cudaStream_t stream = nullptr;
+  bool failed = false;
+  std::vector<erx_config> cfg;
+  std::vector<BStream> host;      // host mirror of the table (pointers, shapes, routes)
+  BStream* table = nullptr;       // device table
+  std::vector<void*> allocs;
+  // work lists
+  BItem* stats_items = nullptr;
+  int n_stats = 0;
+  BItem* ema_items = nullptr;
+  int n_ema = 0;
+  BItem* solve_items[4] = {nullptr, nullptr, nullptr, nullptr};
+  int n_solve[4] = {0, 0, 0, 0};
+  unsigned long long* err = nullptr;
+  // graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // push staging
+  const float** ptr_host[2] = {nullptr, nullptr};
+  const float** ptr_dev = nullptr;
+  cudaEvent_t ptr_ev[2] = {nullptr, nullptr};
+  int ptr_slot = 0;
+};
+
+namespace {
+
+template <typename T>
+erx_status balloc(erx_batch* b, T** p, size_t n) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, std::max<size_t>(1, n) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return ERX_ENOMEM;
+  }
+  b->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return ERX_OK;
+}
+
+void bfree(erx_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (void* p : b->allocs) cudaFree(p);
+  for (int i = 0; i < 2; ++i) {
+    if (b->ptr_host[i]) cudaFreeHost(b->ptr_host[i]);
+    if (b->ptr_ev[i]) cudaEventDestroy(b->ptr_ev[i]);
+  }
+  b->allocs.clear();
+}
+
+bool route_allowed(int form, int route) {
+  switch (form) {
+    case ERX_FORM_FP64: return route == 0;
+    case ERX_FORM_FP32: return route == 1;
+    case ERX_FORM_TF32: return route == 1 || route == 2;
+    case ERX_FORM_BF16: return route == 1 || route == 3;
+  }
+  return false;
+}
+
+int native_route(int form) {
+  return form == ERX_FORM_FP64 ? 0 : form == ERX_FORM_FP32 ? 1 : form == ERX_FORM_TF32 ? 2 : 3;
+}
+
+// (Re)build the score-kernel work lists from the routes in the host table.
+erx_status build_solve_items(erx_batch* b) {
+  for (int r = 0; r < 4; ++r) {
+    std::vector<BItem> items;
+    for (int s = 0; s < b->n; ++s)
+      if (b->host[s].route == r)
+        for (int k = 0; k < batch_solve_tiles(r, b->host[s].W); ++k) items.push_back({s, k});
+    // largest band counts first: their tiles take longest
+    std::stable_sort(items.begin(), items.end(), [&](const BItem& x, const BItem& y) {
+      return b->host[x.s].d > b->host[y.s].d;
+    });
+    b->n_solve[r] = (int)items.size();
+    if (!b->solve_items[r]) {
+      // capacity: every stream's tiles for this route
+      size_t cap = 0;
+      for (int s = 0; s < b->n; ++s) cap += (size_t)batch_solve_tiles(r, b->host[s].W);
+      erx_status st = balloc(b, &b->solve_items[r], cap);
+      if (st != ERX_OK) return st;
+    }
+    if (!items.empty() && cudaMemcpy(b->solve_items[r], items.data(),
+                                     items.size() * sizeof(BItem),
+                                     cudaMemcpyHostToDevice) != cudaSuccess)
+      return ERX_ECUDA;
+  }
+  return ERX_OK;
+}
+
+// The device table's line counts advance on the device; pull them into the
+// host mirror before the mirror is uploaded again.
+erx_status refresh_host(erx_batch* b) {
+  std::vector<BStream> dev(b->n);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+      cudaMemcpy(dev.data(), b->table, sizeof(BStream) * b->n, cudaMemcpyDeviceToHost) !=
+          cudaSuccess)
+    return ERX_ECUDA;
+  for (int i = 0; i < b->n; ++i) b->host[i].t = dev[i].t;
+  return ERX_OK;
+}
+
+erx_status upload_table(erx_batch* b) {
+  if (cudaMemcpy(b->table, b->host.data(), sizeof(BStream) * b->n, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return ERX_ECUDA;
+  return ERX_OK;
+}
+
+void enqueue_step(erx_batch* b, cudaStream_t st) {
+  const bool fp64 = b->form == ERX_FORM_FP64;
+  launch_batch_mean(b->table, b->n, !fp64, st);
+  launch_batch_stats(b->table, b->stats_items, b->n_stats, fp64, st);
+  launch_batch_ema(b->table, b->ema_items, b->n_ema, st);
+  launch_batch_chol(b->table, b->n, b->dmax, !fp64, b->err, st);
+  for (int r = 0; r < 4; ++r) {
+    if (!b->n_solve[r]) continue;
+    if (r <= 1) launch_batch_solve_simt(r, b->table, b->solve_items[r], b->n_solve[r], b->dmax, st);
+    else launch_batch_solve_tc(r == 2 ? 2 : 1, b->table, b->solve_items[r], b->n_solve[r],
+                               b->dmax, b->err, st);
+  }
+  launch_batch_normalise(b->table, b->n, fp64, st);
+}
+
+erx_status capture(erx_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec), b->exec = nullptr;
+  if (b->graph) cudaGraphDestroy(b->graph), b->graph = nullptr;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return ERX_ECUDA;
+  erx_status s = ERX_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    s = ERX_ECUDA;
+  } else {
+    enqueue_step(b, cs);
+    if (cudaStreamEndCapture(cs, &b->graph) != cudaSuccess ||
+        cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+      s = ERX_ECUDA;
+  }
+  cudaStreamDestroy(cs);
+  if (s != ERX_OK) cudaGetLastError();
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream,
+                            erx_batch** out) {
+  if (!out || n < 1 || !cfgs) return ERX_EINVAL;
+  *out = nullptr;
+  const int form = cfgs[0].form;
+  if (form < ERX_FORM_FP64 || form > ERX_FORM_BF16) return ERX_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    const erx_config& c = cfgs[i];
+    if (c.bands < 1 || c.width < 2 || !(c.momentum > 0.0 && c.momentum <= 1.0) ||
+        !(c.ridge >= 0.0) || !std::isfinite(c.ridge) || c.warmup_lines < 0 ||
+        (c.order != ERX_UPDATE_THEN_SCORE && c.order != ERX_SCORE_THEN_UPDATE) ||
+        c.form != form)
+      return ERX_EINVAL;
+    if (c.in_dtype != ERX_F32 || c.proj != ERX_PROJ_NONE || c.bands > kMaxDim ||
+        c.width > (1 << 20))
+      return ERX_EUNSUPPORTED;
+  }
+  erx_batch* b = new (std::nothrow) erx_batch();
+  if (!b) return ERX_ENOMEM;
+  b->n = n;
+  b->form = form;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->cfg.assign(cfgs, cfgs + n);
+  b->host.resize(n);
+  size_t nx = 0, nd = 0, np = 0, ndd = 0, nw = 0;
+  for (int i = 0; i < n; ++i) {
+    const int d = cfgs[i].bands, W = cfgs[i].width;
+    b->dmax = std::max(b->dmax, d);
+    nx += (size_t)W * d;
+    nd += d;
+    np += (size_t)packed_size(d);
+    ndd += (size_t)d * d;
+    nw += W;
+  }
+  const size_t ss = form == ERX_FORM_FP64 ? 8 : 4;
+  erx_status s = ERX_OK;
+  float* ax = nullptr;
+  double *amu, *amh, *ash, *amt, *aks, *akt, *alf, *as2;
+  float* alf32 = nullptr;
+  char *adl = nullptr, *adn = nullptr;
+  uint8_t *amk = nullptr, *adt = nullptr;
+  if (configure_batch_kernels() != cudaSuccess) s = ERX_ECUDA;
+#define BA(p, cnt) \
+  if (s == ERX_OK) s = balloc(b, &p, cnt)
+  BA(ax, nx);
+  BA(amu, nd);
+  BA(amh, nd);
+  BA(ash, nd);
+  BA(amt, nd);
+  BA(aks, np);
+  BA(akt, np);
+  BA(alf, np);
+  BA(alf32, np);
+  BA(as2, ndd);
+  BA(adl, nw * ss);
+  BA(adn, nw * ss);
+  BA(amk, nw);
+  BA(adt, (size_t)n);
+  BA(b->table, (size_t)n);
+  BA(b->err, (size_t)kErrSlots);
+  BA(b->ptr_dev, (size_t)n);
+#undef BA
+  if (s == ERX_OK) {
+    size_t ox = 0, od = 0, op = 0, odd = 0, ow = 0;
+    std::vector<BItem> st_items, ema_items;
+    for (int i = 0; i < n; ++i) {
+      const erx_config& c = cfgs[i];
+      const int d = c.bands, W = c.width;
+      BStream& e = b->host[i];
+      e.x = ax + ox;
+      e.W = W;
+      e.d = d;
+      e.route = native_route(form);
+      e.order = c.order;
+      e.alpha = c.momentum;
+      e.ridge = c.ridge;
+      e.threshold = c.threshold;
+      e.warmup = c.warmup_lines;
+      e.t = 0;
+      e.mu_state = amu + od;
+      e.mu_hat = amh + od;
+      e.shift = ash + od;
+      e.mu_t = amt + od;
+      e.K_state = aks + op;
+      e.K_t = akt + op;
+      e.Lf = alf + op;
+      e.Lf32 = alf32 + op;
+      e.S2f = as2 + odd;
+      e.delta = adl + ow * ss;
+      e.dn = adn + ow * ss;
+      e.mask = amk + ow;
+      e.det = adt + i;
+      for (int k = 0; k < batch_stats_tiles(d); ++k) st_items.push_back({i, k});
+      const int64_t ne = packed_size(d) + d;
+      for (int k = 0; k < (int)((ne + 127) / 128); ++k) ema_items.push_back({i, k});
+      ox += (size_t)W * d;
+      od += d;
+      op += (size_t)packed_size(d);
+      odd += (size_t)d * d;
+      ow += W;
+    }
+    std::stable_sort(st_items.begin(), st_items.end(), [&](const BItem& x, const BItem& y) {
+      return (int64_t)b->host[x.s].W * b->host[x.s].d > (int64_t)b->host[y.s].W * b->host[y.s].d;
+    });
+    b->n_stats = (int)st_items.size();
+    b->n_ema = (int)ema_items.size();
+    s = balloc(b, &b->stats_items, st_items.size());
+    if (s == ERX_OK) s = balloc(b, &b->ema_items, ema_items.size());
+    if (s == ERX_OK &&
+        (cudaMemcpy(b->stats_items, st_items.data(), st_items.size() * sizeof(BItem),
+                    cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(b->ema_items, ema_items.data(), ema_items.size() * sizeof(BItem),
+                    cudaMemcpyHostToDevice) != cudaSuccess))
+      s = ERX_ECUDA;
+  }
+  if (s == ERX_OK) s = build_solve_items(b);
+  if (s == ERX_OK) s = upload_table(b);
+  for (int i = 0; i < 2 && s == ERX_OK; ++i) {
+    if (cudaMallocHost(&b->ptr_host[i], sizeof(float*) * n) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ptr_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      s = ERX_ENOMEM;
+  }
+  if (s == ERX_OK && (cudaMemset(b->err, 0xff, sizeof(unsigned long long) * kErrSlots) !=
+                          cudaSuccess ||
+                      cudaDeviceSynchronize() != cudaSuccess))
+    s = ERX_ECUDA;
+  if (s == ERX_OK) s = capture(b);
+  if (s != ERX_OK) {
+    cudaGetLastError();
+    bfree(b);
+    delete b;
+    return s;
+  }
+  *out = b;
+  return ERX_OK;
+}
+
+erx_status erx_batch_buffers(erx_batch* b, int32_t i, float** line_dev, void** delta_dev,
+                             void** delta_norm_dev, uint8_t** mask_dev, uint8_t** detecting_dev) {
+  if (!b || i < 0 || i >= b->n) return ERX_EINVAL;
+  const BStream& e = b->host[i];
+  if (line_dev) *line_dev = const_cast<float*>(e.x);
+  if (delta_dev) *delta_dev = e.delta;
+  if (delta_norm_dev) *delta_norm_dev = e.dn;
+  if (mask_dev) *mask_dev = e.mask;
+  if (detecting_dev) *detecting_dev = e.det;
+  return ERX_OK;
+}
+
+erx_status erx_batch_push(erx_batch* b, const float* const* lines_dev) {
+  if (!b) return ERX_EINVAL;
+  if (b->failed) return ERX_ECUDA;
+  if (lines_dev) {
+    const int slot = b->ptr_slot;
+    b->ptr_slot ^= 1;
+    // the pointer array of this slot may still feed a copy two pushes back
+    if (cudaEventSynchronize(b->ptr_ev[slot]) != cudaSuccess) {
+      b->failed = true;
+      return ERX_ECUDA;
+    }
+    std::memcpy(b->ptr_host[slot], lines_dev, sizeof(float*) * b->n);
+    int wmax = 1;
+    for (int i = 0; i < b->n; ++i)
+      wmax = std::max<int64_t>(wmax, ((int64_t)b->host[i].W * b->host[i].d + 255) / 256);
+    if (cudaMemcpyAsync(b->ptr_dev, b->ptr_host[slot], sizeof(float*) * b->n,
+                        cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaEventRecord(b->ptr_ev[slot], b->stream) != cudaSuccess) {
+      b->failed = true;
+      return ERX_ECUDA;
+    }
+    dim3 grid((unsigned)std::min(wmax, 64), (unsigned)b->n);
+    gather_kernel<<<grid, 256, 0, b->stream>>>(b->ptr_dev, b->table);
+  }
+  if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    b->failed = true;
+    return ERX_ECUDA;
+  }
+  return ERX_OK;
+}
+
+erx_status erx_batch_sync(erx_batch* b, int64_t* bad_stream) {
+  if (bad_stream) *bad_stream = -1;
+  if (!b) return ERX_EINVAL;
+  if (b->failed) return ERX_ECUDA;
+  unsigned long long e[kErrSlots];
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+      cudaMemcpy(e, b->err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(b->err, 0xff, sizeof(e)) != cudaSuccess) {
+    cudaGetLastError();
+    b->failed = true;
+    return ERX_ECUDA;
+  }
+  for (int k : {(int)kErrTimeout, (int)kErrNotPD}) {
+    if (e[k] != ~0ull) {
+      if (bad_stream) *bad_stream = (int64_t)e[k];
+      return k == kErrTimeout ? ERX_ETIMEOUT : ERX_ENOTPD;
+    }
+  }
+  return ERX_OK;
+}
+
+erx_status erx_batch_get_state(erx_batch* b, int32_t i, int64_t* t, double* mu, double* K) {
+  if (!b || i < 0 || i >= b->n) return ERX_EINVAL;
+  if (b->failed) return ERX_ECUDA;
+  BStream e;
+  const BStream& h = b->host[i];
+  const int d = h.d;
+  const int64_t P = packed_size(d);
+  std::vector<double> kp((size_t)P);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+      cudaMemcpy(&e, b->table + i, sizeof(BStream), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      (mu && cudaMemcpy(mu, h.mu_state, sizeof(double) * d, cudaMemcpyDeviceToHost) !=
+                 cudaSuccess) ||
+      cudaMemcpy(kp.data(), h.K_state, sizeof(double) * P, cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    b->failed = true;
+    return ERX_ECUDA;
+  }
+  if (K)
+    for (int a = 0; a < d; ++a)
+      for (int c = 0; c <= a; ++c) K[(size_t)a * d + c] = K[(size_t)c * d + a] = kp[(size_t)a * (a + 1) / 2 + c];
+  if (t) *t = e.t;
+  return ERX_OK;
+}
+
+erx_status erx_batch_route(const erx_batch* b, int32_t i, int32_t* route) {
+  if (!b || i < 0 || i >= b->n || !route) return ERX_EINVAL;
+  *route = b->host[i].route;
+  return ERX_OK;
+}
+
+erx_status erx_batch_tune(erx_batch* b, int32_t reps, const char* cache_path) {
+  if (!b || reps < 1) return ERX_EINVAL;
+  if (b->failed) return ERX_ECUDA;
+  // band counts present and the routes the form allows
+  std::map<int, std::vector<int>> classes;
+  for (int s = 0; s < b->n; ++s) classes[b->host[s].d].push_back(s);
+  std::vector<int> routes;
+  for (int r = 0; r < 4; ++r)
+    if (route_allowed(b->form, r)) routes.push_back(r);
+  if (routes.size() < 2) return ERX_OK;
+  char dev_name[256] = "gpu";
+  {
+    int dev = 0;
+    cudaDeviceProp p{};
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&p, dev) == cudaSuccess)
+      std::snprintf(dev_name, sizeof dev_name, "%s", p.name);
+    cudaGetLastError();
+  }
+  std::string cache;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char buf[4096];
+      size_t k;
+      while ((k = std::fread(buf, 1, sizeof buf, f)) > 0) cache.append(buf, k);
+      std::fclose(f);
+    }
+  }
+  auto key_of = [&](int d, int wbucket) {
+    char k[320];
+    std::snprintf(k, sizeof k, "\"%s|form%d|d%d|w%d\"", dev_name, b->form, d, wbucket);
+    return std::string(k);
+  };
+  // The scores of the last step are recomputed by the candidate kernels, which
+  // read only the per-step buffers (mu_t, factor) and write scores: the state
+  // does not move.  A step must therefore have run once.
+  bool need_run = true;
+  {
+    BStream e;
+    if (cudaStreamSynchronize(b->stream) == cudaSuccess &&
+        cudaMemcpy(&e, b->table, sizeof(BStream), cudaMemcpyDeviceToHost) == cudaSuccess)
+      need_run = (e.t == 0);
+    cudaGetLastError();
+  }
+  if (need_run) return ERX_ESTATE;
+  if (refresh_host(b) != ERX_OK) {
+    b->failed = true;
+    return ERX_ECUDA;
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return ERX_ECUDA;
+  std::string new_entries;
+  for (auto& kv : classes) {
+    const int d = kv.first;
+    int wsum = 0;
+    for (int s : kv.second) wsum += b->host[s].W;
+    const int wbucket = 1 << (int)std::ceil(std::log2(std::max(1, wsum / (int)kv.second.size())));
+    const std::string key = key_of(d, wbucket);
+    int best = -1;
+    const size_t pos = cache.find(key);
+    if (pos != std::string::npos) {
+      const size_t c = cache.find(':', pos);
+      if (c != std::string::npos) best = std::atoi(cache.c_str() + c + 1);
+      if (!route_allowed(b->form, best)) best = -1;
+    }
+    if (best < 0) {
+      float best_ms = 1e30f;
+      for (int r : routes) {
+        // timing items: this class's streams on route r, in a scratch work list
+        std::vector<BItem> it;
+        for (int s : kv.second)
+          for (int k = 0; k < batch_solve_tiles(r, b->host[s].W); ++k) it.push_back({s, k});
+        BItem* dit = nullptr;
+        if (cudaMalloc(&dit, it.size() * sizeof(BItem)) != cudaSuccess) {
+          cudaGetLastError();
+          continue;
+        }
+        cudaMemcpy(dit, it.data(), it.size() * sizeof(BItem), cudaMemcpyHostToDevice);
+        // the route's score type must match the table's: route 1 vs 2/3 all write float
+        std::vector<BStream> tmp = b->host;
+        for (int s : kv.second) tmp[s].route = r;
+        cudaMemcpy(b->table, tmp.data(), sizeof(BStream) * b->n, cudaMemcpyHostToDevice);
+        float ms = 0.f;
+        for (int pass = 0; pass < 2; ++pass) {   // pass 0 warms up
+          cudaEventRecord(e0, b->stream);
+          for (int k = 0; k < reps; ++k) {
+            if (r <= 1) launch_batch_solve_simt(r, b->table, dit, (int)it.size(), b->dmax, b->stream);
+            else launch_batch_solve_tc(r == 2 ? 2 : 1, b->table, dit, (int)it.size(), b->dmax,
+                                       b->err, b->stream);
+          }
+          cudaEventRecord(e1, b->stream);
+          cudaEventSynchronize(e1);
+          cudaEventElapsedTime(&ms, e0, e1);
+        }
+        cudaFree(dit);
+        if (ms < best_ms) best_ms = ms, best = r;
+      }
+      char line[400];
+      std::snprintf(line, sizeof line, "%s%s: %d", new_entries.empty() && cache.empty() ? "" : ",\n ",
+                    key.c_str(), best);
+      new_entries += line;
+    }
+    for (int s : kv.second) b->host[s].route = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  erx_status s = upload_table(b);
+  if (s == ERX_OK) s = build_solve_items(b);
+  if (s == ERX_OK) s = capture(b);
+  if (s == ERX_OK && cache_path && !new_entries.empty()) {
+    std::string body = cache;
+    const size_t close = body.rfind('}');
+    if (close == std::string::npos) body = "{" + new_entries + "\n}\n";
+    else body = body.substr(0, close) + new_entries + "\n}\n";
+    if (FILE* f = std::fopen(cache_path, "w")) {
+      std::fwrite(body.data(), 1, body.size(), f);
+      std::fclose(f);
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) s = ERX_ECUDA;
+  if (s != ERX_OK) b->failed = true;
+  return s;
+}
+
+erx_status erx_batch_destroy(erx_batch* b) {
+  if (!b) return ERX_OK;
+  cudaStreamSynchronize(b->stream);
+  cudaGetLastError();
+  bfree(b);
+  delete b;
+  return ERX_OK;
+}
+
+}  // extern "C"
+
+namespace erx {
+cudaError_t configure_batch_kernels() {
+  cudaError_t e = configure_factor_kernels();
+  if (e == cudaSuccess) e = configure_solve_kernels();
+  if (e == cudaSuccess) e = configure_solve_tc_kernels();
+  return e;
+}
+}  // namespace erx

@@ -1,0 +1,50 @@
+// Device-side description of a batch of independent line streams advanced one
+// line each per step (the batched form).  One table entry per stream; work
+// items map a CTA of a phase kernel to (stream, tile).
+#pragma once
+
+#include <cstdint>
+
+namespace erx {
+
+struct BStream {
+  const float* x;        // the stream's current line, [W][d] float32 (device)
+  int W, d;
+  int route;             // score kernel: 0 FP64, 1 FP32 SIMT, 2 TF32 MMA, 3 BF16 MMA
+  int order;
+  double alpha, ridge, threshold;
+  int64_t warmup;
+  int64_t t;             // lines seen; advanced on the device at the end of each step
+  double* mu_state;      // d
+  double* K_state;       // d(d+1)/2 packed
+  double* mu_hat;        // d
+  double* shift;         // d
+  double* S2f;           // d x d
+  double* mu_t;          // d
+  double* K_t;           // d(d+1)/2
+  double* Lf;            // d(d+1)/2 blocked factor
+  float* Lf32;           // its float copy
+  void* delta;           // W scores (double for route 0, float otherwise)
+  void* dn;              // W normalised scores (same type)
+  uint8_t* mask;         // W
+  uint8_t* det;          // 1 flag
+};
+
+struct BItem {
+  int s;      // stream
+  int tile;   // tile index within the stream's work for this phase
+};
+
+// Batched phase launchers: each CTA takes items[blockIdx.x].
+void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t st);
+void launch_batch_stats(const BStream* S, const BItem* items, int n_items, bool fp64,
+                        cudaStream_t st);
+void launch_batch_ema(const BStream* S, const BItem* items, int n_items, cudaStream_t st);
+void launch_batch_chol(const BStream* S, int n, int dmax, bool want32,
+                       unsigned long long* err, cudaStream_t st);
+void launch_batch_solve(int route, const BStream* S, const BItem* items, int n_items, int dmax,
+                        unsigned long long* err, cudaStream_t st);
+void launch_batch_normalise(const BStream* S, int n, bool fp64, cudaStream_t st);
+cudaError_t configure_batch_kernels();
+
+}  // namespace erx

@@ -25,6 +25,20 @@ enum { kErrNotPD = 0, kErrRange = 1, kErrTimeout = 2, kErrSlots = 3 };
 
 __host__ __device__ inline int64_t packed_size(int d) { return (int64_t)d * (d + 1) / 2; }
 
+// S3 arithmetic shared by every EMA kernel, with the rounding of each
+// operation fixed (no contraction into FMAs), so that all kernels that update
+// the state produce the same bits.
+#ifdef __CUDACC__
+// K_hat_ab from the scatter S_ab about shift c: (S_ab - p e_a e_b) / (p - 1), e = mu_hat - c
+__device__ __forceinline__ double ema_khat(double S, double ea, double eb, double Wd) {
+  return __dmul_rn(__dsub_rn(S, __dmul_rn(__dmul_rn(Wd, ea), eb)), __drcp_rn(__dsub_rn(Wd, 1.0)));
+}
+// (1 - a) s + a x, both products rounded before the sum (as written in Sec. III-C)
+__device__ __forceinline__ double ema_mix(double s, double x, double alpha, double beta) {
+  return __dadd_rn(__dmul_rn(beta, s), __dmul_rn(alpha, x));
+}
+#endif
+
 // Opt the kernels that need it into large dynamic shared memory on the
 // current device (called once per device at context creation).
 cudaError_t configure_factor_kernels();

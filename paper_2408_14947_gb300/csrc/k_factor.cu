@@ -17,6 +17,7 @@
 // and finite records the line in the error slot and poisons its scores (NaN).
 #include <cmath>
 
+#include "erx_batch.cuh"
 #include "erx_internal.cuh"
 
 namespace erx {
@@ -27,18 +28,16 @@ constexpr int kNB = kFactorBlock;
 
 __device__ __forceinline__ int pidx(int i, int k) { return i * (i + 1) / 2 + k; }
 
-__global__ void __launch_bounds__(kThreads) chol_kernel(const double* __restrict__ K_t, int d,
-                                                       double ridge, double* __restrict__ Lf,
-                                                       float* __restrict__ Lf32,
-                                                       unsigned long long* __restrict__ err,
-                                                       int64_t t0) {
+// Factor one line's K (packed, src) into the blocked factor (dst, dst32);
+// `line` is the global line index reported on a bad pivot.
+__device__ __forceinline__ void chol_body(const double* __restrict__ src, int d, double ridge,
+                                          double* __restrict__ dst, float* __restrict__ d32,
+                                          unsigned long long* __restrict__ err, int64_t line) {
   extern __shared__ __align__(16) double sm[];
   const int P = d * (d + 1) / 2;
   double* A = sm;
   double* col = sm + P;
   __shared__ double s_inv;
-  const int t = blockIdx.x;
-  const double* src = K_t + (int64_t)t * P;
   for (int q = threadIdx.x; q < P; q += kThreads) A[q] = src[q];
   __syncthreads();
   for (int j = threadIdx.x; j < d; j += kThreads) A[pidx(j, j)] += ridge;
@@ -48,7 +47,7 @@ __global__ void __launch_bounds__(kThreads) chol_kernel(const double* __restrict
     if (threadIdx.x == 0) {
       double ajj = A[pidx(j, j)];
       if (!(ajj > 0.0) || !isfinite(ajj)) {
-        atomicMin(&err[kErrNotPD], (unsigned long long)(t0 + t));
+        atomicMin(&err[kErrNotPD], (unsigned long long)line);
         ajj = __longlong_as_double(0x7ff8000000000000ll);
       }
       const double l = sqrt(ajj);
@@ -108,19 +107,44 @@ __global__ void __launch_bounds__(kThreads) chol_kernel(const double* __restrict
     __syncwarp();
   }
   __syncthreads();
-  double* dst = Lf + (int64_t)t * P;
   for (int q = threadIdx.x; q < P; q += kThreads) dst[q] = A[q];
-  if (Lf32) {
-    float* d32 = Lf32 + (int64_t)t * P;
+  if (d32) {
     for (int q = threadIdx.x; q < P; q += kThreads) d32[q] = (float)A[q];
   }
+}
+
+__global__ void __launch_bounds__(kThreads) chol_kernel(const double* __restrict__ K_t, int d,
+                                                       double ridge, double* __restrict__ Lf,
+                                                       float* __restrict__ Lf32,
+                                                       unsigned long long* __restrict__ err,
+                                                       int64_t t0) {
+  const int t = blockIdx.x;
+  const int64_t P = packed_size(d);
+  chol_body(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err, t0 + t);
+}
+
+// Batched form: one CTA per stream.
+__global__ void __launch_bounds__(kThreads) b_chol_kernel(const BStream* __restrict__ S,
+                                                         bool want32,
+                                                         unsigned long long* __restrict__ err) {
+  const BStream& s = S[blockIdx.x];
+  chol_body(s.K_t, s.d, s.ridge, s.Lf, want32 ? s.Lf32 : nullptr, err, blockIdx.x);
 }
 
 }  // namespace
 
 cudaError_t configure_factor_kernels() {
-  return cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)((packed_size(kMaxDim) + kMaxDim) * sizeof(double)));
+  const int m = (int)((packed_size(kMaxDim) + kMaxDim) * sizeof(double));
+  cudaError_t e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(b_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+  return e;
+}
+
+void launch_batch_chol(const BStream* S, int n, int dmax, bool want32, unsigned long long* err,
+                       cudaStream_t st) {
+  const size_t smem = (size_t)(packed_size(dmax) + dmax) * sizeof(double);
+  b_chol_kernel<<<n, kThreads, smem, st>>>(S, want32, err);
 }
 
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, float* Lf32,

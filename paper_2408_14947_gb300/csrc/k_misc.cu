@@ -2,6 +2,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "erx_batch.cuh"
 #include "erx_internal.cuh"
 
 namespace erx {
@@ -55,9 +56,9 @@ __device__ __forceinline__ double ema_stat(const EmaSrc& s, int64_t t, int a, in
     const int64_t s2 = (int64_t)__ldg(s.S2i + t * dd + ab);
     return (double)((int64_t)s.W * s2 - s1a * s1b) * (1.0 / (Wd * (Wd - 1.0)));
   }
-  const double ea = __ldg(s.mu_hat + t * s.d + a) - __ldg(s.shift + t * s.d + a);
-  const double eb = __ldg(s.mu_hat + t * s.d + b) - __ldg(s.shift + t * s.d + b);
-  return (__ldg(s.S2f + t * dd + ab) - Wd * ea * eb) * (1.0 / (Wd - 1.0));
+  const double ea = __dsub_rn(__ldg(s.mu_hat + t * s.d + a), __ldg(s.shift + t * s.d + a));
+  const double eb = __dsub_rn(__ldg(s.mu_hat + t * s.d + b), __ldg(s.shift + t * s.d + b));
+  return ema_khat(__ldg(s.S2f + t * dd + ab), ea, eb, Wd);
 }
 
 __device__ __forceinline__ void ema_element(const EmaSrc& s, int64_t q, int& a, int& b) {
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(128) ema_pass_a(EmaSrc s, int T, double alpha,
   double u = 0.0;
   for (int t = tb; t < te; ++t) {
     const double kh = ema_stat(s, t, a, b);
-    u = (t0 + t == 0) ? kh : beta * u + alpha * kh;
+    u = (t0 + t == 0) ? kh : ema_mix(u, kh, alpha, beta);
   }
   E[(int64_t)g * n + q] = u;
 }
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(128) ema_pass_b(int64_t n, int T, int G, doubl
       for (int i = tb; i < te; ++i) w *= beta;
     }
     const double e = E[(int64_t)g * n + q];
-    s = has_init ? e : w * s + e;
+    s = has_init ? e : __dadd_rn(__dmul_rn(w, s), e);
   }
   *st = s;
 }
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(128) ema_pass_c(EmaSrc s, int T, double alpha,
   for (int t = tb; t < te; ++t) {
     const double kh = ema_stat(s, t, a, b);
     const bool first = (t0 + t == 0);
-    const double post = first ? kh : beta * v + alpha * kh;
+    const double post = first ? kh : ema_mix(v, kh, alpha, beta);
     const double out = (order == 0 || first) ? post : v;
     if (b < 0) mu_t[(int64_t)t * s.d + a] = out;
     else K_t[(int64_t)t * s.P + q] = out;
@@ -162,30 +163,88 @@ __device__ double block_sum(double v, double* sh) {
   return tot;
 }
 
+// One line: delta_N, mask and the warm-up flag of global line `line`.
+template <typename ST>
+__device__ __forceinline__ void normalise_body(const ST* __restrict__ dl, int W, double threshold,
+                                               int64_t line, int64_t warmup,
+                                               ST* __restrict__ dn, uint8_t* __restrict__ mask,
+                                               uint8_t* __restrict__ detecting) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < W; i += blockDim.x) s += to_d(dl[i]);
+  const double mean = block_sum(s, sh) / (double)W;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    const double e = __dsub_rn(to_d(dl[i]), mean);
+    v = __fma_rn(e, e, v);
+  }
+  const double sd = sqrt(block_sum(v, sh) / (double)W);
+  for (int i = threadIdx.x; i < W; i += blockDim.x) {
+    const double z = sd > 0.0 ? (to_d(dl[i]) - mean) / sd : 0.0;
+    if (dn) dn[i] = (ST)z;
+    if (mask) mask[i] = (uint8_t)(z >= threshold);
+  }
+  if (detecting && threadIdx.x == 0) *detecting = (uint8_t)(line >= warmup);
+}
+
 template <typename ST>
 __global__ void __launch_bounds__(256) normalise_kernel(const ST* __restrict__ delta, int W,
                                                         double threshold, int64_t t0,
                                                         int64_t warmup, ST* __restrict__ dn,
                                                         uint8_t* __restrict__ mask,
                                                         uint8_t* __restrict__ detecting) {
-  __shared__ double sh[32];
   const int t = blockIdx.x;
-  const ST* dl = delta + (int64_t)t * W;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < W; i += blockDim.x) s += to_d(dl[i]);
-  const double mean = block_sum(s, sh) / (double)W;
-  double v = 0.0;
-  for (int i = threadIdx.x; i < W; i += blockDim.x) {
-    const double e = to_d(dl[i]) - mean;
-    v += e * e;
+  const int64_t o = (int64_t)t * W;
+  normalise_body<ST>(delta + o, W, threshold, t0 + t, warmup, dn ? dn + o : nullptr,
+                     mask ? mask + o : nullptr, detecting ? detecting + t : nullptr);
+}
+
+// ---- batched form -------------------------------------------------------
+// EMA of one line per stream: each CTA updates 128 state elements of one
+// stream (item tile = element block); line 0 of a stream initialises.
+__global__ void __launch_bounds__(128) b_ema_kernel(BStream* __restrict__ S,
+                                                    const BItem* __restrict__ items) {
+  const BItem it = items[blockIdx.x];
+  BStream& s = S[it.s];
+  const int d = s.d;
+  const int64_t P = packed_size(d);
+  const int64_t q = (int64_t)it.tile * 128 + threadIdx.x;
+  if (q >= P + d) return;
+  const bool first = (s.t == 0);
+  const double alpha = s.alpha, beta = 1.0 - alpha;
+  const double Wd = (double)s.W;
+  if (q < P) {
+    int a = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+    while ((int64_t)a * (a + 1) / 2 > q) --a;
+    while ((int64_t)(a + 1) * (a + 2) / 2 <= q) ++a;
+    const int b = (int)(q - (int64_t)a * (a + 1) / 2);
+    const double ea = __dsub_rn(s.mu_hat[a], s.shift[a]);
+    const double eb = __dsub_rn(s.mu_hat[b], s.shift[b]);
+    const double kh = ema_khat(s.S2f[(int64_t)a * d + b], ea, eb, Wd);
+    const double prev = s.K_state[q];
+    const double post = first ? kh : ema_mix(prev, kh, alpha, beta);
+    s.K_t[q] = (s.order == 0 || first) ? post : prev;
+    s.K_state[q] = post;
+  } else {
+    const int a = (int)(q - P);
+    const double mh = s.mu_hat[a];
+    const double prev = s.mu_state[a];
+    const double post = first ? mh : ema_mix(prev, mh, alpha, beta);
+    s.mu_t[a] = (s.order == 0 || first) ? post : prev;
+    s.mu_state[a] = post;
   }
-  const double sd = sqrt(block_sum(v, sh) / (double)W);
-  for (int i = threadIdx.x; i < W; i += blockDim.x) {
-    const double z = sd > 0.0 ? (to_d(dl[i]) - mean) / sd : 0.0;
-    if (dn) dn[(int64_t)t * W + i] = (ST)z;
-    if (mask) mask[(int64_t)t * W + i] = (uint8_t)(z >= threshold);
-  }
-  if (detecting && threadIdx.x == 0) detecting[t] = (uint8_t)(t0 + t >= warmup);
+}
+
+// Normalisation per stream; thread 0 then advances the stream's line count.
+template <typename ST>
+__global__ void __launch_bounds__(256) b_normalise_kernel(BStream* __restrict__ S) {
+  BStream& s = S[blockIdx.x];
+  const bool st64 = (s.route == 0);
+  if ((sizeof(ST) == 8) == st64)
+    normalise_body<ST>((const ST*)s.delta, s.W, s.threshold, s.t, s.warmup, (ST*)s.dn, s.mask,
+                       s.det);
+  __syncthreads();
+  if (threadIdx.x == 0) s.t += 1;
 }
 
 // ---- S1: sparse random projection Z = X W (Sec. III-B) --------------------
@@ -235,6 +294,15 @@ void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
 size_t ema_scratch_doubles(int d, int T) {
   const int G = (T + kEmaChunk - 1) / kEmaChunk;
   return G <= 1 ? 0 : (size_t)2 * G * (size_t)(packed_size(d) + d);
+}
+
+void launch_batch_ema(const BStream* S, const BItem* items, int n_items, cudaStream_t st) {
+  b_ema_kernel<<<n_items, 128, 0, st>>>(const_cast<BStream*>(S), items);
+}
+
+void launch_batch_normalise(const BStream* S, int n, bool fp64, cudaStream_t st) {
+  if (fp64) b_normalise_kernel<double><<<n, 256, 0, st>>>(const_cast<BStream*>(S));
+  else b_normalise_kernel<float><<<n, 256, 0, st>>>(const_cast<BStream*>(S));
 }
 
 void launch_normalise(bool fp64, const void* delta, int W, int T, double threshold, int64_t t0,

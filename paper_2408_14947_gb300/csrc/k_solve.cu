@@ -20,6 +20,7 @@
 // per pixel.
 #include <cmath>
 
+#include "erx_batch.cuh"
 #include "erx_internal.cuh"
 
 namespace erx {
@@ -33,16 +34,16 @@ __device__ __forceinline__ float to_f(T v) { return (float)v; }
 constexpr int kPixF64 = 64;
 constexpr int kNB = kFactorBlock;
 
+// Pixels tile*64 .. tile*64+63 of one line (x, pixel stride ps) scored with
+// mu (d) and the blocked factor L (packed); delta: the line's W scores.
 template <typename InT>
-__global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
-    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
-    const double* __restrict__ mu_t, const double* __restrict__ Lf, double* __restrict__ delta) {
+__device__ __forceinline__ void solve_fp64_body(const InT* __restrict__ x, int ps, int W, int d,
+                                                const double* __restrict__ mu,
+                                                const double* __restrict__ L,
+                                                double* __restrict__ delta, int tile) {
   extern __shared__ __align__(16) double r[];
   const int dp = d | 1;
-  const int t = blockIdx.y;
-  const int i0 = blockIdx.x * kPixF64;
-  const double* mu = mu_t + (int64_t)t * d;
-  const InT* x = X + (int64_t)t * line_stride;
+  const int i0 = tile * kPixF64;
   for (int e = threadIdx.x; e < kPixF64 * d; e += kPixF64) {
     const int p = e / d, k = e - p * d, i = i0 + p;
     r[p * dp + k] = i < W ? to_d(x[(int64_t)i * ps + k]) - mu[k] : 0.0;
@@ -50,7 +51,6 @@ __global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
   __syncthreads();
   const int i = i0 + threadIdx.x;
   if (i >= W) return;
-  const double* L = Lf + (int64_t)t * packed_size(d);
   double* rr = r + threadIdx.x * dp;
   double d2 = 0.0;
   for (int j0 = 0; j0 < d; j0 += kNB) {
@@ -86,27 +86,35 @@ __global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
       }
     }
   }
-  delta[(int64_t)t * W + i] = sqrt(d2);
+  delta[i] = sqrt(d2);
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
+    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
+    const double* __restrict__ mu_t, const double* __restrict__ Lf, double* __restrict__ delta) {
+  const int t = blockIdx.y;
+  solve_fp64_body<InT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
+                       Lf + (int64_t)t * packed_size(d), delta + (int64_t)t * W, blockIdx.x);
 }
 
 constexpr int kPixF32 = 64;   // pixels per CTA
 constexpr int kOutB = kNB;    // outputs per block of the factor
 
 template <typename InT>
-__global__ void __launch_bounds__(128) solve_fp32_kernel(
-    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
-    const double* __restrict__ mu_t, const float* __restrict__ Lf32, float* __restrict__ delta) {
+__device__ __forceinline__ void solve_fp32_body(const InT* __restrict__ x, int ps, int W, int d,
+                                                const double* __restrict__ mu,
+                                                const float* __restrict__ Lg,
+                                                float* __restrict__ delta, int tile) {
   extern __shared__ __align__(16) float smf[];
   float* rT = smf;                          // [d][kPixF32]: r, then m, k-major
   float* LT = smf + d * kPixF32;            // [d][kOutB]: factor band, k-major
   float* yT = LT + d * kOutB;               // [kOutB][kPixF32]
   __shared__ float mu_hi[kMaxDim], mu_lo[kMaxDim];
   __shared__ float d2w[2][kPixF32];
-  const int t = blockIdx.y;
-  const int i0 = blockIdx.x * kPixF32;
-  const InT* x = X + (int64_t)t * line_stride;
+  const int i0 = tile * kPixF32;
   for (int k = threadIdx.x; k < d; k += 128) {
-    const double m = mu_t[(int64_t)t * d + k];
+    const double m = mu[k];
     const float h = (float)m;
     mu_hi[k] = h;
     mu_lo[k] = (float)(m - (double)h);
@@ -123,7 +131,6 @@ __global__ void __launch_bounds__(128) solve_fp32_kernel(
   const int lp = lane & 7, lo = lane >> 3;
   const int pcol = ph * 32 + lp * 4;        // first of this thread's 4 pixels
   const int ocol = oh * 16 + lo * 4;        // first of its 4 outputs within a block
-  const float* Lg = Lf32 + (int64_t)t * packed_size(d);
   float d2[4] = {0.f, 0.f, 0.f, 0.f};
   for (int j0 = 0; j0 < d; j0 += kOutB) {
     const int j1 = min(d, j0 + kOutB);
@@ -198,8 +205,32 @@ __global__ void __launch_bounds__(128) solve_fp32_kernel(
   __syncthreads();
   if (threadIdx.x < kPixF32) {
     const int i = i0 + threadIdx.x;
-    if (i < W) delta[(int64_t)t * W + i] = sqrtf(d2w[0][threadIdx.x] + d2w[1][threadIdx.x]);
+    if (i < W) delta[i] = sqrtf(d2w[0][threadIdx.x] + d2w[1][threadIdx.x]);
   }
+}
+
+template <typename InT>
+__global__ void __launch_bounds__(128) solve_fp32_kernel(
+    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
+    const double* __restrict__ mu_t, const float* __restrict__ Lf32, float* __restrict__ delta) {
+  const int t = blockIdx.y;
+  solve_fp32_body<InT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
+                       Lf32 + (int64_t)t * packed_size(d), delta + (int64_t)t * W, blockIdx.x);
+}
+
+// Batched form: one CTA per (stream, pixel tile) item.
+__global__ void __launch_bounds__(kPixF64) b_solve_fp64_kernel(const BStream* __restrict__ S,
+                                                               const BItem* __restrict__ items) {
+  const BItem it = items[blockIdx.x];
+  const BStream& s = S[it.s];
+  solve_fp64_body<float>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf, (double*)s.delta, it.tile);
+}
+
+__global__ void __launch_bounds__(128) b_solve_fp32_kernel(const BStream* __restrict__ S,
+                                                           const BItem* __restrict__ items) {
+  const BItem it = items[blockIdx.x];
+  const BStream& s = S[it.s];
+  solve_fp32_body<float>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta, it.tile);
 }
 
 size_t smem_fp64(int d) { return (size_t)kPixF64 * (d | 1) * sizeof(double); }
@@ -220,8 +251,23 @@ cudaError_t configure_solve_kernels() {
   ERX_CFG(solve_fp32_kernel<uint16_t>, m32);
   ERX_CFG(solve_fp32_kernel<float>, m32);
   ERX_CFG(solve_fp32_kernel<double>, m32);
+  ERX_CFG(b_solve_fp64_kernel, m64);
+  ERX_CFG(b_solve_fp32_kernel, m32);
 #undef ERX_CFG
   return e;
+}
+
+int batch_solve_tiles(int route, int W) {
+  return route == 0 ? (W + kPixF64 - 1) / kPixF64
+                    : route == 1 ? (W + kPixF32 - 1) / kPixF32 : (W + 127) / 128;
+}
+
+void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, int n_items,
+                             int dmax, cudaStream_t st) {
+  if (route == 0)
+    b_solve_fp64_kernel<<<n_items, kPixF64, smem_fp64(dmax), st>>>(S, items);
+  else
+    b_solve_fp32_kernel<<<n_items, 128, smem_fp32(dmax), st>>>(S, items);
 }
 
 void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,

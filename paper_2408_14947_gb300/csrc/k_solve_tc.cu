@@ -13,6 +13,7 @@
 // mu split into two floats.  TF32 operands are rounded to nearest (cvt.rna).
 #include <cuda_bf16.h>
 
+#include "erx_batch.cuh"
 #include "erx_internal.cuh"
 #include "tc_util.cuh"
 
@@ -51,20 +52,24 @@ __device__ __forceinline__ uint4 pack16(const float* v) {
 
 // FMT 2: TF32 (4-byte elements, 4 per core row, K = 8 per MMA);
 // FMT 1: BF16 (2-byte elements, 8 per core row, K = 16 per MMA).
+// Pixels tile*128 .. +127 of one line (x, pixel stride ps) with mu (d) and
+// the float blocked factor Lg; delta: the line's W scores; `line` is reported
+// on a timeout.
 template <typename InT, int FMT>
-__global__ void __launch_bounds__(kPix) solve_tc_kernel(
-    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
-    const double* __restrict__ mu_t, const float* __restrict__ Lf32, float* __restrict__ delta,
-    unsigned long long* __restrict__ err, int64_t t0) {
+__device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps, int W, int d,
+                                              const double* __restrict__ mu,
+                                              const float* __restrict__ Lg,
+                                              float* __restrict__ delta,
+                                              unsigned long long* __restrict__ err, int64_t line,
+                                              int tile) {
   constexpr int E = FMT == 2 ? 4 : 2;     // bytes per element
   constexpr int CK = 16 / E;              // elements per 16-byte core row
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
   __shared__ float mu_hi[kMaxDim], mu_lo[kMaxDim];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int t = blockIdx.y;
-  const int i0 = blockIdx.x * kPix;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int i0 = tile * kPix;
   const int dK = (d + kB - 1) / kB * kB;
   const uint32_t sboM = (uint32_t)(dK / CK) * 128u;
   const uint32_t sboY = (uint32_t)(kB / CK) * 128u;
@@ -74,9 +79,8 @@ __global__ void __launch_bounds__(kPix) solve_tc_kernel(
   auto off = [](int row, int k, uint32_t sbo) -> uint32_t {
     return (uint32_t)(row >> 3) * sbo + (uint32_t)(k / CK) * kLBO + (uint32_t)(row & 7) * 16u;
   };
-  const InT* x = X + (int64_t)t * line_stride;
   for (int k = tid; k < d; k += kPix) {
-    const double m = mu_t[(int64_t)t * d + k];
+    const double m = mu[k];
     const float h = (float)m;
     mu_hi[k] = h;
     mu_lo[k] = (float)(m - (double)h);
@@ -106,7 +110,6 @@ __global__ void __launch_bounds__(kPix) solve_tc_kernel(
   tc::fence_after_sync();
   const uint32_t tmem = tslot;
   const uint32_t id = tc::idesc(FMT, kPix, kB);
-  const float* Lg = Lf32 + (int64_t)t * packed_size(d);
   const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
   uint32_t phase = 0;
   bool ok = true;
@@ -219,12 +222,34 @@ __global__ void __launch_bounds__(kPix) solve_tc_kernel(
   if (!ok) {
     // one more bounded wait for the MMAs still in flight before TMEM is released
     tc::mbar_wait(&mbar, phase & 1u, kWaitLimit);
-    if (tid == 0) atomicMin(&err[kErrTimeout], (unsigned long long)(t0 + t));
+    if (tid == 0) atomicMin(&err[kErrTimeout], (unsigned long long)line);
   }
-  if (valid) delta[(int64_t)t * W + i] = ok ? sqrtf(d2) : __int_as_float(0x7fc00000);
+  if (valid) delta[i] = ok ? sqrtf(d2) : __int_as_float(0x7fc00000);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_free(tmem, 64);
+}
+
+template <typename InT, int FMT>
+__global__ void __launch_bounds__(kPix) solve_tc_kernel(
+    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
+    const double* __restrict__ mu_t, const float* __restrict__ Lf32, float* __restrict__ delta,
+    unsigned long long* __restrict__ err, int64_t t0) {
+  const int t = blockIdx.y;
+  solve_tc_body<InT, FMT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
+                          Lf32 + (int64_t)t * packed_size(d), delta + (int64_t)t * W, err,
+                          t0 + t, blockIdx.x);
+}
+
+// Batched form: one CTA per (stream, 128-pixel tile) item.
+template <int FMT>
+__global__ void __launch_bounds__(kPix) b_solve_tc_kernel(const BStream* __restrict__ S,
+                                                          const BItem* __restrict__ items,
+                                                          unsigned long long* __restrict__ err) {
+  const BItem it = items[blockIdx.x];
+  const BStream& s = S[it.s];
+  solve_tc_body<float, FMT>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta, err, it.s,
+                            it.tile);
 }
 
 size_t smem_bytes(int d, int fmt) {
@@ -246,8 +271,18 @@ cudaError_t configure_solve_tc_kernels() {
   ERX_CFG((solve_tc_kernel<uint16_t, 1>), m1);
   ERX_CFG((solve_tc_kernel<float, 1>), m1);
   ERX_CFG((solve_tc_kernel<double, 1>), m1);
+  ERX_CFG((b_solve_tc_kernel<2>), m2);
+  ERX_CFG((b_solve_tc_kernel<1>), m1);
 #undef ERX_CFG
   return e;
+}
+
+void launch_batch_solve_tc(int fmt, const BStream* S, const BItem* items, int n_items, int dmax,
+                           unsigned long long* err, cudaStream_t st) {
+  if (fmt == 2)
+    b_solve_tc_kernel<2><<<n_items, kPix, smem_bytes(dmax, 2), st>>>(S, items, err);
+  else
+    b_solve_tc_kernel<1><<<n_items, kPix, smem_bytes(dmax, 1), st>>>(S, items, err);
 }
 
 void launch_solve_tc(int fmt, int in_type, const void* x, int64_t line_stride, int ps, int W,

@@ -12,6 +12,7 @@
 //
 // Both tile the lower triangle of the d x d output into 64 x 64 blocks, one
 // CTA per (block pair, line); 256 threads each own a 4 x 4 sub-block.
+#include "erx_batch.cuh"
 #include "erx_internal.cuh"
 
 namespace erx {
@@ -115,16 +116,14 @@ __global__ void __launch_bounds__(256) stats_int_kernel(
   }
 }
 
+// Line mean of one line (x: its first sample, pixel stride ps): 256 threads.
 template <typename InT>
-__global__ void __launch_bounds__(256) mean_kernel(const InT* __restrict__ X, int64_t line_stride,
-                                                   int ps, int W, int d, bool float_shift,
-                                                   double* __restrict__ mu_hat,
-                                                   double* __restrict__ shift) {
+__device__ __forceinline__ void mean_body(const InT* __restrict__ x, int ps, int W, int d,
+                                          bool float_shift, double* __restrict__ mu_hat,
+                                          double* __restrict__ shift) {
   __shared__ double part[256];
-  const int t = blockIdx.x;
   const int G = max(1, (int)blockDim.x / d);
   const int g = threadIdx.x / d, b = threadIdx.x % d;
-  const InT* x = X + (int64_t)t * line_stride;
   double s = 0.0;
   if (g < G) {
     for (int i = g; i < W; i += G) s += to_d(x[(int64_t)i * ps + b]);
@@ -135,29 +134,38 @@ __global__ void __launch_bounds__(256) mean_kernel(const InT* __restrict__ X, in
     double tot = 0.0;
     for (int q = 0; q < G; ++q) tot += part[q * d + threadIdx.x];
     const double m = tot / (double)W;
-    mu_hat[(int64_t)t * d + threadIdx.x] = m;
-    shift[(int64_t)t * d + threadIdx.x] = float_shift ? (double)(float)m : m;
+    mu_hat[threadIdx.x] = m;
+    shift[threadIdx.x] = float_shift ? (double)(float)m : m;
   }
 }
 
+template <typename InT>
+__global__ void __launch_bounds__(256) mean_kernel(const InT* __restrict__ X, int64_t line_stride,
+                                                   int ps, int W, int d, bool float_shift,
+                                                   double* __restrict__ mu_hat,
+                                                   double* __restrict__ shift) {
+  const int t = blockIdx.x;
+  mean_body<InT>(X + (int64_t)t * line_stride, ps, W, d, float_shift, mu_hat + (int64_t)t * d,
+                 shift + (int64_t)t * d);
+}
+
+// One 64 x 64 block pair `pair` of the scatter of one line about `shift`
+// (the line's d values), written to s2 (the line's d x d).
 template <typename InT, typename AccT>
-__global__ void __launch_bounds__(256) stats_fp_kernel(const InT* __restrict__ X,
-                                                       int64_t line_stride, int ps, int W, int d,
-                                                       const double* __restrict__ shift,
-                                                       double* __restrict__ S2f) {
+__device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps, int W, int d,
+                                              const double* __restrict__ shift,
+                                              double* __restrict__ s2, int pair) {
   __shared__ __align__(16) AccT xa[KCF][SB];
   __shared__ __align__(16) AccT xb[KCF][SB];
   __shared__ AccT cs[2 * SB];
   int I, J;
-  block_pair(blockIdx.x, I, J);
-  const int t = blockIdx.y;
+  block_pair(pair, I, J);
   const bool diag = (I == J);
-  const InT* x = X + (int64_t)t * line_stride;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int a0 = I * SB, b0 = J * SB;
   if (threadIdx.x < 2 * SB) {
     const int c = threadIdx.x < SB ? a0 + threadIdx.x : b0 + threadIdx.x - SB;
-    cs[threadIdx.x] = c < d ? (AccT)shift[(int64_t)t * d + c] : (AccT)0;
+    cs[threadIdx.x] = c < d ? (AccT)shift[c] : (AccT)0;
   }
   AccT acc[4][4];
 #pragma unroll
@@ -190,7 +198,6 @@ __global__ void __launch_bounds__(256) stats_fp_kernel(const InT* __restrict__ X
     }
     __syncthreads();
   }
-  double* s2 = S2f + (int64_t)t * d * d;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int a = a0 + ty * 4 + i;
@@ -203,10 +210,43 @@ __global__ void __launch_bounds__(256) stats_fp_kernel(const InT* __restrict__ X
   }
 }
 
+template <typename InT, typename AccT>
+__global__ void __launch_bounds__(256) stats_fp_kernel(const InT* __restrict__ X,
+                                                       int64_t line_stride, int ps, int W, int d,
+                                                       const double* __restrict__ shift,
+                                                       double* __restrict__ S2f) {
+  const int t = blockIdx.y;
+  stats_fp_body<InT, AccT>(X + (int64_t)t * line_stride, ps, W, d, shift + (int64_t)t * d,
+                           S2f + (int64_t)t * d * d, blockIdx.x);
+}
+
 // Small d (projected lines, d <= 16): one CTA per line, one thread per entry
 // (a, b) of the lower triangle, walking all pixels; four independent partial
 // sums per thread.  The 64 x 64 tiles above would be nearly all padding here.
 constexpr int kSmallD = 16;
+
+template <typename InT, typename AccT>
+__device__ __forceinline__ void stats_small_body(const InT* __restrict__ x, int ps, int W, int d,
+                                                 const double* __restrict__ shift,
+                                                 double* __restrict__ s2) {
+  const int P = d * (d + 1) / 2;
+  const int q = threadIdx.x;
+  if (q >= P) return;
+  int a = 0;
+  while ((a + 1) * (a + 2) / 2 <= q) ++a;
+  const int b = q - a * (a + 1) / 2;
+  const AccT ca = (AccT)shift[a], cb = (AccT)shift[b];
+  AccT s0 = 0, s1 = 0, s2a = 0, s3 = 0;
+  int i = 0;
+  for (; i + 4 <= W; i += 4) {
+    s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
+    s1 = fma((AccT)x[(int64_t)(i + 1) * ps + a] - ca, (AccT)x[(int64_t)(i + 1) * ps + b] - cb, s1);
+    s2a = fma((AccT)x[(int64_t)(i + 2) * ps + a] - ca, (AccT)x[(int64_t)(i + 2) * ps + b] - cb, s2a);
+    s3 = fma((AccT)x[(int64_t)(i + 3) * ps + a] - ca, (AccT)x[(int64_t)(i + 3) * ps + b] - cb, s3);
+  }
+  for (; i < W; ++i) s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
+  s2[(int64_t)a * d + b] = (double)((s0 + s1) + (s2a + s3));
+}
 
 template <typename InT, typename AccT>
 __global__ void __launch_bounds__(256) stats_small_kernel(const InT* __restrict__ X,
@@ -214,24 +254,8 @@ __global__ void __launch_bounds__(256) stats_small_kernel(const InT* __restrict_
                                                           int d, const double* __restrict__ shift,
                                                           double* __restrict__ S2f) {
   const int t = blockIdx.x;
-  const int P = d * (d + 1) / 2;
-  const int q = threadIdx.x;
-  if (q >= P) return;
-  int a = 0;
-  while ((a + 1) * (a + 2) / 2 <= q) ++a;
-  const int b = q - a * (a + 1) / 2;
-  const InT* x = X + (int64_t)t * line_stride;
-  const AccT ca = (AccT)shift[(int64_t)t * d + a], cb = (AccT)shift[(int64_t)t * d + b];
-  AccT s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  int i = 0;
-  for (; i + 4 <= W; i += 4) {
-    s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
-    s1 = fma((AccT)x[(int64_t)(i + 1) * ps + a] - ca, (AccT)x[(int64_t)(i + 1) * ps + b] - cb, s1);
-    s2 = fma((AccT)x[(int64_t)(i + 2) * ps + a] - ca, (AccT)x[(int64_t)(i + 2) * ps + b] - cb, s2);
-    s3 = fma((AccT)x[(int64_t)(i + 3) * ps + a] - ca, (AccT)x[(int64_t)(i + 3) * ps + b] - cb, s3);
-  }
-  for (; i < W; ++i) s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
-  S2f[(int64_t)t * d * d + (int64_t)a * d + b] = (double)((s0 + s1) + (s2 + s3));
+  stats_small_body<InT, AccT>(X + (int64_t)t * line_stride, ps, W, d, shift + (int64_t)t * d,
+                              S2f + (int64_t)t * d * d);
 }
 
 int n_pairs(int d) {
@@ -239,7 +263,37 @@ int n_pairs(int d) {
   return nb * (nb + 1) / 2;
 }
 
+// Batched form: one CTA per stream (mean) / per (stream, block pair) item.
+__global__ void __launch_bounds__(256) b_mean_kernel(const BStream* __restrict__ S,
+                                                     bool float_shift) {
+  const BStream& s = S[blockIdx.x];
+  mean_body<float>(s.x, s.d, s.W, s.d, float_shift, s.mu_hat, s.shift);
+}
+
+template <typename AccT>
+__global__ void __launch_bounds__(256) b_stats_kernel(const BStream* __restrict__ S,
+                                                      const BItem* __restrict__ items) {
+  const BItem it = items[blockIdx.x];
+  const BStream& s = S[it.s];
+  if (s.d <= kSmallD)
+    stats_small_body<float, AccT>(s.x, s.d, s.W, s.d, s.shift, s.S2f);
+  else
+    stats_fp_body<float, AccT>(s.x, s.d, s.W, s.d, s.shift, s.S2f, it.tile);
+}
+
 }  // namespace
+
+int batch_stats_tiles(int d) { return d <= kSmallD ? 1 : n_pairs(d); }
+
+void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t st) {
+  b_mean_kernel<<<n, 256, 0, st>>>(S, float_shift);
+}
+
+void launch_batch_stats(const BStream* S, const BItem* items, int n_items, bool fp64,
+                        cudaStream_t st) {
+  if (fp64) b_stats_kernel<double><<<n_items, 256, 0, st>>>(S, items);
+  else b_stats_kernel<float><<<n_items, 256, 0, st>>>(S, items);
+}
 
 void launch_stats_int(const uint16_t* x, int64_t line_stride, int W, int d, uint32_t maxv,
                       int T, uint64_t* S1, uint64_t* S2, unsigned long long* err, int64_t t0,

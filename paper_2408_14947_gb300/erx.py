@@ -73,6 +73,15 @@ def load_library() -> C.CDLL:
         "erx_profile_read": (C.c_int, [P, I32, I32, C.POINTER(D), C.POINTER(I64),
                                        C.POINTER(I64)]),
         "erx_kernel_name": (C.c_char_p, [I32]),
+        "erx_batch_create": (C.c_int, [I32, C.POINTER(ErxConfig), P, C.POINTER(P)]),
+        "erx_batch_buffers": (C.c_int, [P, I32, C.POINTER(P), C.POINTER(P), C.POINTER(P),
+                                        C.POINTER(P), C.POINTER(P)]),
+        "erx_batch_push": (C.c_int, [P, P]),
+        "erx_batch_sync": (C.c_int, [P, C.POINTER(I64)]),
+        "erx_batch_get_state": (C.c_int, [P, I32, C.POINTER(I64), P, P]),
+        "erx_batch_route": (C.c_int, [P, I32, C.POINTER(I32)]),
+        "erx_batch_tune": (C.c_int, [P, I32, C.c_char_p]),
+        "erx_batch_destroy": (C.c_int, [P]),
         "erx_push_lines_static": (C.c_int, [C.POINTER(ErxConfig), P, P, P, C.POINTER(I64), P,
                                             I64, I64, P, P, P, P]),
     }
@@ -307,3 +316,117 @@ class Detector:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """A batch of independent streams (erx_batch_*), one line each per step.
+
+    ``streams`` is a list of dicts with ``bands`` and ``width`` (and optional
+    momentum, ridge, warmup, order, threshold); ``form`` is shared.  Inputs and
+    outputs are batch-owned device buffers exposed as torch tensors.
+    """
+
+    def __init__(self, streams, form="fp64", stream=None):
+        import torch
+        self.torch = torch
+        n = len(streams)
+        cfgs = (ErxConfig * n)()
+        for i, sd in enumerate(streams):
+            load_library().erx_config_default(C.byref(cfgs[i]), sd["bands"], sd["width"])
+            c = cfgs[i]
+            c.in_dtype = ERX_F32
+            c.form = {"fp64": ERX_FORM_FP64, "fp32": ERX_FORM_FP32, "tf32": ERX_FORM_TF32,
+                      "bf16": ERX_FORM_BF16}[form]
+            c.momentum = sd.get("momentum", 0.1)
+            c.ridge = sd.get("ridge", 1e-5)
+            c.warmup_lines = sd.get("warmup", 99)
+            c.order = {"update_then_score": ERX_UPDATE_THEN_SCORE,
+                       "score_then_update": ERX_SCORE_THEN_UPDATE}[sd.get("order",
+                                                                      "update_then_score")]
+            c.threshold = sd.get("threshold", 3.0)
+        self.n = n
+        self.streams = streams
+        self.form = form
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(load_library().erx_batch_create(n, cfgs, C.c_void_p(self.stream.cuda_stream),
+                                               C.byref(h)), "erx_batch_create")
+        self.b = h.value
+        self._ptrs = (C.c_void_p * n)()
+
+    def buffers(self, i):
+        """Raw device pointers (line, delta, delta_n, mask, detecting) of stream i."""
+        p = [C.c_void_p() for _ in range(5)]
+        _check(load_library().erx_batch_buffers(self.b, i, *[C.byref(q) for q in p]),
+               "erx_batch_buffers")
+        return [q.value for q in p]
+
+    def push(self, lines=None):
+        """lines: None (inputs already in place) or a list of n CUDA float32
+        tensors (or None entries) holding one line each."""
+        if lines is None:
+            _check(load_library().erx_batch_push(self.b, None), "erx_batch_push")
+            return
+        for i, x in enumerate(lines):
+            self._ptrs[i] = None if x is None else x.data_ptr()
+        _check(load_library().erx_batch_push(self.b, self._ptrs), "erx_batch_push")
+
+    def sync(self):
+        bad = C.c_int64(-1)
+        st = load_library().erx_batch_sync(self.b, C.byref(bad))
+        if st != ERX_OK:
+            raise ErxError(st, "erx_batch_sync", bad.value)
+
+    def state(self, i):
+        import numpy as np
+        d = self.streams[i]["bands"]
+        t = C.c_int64()
+        mu, k = np.zeros(d), np.zeros((d, d))
+        _check(load_library().erx_batch_get_state(self.b, i, C.byref(t), mu.ctypes.data,
+                                                  k.ctypes.data), "erx_batch_get_state")
+        return t.value, mu, k
+
+    def route(self, i):
+        r = C.c_int32()
+        _check(load_library().erx_batch_route(self.b, i, C.byref(r)), "erx_batch_route")
+        return r.value
+
+    def tune(self, reps=3, cache_path=None):
+        _check(load_library().erx_batch_tune(self.b, reps,
+                                             cache_path.encode() if cache_path else None),
+               "erx_batch_tune")
+
+    def views(self, i):
+        """Torch views (no copy) of stream i's batch-owned device buffers:
+        line [W][B] float32, delta and delta_n [W], mask [W], detecting [1]."""
+        torch = self.torch
+        line, dl, dn, mk, dt = self.buffers(i)
+        w, bands = self.streams[i]["width"], self.streams[i]["bands"]
+        st = "<f8" if self.form == "fp64" else "<f4"
+        return (_device_view(line, (w, bands), "<f4"), _device_view(dl, (w,), st),
+                _device_view(dn, (w,), st), _device_view(mk, (w,), "|u1"),
+                _device_view(dt, (1,), "|u1"))
+
+    def close(self):
+        if self.b:
+            load_library().erx_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DevBuf:
+    """__cuda_array_interface__ over a library-owned device buffer."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def _device_view(ptr, shape, typestr):
+    import torch
+    return torch.as_tensor(_DevBuf(ptr, shape, typestr), device="cuda")
