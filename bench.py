@@ -213,6 +213,62 @@ def time_form(make, x, kw, dev, stream, reps: int = 2):
             "kernels_ms": {k: round(v[0] / reps, 3) for k, v in prof.items() if v[2]}}
 
 
+def bench_batched(dev, stream, n_streams: int = 256, n_lines: int = 4, steps: int = 20):
+    """One step = every stream takes one line (erx_batch_push: gather from
+    resident lines + one graph launch).  lines/s counts all streams."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2408_14947_gb300 import Batch, Detector
+    cfgs = synth.stream_configs_c4(n_streams)
+    lines = [torch.from_numpy(synth.gen_lines(c, 0, n_lines)).to(dev) for c in cfgs]
+    shapes = [{"bands": c.bands, "width": c.width} for c in cfgs]
+    out = {"workload": f"{n_streams} streams, widths U{{128..2048}}, bands from "
+                       f"{{8,16,64,108,224}}, float32, {n_lines} resident lines cycled",
+           "bytes_per_step": int(sum(c.width * c.bands * 4 for c in cfgs))}
+    for form in ("fp64", "fp32", "tf32", "bf16"):
+        b = Batch(shapes, form=form, stream=stream)
+        b.push([x[0] for x in lines])
+        if form in ("tf32", "bf16"):
+            b.sync()
+            b.tune(reps=3)
+        for k in range(3):
+            b.push([x[k % n_lines] for x in lines])
+        b.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(steps):
+            b.push([x[k % n_lines] for x in lines])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b.sync()
+        ms = e0.elapsed_time(e1) / steps
+        routes = sorted({b.route(i) for i in range(n_streams)})
+        out[form] = {"lines_per_s": n_streams / (ms / 1000.0), "ms_per_step": ms,
+                     "routes": routes}
+        b.close()
+    # the same lines through 256 separate single-stream contexts, one push each
+    dets = [Detector(c.bands, c.width, in_dtype="f32", form="fp64", block_lines=1,
+                     stream=stream) for c in cfgs]
+    for k in range(2):
+        for d_, x in zip(dets, lines):
+            d_.push(x[k:k + 1])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(5):
+        for d_, x in zip(dets, lines):
+            d_.push(x[k % n_lines:k % n_lines + 1])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    out["fp64_separate_contexts"] = {"lines_per_s": n_streams / (ms / 1000.0), "ms_per_step": ms}
+    for d_ in dets:
+        d_.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -359,6 +415,9 @@ def run_ours(args):
         result["forms_224"] = {"workload": f"{n224} lines x 1024 px x 224 bands f32, "
                                            "Gaussian background, kappa 1e3", **forms224}
         del x224
+
+        # batched form: 256 streams, widths U{128..2048}, bands from {8,16,64,108,224}
+        result["batched"] = bench_batched(dev, stream)
 
         # end to end through the public host-buffer call: pinned input, results to host
         xh = torch.from_numpy(cube.view(np.int16)).pin_memory()

@@ -51,8 +51,9 @@ typedef enum {
   ERX_ETIMEOUT = 8      /* a bounded wait inside a kernel gave up; results of the call are invalid */
 } erx_status;
 
-/* projection (Sec. III-B) */
-enum { ERX_PROJ_NONE = 0, ERX_PROJ_SRP = 1 };
+/* projection (Sec. III-B): none, sparse random projection, or a trained
+ * band encoder (erx_encoder, attached with erx_set_encoder) */
+enum { ERX_PROJ_NONE = 0, ERX_PROJ_SRP = 1, ERX_PROJ_LEARNED = 2 };
 /* order of update and scoring (Sec. III-C/III-D: the paper scores with mu_t, L_t) */
 enum { ERX_UPDATE_THEN_SCORE = 0, ERX_SCORE_THEN_UPDATE = 1 };
 /* input sample type, lines laid out [pixel][band] (band-interleaved-by-pixel) */
@@ -187,6 +188,85 @@ erx_status erx_push_lines_static(const erx_config* cfg, void* cuda_stream, doubl
                                  int64_t n_lines, int64_t line_stride_bytes, void* delta_dev,
                                  void* delta_norm_dev, uint8_t* mask_dev, uint8_t* detecting_dev);
 
+/* ---- Learned band encoder --------------------------------------------------
+ *
+ * A learned counterpart of the sparse random projection (Sec. III-B; the paper
+ * names learning-based extensions as future work, Sec. V): an MLP from b bands
+ * to k codes, c = W2 relu(W1 xn + b1) + b2 with xn = (x - shift) * scale,
+ * trained on the GPU so that ERX on the codes ranks pixels as full-band ERX
+ * does.  Weights are kept in FP32 (master) with bf16 copies for the forward and
+ * backward products (FP32 accumulation).  Parameters are laid out as one
+ * vector [W1 (k1 = hidden x bands, row-major) | b1 | W2 (k x hidden) | b2]. */
+typedef struct erx_encoder erx_encoder;
+
+typedef struct {
+  double momentum;     /* alpha of the code-space EMA during training (Sec. III-C) */
+  double ridge;        /* eps of the code-space factor (Sec. III-D) */
+  float lr, beta1, beta2, eps, weight_decay;   /* AdamW */
+} erx_train_opts;
+
+/* alpha 0.1, ridge 1e-5, lr 1e-3, betas (0.9, 0.999), eps 1e-8, weight decay 1e-4 */
+void erx_train_opts_default(erx_train_opts* o);
+
+/* Create an encoder bands -> hidden -> k (bands <= 256, hidden <= 256,
+ * 2 <= k <= 32, and 2 (bands + k) hidden + 256 (bands + hidden) bytes within
+ * one CTA's shared memory; ERX_EUNSUPPORTED otherwise) on the current device, initial weights He-scaled normal draws
+ * from SplitMix64(seed) (Box-Muller), biases 0, input normalisation identity.
+ * All its work runs on cuda_stream. */
+erx_status erx_encoder_create(int32_t bands, int32_t hidden, int32_t k, uint64_t seed,
+                              void* cuda_stream, erx_encoder** out);
+
+/* Per-band input normalisation xn = (x - shift) * scale (host arrays, bands each). */
+erx_status erx_encoder_set_norm(erx_encoder* e, const float* shift_host, const float* scale_host);
+
+/* Copy the parameter vector out (theta_out, may be NULL) and/or replace it
+ * (theta_in, may be NULL; also resets the AdamW moments).  Host arrays of
+ * erx_encoder_nparams(e) floats.  Synchronises. */
+erx_status erx_encoder_params(erx_encoder* e, float* theta_out, const float* theta_in);
+int64_t erx_encoder_nparams(const erx_encoder* e);
+/* k; *bands and *hidden (may be NULL) receive the other sizes; -1 for NULL. */
+int32_t erx_encoder_dims(const erx_encoder* e, int32_t* bands, int32_t* hidden);
+
+/* Forget the code-space EMA used by training (the next line initialises it). */
+erx_status erx_encoder_reset_stats(erx_encoder* e);
+
+/* Codes of n_pix pixels: x_dev [n_pix][bands] float -> codes_dev [n_pix][k] float. */
+erx_status erx_encoder_forward(erx_encoder* e, const float* x_dev, int64_t n_pix,
+                               float* codes_dev);
+
+/* Train on n_lines consecutive lines (lines_dev [n][width][bands] float,
+ * targets_dev [n][width] double: full-band ERX delta of those lines), one
+ * AdamW step per line in order, continuing the code-space EMA.  loss_host (may
+ * be NULL): per-line loss, which synchronises every line. */
+erx_status erx_encoder_train(erx_encoder* e, const float* lines_dev, int64_t n_lines,
+                             int32_t width, const double* targets_dev, const erx_train_opts* o,
+                             float* loss_host);
+
+/* Gradient of one line's loss (host vector of nparams) without updating the
+ * weights; advances the code-space EMA like a training step.  Synchronises. */
+erx_status erx_encoder_line_grad(erx_encoder* e, const float* line_dev, int32_t width,
+                                 const double* target_dev, const erx_train_opts* o,
+                                 float* grad_host, float* loss_host);
+
+erx_status erx_encoder_destroy(erx_encoder* e);
+
+/* Attach a trained encoder to a context created with proj = ERX_PROJ_LEARNED
+ * (proj_dim = the encoder's k, in_dtype ERX_F32, bands = the encoder's bands):
+ * its codes replace S1.  The encoder must outlive the context's use of it.
+ * audit_every > 0 turns on the drift monitor: every audit_every-th line is
+ * also scored by an internal full-band context of the same form (fed only the
+ * audited lines, with momentum 1 - (1 - alpha)^audit_every), and the Spearman
+ * rank correlation between the two score vectors of that line is recorded; once
+ * it falls below min_rank_corr the context falls back to full-band ERX for
+ * every later line (the internal context then takes every line with alpha). */
+erx_status erx_set_encoder(erx_ctx* ctx, erx_encoder* enc, int32_t audit_every,
+                           double min_rank_corr);
+
+/* Drift monitor readout: last and lowest audited rank correlation (NaN before
+ * the first audit), number of audits, and whether the fallback is active. */
+erx_status erx_get_drift(erx_ctx* ctx, double* last_corr, double* min_corr, int64_t* audits,
+                         int32_t* fallback);
+
 /* ---- Batched form: many independent streams, one line each per step ------
  *
  * A batch holds n independent ERX streams, each with its own width, band
@@ -252,7 +332,8 @@ enum {
   ERX_K_NORMALISE = 8,  /* S6 normalisation */
   ERX_K_STATS_TC = 9,   /* S2 exact integer sums on the tensor cores */
   ERX_K_SOLVE_TC = 10,  /* S5 scores on the tensor cores (TF32 / BF16) */
-  ERX_K_COUNT = 11
+  ERX_K_ENCODE = 11,    /* S1 learned band encoder (codes) */
+  ERX_K_COUNT = 12
 };
 
 /* Per-kernel timing.  While enabled (on != 0), every kernel the context

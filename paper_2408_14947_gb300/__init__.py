@@ -13,5 +13,6 @@ from .erx import (  # noqa: F401
     erx_config_default, erx_create, erx_push_lines, erx_push_lines_host, erx_sync, erx_reset,
     erx_get_state, erx_set_state, erx_dim, erx_get_projection, erx_srp_weights, erx_destroy,
     erx_status_str, Detector, erx_profile_enable, erx_profile_read, erx_kernel_name,
-    ERX_K_COUNT, erx_push_lines_static, Batch,
+    ERX_K_COUNT, erx_push_lines_static, Batch, Encoder, erx_train_opts_default,
+    ERX_PROJ_LEARNED,
 )

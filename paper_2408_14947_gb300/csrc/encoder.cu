@@ -1,0 +1,596 @@
+// Learned band encoder: codes c = W2 relu(W1 xn + b1) + b2, xn = (x - shift) * scale.
+//
+// The learned counterpart of the sparse random projection (Sec. III-B; the
+// paper names learning-based extensions as future work): ERX then runs on k
+// codes instead of b bands.  It is trained on the GPU so that code-space ERX
+// ranks pixels like full-band ERX, one line per step in stream order:
+//   1. forward: codes of the line's p pixels (weights bf16, FP32 accumulation);
+//   2. code statistics: line mean/covariance, EMA update, Cholesky of K_e + eps I
+//      (the pipeline's own kernels; the statistics are constants for the gradient);
+//   3. loss and dL/dc per pixel: delta = |L^-1 r|, u = L^-T L^-1 r,
+//      dL/dc = (2/p) (log1p(delta) - log1p(target)) / ((1 + delta) delta) u;
+//   4. backward: per 64-pixel tile, partial dW2 = dc^T h, dh = (dc W2) * [a > 0],
+//      partial dW1 = dh^T xn (and the bias sums);
+//   5. deterministic reduction of the tile partials fused with AdamW on the
+//      FP32 master weights, which also refreshes their bf16 copies.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/erx.h"
+#include "erx_internal.cuh"
+
+using namespace erx;
+
+namespace {
+
+constexpr int kTile = 64;       // pixels per CTA
+constexpr int kThreads = 256;
+constexpr int kMaxB = 256, kMaxH = 256, kMaxK = 32;
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+
+// ---- forward --------------------------------------------------------------
+// smem: W1T [b][h] bf16, W2T [h][k] bf16, xT [b][64] f32, hT [h][64] f32
+__global__ void __launch_bounds__(kThreads) enc_fwd_kernel(
+    const float* __restrict__ x, int64_t n, int b, int h, int k, const float* __restrict__ shift,
+    const float* __restrict__ scale, const __nv_bfloat16* __restrict__ W1,
+    const float* __restrict__ b1, const __nv_bfloat16* __restrict__ W2,
+    const float* __restrict__ b2, float* __restrict__ codes, __nv_bfloat16* __restrict__ hout) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __nv_bfloat16* W1T = reinterpret_cast<__nv_bfloat16*>(sm);            // [b][h]
+  __nv_bfloat16* W2T = W1T + (size_t)b * h;                              // [h][k]
+  float* xT = reinterpret_cast<float*>(W2T + (size_t)h * k);             // [b][64]
+  float* hT = xT + (size_t)b * kTile;                                    // [h][64]
+  const int tid = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * kTile;
+  for (int e = tid; e < h * b; e += kThreads) {
+    const int j = e / b, q = e % b;
+    W1T[(size_t)q * h + j] = W1[e];
+  }
+  for (int e = tid; e < k * h; e += kThreads) {
+    const int c = e / h, j = e % h;
+    W2T[(size_t)j * k + c] = W2[e];
+  }
+  for (int e = tid; e < kTile * b; e += kThreads) {
+    const int p = e / b, q = e % b;
+    const int64_t i = i0 + p;
+    xT[(size_t)q * kTile + p] = i < n ? (x[i * b + q] - shift[q]) * scale[q] : 0.f;
+  }
+  __syncthreads();
+  // layer 1: thread owns 4 pixels x (h / 16) hidden units
+  const int px = (tid >> 4) * 4, jg = tid & 15;
+  for (int j0 = jg; j0 < h; j0 += 16) {
+    float acc[4] = {b1[j0], b1[j0], b1[j0], b1[j0]};
+    for (int q = 0; q < b; ++q) {
+      const float w = bf(W1T[(size_t)q * h + j0]);
+      const float4 xv = *reinterpret_cast<const float4*>(xT + (size_t)q * kTile + px);
+      acc[0] = fmaf(w, xv.x, acc[0]);
+      acc[1] = fmaf(w, xv.y, acc[1]);
+      acc[2] = fmaf(w, xv.z, acc[2]);
+      acc[3] = fmaf(w, xv.w, acc[3]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) hT[(size_t)j0 * kTile + px + a] = fmaxf(acc[a], 0.f);
+  }
+  __syncthreads();
+  if (hout) {
+    for (int e = tid; e < kTile * h; e += kThreads) {
+      const int p = e / h, j = e % h;
+      const int64_t i = i0 + p;
+      if (i < n) hout[i * h + j] = __float2bfloat16_rn(hT[(size_t)j * kTile + p]);
+    }
+  }
+  // layer 2: thread owns 4 pixels x (k / 16) codes
+  for (int c = jg; c < k; c += 16) {
+    float acc[4] = {b2[c], b2[c], b2[c], b2[c]};
+    for (int j = 0; j < h; ++j) {
+      const float w = bf(W2T[(size_t)j * k + c]);
+      const float4 hv = *reinterpret_cast<const float4*>(hT + (size_t)j * kTile + px);
+      acc[0] = fmaf(w, hv.x, acc[0]);
+      acc[1] = fmaf(w, hv.y, acc[1]);
+      acc[2] = fmaf(w, hv.z, acc[2]);
+      acc[3] = fmaf(w, hv.w, acc[3]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int64_t i = i0 + px + a;
+      if (i < n) codes[i * k + c] = acc[a];
+    }
+  }
+}
+
+// ---- loss and dL/dc -------------------------------------------------------
+// Lf: the line's code factor (k <= 32: one diagonal block, i.e. L^-1, packed).
+__global__ void __launch_bounds__(kThreads) enc_loss_kernel(
+    const float* __restrict__ codes, int p, int k, const double* __restrict__ mu_e,
+    const float* __restrict__ Lf, const double* __restrict__ target, float* __restrict__ dc,
+    float* __restrict__ loss_part) {
+  __shared__ float Li[kMaxK * (kMaxK + 1) / 2];
+  __shared__ float mu[kMaxK];
+  __shared__ float red[kThreads / 32];
+  const int P = k * (k + 1) / 2;
+  for (int e = threadIdx.x; e < P; e += kThreads) Li[e] = Lf[e];
+  for (int e = threadIdx.x; e < k; e += kThreads) mu[e] = (float)mu_e[e];
+  __syncthreads();
+  const int i = blockIdx.x * kThreads + threadIdx.x;
+  float l2 = 0.f;
+  if (i < p) {
+    float r[kMaxK], m[kMaxK];
+    for (int a = 0; a < k; ++a) r[a] = codes[(int64_t)i * k + a] - mu[a];
+    float d2 = 0.f;
+    for (int a = 0; a < k; ++a) {
+      float s = 0.f;
+      for (int c = 0; c <= a; ++c) s = fmaf(Li[a * (a + 1) / 2 + c], r[c], s);
+      m[a] = s;
+      d2 = fmaf(s, s, d2);
+    }
+    const float delta = sqrtf(d2);
+    const float diff = log1pf(delta) - log1pf((float)target[i]);
+    l2 = diff * diff;
+    const float coef = delta > 0.f ? 2.f * diff / ((1.f + delta) * delta * (float)p) : 0.f;
+    for (int c = 0; c < k; ++c) {          // u = L^-T m
+      float s = 0.f;
+      for (int a = c; a < k; ++a) s = fmaf(Li[a * (a + 1) / 2 + c], m[a], s);
+      dc[(int64_t)i * k + c] = coef * s;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) l2 += __shfl_xor_sync(0xffffffffu, l2, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    loss_part[blockIdx.x] = s;
+  }
+}
+
+// ---- backward partials per 64-pixel tile ----------------------------------
+// part layout per tile: [W1 (h*b) | b1 (h) | W2 (k*h) | b2 (k)]
+__global__ void __launch_bounds__(kThreads) enc_bwd_kernel(
+    const float* __restrict__ x, int p, int b, int h, int k, const float* __restrict__ shift,
+    const float* __restrict__ scale, const __nv_bfloat16* __restrict__ W2,
+    const __nv_bfloat16* __restrict__ hbuf, const float* __restrict__ dc,
+    float* __restrict__ part) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  float* xs = reinterpret_cast<float*>(sm);                 // [64][b]
+  float* hs = xs + (size_t)kTile * b;                       // [64][h]
+  float* dcs = hs + (size_t)kTile * h;                      // [64][k]
+  float* dhs = dcs + (size_t)kTile * k;                     // [64][h]
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * kTile;
+  const int np = min(kTile, p - i0);
+  for (int e = tid; e < kTile * b; e += kThreads) {
+    const int q = e % b, pp = e / b;
+    xs[e] = pp < np ? (x[(int64_t)(i0 + pp) * b + q] - shift[q]) * scale[q] : 0.f;
+  }
+  for (int e = tid; e < kTile * h; e += kThreads) {
+    const int pp = e / h;
+    hs[e] = pp < np ? bf(hbuf[(int64_t)(i0 + pp) * h + e % h]) : 0.f;
+  }
+  for (int e = tid; e < kTile * k; e += kThreads) {
+    const int pp = e / k;
+    dcs[e] = pp < np ? dc[(int64_t)(i0 + pp) * k + e % k] : 0.f;
+  }
+  __syncthreads();
+  // dh = (dc W2) * [h > 0]
+  for (int e = tid; e < kTile * h; e += kThreads) {
+    const int pp = e / h, j = e % h;
+    float s = 0.f;
+    if (hs[e] > 0.f)
+      for (int c = 0; c < k; ++c) s = fmaf(dcs[pp * k + c], bf(W2[(size_t)c * h + j]), s);
+    dhs[e] = s;
+  }
+  __syncthreads();
+  float* out = part + (size_t)blockIdx.x * ((size_t)h * b + h + (size_t)k * h + k);
+  for (int e = tid; e < h * b; e += kThreads) {       // dW1[j][q] = sum_p dh[p][j] xn[p][q]
+    const int j = e / b, q = e % b;
+    float s = 0.f;
+    for (int pp = 0; pp < kTile; ++pp) s = fmaf(dhs[pp * h + j], xs[pp * b + q], s);
+    out[e] = s;
+  }
+  for (int j = tid; j < h; j += kThreads) {
+    float s = 0.f;
+    for (int pp = 0; pp < kTile; ++pp) s += dhs[pp * h + j];
+    out[(size_t)h * b + j] = s;
+  }
+  float* o2 = out + (size_t)h * b + h;
+  for (int e = tid; e < k * h; e += kThreads) {       // dW2[c][j] = sum_p dc[p][c] h[p][j]
+    const int c = e / h, j = e % h;
+    float s = 0.f;
+    for (int pp = 0; pp < kTile; ++pp) s = fmaf(dcs[pp * k + c], hs[pp * h + j], s);
+    o2[e] = s;
+  }
+  for (int c = tid; c < k; c += kThreads) {
+    float s = 0.f;
+    for (int pp = 0; pp < kTile; ++pp) s += dcs[pp * k + c];
+    o2[(size_t)k * h + c] = s;
+  }
+}
+
+// ---- reduction over tiles + AdamW -----------------------------------------
+__global__ void __launch_bounds__(256) enc_adamw_kernel(
+    const float* __restrict__ part, int ntiles, int64_t nparam, float* __restrict__ theta,
+    float* __restrict__ m, float* __restrict__ v, float* __restrict__ grad_out, int apply,
+    float lr, float beta1, float beta2, float eps, float wd, float c1, float c2,
+    __nv_bfloat16* __restrict__ w1b, int64_t n_w1, __nv_bfloat16* __restrict__ w2b,
+    int64_t off_w2, int64_t n_w2) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nparam) return;
+  float g = 0.f;
+  for (int t = 0; t < ntiles; ++t) g += part[(int64_t)t * nparam + e];
+  if (grad_out) grad_out[e] = g;
+  if (!apply) return;
+  const float mm = beta1 * m[e] + (1.f - beta1) * g;
+  const float vv = beta2 * v[e] + (1.f - beta2) * g * g;
+  m[e] = mm;
+  v[e] = vv;
+  const float th = theta[e] - lr * ((mm / c1) / (sqrtf(vv / c2) + eps) + wd * theta[e]);
+  theta[e] = th;
+  if (e < n_w1) w1b[e] = __float2bfloat16_rn(th);
+  else if (e >= off_w2 && e < off_w2 + n_w2) w2b[e - off_w2] = __float2bfloat16_rn(th);
+}
+
+__global__ void enc_sum_kernel(const float* __restrict__ part, int n, float* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                               int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+size_t fwd_smem(int b, int h, int k) {
+  return (size_t)b * h * 2 + (size_t)h * k * 2 + (size_t)b * kTile * 4 + (size_t)h * kTile * 4;
+}
+size_t bwd_smem(int b, int h, int k) {
+  return (size_t)kTile * (b + h + k + h) * 4;
+}
+
+uint64_t sm64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// standard normal from two SplitMix64 outputs (Box-Muller)
+double normal_at(uint64_t seed, uint64_t k) {
+  const double u1 = ((double)(sm64(seed, 2 * k) >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = (double)(sm64(seed, 2 * k + 1) >> 11) * 0x1.0p-53;
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+}  // namespace
+
+struct erx_encoder {
+  int b = 0, h = 0, k = 0;
+  cudaStream_t stream = nullptr;
+  bool failed = false;
+  int64_t nparam = 0, off_b1 = 0, off_w2 = 0, off_b2 = 0;
+  float* theta = nullptr;      // [W1 | b1 | W2 | b2] FP32 master
+  float* mom1 = nullptr;
+  float* mom2 = nullptr;
+  __nv_bfloat16* w1b = nullptr;
+  __nv_bfloat16* w2b = nullptr;
+  float* shift = nullptr;
+  float* scale = nullptr;
+  int64_t adam_k = 0;
+  // training scratch for lines of up to cap_p pixels
+  int cap_p = 0;
+  float* codes = nullptr;
+  __nv_bfloat16* hbuf = nullptr;
+  float* dc = nullptr;
+  float* part = nullptr;
+  float* loss_part = nullptr;
+  float* loss_dev = nullptr;
+  float* grad = nullptr;
+  // code-space statistics (pipeline buffers, one line)
+  double *mu_hat = nullptr, *shiftc = nullptr, *S2f = nullptr, *mu_t = nullptr, *K_t = nullptr,
+         *Lf = nullptr, *mu_e = nullptr, *K_e = nullptr;
+  float* Lf32 = nullptr;
+  unsigned long long* err = nullptr;
+  int64_t t_codes = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+erx_status ealloc(erx_encoder* e, T** p, size_t n) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, std::max<size_t>(1, n) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return ERX_ENOMEM;
+  }
+  e->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return ERX_OK;
+}
+
+erx_status ensure_capacity(erx_encoder* e, int p) {
+  if (p <= e->cap_p) return ERX_OK;
+  const int ntile = (p + kTile - 1) / kTile;
+  erx_status s = ealloc(e, &e->codes, (size_t)p * e->k);
+  if (s == ERX_OK) s = ealloc(e, &e->hbuf, (size_t)p * e->h);
+  if (s == ERX_OK) s = ealloc(e, &e->dc, (size_t)p * e->k);
+  if (s == ERX_OK) s = ealloc(e, &e->part, (size_t)ntile * e->nparam);
+  if (s == ERX_OK) s = ealloc(e, &e->loss_part, (size_t)(p + kThreads - 1) / kThreads);
+  if (s == ERX_OK) e->cap_p = p;
+  return s;
+}
+
+erx_status ecuda(erx_encoder* e, cudaError_t c) {
+  if (c == cudaSuccess) return ERX_OK;
+  cudaGetLastError();
+  e->failed = true;
+  return ERX_ECUDA;
+}
+
+// forward of n pixels into `codes` (and hidden activations into hout when given)
+void forward(erx_encoder* e, const float* x, int64_t n, float* codes, __nv_bfloat16* hout,
+             cudaStream_t st) {
+  const int64_t tiles = (n + kTile - 1) / kTile;
+  enc_fwd_kernel<<<(unsigned)tiles, kThreads, fwd_smem(e->b, e->h, e->k), st>>>(
+      x, n, e->b, e->h, e->k, e->shift, e->scale, e->w1b, e->theta + e->off_b1, e->w2b,
+      e->theta + e->off_b2, codes, hout);
+}
+
+// One line: forward, code statistics (update then score), loss, backward and,
+// when `apply`, the AdamW step.  grad_out (device, nparam) receives the gradient.
+erx_status train_line(erx_encoder* e, const float* line, int p, const double* target,
+                      const erx_train_opts* o, int apply, float* grad_out) {
+  cudaStream_t st = e->stream;
+  erx_status s = ensure_capacity(e, p);
+  if (s != ERX_OK) return s;
+  forward(e, line, p, e->codes, e->hbuf, st);
+  const int k = e->k;
+  launch_mean(ERX_F32, e->codes, 0, k, p, k, 1, false, e->mu_hat, e->shiftc, st);
+  launch_stats_fp(ERX_F32, true, e->codes, 0, k, p, k, 1, e->shiftc, e->S2f, st);
+  launch_ema_scan(false, nullptr, nullptr, e->mu_hat, e->shiftc, e->S2f, 1, k, p, o->momentum,
+                  e->t_codes, ERX_UPDATE_THEN_SCORE, e->mu_e, e->K_e, e->mu_t, e->K_t, nullptr,
+                  st);
+  launch_chol_inv(e->K_t, k, 1, o->ridge, e->Lf, e->Lf32, e->err, e->t_codes, st);
+  e->t_codes += 1;
+  const int nlb = (p + kThreads - 1) / kThreads;
+  enc_loss_kernel<<<nlb, kThreads, 0, st>>>(e->codes, p, k, e->mu_t, e->Lf32, target, e->dc,
+                                            e->loss_part);
+  enc_sum_kernel<<<1, 32, 0, st>>>(e->loss_part, nlb, e->loss_dev);
+  const int ntile = (p + kTile - 1) / kTile;
+  enc_bwd_kernel<<<ntile, kThreads, bwd_smem(e->b, e->h, k), st>>>(
+      line, p, e->b, e->h, k, e->shift, e->scale, e->w2b, e->hbuf, e->dc, e->part);
+  float c1 = 1.f, c2 = 1.f;
+  if (apply) {
+    e->adam_k += 1;
+    c1 = (float)(1.0 - std::pow((double)o->beta1, (double)e->adam_k));
+    c2 = (float)(1.0 - std::pow((double)o->beta2, (double)e->adam_k));
+  }
+  enc_adamw_kernel<<<(unsigned)((e->nparam + 255) / 256), 256, 0, st>>>(
+      e->part, ntile, e->nparam, e->theta, e->mom1, e->mom2, grad_out, apply, o->lr, o->beta1,
+      o->beta2, o->eps, o->weight_decay, c1, c2, e->w1b, (int64_t)e->h * e->b, e->w2b, e->off_w2,
+      (int64_t)e->k * e->h);
+  return ecuda(e, cudaGetLastError());
+}
+
+}  // namespace
+
+namespace erx {
+int encoder_k(const erx_encoder* e) { return e->k; }
+int encoder_bands(const erx_encoder* e) { return e->b; }
+void encoder_forward_on(erx_encoder* e, const float* x, int64_t n, float* codes, cudaStream_t st) {
+  forward(e, x, n, codes, nullptr, st);
+}
+}  // namespace erx
+
+extern "C" {
+
+void erx_train_opts_default(erx_train_opts* o) {
+  if (!o) return;
+  o->momentum = 0.1;
+  o->ridge = 1e-5;
+  o->lr = 1e-3f;
+  o->beta1 = 0.9f;
+  o->beta2 = 0.999f;
+  o->eps = 1e-8f;
+  o->weight_decay = 1e-4f;
+}
+
+erx_status erx_encoder_create(int32_t bands, int32_t hidden, int32_t k, uint64_t seed,
+                              void* cuda_stream, erx_encoder** out) {
+  if (!out) return ERX_EINVAL;
+  *out = nullptr;
+  if (bands < 1 || hidden < 1 || k < 2) return ERX_EINVAL;
+  if (bands > kMaxB || hidden > kMaxH || k > kMaxK) return ERX_EUNSUPPORTED;
+  erx_encoder* e = new (std::nothrow) erx_encoder();
+  if (!e) return ERX_ENOMEM;
+  e->b = bands;
+  e->h = hidden;
+  e->k = k;
+  e->stream = (cudaStream_t)cuda_stream;
+  e->off_b1 = (int64_t)hidden * bands;
+  e->off_w2 = e->off_b1 + hidden;
+  e->off_b2 = e->off_w2 + (int64_t)k * hidden;
+  e->nparam = e->off_b2 + k;
+  const int64_t P = packed_size(k);
+  erx_status s = ERX_OK;
+#define EA(p, n) \
+  if (s == ERX_OK) s = ealloc(e, &e->p, (size_t)(n))
+  EA(theta, e->nparam);
+  EA(mom1, e->nparam);
+  EA(mom2, e->nparam);
+  EA(grad, e->nparam);
+  EA(w1b, (int64_t)hidden * bands);
+  EA(w2b, (int64_t)k * hidden);
+  EA(shift, bands);
+  EA(scale, bands);
+  EA(loss_dev, 1);
+  EA(mu_hat, k);
+  EA(shiftc, k);
+  EA(S2f, (int64_t)k * k);
+  EA(mu_t, k);
+  EA(K_t, P);
+  EA(Lf, P);
+  EA(Lf32, P);
+  EA(mu_e, k);
+  EA(K_e, P);
+  EA(err, kErrSlots);
+#undef EA
+  if (s == ERX_OK) {
+    // the forward keeps both weight matrices and a 64-pixel tile in shared memory
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (fwd_smem(bands, hidden, k) > (size_t)optin || bwd_smem(bands, hidden, k) > (size_t)optin)
+      s = ERX_EUNSUPPORTED;
+    else if (configure_factor_kernels() != cudaSuccess ||
+             cudaFuncSetAttribute(enc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fwd_smem(bands, hidden, k)) != cudaSuccess ||
+             cudaFuncSetAttribute(enc_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bwd_smem(bands, hidden, k)) != cudaSuccess)
+      s = ERX_ECUDA;
+  }
+  if (s == ERX_OK) {
+    // He-style initial weights from a counter-based normal draw (SplitMix64 + Box-Muller)
+    std::vector<float> th((size_t)e->nparam, 0.f);
+    const double s1 = std::sqrt(2.0 / bands), s2 = std::sqrt(1.0 / hidden);
+    for (int64_t i = 0; i < e->off_b1; ++i) th[i] = (float)(normal_at(seed, i) * s1);
+    for (int64_t i = 0; i < (int64_t)k * hidden; ++i)
+      th[e->off_w2 + i] = (float)(normal_at(seed ^ 0x5A5A5A5Aull, i) * s2);
+    std::vector<float> ones(bands, 1.f), zeros(bands, 0.f);
+    if (cudaMemcpy(e->theta, th.data(), th.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(e->mom1, 0, e->nparam * 4) != cudaSuccess ||
+        cudaMemset(e->mom2, 0, e->nparam * 4) != cudaSuccess ||
+        cudaMemcpy(e->shift, zeros.data(), bands * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e->scale, ones.data(), bands * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(e->err, 0xff, sizeof(unsigned long long) * kErrSlots) != cudaSuccess)
+      s = ERX_ECUDA;
+    if (s == ERX_OK) {
+      to_bf16_kernel<<<(unsigned)((e->off_b1 + 255) / 256), 256>>>(e->theta, e->w1b, e->off_b1);
+      to_bf16_kernel<<<(unsigned)(((int64_t)k * hidden + 255) / 256), 256>>>(
+          e->theta + e->off_w2, e->w2b, (int64_t)k * hidden);
+      if (cudaDeviceSynchronize() != cudaSuccess) s = ERX_ECUDA;
+    }
+  }
+  if (s != ERX_OK) {
+    cudaGetLastError();
+    for (void* p : e->allocs) cudaFree(p);
+    delete e;
+    return s;
+  }
+  *out = e;
+  return ERX_OK;
+}
+
+erx_status erx_encoder_set_norm(erx_encoder* e, const float* shift, const float* scale) {
+  if (!e || !shift || !scale) return ERX_EINVAL;
+  if (e->failed) return ERX_ECUDA;
+  if (cudaStreamSynchronize(e->stream) != cudaSuccess ||
+      cudaMemcpy(e->shift, shift, e->b * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(e->scale, scale, e->b * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return ecuda(e, cudaGetLastError());
+  return ERX_OK;
+}
+
+erx_status erx_encoder_params(erx_encoder* e, float* theta_out, const float* theta_in) {
+  if (!e || (!theta_out && !theta_in)) return ERX_EINVAL;
+  if (e->failed) return ERX_ECUDA;
+  if (cudaStreamSynchronize(e->stream) != cudaSuccess) return ecuda(e, cudaGetLastError());
+  if (theta_in) {
+    if (cudaMemcpy(e->theta, theta_in, e->nparam * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(e->mom1, 0, e->nparam * 4) != cudaSuccess ||
+        cudaMemset(e->mom2, 0, e->nparam * 4) != cudaSuccess)
+      return ecuda(e, cudaGetLastError());
+    e->adam_k = 0;
+    to_bf16_kernel<<<(unsigned)((e->off_b1 + 255) / 256), 256, 0, e->stream>>>(e->theta, e->w1b,
+                                                                                e->off_b1);
+    to_bf16_kernel<<<(unsigned)(((int64_t)e->k * e->h + 255) / 256), 256, 0, e->stream>>>(
+        e->theta + e->off_w2, e->w2b, (int64_t)e->k * e->h);
+    if (cudaStreamSynchronize(e->stream) != cudaSuccess) return ecuda(e, cudaGetLastError());
+  }
+  if (theta_out &&
+      cudaMemcpy(theta_out, e->theta, e->nparam * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ecuda(e, cudaGetLastError());
+  return ERX_OK;
+}
+
+int64_t erx_encoder_nparams(const erx_encoder* e) { return e ? e->nparam : -1; }
+
+erx_status erx_encoder_reset_stats(erx_encoder* e) {
+  if (!e) return ERX_EINVAL;
+  e->t_codes = 0;
+  return ERX_OK;
+}
+
+erx_status erx_encoder_forward(erx_encoder* e, const float* x_dev, int64_t n_pix,
+                               float* codes_dev) {
+  if (!e || n_pix < 0 || (n_pix > 0 && (!x_dev || !codes_dev))) return ERX_EINVAL;
+  if (e->failed) return ERX_ECUDA;
+  if (n_pix == 0) return ERX_OK;
+  forward(e, x_dev, n_pix, codes_dev, nullptr, e->stream);
+  return ecuda(e, cudaGetLastError());
+}
+
+erx_status erx_encoder_train(erx_encoder* e, const float* lines_dev, int64_t n_lines,
+                             int32_t width, const double* targets_dev, const erx_train_opts* o,
+                             float* loss_host) {
+  if (!e || !o || n_lines < 0 || width < 2 || (n_lines > 0 && (!lines_dev || !targets_dev)))
+    return ERX_EINVAL;
+  if (e->failed) return ERX_ECUDA;
+  for (int64_t t = 0; t < n_lines; ++t) {
+    erx_status s = train_line(e, lines_dev + t * (int64_t)width * e->b, width,
+                              targets_dev + t * (int64_t)width, o, 1, nullptr);
+    if (s != ERX_OK) return s;
+    if (loss_host) {
+      float l = 0.f;
+      if (cudaMemcpyAsync(&l, e->loss_dev, 4, cudaMemcpyDeviceToHost, e->stream) != cudaSuccess ||
+          cudaStreamSynchronize(e->stream) != cudaSuccess)
+        return ecuda(e, cudaGetLastError());
+      loss_host[t] = l / (float)width;
+    }
+  }
+  return ERX_OK;
+}
+
+erx_status erx_encoder_line_grad(erx_encoder* e, const float* line_dev, int32_t width,
+                                 const double* target_dev, const erx_train_opts* o,
+                                 float* grad_host, float* loss_host) {
+  if (!e || !o || !line_dev || !target_dev || width < 2 || !grad_host) return ERX_EINVAL;
+  if (e->failed) return ERX_ECUDA;
+  erx_status s = train_line(e, line_dev, width, target_dev, o, 0, e->grad);
+  if (s != ERX_OK) return s;
+  float l = 0.f;
+  if (cudaStreamSynchronize(e->stream) != cudaSuccess ||
+      cudaMemcpy(grad_host, e->grad, e->nparam * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&l, e->loss_dev, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ecuda(e, cudaGetLastError());
+  if (loss_host) *loss_host = l / (float)width;
+  return ERX_OK;
+}
+
+erx_status erx_encoder_destroy(erx_encoder* e) {
+  if (!e) return ERX_OK;
+  cudaStreamSynchronize(e->stream);
+  cudaGetLastError();
+  for (void* p : e->allocs) cudaFree(p);
+  delete e;
+  return ERX_OK;
+}
+
+int32_t erx_encoder_dims(const erx_encoder* e, int32_t* bands, int32_t* hidden) {
+  if (!e) return -1;
+  if (bands) *bands = e->b;
+  if (hidden) *hidden = e->h;
+  return e->k;
+}
+
+}  // extern "C"

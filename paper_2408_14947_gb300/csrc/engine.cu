@@ -65,6 +65,16 @@ struct erx_ctx {
   struct Pending { int k; cudaEvent_t a, b; };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> spare_events;
+  // learned projection and its drift monitor
+  erx_encoder* enc = nullptr;
+  int audit_every = 0;
+  double min_corr_thr = 0.0;
+  erx_ctx* audit = nullptr;
+  bool fallback = false;
+  double last_corr = NAN, min_corr = NAN;
+  int64_t audits = 0;
+  void* audit_delta = nullptr;       // device, up to T lines of scores
+  std::vector<char> h_learned, h_full;
 };
 
 namespace {
@@ -94,6 +104,7 @@ void free_all(erx_ctx* c) {
   }
   if (c->h_out) cudaFreeHost(c->h_out);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->audit) erx_destroy(c->audit), c->audit = nullptr;
   for (auto& p : c->pending) cudaEventDestroy(p.a), cudaEventDestroy(p.b);
   for (auto e : c->spare_events) cudaEventDestroy(e);
   c->pending.clear();
@@ -168,7 +179,11 @@ erx_status validate(const erx_config* cfg) {
   if (cfg->bands < 1 || cfg->width < 2) return ERX_EINVAL;
   if (!(cfg->momentum > 0.0 && cfg->momentum <= 1.0)) return ERX_EINVAL;
   if (!(cfg->ridge >= 0.0) || !std::isfinite(cfg->ridge)) return ERX_EINVAL;
-  if (cfg->proj != ERX_PROJ_NONE && cfg->proj != ERX_PROJ_SRP) return ERX_EINVAL;
+  if (cfg->proj != ERX_PROJ_NONE && cfg->proj != ERX_PROJ_SRP && cfg->proj != ERX_PROJ_LEARNED)
+    return ERX_EINVAL;
+  if (cfg->proj == ERX_PROJ_LEARNED &&
+      (cfg->in_dtype != ERX_F32 || cfg->proj_dim < 2 || cfg->proj_dim > 32))
+    return ERX_EINVAL;
   if (cfg->proj == ERX_PROJ_SRP && (cfg->proj_dim < 1 || cfg->proj_dim > cfg->bands))
     return ERX_EINVAL;
   if (cfg->order != ERX_UPDATE_THEN_SCORE && cfg->order != ERX_SCORE_THEN_UPDATE)
@@ -177,16 +192,27 @@ erx_status validate(const erx_config* cfg) {
   if (cfg->in_dtype == ERX_U16 && (cfg->in_bits < 1 || cfg->in_bits > 16)) return ERX_EINVAL;
   if (cfg->form < ERX_FORM_FP64 || cfg->form > ERX_FORM_BF16) return ERX_EINVAL;
   if (cfg->block_lines < 0 || cfg->warmup_lines < 0) return ERX_EINVAL;
-  const int d = cfg->proj == ERX_PROJ_SRP ? cfg->proj_dim : cfg->bands;
+  const int d = cfg->proj != ERX_PROJ_NONE ? cfg->proj_dim : cfg->bands;
   if (d > kMaxDim || cfg->width > (1 << 20) || cfg->bands > 65536) return ERX_EUNSUPPORTED;
   return ERX_OK;
 }
 
 // Enqueue the whole step for `n` lines at `x` (device), outputs at line offset 0 of the given
 // pointers.
+erx_status audit_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems, void* delta);
+
 erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems, void* delta,
                      void* dn, uint8_t* mask, uint8_t* det) {
   const int T = (int)n, W = c->W, d = c->d, B = c->B;
+  const bool learned = c->cfg.proj == ERX_PROJ_LEARNED;
+  if (learned && !c->enc) return ERX_ESTATE;
+  if (learned && c->fallback) {
+    // full-band ERX for every line from here on
+    const size_t es = elem_size(c->cfg.in_dtype);
+    erx_status s = erx_push_lines(c->audit, x, n, stride_elems * (int64_t)es, delta, dn, mask, det);
+    c->t += n;
+    return s;
+  }
   const int in_t = c->cfg.in_dtype;
   cudaStream_t st = c->stream;
   const void* zsrc = x;
@@ -199,6 +225,20 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
                    c->Z, st);
     zsrc = c->Z;
     ztype = c->fp64 ? ERX_F64 : ERX_F32;
+    zstride = (int64_t)W * d;
+    ps = d;
+  } else if (learned) {
+    KernelScope ks(c, ERX_K_ENCODE);
+    const float* xf = (const float*)x;
+    if (stride_elems == (int64_t)W * B) {
+      encoder_forward_on(c->enc, xf, (int64_t)T * W, (float*)c->Z, st);
+    } else {
+      for (int j = 0; j < T; ++j)
+        encoder_forward_on(c->enc, xf + j * stride_elems, W, (float*)c->Z + (int64_t)j * W * d,
+                           st);
+    }
+    zsrc = c->Z;
+    ztype = ERX_F32;
     zstride = (int64_t)W * d;
     ps = d;
   }
@@ -245,8 +285,84 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
     launch_normalise(c->fp64, delta, W, T, c->cfg.threshold, c->t, c->cfg.warmup_lines, dn,
                      mask, det, st);
   }
+  const erx_status rs = check_cuda(c, cudaGetLastError());
+  if (rs == ERX_OK && learned && c->audit_every > 0) {
+    const erx_status as = audit_block(c, x, n, stride_elems, delta);
+    c->t += n;
+    return as;
+  }
   c->t += n;
-  return check_cuda(c, cudaGetLastError());
+  return rs;
+}
+
+double spearman(const double* a, const double* b, int n) {
+  auto ranks = [n](const double* v) {
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [v](int x, int y) { return v[x] < v[y]; });
+    std::vector<double> r(n);
+    for (int i = 0; i < n;) {          // mid-ranks for ties
+      int j = i;
+      while (j + 1 < n && v[idx[j + 1]] == v[idx[i]]) ++j;
+      for (int q = i; q <= j; ++q) r[idx[q]] = 0.5 * (i + j);
+      i = j + 1;
+    }
+    return r;
+  };
+  const std::vector<double> ra = ranks(a), rb = ranks(b);
+  double ma = 0, mb = 0;
+  for (int i = 0; i < n; ++i) ma += ra[i], mb += rb[i];
+  ma /= n, mb /= n;
+  double sab = 0, saa = 0, sbb = 0;
+  for (int i = 0; i < n; ++i) {
+    sab += (ra[i] - ma) * (rb[i] - mb);
+    saa += (ra[i] - ma) * (ra[i] - ma);
+    sbb += (rb[i] - mb) * (rb[i] - mb);
+  }
+  return (saa > 0 && sbb > 0) ? sab / std::sqrt(saa * sbb) : 1.0;
+}
+
+// Score every audit_every-th line of the block with the full-band context and
+// compare the two rankings of that line's pixels.
+erx_status audit_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems, void* delta) {
+  const int64_t N = c->audit_every;
+  const int64_t j0 = (N - (c->t % N)) % N;
+  if (j0 >= n) return ERX_OK;
+  const int64_t m = (n - 1 - j0) / N + 1;
+  const int W = c->W;
+  const size_t es = elem_size(c->cfg.in_dtype);
+  const size_t ss = c->fp64 ? 8 : 4;
+  const char* xa = (const char*)x + j0 * stride_elems * (int64_t)es;
+  erx_status s = erx_push_lines(c->audit, xa, m, N * stride_elems * (int64_t)es, c->audit_delta,
+                                nullptr, nullptr, nullptr);
+  if (s != ERX_OK) return s;
+  c->h_learned.resize((size_t)m * W * ss);
+  c->h_full.resize((size_t)m * W * ss);
+  if (cudaStreamSynchronize(c->audit->stream) != cudaSuccess ||
+      cudaMemcpy2DAsync(c->h_learned.data(), W * ss, (const char*)delta + j0 * W * ss, N * W * ss,
+                        W * ss, (size_t)m, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->h_full.data(), c->audit_delta, (size_t)m * W * ss,
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return check_cuda(c, cudaGetLastError());
+  std::vector<double> a(W), b(W);
+  for (int64_t j = 0; j < m; ++j) {
+    for (int i = 0; i < W; ++i) {
+      const size_t o = (size_t)j * W + i;
+      a[i] = ss == 8 ? ((const double*)c->h_learned.data())[o] : ((const float*)c->h_learned.data())[o];
+      b[i] = ss == 8 ? ((const double*)c->h_full.data())[o] : ((const float*)c->h_full.data())[o];
+    }
+    const double rc = spearman(a.data(), b.data(), W);
+    c->last_corr = rc;
+    c->min_corr = std::isnan(c->min_corr) ? rc : std::min(c->min_corr, rc);
+    c->audits += 1;
+    if (rc < c->min_corr_thr && !c->fallback) {
+      c->fallback = true;
+      c->audit->cfg.momentum = c->cfg.momentum;
+      c->audit->t = c->t + n;       // next line the fallback scores is global line t + n
+    }
+  }
+  return ERX_OK;
 }
 
 }  // namespace
@@ -299,7 +415,7 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   c->cfg.srp_weights = nullptr;
   c->B = cfg->bands;
   c->W = cfg->width;
-  c->d = cfg->proj == ERX_PROJ_SRP ? cfg->proj_dim : cfg->bands;
+  c->d = cfg->proj != ERX_PROJ_NONE ? cfg->proj_dim : cfg->bands;
   c->stream = (cudaStream_t)cuda_stream;
   c->fp64 = cfg->form == ERX_FORM_FP64;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
@@ -329,8 +445,10 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   }
   // block size: keep the per-block scratch near 256 MiB
   const int64_t P = packed_size(d);
+  const bool learned = cfg->proj == ERX_PROJ_LEARNED;
   size_t per_line = (size_t)P * 8 * 2 + (size_t)d * 8 * 4 + (size_t)d * d * 8 +
-                    (c->fp64 ? 0 : (size_t)P * 4) + (c->w_host.empty() ? 0 : (size_t)W * d * 8);
+                    (c->fp64 ? 0 : (size_t)P * 4) +
+                    (c->w_host.empty() && !learned ? 0 : (size_t)W * d * 8);
   int T = cfg->block_lines > 0 ? cfg->block_lines
                                : (int)std::max<size_t>(1, (256ull << 20) / per_line);
   T = std::min(T, 4096);
@@ -361,6 +479,11 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   ERX_A(err, kErrSlots);
   if (ema_scratch_doubles(d, T) > 0) ERX_A(ema_scratch, ema_scratch_doubles(d, T));
 #undef ERX_A
+  if (s == ERX_OK && learned) {
+    float* zp = nullptr;
+    s = dalloc(c, &zp, (size_t)T * W * d);
+    c->Z = zp;
+  }
   if (s == ERX_OK && !c->w_host.empty()) {
     std::vector<int> cp(d + 1, 0), rw;
     std::vector<double> vl;
@@ -623,6 +746,40 @@ erx_status erx_get_projection(const erx_ctx* c, double* w) {
   return ERX_OK;
 }
 
+erx_status erx_set_encoder(erx_ctx* c, erx_encoder* enc, int32_t audit_every,
+                           double min_rank_corr) {
+  if (!c || !enc || audit_every < 0) return ERX_EINVAL;
+  if (c->cfg.proj != ERX_PROJ_LEARNED) return ERX_ESTATE;
+  if (encoder_k(enc) != c->d || encoder_bands(enc) != c->B) return ERX_EINVAL;
+  c->enc = enc;
+  c->audit_every = audit_every;
+  c->min_corr_thr = min_rank_corr;
+  if (audit_every > 0 && !c->audit) {
+    erx_config a = c->cfg;
+    a.proj = ERX_PROJ_NONE;
+    a.block_lines = std::max(1, c->T / audit_every + 1);
+    a.momentum = 1.0 - std::pow(1.0 - c->cfg.momentum, (double)audit_every);
+    erx_status s = erx_create(&a, c->stream, &c->audit);
+    if (s != ERX_OK) return s;
+    void* p = nullptr;
+    const size_t ss = c->fp64 ? 8 : 4;
+    s = dalloc(c, (char**)&p, (size_t)(c->T / audit_every + 1) * c->W * ss);
+    if (s != ERX_OK) return s;
+    c->audit_delta = p;
+  }
+  return ERX_OK;
+}
+
+erx_status erx_get_drift(erx_ctx* c, double* last_corr, double* min_corr, int64_t* audits,
+                         int32_t* fallback) {
+  if (!c) return ERX_EINVAL;
+  if (last_corr) *last_corr = c->last_corr;
+  if (min_corr) *min_corr = c->min_corr;
+  if (audits) *audits = c->audits;
+  if (fallback) *fallback = c->fallback ? 1 : 0;
+  return ERX_OK;
+}
+
 erx_status erx_profile_enable(erx_ctx* c, int32_t on) {
   if (!c) return ERX_EINVAL;
   c->profiling = on != 0;
@@ -648,7 +805,7 @@ const char* erx_kernel_name(int32_t k) {
   static const char* names[ERX_K_COUNT] = {"project",    "stats_int",  "mean",
                                            "stats_fp",   "ema_scan",   "chol",
                                            "solve_fp64", "solve_fp32", "normalise",
-                                           "stats_tc",   "solve_tc"};
+                                           "stats_tc",   "solve_tc",   "encode"};
   return (k >= 0 && k < ERX_K_COUNT) ? names[k] : nullptr;
 }
 

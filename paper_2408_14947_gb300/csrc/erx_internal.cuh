@@ -109,3 +109,10 @@ void launch_project(int in_type, const void* x, int64_t line_stride, int B, int 
                     void* z, cudaStream_t st);
 
 }  // namespace erx
+struct erx_encoder;
+namespace erx {
+int encoder_k(const ::erx_encoder* e);
+int encoder_bands(const ::erx_encoder* e);
+void encoder_forward_on(::erx_encoder* e, const float* x, int64_t n, float* codes,
+                        cudaStream_t st);
+}  // namespace erx

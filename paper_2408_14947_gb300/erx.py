@@ -16,7 +16,7 @@ lib_path = os.path.join(_PKG, "_lib", "liberx.so")
 ERX_OK, ERX_EINVAL, ERX_ENOMEM, ERX_ECUDA, ERX_ENOTPD, ERX_ERANGE, ERX_ESTATE, \
     ERX_EUNSUPPORTED, ERX_ETIMEOUT = range(9)
 ERX_FLAG_SIMT_STATS = 1
-ERX_PROJ_NONE, ERX_PROJ_SRP = 0, 1
+ERX_PROJ_NONE, ERX_PROJ_SRP, ERX_PROJ_LEARNED = 0, 1, 2
 ERX_UPDATE_THEN_SCORE, ERX_SCORE_THEN_UPDATE = 0, 1
 ERX_U16, ERX_F32, ERX_F64 = 0, 1, 2
 ERX_FORM_FP64, ERX_FORM_FP32, ERX_FORM_TF32, ERX_FORM_BF16 = 0, 1, 2, 3
@@ -33,6 +33,12 @@ class ErxConfig(C.Structure):
         ("threshold", C.c_double), ("block_lines", C.c_int32), ("flags", C.c_int32),
         ("srp_weights", C.POINTER(C.c_double)),
     ]
+
+
+class ErxTrainOpts(C.Structure):
+    _fields_ = [("momentum", C.c_double), ("ridge", C.c_double), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("weight_decay", C.c_float)]
 
 
 class ErxError(RuntimeError):
@@ -73,6 +79,20 @@ def load_library() -> C.CDLL:
         "erx_profile_read": (C.c_int, [P, I32, I32, C.POINTER(D), C.POINTER(I64),
                                        C.POINTER(I64)]),
         "erx_kernel_name": (C.c_char_p, [I32]),
+        "erx_train_opts_default": (None, [C.POINTER(ErxTrainOpts)]),
+        "erx_encoder_create": (C.c_int, [I32, I32, I32, U64, P, C.POINTER(P)]),
+        "erx_encoder_set_norm": (C.c_int, [P, P, P]),
+        "erx_encoder_params": (C.c_int, [P, P, P]),
+        "erx_encoder_nparams": (I64, [P]),
+        "erx_encoder_dims": (I32, [P, C.POINTER(I32), C.POINTER(I32)]),
+        "erx_encoder_reset_stats": (C.c_int, [P]),
+        "erx_encoder_forward": (C.c_int, [P, P, I64, P]),
+        "erx_encoder_train": (C.c_int, [P, P, I64, I32, P, C.POINTER(ErxTrainOpts), P]),
+        "erx_encoder_line_grad": (C.c_int, [P, P, I32, P, C.POINTER(ErxTrainOpts), P, P]),
+        "erx_encoder_destroy": (C.c_int, [P]),
+        "erx_set_encoder": (C.c_int, [P, P, I32, D]),
+        "erx_get_drift": (C.c_int, [P, C.POINTER(D), C.POINTER(D), C.POINTER(I64),
+                                    C.POINTER(I32)]),
         "erx_batch_create": (C.c_int, [I32, C.POINTER(ErxConfig), P, C.POINTER(P)]),
         "erx_batch_buffers": (C.c_int, [P, I32, C.POINTER(P), C.POINTER(P), C.POINTER(P),
                                         C.POINTER(P), C.POINTER(P)]),
@@ -177,7 +197,7 @@ def erx_srp_weights(bands: int, dim: int, seed: int):
     return w
 
 
-ERX_K_COUNT = 11
+ERX_K_COUNT = 12
 
 
 def erx_push_lines_static(cfg, stream, mu_ptr, k_ptr, t, lines_ptr, n_lines, stride_bytes,
@@ -222,12 +242,15 @@ class Detector:
     def __init__(self, bands, width, momentum=0.1, proj="none", proj_dim=5, seed=0, ridge=1e-5,
                  warmup=99, order="update_then_score", in_dtype="f32", in_bits=16,
                  form="fp64", threshold=3.0, block_lines=0, srp_weights=None, stream=None,
-                 simt_stats=False):
+                 simt_stats=False, encoder=None, audit_every=0, min_rank_corr=0.0):
         import torch
         self.torch = torch
         cfg = erx_config_default(bands, width)
         cfg.momentum = momentum
-        cfg.proj = {"none": ERX_PROJ_NONE, "srp": ERX_PROJ_SRP}[proj]
+        cfg.proj = {"none": ERX_PROJ_NONE, "srp": ERX_PROJ_SRP,
+                    "learned": ERX_PROJ_LEARNED}[proj if encoder is None else "learned"]
+        if encoder is not None:
+            proj_dim = encoder.k
         cfg.proj_dim = proj_dim
         cfg.seed = seed
         cfg.ridge = ridge
@@ -255,6 +278,10 @@ class Detector:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = erx_create(cfg, self.stream.cuda_stream)
         self.dim = erx_dim(self.ctx)
+        self.encoder = encoder
+        if encoder is not None:
+            _check(load_library().erx_set_encoder(self.ctx, encoder.e, audit_every,
+                                                  min_rank_corr), "erx_set_encoder")
 
     def push(self, lines, out=None):
         torch = self.torch
@@ -295,6 +322,13 @@ class Detector:
 
     def projection(self):
         return erx_get_projection(self.ctx, self.bands)
+
+    def drift(self):
+        """(last rank correlation, lowest, audits, fallback active)."""
+        last, low, n, fb = C.c_double(), C.c_double(), C.c_int64(), C.c_int32()
+        _check(load_library().erx_get_drift(self.ctx, C.byref(last), C.byref(low), C.byref(n),
+                                            C.byref(fb)), "erx_get_drift")
+        return last.value, low.value, n.value, bool(fb.value)
 
     def profile(self, on: bool = True):
         erx_profile_enable(self.ctx, on)
@@ -430,3 +464,97 @@ class _DevBuf:
 def _device_view(ptr, shape, typestr):
     import torch
     return torch.as_tensor(_DevBuf(ptr, shape, typestr), device="cuda")
+
+
+def erx_train_opts_default() -> ErxTrainOpts:
+    o = ErxTrainOpts()
+    load_library().erx_train_opts_default(C.byref(o))
+    return o
+
+
+class Encoder:
+    """Learned band encoder (erx_encoder_*): bands -> hidden -> k, trained on the GPU."""
+
+    def __init__(self, bands=224, hidden=128, k=32, seed=0, stream=None):
+        import torch
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(load_library().erx_encoder_create(bands, hidden, k, C.c_uint64(seed),
+                                                 C.c_void_p(self.stream.cuda_stream),
+                                                 C.byref(h)), "erx_encoder_create")
+        self.e = h.value
+        self.bands, self.hidden, self.k = bands, hidden, k
+        self.nparams = int(load_library().erx_encoder_nparams(self.e))
+
+    def set_norm(self, shift, scale):
+        import numpy as np
+        s = np.ascontiguousarray(shift, np.float32)
+        c = np.ascontiguousarray(scale, np.float32)
+        _check(load_library().erx_encoder_set_norm(self.e, s.ctypes.data, c.ctypes.data),
+               "erx_encoder_set_norm")
+
+    def params(self, new=None):
+        """Current parameter vector (numpy float32); `new` replaces it first."""
+        import numpy as np
+        out = np.zeros(self.nparams, np.float32)
+        src = None
+        if new is not None:
+            src = np.ascontiguousarray(new, np.float32)
+        _check(load_library().erx_encoder_params(self.e, out.ctypes.data,
+                                                 None if src is None else src.ctypes.data),
+               "erx_encoder_params")
+        return out
+
+    def split(self, theta):
+        b, h, k = self.bands, self.hidden, self.k
+        o1 = h * b
+        return {"W1": theta[:o1].reshape(h, b), "b1": theta[o1:o1 + h],
+                "W2": theta[o1 + h:o1 + h + k * h].reshape(k, h), "b2": theta[o1 + h + k * h:]}
+
+    def reset_stats(self):
+        _check(load_library().erx_encoder_reset_stats(self.e), "erx_encoder_reset_stats")
+
+    def forward(self, x):
+        """x: CUDA float32 [..., bands] -> codes [..., k]."""
+        torch = self.torch
+        xc = x.contiguous()
+        n = xc.numel() // self.bands
+        out = torch.empty(xc.shape[:-1] + (self.k,), dtype=torch.float32, device=x.device)
+        _check(load_library().erx_encoder_forward(self.e, xc.data_ptr(), n, out.data_ptr()),
+               "erx_encoder_forward")
+        return out
+
+    def train(self, lines, targets, opts=None, want_loss=False):
+        """lines: CUDA float32 [n][p][bands]; targets: CUDA float64 [n][p]."""
+        import numpy as np
+        opts = opts or erx_train_opts_default()
+        n, p, _ = lines.shape
+        loss = np.zeros(n, np.float32) if want_loss else None
+        _check(load_library().erx_encoder_train(
+            self.e, lines.data_ptr(), n, p, targets.data_ptr(), C.byref(opts),
+            None if loss is None else loss.ctypes.data), "erx_encoder_train")
+        return loss
+
+    def line_grad(self, line, target, opts=None):
+        import numpy as np
+        opts = opts or erx_train_opts_default()
+        g = np.zeros(self.nparams, np.float32)
+        loss = C.c_float()
+        p = line.shape[0]
+        _check(load_library().erx_encoder_line_grad(self.e, line.data_ptr(), p,
+                                                    target.data_ptr(), C.byref(opts),
+                                                    g.ctypes.data, C.byref(loss)),
+               "erx_encoder_line_grad")
+        return g, loss.value
+
+    def close(self):
+        if self.e:
+            load_library().erx_encoder_destroy(self.e)
+            self.e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

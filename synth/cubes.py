@@ -72,6 +72,8 @@ class SceneConfig:
     cluster: int = 1
     dn_max: int = 0
     scale: float = 1.0            # multiplies reflectance before storage (f32 only)
+    anomaly_mix: tuple | None = None  # (lo, hi): anomalies are (1-f) background + f target,
+                                      # f ~ U(lo, hi) per pixel (weak, sub-pixel targets)
 
     @property
     def dtype(self):
@@ -215,8 +217,14 @@ def _line_mix(cfg: SceneConfig, t: int, cache: dict) -> np.ndarray:
     x += r.standard_normal((cfg.width, cfg.bands), dtype=np.float32) * np.float32(cfg.noise)
     m = _cluster_mask(cfg, t)
     if m.any():
-        x[m] = anom.astype(np.float32) + r.standard_normal(
-            (int(m.sum()), cfg.bands), dtype=np.float32) * np.float32(cfg.noise)
+        na = int(m.sum())
+        target = anom.astype(np.float32) + r.standard_normal(
+            (na, cfg.bands), dtype=np.float32) * np.float32(cfg.noise)
+        if cfg.anomaly_mix is None:
+            x[m] = target
+        else:
+            f = r.uniform(cfg.anomaly_mix[0], cfg.anomaly_mix[1], size=(na, 1)).astype(np.float32)
+            x[m] = (1.0 - f) * x[m] + f * target
     np.clip(x, 0.0, 1.0, out=x)
     if cfg.dn_max > 0:
         return np.rint(x * np.float32(cfg.dn_max)).astype(np.uint16)
