@@ -43,7 +43,12 @@ def _gen_worker(args):
     shm = shared_memory.SharedMemory(name=name)
     try:
         arr = np.ndarray(shape, dtype=dtype, buffer=shm.buf)
-        cfg = synth.dn_c2(**cfg_kw) if kind == "c2" else synth.cov_c3(**cfg_kw)
+        if kind == "c2":
+            cfg = synth.dn_c2(**cfg_kw)
+        elif kind == "c5":
+            cfg = c5_config(**cfg_kw)
+        else:
+            cfg = synth.cov_c3(**cfg_kw)
         synth.gen_lines(cfg, t0, n, out=arr[t0:t0 + n])
     finally:
         shm.close()
@@ -63,7 +68,7 @@ def make_cube(n_lines: int, seed: int = 0, workers: int | None = None, kind: str
     nbytes = int(np.prod(shape)) * np.dtype(dtype).itemsize
     workers = workers or min(16, len(os.sched_getaffinity(0)))
     kw = {"seed": seed, "width": width, "bands": bands}
-    if kind != "c2":
+    if kind == "c3":
         kw["kappa"] = kappa
     shm = shared_memory.SharedMemory(create=True, size=nbytes)
     try:
@@ -78,6 +83,15 @@ def make_cube(n_lines: int, seed: int = 0, workers: int | None = None, kind: str
         shm.close()
         shm.unlink()
     return out
+
+
+def c5_config(seed=0, width=1024, bands=224):
+    """224-band reflectance stream with weak targets: 1 % of pixels in 3 x 3
+    clusters mix a target spectrum into the background at 5-30 %."""
+    import synth
+    return synth.SceneConfig(bands=bands, width=width, seed=seed, n_end=(3, 5), noise=0.01,
+                             scene_lines=2000, drift=0.05, anomaly_frac=0.01, cluster=3,
+                             anomaly_mix=(0.05, 0.3))
 
 
 def dist_info():
@@ -269,6 +283,71 @@ def bench_batched(dev, stream, n_streams: int = 256, n_lines: int = 4, steps: in
     return out
 
 
+def bench_learned(dev, stream, n_train: int = 2000, n_test: int = 200):
+    """Train the 224 -> 128 -> 32 encoder on n_train lines x 1024 px (about 2e6
+    spectra) against full-band FP64 ERX scores, then compare the learned form
+    with full-band ERX and SRP-32 on held-out lines: lines/s, per-line AUC of
+    the planted weak targets, rank correlation with full-band scores."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2408_14947_gb300 import Detector, Encoder, erx_train_opts_default
+    W, B, K = 1024, 224, 32
+    cube = make_cube(n_train + n_test, seed=11, kind="c5", width=W, bands=B)
+    labels = synth.anomaly_mask(c5_config(seed=11, width=W, bands=B), n_train, n_test)
+    flat = cube[:200].reshape(-1, B)
+    shift, scale = flat.mean(0), 1.0 / (flat.std(0) + 1e-3)
+    x = torch.from_numpy(cube).to(dev)
+    del cube, flat
+    full = Detector(B, W, in_dtype="f32", form="fp64", warmup=0, stream=stream)
+    fd = full.push(x)[0]
+    full.sync()
+    full.close()
+    enc = Encoder(B, 128, K, seed=0, stream=stream)
+    enc.set_norm(shift, scale)
+    o = erx_train_opts_default()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    enc.train(x[:n_train], fd[:n_train], o)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    xt = x[n_train:]
+    out = {"workload": f"{n_train} training lines + {n_test} held-out lines x {W} px x {B} "
+                       "bands f32, weak 3x3 targets (5-30 % mixing)",
+           "train_spectra": n_train * W, "train_seconds": train_s,
+           "train_spectra_per_s": n_train * W / train_s}
+
+    def auc(score, lab):
+        pos, neg = score[lab], score[~lab]
+        allv = np.concatenate([pos, neg])
+        r = np.argsort(np.argsort(allv)) + 1.0
+        return (r[:pos.size].sum() - pos.size * (pos.size + 1) / 2) / (pos.size * neg.size)
+
+    def rank_corr(a, b):
+        return np.corrcoef(np.argsort(np.argsort(a)), np.argsort(np.argsort(b)))[0, 1]
+
+    ref = fd[n_train:].cpu().numpy()
+    rows = {}
+    for name, kw in (("learned_fp32", {"form": "fp32", "encoder": enc}),
+                     ("learned_fp64", {"form": "fp64", "encoder": enc}),
+                     ("srp32_fp32", {"form": "fp32", "proj": "srp", "proj_dim": 32, "seed": 5}),
+                     ("full_fp64", {"form": "fp64"}), ("full_fp32", {"form": "fp32"}),
+                     ("full_bf16", {"form": "bf16"})):
+        speed = time_form(lambda **k: Detector(B, W, in_dtype="f32", warmup=0, stream=stream, **k),
+                          xt, kw, dev, stream)
+        d_ = Detector(B, W, in_dtype="f32", warmup=0, stream=stream, **kw)
+        s_ = d_.push(xt)[0].cpu().numpy()
+        d_.close()
+        aucs = [auc(s_[t], labels[t]) for t in range(n_test) if labels[t].any()]
+        rows[name] = {"lines_per_s": speed["lines_per_s"], "auc": float(np.mean(aucs)),
+                      "rank_corr_full": float(np.mean([rank_corr(s_[t], ref[t])
+                                                       for t in range(n_test)]))}
+    out["forms"] = rows
+    enc.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -418,6 +497,9 @@ def run_ours(args):
 
         # batched form: 256 streams, widths U{128..2048}, bands from {8,16,64,108,224}
         result["batched"] = bench_batched(dev, stream)
+
+        # learned form: encoder trained on the method's own full-band scores
+        result["learned"] = bench_learned(dev, stream)
 
         # end to end through the public host-buffer call: pinned input, results to host
         xh = torch.from_numpy(cube.view(np.int16)).pin_memory()
