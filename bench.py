@@ -540,7 +540,10 @@ def main():
     ap.add_argument("--ref-lines", type=int, default=1000)
     ap.add_argument("--latency-lines", type=int, default=5000)
     ap.add_argument("--quick", action="store_true", help="skip latency, forms, e2e, baseline")
+    ap.add_argument("--lines", type=int, default=LINES,
+                    help="lines of the workload cube (smaller cubes for profiler captures)")
     args = ap.parse_args()
+    globals()["LINES"] = args.lines
     if args.impl == "reference":
         run_reference(args)
     else:
