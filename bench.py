@@ -429,9 +429,15 @@ def run_ours(args):
         peak, unit, bound = IMAD_PEAK_GOPS * 2, "GOP/s", "alu"
     else:
         peak, unit, bound = FP64_PEAK_GFLOPS, "GFLOP/s", "alu"
+    # DRAM bytes (read + write) of one solve_fp64 launch from the ncu capture in
+    # profiles/solve_fp64_c2_2000x640x108.md: 271.5 MB for 1405 lines, scaled to
+    # this run's average lines per launch (traffic grows with the lines).
+    traffic = 271.5e6 * lines_per_launch / 1405.0 if dom == "solve_fp64" else None
     roof = {"bound": bound, "pipe": "fp64" if dom != "stats_int" else "int32", "kernel": dom,
             "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-            "traffic": None, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2070 MHz"}
+            "traffic": traffic, "algorithmic_bytes": (WIDTH * BANDS * 2 + WIDTH * 8 +
+                                                      8 * BANDS * (BANDS + 1) / 2) * lines_per_launch,
+            "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2070 MHz"}
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[2] / args.steps,
                    "share": v[0] / max(1e-9, sum(w[0] for w in prof.values()))}
                for k, v in prof.items() if v[2]}
