@@ -8,7 +8,7 @@
 // d/32 small inverses (d * 32^2 / 6 DFMA) instead of the full d^3/6.
 //
 // The packed factor (d(d+1)/2 doubles, 197 KiB at d = 224) lives in shared
-// memory.  Right-looking Cholesky: per column j the pivot is checked and
+// memory; each pivot takes one reciprocal square root (l_jj = a_jj rsqrt(a_jj)).  Right-looking Cholesky: per column j the pivot is checked and
 // square-rooted, the column scaled, and the trailing triangle updated
 // A_ik -= l_ij l_kj with its elements spread evenly over all threads (the FP64
 // pipe is 2 lanes/clk/SM on GB300, so idle lanes of a partial warp cost as
@@ -36,7 +36,8 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   extern __shared__ __align__(16) double sm[];
   const int P = d * (d + 1) / 2;
   double* A = sm;
-  double* col = sm + P;
+  double* col = sm + P;          // scaled column of the current step
+  double* rdiag = col + d;       // 1 / l_jj
   __shared__ double s_inv;
   for (int q = threadIdx.x; q < P; q += kThreads) A[q] = src[q];
   __syncthreads();
@@ -50,9 +51,10 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
         atomicMin(&err[kErrNotPD], (unsigned long long)line);
         ajj = __longlong_as_double(0x7ff8000000000000ll);
       }
-      const double l = sqrt(ajj);
-      A[pidx(j, j)] = l;
-      s_inv = 1.0 / l;
+      const double ri = rsqrt(ajj);                   // 1 / l_jj
+      A[pidx(j, j)] = ajj * ri;                       // l_jj
+      s_inv = ri;
+      rdiag[j] = ri;
     }
     __syncthreads();
     const double inv = s_inv;
@@ -77,34 +79,29 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
     __syncthreads();
   }
 
-  for (int i = threadIdx.x; i < d; i += kThreads) col[i] = 1.0 / A[pidx(i, i)];
   __syncthreads();
-  // invert each 32 x 32 diagonal block: warp w takes blocks w, w + 8, ...
+  // invert each 32 x 32 diagonal block in place, warp w taking blocks w, w + 8, ...:
+  // columns right to left; with T = the already inverted trailing part of the
+  // block, column j becomes -(1/l_jj) T l_col (lane i computes row i), so no
+  // per-lane arrays are needed and the kernel keeps few registers.
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (d + kNB - 1) / kNB;
   for (int bk = warp; bk < nblk; bk += kThreads / 32) {
     const int j0 = bk * kNB;
     const int nb = min(kNB, d - j0);
-    // lane c: column c of the block inverse, x_i for i >= c (x_c = 1 / L_cc)
-    double x[kNB];
-#pragma unroll
-    for (int i = 0; i < kNB; ++i) x[i] = 0.0;
-    const int c = lane;
-#pragma unroll
-    for (int i = 0; i < kNB; ++i) {
-      if (i < nb && i >= c) {
-        double s = (i == c) ? 1.0 : 0.0;
-#pragma unroll
-        for (int k = 0; k < i; ++k)
-          if (k >= c) s = fma(-A[pidx(j0 + i, j0 + k)], x[k], s);
-        x[i] = s * col[j0 + i];
+    for (int j = nb - 1; j >= 0; --j) {
+      const double djj = rdiag[j0 + j];               // 1 / l_jj
+      const int i = lane;
+      double s = 0.0;
+      if (i > j && i < nb) {
+        const double* Ti = A + pidx(j0 + i, j0);
+        for (int k = j + 1; k <= i; ++k) s = fma(Ti[k], A[pidx(j0 + k, j0 + j)], s);
       }
+      __syncwarp();
+      if (i > j && i < nb) A[pidx(j0 + i, j0 + j)] = -djj * s;
+      if (i == j) A[pidx(j0 + j, j0 + j)] = djj;
+      __syncwarp();
     }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < kNB; ++i)
-      if (i < nb && i >= c) A[pidx(j0 + i, j0 + c)] = x[i];
-    __syncwarp();
   }
   __syncthreads();
   for (int q = threadIdx.x; q < P; q += kThreads) dst[q] = A[q];
@@ -113,7 +110,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   }
 }
 
-__global__ void __launch_bounds__(kThreads) chol_kernel(const double* __restrict__ K_t, int d,
+__global__ void __launch_bounds__(kThreads, 4) chol_kernel(const double* __restrict__ K_t, int d,
                                                        double ridge, double* __restrict__ Lf,
                                                        float* __restrict__ Lf32,
                                                        unsigned long long* __restrict__ err,
@@ -124,7 +121,7 @@ __global__ void __launch_bounds__(kThreads) chol_kernel(const double* __restrict
 }
 
 // Batched form: one CTA per stream.
-__global__ void __launch_bounds__(kThreads) b_chol_kernel(const BStream* __restrict__ S,
+__global__ void __launch_bounds__(kThreads, 4) b_chol_kernel(const BStream* __restrict__ S,
                                                          bool want32,
                                                          unsigned long long* __restrict__ err) {
   const BStream& s = S[blockIdx.x];
@@ -134,7 +131,7 @@ __global__ void __launch_bounds__(kThreads) b_chol_kernel(const BStream* __restr
 }  // namespace
 
 cudaError_t configure_factor_kernels() {
-  const int m = (int)((packed_size(kMaxDim) + kMaxDim) * sizeof(double));
+  const int m = (int)((packed_size(kMaxDim) + 2 * kMaxDim) * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(b_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
@@ -143,13 +140,13 @@ cudaError_t configure_factor_kernels() {
 
 void launch_batch_chol(const BStream* S, int n, int dmax, bool want32, unsigned long long* err,
                        cudaStream_t st) {
-  const size_t smem = (size_t)(packed_size(dmax) + dmax) * sizeof(double);
+  const size_t smem = (size_t)(packed_size(dmax) + 2 * dmax) * sizeof(double);
   b_chol_kernel<<<n, kThreads, smem, st>>>(S, want32, err);
 }
 
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, float* Lf32,
                      unsigned long long* err, int64_t t0, cudaStream_t st) {
-  const size_t smem = (size_t)(packed_size(d) + d) * sizeof(double);
+  const size_t smem = (size_t)(packed_size(d) + 2 * d) * sizeof(double);
   chol_kernel<<<T, kThreads, smem, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
 }
 

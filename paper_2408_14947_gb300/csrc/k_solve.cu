@@ -62,15 +62,13 @@ __device__ __forceinline__ void solve_fp64_body(const InT* __restrict__ x, int p
       if (jj < nb) {
         const int j = j0 + jj;
         const double* Lj = L + j * (j + 1) / 2;
-        double a0 = rr[j], a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int k = 0;
-        for (; k + 4 <= j0; k += 4) {
+        // two chains (one combining addition per row); j0 is a multiple of 32
+        double a0 = rr[j], a1 = 0.0;
+        for (int k = 0; k < j0; k += 2) {
           a0 = fma(-__ldg(Lj + k), rr[k], a0);
           a1 = fma(-__ldg(Lj + k + 1), rr[k + 1], a1);
-          a2 = fma(-__ldg(Lj + k + 2), rr[k + 2], a2);
-          a3 = fma(-__ldg(Lj + k + 3), rr[k + 3], a3);
         }
-        y[jj] = (j0 > 0) ? (a0 + a1) + (a2 + a3) : a0;
+        y[jj] = (j0 > 0) ? a0 + a1 : a0;
       }
     }
 #pragma unroll
