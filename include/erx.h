@@ -333,7 +333,8 @@ enum {
   ERX_K_STATS_TC = 9,   /* S2 exact integer sums on the tensor cores */
   ERX_K_SOLVE_TC = 10,  /* S5 scores on the tensor cores (TF32 / BF16) */
   ERX_K_ENCODE = 11,    /* S1 learned band encoder (codes) */
-  ERX_K_COUNT = 12
+  ERX_K_TRINV = 12,     /* S4 full inverse of the factor in FP32 (FP32/TF32/BF16 forms) */
+  ERX_K_COUNT = 13
 };
 
 /* Per-kernel timing.  While enabled (on != 0), every kernel the context

@@ -166,6 +166,7 @@ void enqueue_step(erx_batch* b, cudaStream_t st) {
   launch_batch_stats(b->table, b->stats_items, b->n_stats, fp64, st);
   launch_batch_ema(b->table, b->ema_items, b->n_ema, st);
   launch_batch_chol(b->table, b->n, b->dmax, !fp64, b->err, st);
+  if (!fp64) launch_batch_trinv32(b->table, b->n, b->dmax, st);
   for (int r = 0; r < 4; ++r) {
     if (!b->n_solve[r]) continue;
     if (r <= 1) launch_batch_solve_simt(r, b->table, b->solve_items[r], b->n_solve[r], b->dmax, st);

@@ -269,6 +269,10 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
     launch_chol_inv(c->K_t, d, T, c->cfg.ridge, c->Linv, c->fp64 ? nullptr : c->Linv32, c->err,
                     c->t, st);
   }
+  if (!c->fp64) {
+    KernelScope ks(c, ERX_K_TRINV);
+    launch_trinv32(c->Linv32, d, T, st);
+  }
   if (c->fp64) {
     KernelScope ks(c, ERX_K_SOLVE_FP64);
     launch_solve_fp64(ztype, zsrc, zstride, ps, W, d, T, c->mu_t, c->Linv, (double*)delta, st);
@@ -805,7 +809,8 @@ const char* erx_kernel_name(int32_t k) {
   static const char* names[ERX_K_COUNT] = {"project",    "stats_int",  "mean",
                                            "stats_fp",   "ema_scan",   "chol",
                                            "solve_fp64", "solve_fp32", "normalise",
-                                           "stats_tc",   "solve_tc",   "encode"};
+                                           "stats_tc",   "solve_tc",   "encode",
+                                           "trinv32"};
   return (k >= 0 && k < ERX_K_COUNT) ? names[k] : nullptr;
 }
 

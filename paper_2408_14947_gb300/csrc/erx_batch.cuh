@@ -40,6 +40,7 @@ void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t s
 void launch_batch_stats(const BStream* S, const BItem* items, int n_items, bool fp64,
                         cudaStream_t st);
 void launch_batch_ema(const BStream* S, const BItem* items, int n_items, cudaStream_t st);
+void launch_batch_trinv32(const BStream* S, int n, int dmax, cudaStream_t st);
 void launch_batch_chol(const BStream* S, int n, int dmax, bool want32,
                        unsigned long long* err, cudaStream_t st);
 void launch_batch_solve(int route, const BStream* S, const BItem* items, int n_items, int dmax,

@@ -82,6 +82,9 @@ void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Linv, float* Linv32,
                      unsigned long long* err, int64_t t0, cudaStream_t st);
 
+// In place: the float blocked factor of T lines becomes the full L^{-1} (FP32).
+void launch_trinv32(float* Lf32, int d, int T, cudaStream_t st);
+
 // delta_i = || m_i ||, L m_i = z_i - mu_t solved block by block, FP64 arithmetic.
 void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
                        int T, const double* mu_t, const double* Linv, double* delta,

@@ -128,13 +128,83 @@ __global__ void __launch_bounds__(kThreads, 4) b_chol_kernel(const BStream* __re
   chol_body(s.K_t, s.d, s.ridge, s.Lf, want32 ? s.Lf32 : nullptr, err, blockIdx.x);
 }
 
+// Full inverse X = L^{-1} in FP32 from the float blocked factor, for the FP32,
+// TF32 and BF16 forms (their score kernels then apply X with one triangular
+// product instead of a block-by-block solve).  One CTA per line, in place in
+// shared memory and in the caller's buffer.  Column blocks left to right, row
+// blocks top to bottom:  X_KK = D_K (already stored),
+//   X_JK = -D_J (sum_{M=K}^{J-1} L_JM X_MK),   J > K,
+// which reads only L entries of rows >= J and X entries of column block K
+// above row block J, so X_JK can overwrite L_JK.  d^3/6 FP32 multiply-adds.
+__device__ __forceinline__ void trinv32_body(float* __restrict__ Lf32, int d) {
+  extern __shared__ __align__(16) float S[];
+  __shared__ float Tm[kNB * kNB];
+  const int P = d * (d + 1) / 2;
+  for (int q = threadIdx.x; q < P; q += kThreads) S[q] = Lf32[q];
+  __syncthreads();
+  const int nblk = (d + kNB - 1) / kNB;
+  for (int K = 0; K < nblk; ++K) {
+    const int k0 = K * kNB, k1 = min(d, k0 + kNB);
+    for (int J = K + 1; J < nblk; ++J) {
+      const int j0 = J * kNB, j1 = min(d, j0 + kNB);
+      // T = sum_M L_JM X_MK over columns m in [k0, j0)
+      for (int e = threadIdx.x; e < kNB * kNB; e += kThreads) {
+        const int jj = e / kNB, kk = e % kNB;
+        const int j = j0 + jj, k = k0 + kk;
+        float acc = 0.f;
+        if (j < j1 && k < k1) {
+          const float* Lj = S + pidx(j, 0);
+          for (int m = k; m < j0; ++m) acc = fmaf(Lj[m], S[pidx(m, k)], acc);
+        }
+        Tm[e] = acc;
+      }
+      __syncthreads();
+      // X_JK = -D_J T (D_J lower triangular, rows j, cols i <= j of block J)
+      for (int e = threadIdx.x; e < kNB * kNB; e += kThreads) {
+        const int jj = e / kNB, kk = e % kNB;
+        const int j = j0 + jj, k = k0 + kk;
+        if (j < j1 && k < k1) {
+          const float* Dj = S + pidx(j, j0);
+          float acc = 0.f;
+          for (int ii = 0; ii <= jj; ++ii) acc = fmaf(Dj[ii], Tm[ii * kNB + kk], acc);
+          S[pidx(j, k)] = -acc;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int q = threadIdx.x; q < P; q += kThreads) Lf32[q] = S[q];
+}
+
+__global__ void __launch_bounds__(kThreads) trinv32_kernel(float* __restrict__ Lf32, int d) {
+  trinv32_body(Lf32 + (int64_t)blockIdx.x * packed_size(d), d);
+}
+
+__global__ void __launch_bounds__(kThreads) b_trinv32_kernel(const BStream* __restrict__ S) {
+  const BStream& s = S[blockIdx.x];
+  trinv32_body(s.Lf32, s.d);
+}
+
 }  // namespace
+
+void launch_trinv32(float* Lf32, int d, int T, cudaStream_t st) {
+  trinv32_kernel<<<T, kThreads, (size_t)packed_size(d) * sizeof(float), st>>>(Lf32, d);
+}
+
+void launch_batch_trinv32(const BStream* S, int n, int dmax, cudaStream_t st) {
+  b_trinv32_kernel<<<n, kThreads, (size_t)packed_size(dmax) * sizeof(float), st>>>(S);
+}
 
 cudaError_t configure_factor_kernels() {
   const int m = (int)((packed_size(kMaxDim) + 2 * kMaxDim) * sizeof(double));
   cudaError_t e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(b_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+  const int m32 = (int)(packed_size(kMaxDim) * sizeof(float));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(trinv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m32);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(b_trinv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m32);
   return e;
 }
 

@@ -1,21 +1,21 @@
 // S5 (Sec. III-D): delta_i = sqrt(m_i . m_i) with L_t m_i = z_i - mu_t.
 //
-// Both forms solve block by block with the blocked factor of k_factor.cu
+// FP64 form: solves block by block with the blocked factor of k_factor.cu
 // (packed L_t whose 32 x 32 diagonal blocks hold D_J = L_JJ^{-1}):
 //   y_J = r_J - sum_{k < j0} L_Jk m_k,   m_J = D_J y_J,
 // exactly d(d+1)/2 multiply-adds per pixel, as forward substitution.
-//
-// FP64 form: one thread per pixel.  The pixel's centred vector r_i is staged
+// one thread per pixel.  The pixel's centred vector r_i is staged
 // in shared memory (odd row pitch, so the 8-byte loads of a warp hit distinct
 // bank pairs) and overwritten by m_i block by block; rows of the factor are
 // read with warp-uniform loads; the 32 values y_J of a block sit in
 // registers.  The kernel is bound by the FP64 pipe (2 DFMA/clk/SM on GB300).
 //
-// FP32 form: register-tiled over pixels x outputs.  A CTA owns 64 pixels;
-// four warps cover 64 pixels x 32 outputs of a block, each thread a 4 x 4
-// tile; R^T (then M^T) is kept k-major in shared memory and each 32-row band
-// of the factor is staged k-major, so both operand loads are 16-byte and
-// conflict-free.  The centred samples are (x - mu_hi) - mu_lo with mu split
+// FP32 form: with the full inverse X = L^{-1} (FP32, from the blocked factor),
+// m = X r is one lower-triangular product, register-tiled over pixels x
+// outputs.  A CTA owns 64 pixels; four warps cover 64 pixels x 32 outputs of
+// a block, each thread a 4 x 4 tile; R^T is kept k-major in shared memory and
+// each 32-row band of X is staged k-major, so both operand loads are 16-byte
+// and conflict-free.  The centred samples are (x - mu_hi) - mu_lo with mu split
 // into two floats, which keeps r accurate to float rounding without FP64 work
 // per pixel.
 #include <cmath>
@@ -105,9 +105,8 @@ __device__ __forceinline__ void solve_fp32_body(const InT* __restrict__ x, int p
                                                 const float* __restrict__ Lg,
                                                 float* __restrict__ delta, int tile) {
   extern __shared__ __align__(16) float smf[];
-  float* rT = smf;                          // [d][kPixF32]: r, then m, k-major
-  float* LT = smf + d * kPixF32;            // [d][kOutB]: factor band, k-major
-  float* yT = LT + d * kOutB;               // [kOutB][kPixF32]
+  float* rT = smf;                          // [d][kPixF32]: r, k-major
+  float* LT = smf + d * kPixF32;            // [d][kOutB]: rows of L^{-1}, k-major
   __shared__ float mu_hi[kMaxDim], mu_lo[kMaxDim];
   __shared__ float d2w[2][kPixF32];
   const int i0 = tile * kPixF32;
@@ -138,56 +137,27 @@ __device__ __forceinline__ void solve_fp32_body(const InT* __restrict__ x, int p
       LT[k * kOutB + jj] = (j < d && k <= j) ? Lg[j * (j + 1) / 2 + k] : 0.f;
     }
     __syncthreads();
+    // m_J = X_{J, k < j1} r (X = L^{-1}: lower triangular, zeros above the diagonal)
     float acc[4][4];
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = j0 + ocol + b;
-#pragma unroll
-      for (int a = 0; a < 4; ++a) acc[a][b] = j < d ? rT[j * kPixF32 + pcol + a] : 0.f;
-    }
-#pragma unroll 4
-    for (int k = 0; k < j0; ++k) {
-      const float4 mv = *reinterpret_cast<const float4*>(rT + k * kPixF32 + pcol);
-      const float4 lv = *reinterpret_cast<const float4*>(LT + k * kOutB + ocol);
-      const float ma[4] = {mv.x, mv.y, mv.z, mv.w};
-      const float la[4] = {lv.x, lv.y, lv.z, lv.w};
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(-ma[a], la[b], acc[a][b]);
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) yT[(ocol + b) * kPixF32 + pcol + a] = acc[a][b];
-    __syncthreads();
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    const int nb = j1 - j0;
 #pragma unroll 4
-    for (int kk = 0; kk < nb; ++kk) {
-      const float4 yv = *reinterpret_cast<const float4*>(yT + kk * kPixF32 + pcol);
-      const float4 lv = *reinterpret_cast<const float4*>(LT + (j0 + kk) * kOutB + ocol);
-      const float ya[4] = {yv.x, yv.y, yv.z, yv.w};
+    for (int k = 0; k < j1; ++k) {
+      const float4 rv = *reinterpret_cast<const float4*>(rT + k * kPixF32 + pcol);
+      const float4 lv = *reinterpret_cast<const float4*>(LT + k * kOutB + ocol);
+      const float ra[4] = {rv.x, rv.y, rv.z, rv.w};
       const float la[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ya[a], la[b], acc[a][b]);
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ra[a], la[b], acc[a][b]);
     }
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int j = j0 + ocol + b;
-      if (j < d) {
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          rT[j * kPixF32 + pcol + a] = acc[a][b];
-          d2[a] = fmaf(acc[a][b], acc[a][b], d2[a]);
-        }
-      }
-    }
+      for (int b = 0; b < 4; ++b) d2[a] = fmaf(acc[a][b], acc[a][b], d2[a]);
   }
   // reduce over the 4 output groups of a warp (lane bits 3, 4), then the 2 output halves
 #pragma unroll
@@ -233,7 +203,7 @@ __global__ void __launch_bounds__(128) b_solve_fp32_kernel(const BStream* __rest
 
 size_t smem_fp64(int d) { return (size_t)kPixF64 * (d | 1) * sizeof(double); }
 size_t smem_fp32(int d) {
-  return ((size_t)d * (kPixF32 + kOutB) + (size_t)kOutB * kPixF32) * sizeof(float);
+  return (size_t)d * (kPixF32 + kOutB) * sizeof(float);
 }
 
 }  // namespace

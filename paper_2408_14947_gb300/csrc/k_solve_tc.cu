@@ -1,16 +1,16 @@
 // S5 (Sec. III-D) on the tensor cores: TF32 or BF16 operands, FP32 accumulation.
 //
-// A CTA owns 128 pixels of a line (the M = 128 rows of the MMA; pixel p is
-// TMEM lane p) and solves L m = r for all of them block by block with the
-// blocked factor (32 x 32 diagonal blocks stored inverted):
-//   acc1 = M_{<J} L_{J,<J}^T          (K = j0, the m values found so far)
-//   y_J  = r_J - acc1                 (FP32, r_J re-read from the line)
-//   acc2 = y_J D_J^T                  (K = 32)
-//   m_J  = acc2,  delta^2 += |m_J|^2  (FP32), m_J written back as an operand.
-// All operand tiles are K-major, no swizzle, in shared memory; one thread
-// issues the MMAs (M = 128, N = 32) and commits them to an mbarrier that the
-// CTA waits on with a bounded poll.  r is formed as (x - mu_hi) - mu_lo with
-// mu split into two floats.  TF32 operands are rounded to nearest (cvt.rna).
+// With the full inverse X = L_t^{-1} (FP32, made from the blocked factor by
+// trinv32), the scores of a 128-pixel tile are one lower-triangular product
+//   M = R X^T  (R: 128 x d centred pixels),  delta_i = |M_i|,
+// computed as independent 128 x 32 output blocks: block J needs K = j0 + 32
+// (X is zero above its diagonal).  The pixels' rows of R stay in shared memory
+// for the whole tile; the 32 rows of X of block J are staged into one of two
+// buffers while the MMAs of block J-1 run (one thread issues them and commits
+// them to the buffer's mbarrier), and all blocks accumulate into their own TMEM
+// columns, drained once at the end (pixel p is TMEM lane p).  Operand tiles are
+// K-major, no swizzle.  r is formed as (x - mu_hi) - mu_lo with mu split into
+// two floats; TF32 operands are rounded to nearest (cvt.rna).
 #include <cuda_bf16.h>
 
 #include "erx_batch.cuh"
@@ -50,33 +50,40 @@ __device__ __forceinline__ uint4 pack16(const float* v) {
   }
 }
 
+__host__ __device__ inline int tc_dk(int d) { return (d + kB - 1) / kB * kB; }
+// TMEM columns: the smallest power of two >= dK (at least 32)
+__host__ __device__ inline uint32_t tc_cols(int d) {
+  const int dk = tc_dk(d);
+  return dk <= 32 ? 32u : dk <= 64 ? 64u : dk <= 128 ? 128u : 256u;
+}
+
 // FMT 2: TF32 (4-byte elements, 4 per core row, K = 8 per MMA);
 // FMT 1: BF16 (2-byte elements, 8 per core row, K = 16 per MMA).
-// Pixels tile*128 .. +127 of one line (x, pixel stride ps) with mu (d) and
-// the float blocked factor Lg; delta: the line's W scores; `line` is reported
-// on a timeout.
+// Pixels tile*128 .. +127 of one line (x, pixel stride ps) with mu (d) and the
+// FP32 inverse factor Xg (packed lower); delta: the line's W scores; `line` is
+// reported on a timeout.
 template <typename InT, int FMT>
 __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps, int W, int d,
                                               const double* __restrict__ mu,
-                                              const float* __restrict__ Lg,
+                                              const float* __restrict__ Xg,
                                               float* __restrict__ delta,
                                               unsigned long long* __restrict__ err, int64_t line,
                                               int tile) {
   constexpr int E = FMT == 2 ? 4 : 2;     // bytes per element
   constexpr int CK = 16 / E;              // elements per 16-byte core row
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tslot;
   __shared__ float mu_hi[kMaxDim], mu_lo[kMaxDim];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int i0 = tile * kPix;
-  const int dK = (d + kB - 1) / kB * kB;
-  const uint32_t sboM = (uint32_t)(dK / CK) * 128u;
-  const uint32_t sboY = (uint32_t)(kB / CK) * 128u;
-  unsigned char* Mt = sm;                                  // [128][dK]
-  unsigned char* Lt = Mt + (size_t)kPix * dK * E;          // [32][dK]
-  unsigned char* Yt = Lt + (size_t)kB * dK * E;            // [128][32]
-  auto off = [](int row, int k, uint32_t sbo) -> uint32_t {
+  const int dK = tc_dk(d);
+  const uint32_t ncols = tc_cols(d);
+  const uint32_t sbo = (uint32_t)(dK / CK) * 128u;
+  unsigned char* Rt = sm;                                  // [128][dK]
+  unsigned char* Xt0 = Rt + (size_t)kPix * dK * E;         // [2][32][dK]
+  const size_t xt_bytes = (size_t)kB * dK * E;
+  auto off = [sbo](int row, int k) -> uint32_t {
     return (uint32_t)(row >> 3) * sbo + (uint32_t)(k / CK) * kLBO + (uint32_t)(row & 7) * 16u;
   };
   for (int k = tid; k < d; k += kPix) {
@@ -85,13 +92,14 @@ __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps,
     mu_hi[k] = h;
     mu_lo[k] = (float)(m - (double)h);
   }
-  if (warp == 0) tc::tmem_alloc(&tslot, 64);
+  if (warp == 0) tc::tmem_alloc(&tslot, ncols);
   if (tid == 0) {
-    tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
     tc::fence_mbar_init();
   }
   __syncthreads();
-  // r of this thread's pixel into its row of Mt (zero beyond d or beyond the line)
+  // r of this thread's pixel into its row of Rt (zero beyond d or beyond the line)
   const int p = tid, i = i0 + p;
   const bool valid = i < W;
   const InT* xp = x + (int64_t)(valid ? i : 0) * ps;
@@ -102,132 +110,91 @@ __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps,
       const int k = k0 + u;
       v[u] = (valid && k < d) ? (to_f(xp[k]) - mu_hi[k]) - mu_lo[k] : 0.f;
     }
-    *reinterpret_cast<uint4*>(Mt + off(p, k0, sboM) + (k0 % CK) * E) = pack16<FMT>(v);
+    *reinterpret_cast<uint4*>(Rt + off(p, k0)) = pack16<FMT>(v);
   }
-  tc::fence_async_smem();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tslot;
   const uint32_t id = tc::idesc(FMT, kPix, kB);
-  const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-  uint32_t phase = 0;
+  const int nblk = dK / kB;
   bool ok = true;
-  float d2 = 0.f;
-  for (int j0 = 0; j0 < d && ok; j0 += kB) {
-    // stage rows j0..j0+31 of the blocked factor, columns k < j0 + 32
-    const int kcols = j0 + kB;
+  for (int J = 0; J < nblk && ok; ++J) {
+    const int b = J & 1;
+    unsigned char* Xt = Xt0 + b * xt_bytes;
+    if (J >= 2) {
+      const bool w_ok = tc::mbar_wait(&mbar[b], (uint32_t)((J - 2) >> 1) & 1u, kWaitLimit);
+      if (__syncthreads_or(!w_ok)) {
+        ok = false;
+        break;
+      }
+    }
+    // rows j0 .. j0+31 of X, columns k < j0 + 32 (zero above the diagonal and beyond d)
+    const int j0 = J * kB, kcols = j0 + kB;
     for (int e = tid; e < kB * (kcols / CK); e += kPix) {
       const int jj = e % kB, kg = e / kB, j = j0 + jj;
       float v[CK];
 #pragma unroll
       for (int u = 0; u < CK; ++u) {
         const int k = kg * CK + u;
-        v[u] = (j < d && k <= j) ? Lg[j * (j + 1) / 2 + k] : 0.f;
+        v[u] = (j < d && k <= j) ? Xg[j * (j + 1) / 2 + k] : 0.f;
       }
-      *reinterpret_cast<uint4*>(Lt + off(jj, kg * CK, sboM)) = pack16<FMT>(v);
+      *reinterpret_cast<uint4*>(Xt + off(jj, kg * CK)) = pack16<FMT>(v);
     }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    float y[kB];
-    // r_J of this pixel
-#pragma unroll
-    for (int jj = 0; jj < kB; ++jj) {
-      const int k = j0 + jj;
-      y[jj] = (valid && k < d) ? (to_f(xp[k]) - mu_hi[k]) - mu_lo[k] : 0.f;
-    }
-    if (j0 > 0) {
-      if (tid == 0) {
-        const uint32_t aM = tc::smem_u32(Mt), aL = tc::smem_u32(Lt);
-        for (int kk = 0; kk < j0 / (2 * CK); ++kk) {
-          const uint32_t ko = (uint32_t)kk * 2u * kLBO;
-          const uint64_t da = tc::desc(aM + ko, kLBO, sboM);
-          const uint64_t db = tc::desc(aL + ko, kLBO, sboM);
-          if (FMT == 2) tc::mma_tf32(tmem, da, db, id, kk > 0);
-          else tc::mma_bf16(tmem, da, db, id, kk > 0);
-        }
-        tc::commit(&mbar);
-      }
-      const bool w_ok = tc::mbar_wait(&mbar, phase & 1u, kWaitLimit);
-      if (__syncthreads_or(!w_ok)) {
-        ok = false;
-        break;
-      }
-      ++phase;
-      tc::fence_after_sync();
-      uint32_t a0[16], a1[16];
-      tc::tmem_ld16(lane_base, a0);
-      tc::tmem_ld16(lane_base + 16, a1);
-      tc::tmem_ld_wait();
-#pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        y[jj] -= __uint_as_float(a0[jj]);
-        y[jj + 16] -= __uint_as_float(a1[jj]);
-      }
-    }
-    // y_J into Yt (row p)
-#pragma unroll
-    for (int k0 = 0; k0 < kB; k0 += CK)
-      *reinterpret_cast<uint4*>(Yt + off(p, k0, sboY)) = pack16<FMT>(y + k0);
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (tid == 0) {
-      const uint32_t aY = tc::smem_u32(Yt);
-      const uint32_t aD = tc::smem_u32(Lt) + (uint32_t)(j0 / CK) * kLBO;
-      for (int kk = 0; kk < kB / (2 * CK); ++kk) {
+      const uint32_t aR = tc::smem_u32(Rt), aX = tc::smem_u32(Xt);
+      for (int kk = 0; kk < kcols / (2 * CK); ++kk) {
         const uint32_t ko = (uint32_t)kk * 2u * kLBO;
-        const uint64_t da = tc::desc(aY + ko, kLBO, sboY);
-        const uint64_t db = tc::desc(aD + ko, kLBO, sboM);
-        if (FMT == 2) tc::mma_tf32(tmem + 32, da, db, id, kk > 0);
-        else tc::mma_bf16(tmem + 32, da, db, id, kk > 0);
+        const uint64_t da = tc::desc(aR + ko, kLBO, sbo);
+        const uint64_t db = tc::desc(aX + ko, kLBO, sbo);
+        if (FMT == 2) tc::mma_tf32(tmem + (uint32_t)j0, da, db, id, kk > 0);
+        else tc::mma_bf16(tmem + (uint32_t)j0, da, db, id, kk > 0);
       }
-      tc::commit(&mbar);
+      tc::commit(&mbar[b]);
     }
-    const bool w_ok = tc::mbar_wait(&mbar, phase & 1u, kWaitLimit);
-    if (__syncthreads_or(!w_ok)) {
-      ok = false;
-      break;
-    }
-    ++phase;
-    tc::fence_after_sync();
-    uint32_t m0[16], m1[16];
-    tc::tmem_ld16(lane_base + 32, m0);
-    tc::tmem_ld16(lane_base + 48, m1);
-    tc::tmem_ld_wait();
-    float mv[kB];
-#pragma unroll
-    for (int jj = 0; jj < 16; ++jj) {
-      mv[jj] = __uint_as_float(m0[jj]);
-      mv[jj + 16] = __uint_as_float(m1[jj]);
-    }
-#pragma unroll
-    for (int jj = 0; jj < kB; ++jj)
-      if (j0 + jj < d) d2 = fmaf(mv[jj], mv[jj], d2);
-    // m_J replaces r_J in Mt (read by later blocks); zero beyond d
-#pragma unroll
-    for (int jj = 0; jj < kB; ++jj)
-      if (j0 + jj >= d) mv[jj] = 0.f;
-#pragma unroll
-    for (int k0 = 0; k0 < kB; k0 += CK)
-      *reinterpret_cast<uint4*>(Mt + off(p, j0 + k0, sboM)) = pack16<FMT>(mv + k0);
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
   }
-  if (!ok) {
+  // wait for the last commit of each buffer
+  uint32_t pending_parity[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  for (int J = nblk - 1; J >= 0 && J >= nblk - 2; --J) {
+    pending[J & 1] = true;
+    pending_parity[J & 1] = (uint32_t)(J >> 1) & 1u;
+  }
+  if (ok) {
+    bool w_ok = true;
+    for (int b = 0; b < 2; ++b)
+      if (pending[b]) w_ok &= tc::mbar_wait(&mbar[b], pending_parity[b], kWaitLimit);
+    ok = !__syncthreads_or(!w_ok);
+  }
+  float d2 = 0.f;
+  if (ok) {
+    tc::fence_after_sync();
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+    for (int c0 = 0; c0 < dK; c0 += 16) {
+      uint32_t v[16];
+      tc::tmem_ld16(lane_base + (uint32_t)c0, v);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j < d) {
+          const float m = __uint_as_float(v[j]);
+          d2 = fmaf(m, m, d2);
+        }
+    }
+  } else {
     // one more bounded wait for the MMAs still in flight before TMEM is released
-    tc::mbar_wait(&mbar, phase & 1u, kWaitLimit);
+    for (int b = 0; b < 2; ++b)
+      if (pending[b]) tc::mbar_wait(&mbar[b], pending_parity[b], kWaitLimit);
     if (tid == 0) atomicMin(&err[kErrTimeout], (unsigned long long)line);
   }
   if (valid) delta[i] = ok ? sqrtf(d2) : __int_as_float(0x7fc00000);
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_free(tmem, 64);
+  if (warp == 0) tc::tmem_free(tmem, ncols);
 }
 
 template <typename InT, int FMT>
@@ -254,8 +221,7 @@ __global__ void __launch_bounds__(kPix) b_solve_tc_kernel(const BStream* __restr
 
 size_t smem_bytes(int d, int fmt) {
   const int E = fmt == 2 ? 4 : 2;
-  const int dK = (d + kB - 1) / kB * kB;
-  return (size_t)(kPix * dK + kB * dK + kPix * kB) * E;
+  return (size_t)(kPix + 2 * kB) * tc_dk(d) * E;
 }
 
 }  // namespace

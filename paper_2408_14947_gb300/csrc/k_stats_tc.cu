@@ -40,9 +40,11 @@ __device__ __forceinline__ uint32_t tile_off(int m, int g) {
 }
 
 __device__ __forceinline__ uint32_t bf16_pair(uint32_t a, uint32_t b) {
-  // small non-negative integers (< 256) are exact in bf16: value v -> bits of float(v) >> 16
-  const uint32_t fa = __float_as_uint((float)a) >> 16;
-  const uint32_t fb = __float_as_uint((float)b) >> 16;
+  // small non-negative integers (< 256) are exact in bf16: value v -> bits of float(v) >> 16.
+  // float(v) for v < 2^23 without an int-to-float conversion: the float whose
+  // mantissa holds v above 2^23, minus 2^23 (exact).
+  const uint32_t fa = __float_as_uint(__uint_as_float(0x4B000000u | a) - 8388608.0f) >> 16;
+  const uint32_t fb = __float_as_uint(__uint_as_float(0x4B000000u | b) - 8388608.0f) >> 16;
   return fa | (fb << 16);
 }
 
@@ -162,9 +164,11 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_kernel(
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int n = c0 + j;
-          const uint64_t v = 4096ull * (uint64_t)__uint_as_float(hh[j]) +
-                             64ull * (uint64_t)__uint_as_float(md[j]) +
-                             (uint64_t)__uint_as_float(ll[j]);
+          if (n > m && n != d) continue;        // upper triangle: not needed
+          // each accumulator holds an exact integer below 2^24: convert through u32
+          const uint64_t v = ((uint64_t)__float2uint_rz(__uint_as_float(hh[j])) << 12) +
+                             ((uint64_t)__float2uint_rz(__uint_as_float(md[j])) << 6) +
+                             (uint64_t)__float2uint_rz(__uint_as_float(ll[j]));
           if (n < d) {
             if (n <= m) s2[(int64_t)m * d + n] = v;
           } else if (n == d) {
@@ -186,6 +190,189 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_kernel(
   if (warp == 0) tc::tmem_free(tmem, kTmemCols);
 }
 
+// Same sums, with the line's 64-pixel chunks brought into a 4-stage ring in
+// shared memory by bulk asynchronous copies (cp.async.bulk, completing on an
+// mbarrier with a transaction count) that thread 0 issues kRawStages chunks
+// ahead, so the global-memory latency overlaps the conversion and the MMAs.
+// Needs 16-byte aligned lines and p * d * 2 a multiple of 16.
+constexpr int kRawStages = 4;
+constexpr int kRawBytes = 16384;                  // >= 64 px * 127 bands * 2 B
+constexpr int kBulkSmem = 4 * kTileBytes + kRawStages * kRawBytes;
+
+__global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
+    const uint16_t* __restrict__ X, int64_t line_stride, int W, int d, uint32_t maxv, int T,
+    uint64_t* __restrict__ S1, uint64_t* __restrict__ S2, unsigned long long* __restrict__ err,
+    int64_t t0) {
+  extern __shared__ __align__(1024) unsigned char sm[];   // [2][H|L] tiles, then raw ring
+  unsigned char* raw = sm + 4 * kTileBytes;
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t rbar[kRawStages];
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int np = ((d + 1) + 15) & ~15;
+  for (int i = tid; i < 4 * kTileBytes / 16; i += kThreads)
+    reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    for (int r = 0; r < kRawStages; ++r) tc::mbar_init(&rbar[r], 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, kTmemCols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const uint32_t id = tc::idesc(1, kRows, np);
+  const int nchunk = (W + kKC - 1) / kKC;
+  const int nlines = blockIdx.x < T ? (T - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int Q = nlines * nchunk;
+  const int items = (d + 1) * (kKC / 8);
+  // chunk q of this CTA: line blockIdx.x + (q / nchunk) * gridDim.x, chunk q % nchunk
+  auto issue = [&](int q) {
+    if (q >= Q) return;
+    const int slot = q % kRawStages;
+    const int t = blockIdx.x + (q / nchunk) * gridDim.x, ci = q % nchunk;
+    const int npx = min(kKC, W - ci * kKC);
+    const uint32_t bytes = (uint32_t)npx * (uint32_t)d * 2u;
+    tc::mbar_expect_tx(&rbar[slot], bytes);
+    tc::bulk_g2s(raw + slot * kRawBytes, X + (int64_t)t * line_stride + (int64_t)ci * kKC * d,
+                 bytes, &rbar[slot]);
+  };
+  if (tid == 0)
+    for (int q = 0; q < kRawStages; ++q) issue(q);
+  int issued_raw = min(Q, kRawStages);
+  uint32_t issued[2] = {0u, 0u}, done[2] = {0u, 0u};
+  bool timed_out = false, bad = false;
+  int q = 0;
+  for (; q < Q && !timed_out; ++q) {
+    const int t = blockIdx.x + (q / nchunk) * gridDim.x, ci = q % nchunk;
+    const int b = q & 1;
+    if (issued[b] != done[b]) {
+      const bool ok = tc::mbar_wait(&mbar[b], done[b] & 1u, kWaitLimit);
+      if (ok) ++done[b];
+      if (__syncthreads_or(!ok)) {
+        timed_out = true;
+        break;
+      }
+    }
+    {
+      const bool ok = tc::mbar_wait(&rbar[q % kRawStages], (uint32_t)(q / kRawStages) & 1u,
+                                    kWaitLimit);
+      if (__syncthreads_or(!ok)) {
+        timed_out = true;
+        break;
+      }
+    }
+    const uint16_t* rw = reinterpret_cast<const uint16_t*>(raw + (q % kRawStages) * kRawBytes);
+    unsigned char* tH = sm + b * 2 * kTileBytes;
+    unsigned char* tL = tH + kTileBytes;
+    const int npx = min(kKC, W - ci * kKC);
+    for (int it = tid; it < items; it += kThreads) {
+      const int m = it % (d + 1), g = it / (d + 1);
+      uint32_t hv[4], lv[4];
+#pragma unroll
+      for (int qq = 0; qq < 8; qq += 2) {
+        uint32_t v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int px = g * 8 + qq + u;
+          uint32_t sv = 0u;
+          if (px < npx) sv = (m < d) ? (uint32_t)rw[px * d + m] : 1u;
+          bad |= (m < d) && (sv > maxv);
+          v[u] = sv;
+        }
+        hv[qq / 2] = bf16_pair(v[0] >> 6, v[1] >> 6);
+        lv[qq / 2] = bf16_pair(v[0] & 63u, v[1] & 63u);
+      }
+      const uint32_t off = tile_off(m, g);
+      *reinterpret_cast<uint4*>(tH + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+      *reinterpret_cast<uint4*>(tL + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t aH = tc::smem_u32(tH), aL = tc::smem_u32(tL);
+#pragma unroll
+      for (int s2 = 0; s2 < kKC / 16; ++s2) {
+        const uint32_t ko = (uint32_t)s2 * 2u * kLBO;
+        const uint64_t dH = tc::desc(aH + ko, kLBO, kSBO);
+        const uint64_t dL = tc::desc(aL + ko, kLBO, kSBO);
+        const uint32_t acc = (ci > 0 || s2 > 0) ? 1u : 0u;
+        tc::mma_bf16(tmem + kColHH, dH, dH, id, acc);
+        tc::mma_bf16(tmem + kColMid, dH, dL, id, acc);
+        tc::mma_bf16(tmem + kColMid, dL, dH, id, 1u);
+        tc::mma_bf16(tmem + kColLL, dL, dL, id, acc);
+      }
+      tc::commit(&mbar[b]);
+      issue(q + kRawStages);      // this chunk's raw slot is free: every thread converted it
+    }
+    issued_raw = min(Q, q + 1 + kRawStages);
+    ++issued[b];
+    if (ci != nchunk - 1) continue;
+    // end of line t: range flag, wait for its MMAs, drain
+    if (__syncthreads_or(bad)) {
+      if (tid == 0) atomicMin(&err[kErrRange], (unsigned long long)(t0 + t));
+    }
+    bad = false;
+    for (int bb = 0; bb < 2; ++bb) {
+      if (issued[bb] != done[bb]) {
+        const bool ok = tc::mbar_wait(&mbar[bb], done[bb] & 1u, kWaitLimit);
+        if (ok) ++done[bb];
+        timed_out |= !ok;
+      }
+    }
+    if (__syncthreads_or(timed_out)) {
+      timed_out = true;
+      break;
+    }
+    tc::fence_after_sync();
+    const int m = 32 * (warp & 3) + lane;
+    uint64_t* s2p = S2 + (int64_t)t * d * d;
+    for (int c0 = (warp >> 2) * 16; c0 < np; c0 += 32) {
+      uint32_t hh[16], md[16], ll[16];
+      const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
+      tc::tmem_ld16(lane_base + kColHH, hh);
+      tc::tmem_ld16(lane_base + kColMid, md);
+      tc::tmem_ld16(lane_base + kColLL, ll);
+      tc::tmem_ld_wait();
+      if (m < d) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c0 + j;
+          if (n > m && n != d) continue;        // upper triangle: not needed
+          // each accumulator holds an exact integer below 2^24: convert through u32
+          const uint64_t v = ((uint64_t)__float2uint_rz(__uint_as_float(hh[j])) << 12) +
+                             ((uint64_t)__float2uint_rz(__uint_as_float(md[j])) << 6) +
+                             (uint64_t)__float2uint_rz(__uint_as_float(ll[j]));
+          if (n < d) {
+            if (n <= m) s2p[(int64_t)m * d + n] = v;
+          } else if (n == d) {
+            S1[(int64_t)t * d + m] = v;
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
+  if (timed_out) {
+    if (tid == 0) atomicMin(&err[kErrTimeout], (unsigned long long)(t0 + blockIdx.x));
+    // copies and MMAs still in flight get one more bounded wait before the CTA leaves
+    for (int r = q; r < issued_raw; ++r)
+      tc::mbar_wait(&rbar[r % kRawStages], (uint32_t)(r / kRawStages) & 1u, kWaitLimit);
+    for (int bb = 0; bb < 2; ++bb)
+      if (issued[bb] != done[bb]) tc::mbar_wait(&mbar[bb], done[bb] & 1u, kWaitLimit);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, kTmemCols);
+}
+
 }  // namespace
 
 bool stats_tc_supported(int d, int W, int bits) {
@@ -193,16 +380,26 @@ bool stats_tc_supported(int d, int W, int bits) {
 }
 
 cudaError_t configure_stats_tc_kernel() {
-  return cudaFuncSetAttribute(stats_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kSmemBytes);
+  cudaError_t e =
+      cudaFuncSetAttribute(stats_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stats_tc_bulk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kBulkSmem);
+  return e;
 }
 
 void launch_stats_tc(const uint16_t* x, int64_t line_stride, int W, int d, uint32_t maxv, int T,
                      int n_sm, uint64_t* S1, uint64_t* S2, unsigned long long* err, int64_t t0,
                      cudaStream_t st) {
   const int grid = T < n_sm ? T : n_sm;
-  stats_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, line_stride, W, d, maxv, T, S1, S2,
-                                                          err, t0);
+  const bool aligned = ((uintptr_t)x % 16 == 0) && ((line_stride * 2) % 16 == 0) &&
+                       (((int64_t)W * d * 2) % 16 == 0);
+  if (aligned)
+    stats_tc_bulk_kernel<<<grid, kThreads, kBulkSmem, st>>>(x, line_stride, W, d, maxv, T, S1,
+                                                            S2, err, t0);
+  else
+    stats_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, line_stride, W, d, maxv, T, S1, S2,
+                                                        err, t0);
 }
 
 }  // namespace erx

@@ -49,8 +49,8 @@ constexpr size_t kOffShift = kOffS1 + kVecB;       // centring shift
 constexpr size_t kOffS2 = kOffShift + kVecB;       // sum x x^T (u64) | centred scatter (double)
 constexpr size_t kOffMuT = kOffS2 + kMatB;         // mu the line is scored with
 constexpr size_t kOffKT = kOffMuT + kVecB;         // K the line is scored with (packed)
-constexpr size_t kOffLinv = kOffKT + kPackB;       // L^{-1} (packed)
-constexpr size_t kOffLinv32 = kOffLinv + kPackB;   // its float copy
+constexpr size_t kOffLinv = kOffKT + kPackB;       // blocked factor (packed)
+constexpr size_t kOffLinv32 = kOffLinv + kPackB;   // its float copy, then L^{-1} in FP32
 constexpr size_t kOffErr = kOffLinv32 + kPack32B;  // deferred error slots
 constexpr size_t kScratchBytes = kOffErr + kErrB;  // about 0.9 MiB
 
@@ -157,6 +157,7 @@ extern "C" erx_status erx_push_lines_static(const erx_config* cfg, void* cuda_st
     launch_ema_scan(int_stats, S1i, S2i, mu_hat, shift, S2f, 1, d, W, cfg->momentum, t,
                     cfg->order, mu_dev, K_dev, mu_t, K_t, nullptr, st);
     launch_chol_inv(K_t, d, 1, cfg->ridge, Linv, fp64 ? nullptr : Linv32, err, t, st);
+    if (!fp64) launch_trinv32(Linv32, d, 1, st);
     if (fp64)
       launch_solve_fp64(cfg->in_dtype, x, stride, d, W, d, 1, mu_t, Linv, (double*)delta, st);
     else

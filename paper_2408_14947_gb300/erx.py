@@ -197,7 +197,7 @@ def erx_srp_weights(bands: int, dim: int, seed: int):
     return w
 
 
-ERX_K_COUNT = 12
+ERX_K_COUNT = 13
 
 
 def erx_push_lines_static(cfg, stream, mu_ptr, k_ptr, t, lines_ptr, n_lines, stride_bytes,
