@@ -18,6 +18,7 @@
 // and conflict-free.  The centred samples are (x - mu_hi) - mu_lo with mu split
 // into two floats, which keeps r accurate to float rounding without FP64 work
 // per pixel.
+#include <algorithm>
 #include <cmath>
 
 #include "erx_batch.cuh"
@@ -62,13 +63,12 @@ __device__ __forceinline__ void solve_fp64_body(const InT* __restrict__ x, int p
       if (jj < nb) {
         const int j = j0 + jj;
         const double* Lj = L + j * (j + 1) / 2;
-        // two chains (one combining addition per row); j0 is a multiple of 32
-        double a0 = rr[j], a1 = 0.0;
-        for (int k = 0; k < j0; k += 2) {
-          a0 = fma(-__ldg(Lj + k), rr[k], a0);
-          a1 = fma(-__ldg(Lj + k + 1), rr[k + 1], a1);
-        }
-        y[jj] = (j0 > 0) ? a0 + a1 : a0;
+        // one chain: a warp's DFMA holds its SMSP's share of the FP64 pipe
+        // (0.5 lane/clk) for longer than the result latency, so a dependent
+        // chain does not stall, and no combining additions are needed
+        double a0 = rr[j];
+        for (int k = 0; k < j0; ++k) a0 = fma(-__ldg(Lj + k), rr[k], a0);
+        y[jj] = a0;
       }
     }
 #pragma unroll
@@ -87,13 +87,21 @@ __device__ __forceinline__ void solve_fp64_body(const InT* __restrict__ x, int p
   delta[i] = sqrt(d2);
 }
 
+// Persistent grid (a whole number of waves): CTA c takes tiles c, c + grid, ...
+// of the T x ntiles (line, tile) pairs.
 template <typename InT>
 __global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
     const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
-    const double* __restrict__ mu_t, const double* __restrict__ Lf, double* __restrict__ delta) {
-  const int t = blockIdx.y;
-  solve_fp64_body<InT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
-                       Lf + (int64_t)t * packed_size(d), delta + (int64_t)t * W, blockIdx.x);
+    const double* __restrict__ mu_t, const double* __restrict__ Lf, double* __restrict__ delta,
+    int T) {
+  const int ntiles = (W + kPixF64 - 1) / kPixF64;
+  const int64_t total = (int64_t)T * ntiles;
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const int t = (int)(w / ntiles), tile = (int)(w % ntiles);
+    __syncthreads();          // the previous tile's threads are done with shared memory
+    solve_fp64_body<InT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
+                         Lf + (int64_t)t * packed_size(d), delta + (int64_t)t * W, tile);
+  }
 }
 
 constexpr int kPixF32 = 64;   // pixels per CTA
@@ -241,17 +249,34 @@ void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, in
 void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
                        int T, const double* mu_t, const double* Linv, double* delta,
                        cudaStream_t st) {
-  dim3 grid((W + kPixF64 - 1) / kPixF64, T);
   const size_t sm = smem_fp64(d);
+  // a whole number of waves: resident CTAs per SM times the SM count
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (n_sm <= 0) n_sm = 1;
+  }
+  int per_sm = 1;
+  if (in_type == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fp64_kernel<uint16_t>, kPixF64, sm);
+  else if (in_type == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fp64_kernel<float>, kPixF64, sm);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fp64_kernel<double>, kPixF64, sm);
+  per_sm = std::max(1, per_sm);
+  const int64_t total = (int64_t)T * ((W + kPixF64 - 1) / kPixF64);
+  const int grid = (int)std::min<int64_t>(total, (int64_t)n_sm * per_sm);
   if (in_type == 0)
     solve_fp64_kernel<uint16_t><<<grid, kPixF64, sm, st>>>((const uint16_t*)x, line_stride, ps,
-                                                           W, d, mu_t, Linv, delta);
+                                                           W, d, mu_t, Linv, delta, T);
   else if (in_type == 1)
     solve_fp64_kernel<float><<<grid, kPixF64, sm, st>>>((const float*)x, line_stride, ps, W, d,
-                                                        mu_t, Linv, delta);
+                                                        mu_t, Linv, delta, T);
   else
     solve_fp64_kernel<double><<<grid, kPixF64, sm, st>>>((const double*)x, line_stride, ps, W,
-                                                         d, mu_t, Linv, delta);
+                                                         d, mu_t, Linv, delta, T);
 }
 
 void launch_solve_fp32(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
