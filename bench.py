@@ -94,6 +94,30 @@ def c5_config(seed=0, width=1024, bands=224):
                              anomaly_mix=(0.05, 0.3))
 
 
+def workload_config():
+    """The workload every arm reports (reference and ours)."""
+    return {"workload": f"C2: {LINES} lines x {WIDTH} px x {BANDS} bands u16 12-bit, "
+                        f"scenes of 2000 lines, 0.2% 3x3 anomalies",
+            "form": "fp64", "projection": "none (d = 108)", "alpha": 0.1,
+            "l2": "inputs (2.76 GB) larger than L2; no flush"}
+
+
+def max_over_ranks(value: float, device) -> float:
+    """Largest value over all ranks (the slowest rank's time); identity at N = 1."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(lines_per_rank: int, world: int, ms_max: float) -> float:
+    """Lines/s of the whole job: every rank's lines over the slowest rank's time."""
+    return lines_per_rank * world / (ms_max / 1000.0)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -189,8 +213,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sample / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"C2: {LINES} lines x {WIDTH} px x {BANDS} bands u16 12-bit",
-                       "sample_lines_per_step": sample},
+            "config": dict(workload_config(), sample_lines_per_step=sample),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -403,13 +426,11 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     prof = det.profile_read(reset=True)
     det.profile(False)
+    ms_total = max_over_ranks(ms_total, dev)
     if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         torch.distributed.barrier()
-        ms_total = float(t.item())
     ms_step = ms_total / args.steps
-    value = LINES * world / (ms_step / 1000.0)
+    value = whole_job_rate(LINES, world, ms_step)
     launches = sum(v[2] for v in prof.values())
 
     # roofline of the dominant kernel: the FP64 score kernel (d(d+1)/2 + d DFMA per pixel)
@@ -446,13 +467,10 @@ def run_ours(args):
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
               "data": "synthetic",
-              "config": {"workload": f"C2: {LINES} lines x {WIDTH} px x {BANDS} bands u16 "
-                                     f"12-bit, scenes of 2000 lines, 0.2% 3x3 anomalies",
-                         "form": "fp64", "projection": "none (d = 108)", "alpha": 0.1,
-                         "block_lines": det.cfg.block_lines or "auto",
-                         "l2": "inputs (2.76 GB) larger than L2; no flush",
-                         "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                         "gen_seconds": round(gen_s, 1)},
+              "config": dict(workload_config(),
+                             block_lines=det.cfg.block_lines or "auto",
+                             parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                             gen_seconds=round(gen_s, 1)),
               "gpu_launches": launches, "roofline": roof, "kernels": kernels,
               "clocks": clk.summary()}
 
