@@ -87,10 +87,77 @@ __device__ __forceinline__ void solve_fp64_body(const InT* __restrict__ x, int p
   delta[i] = sqrt(d2);
 }
 
+// Large d (> 128): a 64-pixel tile holds 113 KiB of residuals, so two CTAs fit
+// on an SM; with one thread per pixel that is four warps, one per SMSP, too
+// few to cover the latency of the dependent DFMA chains and the L2 reads of L.
+// Here two threads share each pixel (128 threads, eight warps per SM): per
+// 32-row block they take the even and the odd rows of y_J (written in place
+// of r_J), then the even and the odd rows of m_J = D_J y_J, held in registers
+// until both have read y_J.  No shared memory beyond the residual tile; every
+// sum is taken in the same order as in the one-thread body, so both give the
+// same bits.
+template <typename InT>
+__device__ __forceinline__ void solve_fp64_pair_body(const InT* __restrict__ x, int ps, int W,
+                                                     int d, const double* __restrict__ mu,
+                                                     const double* __restrict__ L,
+                                                     double* __restrict__ delta, int tile) {
+  extern __shared__ __align__(16) double r[];
+  const int dp = d | 1;
+  const int i0 = tile * kPixF64;
+  for (int e = threadIdx.x; e < kPixF64 * d; e += 2 * kPixF64) {
+    const int p = e / d, k = e - p * d, i = i0 + p;
+    r[p * dp + k] = i < W ? to_d(x[(int64_t)i * ps + k]) - mu[k] : 0.0;
+  }
+  __syncthreads();
+  const int p = threadIdx.x % kPixF64, h = threadIdx.x / kPixF64;   // pixel, row parity
+  const int i = i0 + p;
+  double* rr = r + p * dp;
+  for (int j0 = 0; j0 < d; j0 += kNB) {
+    const int nb = min(kNB, d - j0);
+#pragma unroll
+    for (int u = 0; u < kNB / 2; ++u) {
+      const int jj = 2 * u + h;
+      if (jj < nb) {
+        const int j = j0 + jj;
+        const double* Lj = L + j * (j + 1) / 2;
+        double a0 = rr[j];
+        for (int k = 0; k < j0; ++k) a0 = fma(-__ldg(Lj + k), rr[k], a0);
+        rr[j] = a0;
+      }
+    }
+    __syncthreads();
+    double m[kNB / 2];
+#pragma unroll
+    for (int u = 0; u < kNB / 2; ++u) {
+      const int jj = 2 * u + h;
+      double s = 0.0;
+      if (jj < nb) {
+        const double* Dj = L + (j0 + jj) * (j0 + jj + 1) / 2 + j0;
+        const double* yj = rr + j0;
+#pragma unroll
+        for (int kk = 0; kk <= 2 * u; ++kk) s = fma(__ldg(Dj + kk), yj[kk], s);
+        if (h) s = fma(__ldg(Dj + 2 * u + 1), yj[2 * u + 1], s);
+      }
+      m[u] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kNB / 2; ++u)
+      if (2 * u + h < nb) rr[j0 + 2 * u + h] = m[u];
+    __syncthreads();
+  }
+  // the squares are summed in row order by one thread, as in the one-thread body
+  if (h == 0 && i < W) {
+    double d2 = 0.0;
+    for (int j = 0; j < d; ++j) d2 = fma(rr[j], rr[j], d2);
+    delta[i] = sqrt(d2);
+  }
+}
+
 // Persistent grid (a whole number of waves): CTA c takes tiles c, c + grid, ...
 // of the T x ntiles (line, tile) pairs.
-template <typename InT>
-__global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
+template <typename InT, bool PAIR>
+__global__ void __launch_bounds__(PAIR ? 2 * kPixF64 : kPixF64) solve_fp64_kernel(
     const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
     const double* __restrict__ mu_t, const double* __restrict__ Lf, double* __restrict__ delta,
     int T) {
@@ -99,8 +166,12 @@ __global__ void __launch_bounds__(kPixF64) solve_fp64_kernel(
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
     const int t = (int)(w / ntiles), tile = (int)(w % ntiles);
     __syncthreads();          // the previous tile's threads are done with shared memory
-    solve_fp64_body<InT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
-                         Lf + (int64_t)t * packed_size(d), delta + (int64_t)t * W, tile);
+    if (PAIR)
+      solve_fp64_pair_body<InT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
+                                Lf + (int64_t)t * packed_size(d), delta + (int64_t)t * W, tile);
+    else
+      solve_fp64_body<InT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
+                           Lf + (int64_t)t * packed_size(d), delta + (int64_t)t * W, tile);
   }
 }
 
@@ -221,9 +292,24 @@ cudaError_t configure_solve_kernels() {
   const int m64 = (int)smem_fp64(kMaxDim), m32 = (int)smem_fp32(kMaxDim);
 #define ERX_CFG(K, M) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, M)
-  ERX_CFG(solve_fp64_kernel<uint16_t>, m64);
-  ERX_CFG(solve_fp64_kernel<float>, m64);
-  ERX_CFG(solve_fp64_kernel<double>, m64);
+  ERX_CFG((solve_fp64_kernel<uint16_t, false>), m64);
+  ERX_CFG((solve_fp64_kernel<float, false>), m64);
+  ERX_CFG((solve_fp64_kernel<double, false>), m64);
+  ERX_CFG((solve_fp64_kernel<uint16_t, true>), m64);
+  ERX_CFG((solve_fp64_kernel<float, true>), m64);
+  ERX_CFG((solve_fp64_kernel<double, true>), m64);
+  // residual tiles take nearly all of the SM's shared memory (two 113 KiB
+  // tiles at d = 224); L streams through L2
+#define ERX_CARVE(K)     \
+  if (e == cudaSuccess) \
+  e = cudaFuncSetAttribute(K, cudaFuncAttributePreferredSharedMemoryCarveout, 100)
+  ERX_CARVE((solve_fp64_kernel<uint16_t, false>));
+  ERX_CARVE((solve_fp64_kernel<float, false>));
+  ERX_CARVE((solve_fp64_kernel<double, false>));
+  ERX_CARVE((solve_fp64_kernel<uint16_t, true>));
+  ERX_CARVE((solve_fp64_kernel<float, true>));
+  ERX_CARVE((solve_fp64_kernel<double, true>));
+#undef ERX_CARVE
   ERX_CFG(solve_fp32_kernel<uint16_t>, m32);
   ERX_CFG(solve_fp32_kernel<float>, m32);
   ERX_CFG(solve_fp32_kernel<double>, m32);
@@ -246,9 +332,12 @@ void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, in
     b_solve_fp32_kernel<<<n_items, 128, smem_fp32(dmax), st>>>(S, items);
 }
 
-void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
-                       int T, const double* mu_t, const double* Linv, double* delta,
-                       cudaStream_t st) {
+constexpr int kPairMinD = 129;   // the paired kernel from here on
+
+template <typename InT, bool PAIR>
+void launch_fp64_t(const InT* x, int64_t line_stride, int ps, int W, int d, int T,
+                   const double* mu_t, const double* Linv, double* delta, cudaStream_t st) {
+  const int threads = PAIR ? 2 * kPixF64 : kPixF64;
   const size_t sm = smem_fp64(d);
   // a whole number of waves: resident CTAs per SM times the SM count
   static int n_sm = 0;
@@ -259,24 +348,32 @@ void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, 
     if (n_sm <= 0) n_sm = 1;
   }
   int per_sm = 1;
-  if (in_type == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fp64_kernel<uint16_t>, kPixF64, sm);
-  else if (in_type == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fp64_kernel<float>, kPixF64, sm);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fp64_kernel<double>, kPixF64, sm);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fp64_kernel<InT, PAIR>, threads,
+                                                sm);
   per_sm = std::max(1, per_sm);
   const int64_t total = (int64_t)T * ((W + kPixF64 - 1) / kPixF64);
   const int grid = (int)std::min<int64_t>(total, (int64_t)n_sm * per_sm);
-  if (in_type == 0)
-    solve_fp64_kernel<uint16_t><<<grid, kPixF64, sm, st>>>((const uint16_t*)x, line_stride, ps,
-                                                           W, d, mu_t, Linv, delta, T);
-  else if (in_type == 1)
-    solve_fp64_kernel<float><<<grid, kPixF64, sm, st>>>((const float*)x, line_stride, ps, W, d,
-                                                        mu_t, Linv, delta, T);
-  else
-    solve_fp64_kernel<double><<<grid, kPixF64, sm, st>>>((const double*)x, line_stride, ps, W,
-                                                         d, mu_t, Linv, delta, T);
+  solve_fp64_kernel<InT, PAIR><<<grid, threads, sm, st>>>(x, line_stride, ps, W, d, mu_t, Linv,
+                                                          delta, T);
+}
+
+void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
+                       int T, const double* mu_t, const double* Linv, double* delta,
+                       cudaStream_t st) {
+  const bool pair = d >= kPairMinD;
+#define ERX_F64(IT)                                                                          \
+  if (pair)                                                                                  \
+    launch_fp64_t<IT, true>((const IT*)x, line_stride, ps, W, d, T, mu_t, Linv, delta, st); \
+  else                                                                                       \
+    launch_fp64_t<IT, false>((const IT*)x, line_stride, ps, W, d, T, mu_t, Linv, delta, st)
+  if (in_type == 0) {
+    ERX_F64(uint16_t);
+  } else if (in_type == 1) {
+    ERX_F64(float);
+  } else {
+    ERX_F64(double);
+  }
+#undef ERX_F64
 }
 
 void launch_solve_fp32(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,

@@ -149,38 +149,41 @@ __global__ void __launch_bounds__(256) mean_kernel(const InT* __restrict__ X, in
                  shift + (int64_t)t * d);
 }
 
-// One 64 x 64 block pair `pair` of the scatter of one line about `shift`
-// (the line's d values), written to s2 (the line's d x d).
-template <typename InT, typename AccT>
+// One SBT x SBT block pair `pair` of the scatter of one line about `shift`
+// (the line's d values), written to s2 (the line's d x d).  256 threads, each
+// an (SBT/16) x (SBT/16) sub-block; SBT = 32 wastes less of the triangle
+// (used in FP64, where every multiply-add counts), SBT = 64 reuses registers more.
+template <typename InT, typename AccT, int SBT = SB>
 __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps, int W, int d,
                                               const double* __restrict__ shift,
                                               double* __restrict__ s2, int pair) {
-  __shared__ __align__(16) AccT xa[KCF][SB];
-  __shared__ __align__(16) AccT xb[KCF][SB];
-  __shared__ AccT cs[2 * SB];
+  constexpr int TP = SBT / 16;
+  __shared__ __align__(16) AccT xa[KCF][SBT];
+  __shared__ __align__(16) AccT xb[KCF][SBT];
+  __shared__ AccT cs[2 * SBT];
   int I, J;
   block_pair(pair, I, J);
   const bool diag = (I == J);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int a0 = I * SB, b0 = J * SB;
-  if (threadIdx.x < 2 * SB) {
-    const int c = threadIdx.x < SB ? a0 + threadIdx.x : b0 + threadIdx.x - SB;
+  const int a0 = I * SBT, b0 = J * SBT;
+  if (threadIdx.x < 2 * SBT) {
+    const int c = threadIdx.x < SBT ? a0 + threadIdx.x : b0 + threadIdx.x - SBT;
     cs[threadIdx.x] = c < d ? (AccT)shift[c] : (AccT)0;
   }
-  AccT acc[4][4];
+  AccT acc[TP][TP];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TP; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = (AccT)0;
-  const AccT(*xbp)[SB] = diag ? xa : xb;
+    for (int j = 0; j < TP; ++j) acc[i][j] = (AccT)0;
+  const AccT(*xbp)[SBT] = diag ? xa : xb;
   __syncthreads();
   for (int i0 = 0; i0 < W; i0 += KCF) {
-    for (int e = threadIdx.x; e < KCF * SB; e += 256) {
-      const int p = e / SB, c = e % SB, i = i0 + p;
+    for (int e = threadIdx.x; e < KCF * SBT; e += 256) {
+      const int p = e / SBT, c = e % SBT, i = i0 + p;
       AccT va = 0, vb = 0;
       if (i < W) {
         if (a0 + c < d) va = (AccT)x[(int64_t)i * ps + a0 + c] - cs[c];
-        if (!diag && b0 + c < d) vb = (AccT)x[(int64_t)i * ps + b0 + c] - cs[SB + c];
+        if (!diag && b0 + c < d) vb = (AccT)x[(int64_t)i * ps + b0 + c] - cs[SBT + c];
       }
       xa[p][c] = va;
       if (!diag) xb[p][c] = vb;
@@ -188,36 +191,36 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
     __syncthreads();
     const int kn = min(KCF, W - i0);
     for (int k = 0; k < kn; ++k) {
-      AccT a[4], b[4];
+      AccT a[TP], b[TP];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = xa[k][ty * 4 + i], b[i] = xbp[k][tx * 4 + i];
+      for (int i = 0; i < TP; ++i) a[i] = xa[k][ty * TP + i], b[i] = xbp[k][tx * TP + i];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TP; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < TP; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int a = a0 + ty * 4 + i;
+  for (int i = 0; i < TP; ++i) {
+    const int a = a0 + ty * TP + i;
     if (a >= d) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int b = b0 + tx * 4 + j;
+    for (int j = 0; j < TP; ++j) {
+      const int b = b0 + tx * TP + j;
       if (b < d) s2[(int64_t)a * d + b] = (double)acc[i][j];
     }
   }
 }
 
-template <typename InT, typename AccT>
+template <typename InT, typename AccT, int SBT>
 __global__ void __launch_bounds__(256) stats_fp_kernel(const InT* __restrict__ X,
                                                        int64_t line_stride, int ps, int W, int d,
                                                        const double* __restrict__ shift,
                                                        double* __restrict__ S2f) {
   const int t = blockIdx.y;
-  stats_fp_body<InT, AccT>(X + (int64_t)t * line_stride, ps, W, d, shift + (int64_t)t * d,
-                           S2f + (int64_t)t * d * d, blockIdx.x);
+  stats_fp_body<InT, AccT, SBT>(X + (int64_t)t * line_stride, ps, W, d, shift + (int64_t)t * d,
+                                S2f + (int64_t)t * d * d, blockIdx.x);
 }
 
 // Small d (projected lines, d <= 16): one CTA per line, one thread per entry
@@ -258,8 +261,8 @@ __global__ void __launch_bounds__(256) stats_small_kernel(const InT* __restrict_
                               S2f + (int64_t)t * d * d);
 }
 
-int n_pairs(int d) {
-  const int nb = (d + SB - 1) / SB;
+int n_pairs(int d, int sb = SB) {
+  const int nb = (d + sb - 1) / sb;
   return nb * (nb + 1) / 2;
 }
 
@@ -336,9 +339,11 @@ void launch_stats_fp(int in_type, bool fp64, const void* x, int64_t line_stride,
 #undef ERX_SMALL
     return;
   }
-  dim3 grid(n_pairs(d), T);
-#define ERX_SFP(IT, AT) \
-  stats_fp_kernel<IT, AT><<<grid, 256, 0, st>>>((const IT*)x, line_stride, ps, W, d, shift, S2f)
+  // FP64: 32 x 32 blocks (less of the triangle wasted); FP32: 64 x 64
+  const dim3 grid(n_pairs(d, fp64 ? 32 : SB), T);
+#define ERX_SFP(IT, AT)                                                                     \
+  stats_fp_kernel<IT, AT, sizeof(AT) == 8 ? 32 : SB><<<grid, 256, 0, st>>>(              \
+      (const IT*)x, line_stride, ps, W, d, shift, S2f)
   if (fp64) {
     if (in_type == 0) ERX_SFP(uint16_t, double);
     else if (in_type == 1) ERX_SFP(float, double);
