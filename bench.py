@@ -264,10 +264,10 @@ def bench_batched(dev, stream, n_streams: int = 256, n_lines: int = 4, steps: in
     out = {"workload": f"{n_streams} streams, widths U{{128..2048}}, bands from "
                        f"{{8,16,64,108,224}}, float32, {n_lines} resident lines cycled",
            "bytes_per_step": int(sum(c.width * c.bands * 4 for c in cfgs))}
-    for form in ("fp64", "fp32", "tf32", "bf16"):
+    for form in ("fp64", "fp32", "tf32", "bf16", "tf32x3"):
         b = Batch(shapes, form=form, stream=stream)
         b.push([x[0] for x in lines])
-        if form in ("tf32", "bf16"):
+        if form in ("tf32", "bf16", "tf32x3"):
             b.sync()
             b.tune(reps=3)
         for k in range(3):
@@ -497,7 +497,7 @@ def run_ours(args):
         # other forms on the same cube, same step definition
         forms = {}
         for name, kw in (("fp32", {"form": "fp32"}), ("tf32", {"form": "tf32"}),
-                         ("bf16", {"form": "bf16"}),
+                         ("bf16", {"form": "bf16"}), ("tf32x3", {"form": "tf32x3"}),
                          ("fp64_srp5", {"form": "fp64", "proj": "srp", "proj_dim": 5}),
                          ("fp32_srp5", {"form": "fp32", "proj": "srp", "proj_dim": 5})):
             forms[name] = time_form(lambda **k: Detector(BANDS, WIDTH, in_dtype="u16",
@@ -511,7 +511,7 @@ def run_ours(args):
         x224 = torch.from_numpy(cube224).to(dev)
         del cube224
         forms224 = {}
-        for name in ("fp64", "fp32", "tf32", "bf16"):
+        for name in ("fp64", "fp32", "tf32", "bf16", "tf32x3"):
             forms224[name] = time_form(lambda **k: Detector(224, 1024, in_dtype="f32",
                                                             stream=stream, **k),
                                        x224, {"form": name}, dev, stream)

@@ -58,14 +58,26 @@ enum { ERX_PROJ_NONE = 0, ERX_PROJ_SRP = 1, ERX_PROJ_LEARNED = 2 };
 enum { ERX_UPDATE_THEN_SCORE = 0, ERX_SCORE_THEN_UPDATE = 1 };
 /* input sample type, lines laid out [pixel][band] (band-interleaved-by-pixel) */
 enum { ERX_U16 = 0, ERX_F32 = 1, ERX_F64 = 2 };
-/* flags: ERX_FLAG_SIMT_STATS keeps S2 off the tensor cores (exact integer
- * sums by 32-bit integer multiply-adds instead); results are identical */
+/* flags: ERX_FLAG_SIMT_STATS keeps S2 off the tensor cores: exact integer
+ * sums by 32-bit integer multiply-adds for u16 lines (identical results), the
+ * FP32 SIMT scatter for floating-point lines in the tensor-core forms */
 enum { ERX_FLAG_SIMT_STATS = 1 };
 /* arithmetic form of S5 (and of S2 for floating input); S3 and S4 are FP64 in
  * every form, and u16 input without projection always gets exact integer S2.
  * FP64: FP64 arithmetic.  FP32: FP32 SIMT arithmetic.  TF32 / BF16: tensor-core
- * MMAs with TF32 / BF16 operands and FP32 accumulation. */
-enum { ERX_FORM_FP64 = 0, ERX_FORM_FP32 = 1, ERX_FORM_TF32 = 2, ERX_FORM_BF16 = 3 };
+ * MMAs with TF32 / BF16 operands and FP32 accumulation.  TF32X3: tensor-core
+ * MMAs on split operands v = hi + lo (both TF32), accumulating
+ * hi hi' + hi lo' + lo hi' in FP32 (near-FP32 products at three MMAs each).
+ * In the tensor-core forms, S2 of floating-point lines runs on the tensor
+ * cores too (unless ERX_FLAG_SIMT_STATS is set, or the lines are not 16-byte
+ * aligned with p * d a multiple of 4: then FP32 SIMT). */
+enum {
+  ERX_FORM_FP64 = 0,
+  ERX_FORM_FP32 = 1,
+  ERX_FORM_TF32 = 2,
+  ERX_FORM_BF16 = 3,
+  ERX_FORM_TF32X3 = 4
+};
 
 typedef struct {
   int32_t bands;        /* b >= 1 */
@@ -303,12 +315,14 @@ erx_status erx_batch_sync(erx_batch* b, int64_t* bad_stream);
 /* State of stream i (host pointers, as erx_get_state).  Synchronises. */
 erx_status erx_batch_get_state(erx_batch* b, int32_t i, int64_t* t, double* mu, double* K);
 
-/* Score kernel chosen for stream i: 0 FP64, 1 FP32 SIMT, 2 TF32 MMA, 3 BF16 MMA. */
+/* Score kernel chosen for stream i: 0 FP64, 1 FP32 SIMT, 2 TF32 MMA, 3 BF16 MMA,
+ * 4 3xTF32 MMA. */
 erx_status erx_batch_route(const erx_batch* b, int32_t i, int32_t* route);
 
 /* Autotuner: for every band count in the batch, time each score kernel the
  * form allows (TF32 form: TF32 MMA or FP32 SIMT; BF16 form: BF16 MMA or FP32
- * SIMT; FP64 and FP32 forms have one) over that count's streams, `reps` runs
+ * SIMT; TF32X3 form: 3xTF32 MMA or FP32 SIMT; FP64 and FP32 forms have one)
+ * over that count's streams, `reps` runs
  * each with CUDA events, keep the fastest and re-capture the step.  Needs one
  * step pushed before (ERX_ESTATE otherwise); overwrites the last step's scores,
  * not the state.  cache_path (may be NULL): a JSON object of earlier choices
@@ -331,10 +345,11 @@ enum {
   ERX_K_SOLVE_FP32 = 7, /* S5 scores, FP32 */
   ERX_K_NORMALISE = 8,  /* S6 normalisation */
   ERX_K_STATS_TC = 9,   /* S2 exact integer sums on the tensor cores */
-  ERX_K_SOLVE_TC = 10,  /* S5 scores on the tensor cores (TF32 / BF16) */
+  ERX_K_SOLVE_TC = 10,  /* S5 scores on the tensor cores (TF32 / BF16 / 3xTF32) */
   ERX_K_ENCODE = 11,    /* S1 learned band encoder (codes) */
-  ERX_K_TRINV = 12,     /* S4 full inverse of the factor in FP32 (FP32/TF32/BF16 forms) */
-  ERX_K_COUNT = 13
+  ERX_K_TRINV = 12,     /* S4 full inverse of the factor in FP32 (non-FP64 forms) */
+  ERX_K_SYRK_TC = 13,   /* S2 centred scatter of floating lines on the tensor cores */
+  ERX_K_COUNT = 14
 };
 
 /* Per-kernel timing.  While enabled (on != 0), every kernel the context

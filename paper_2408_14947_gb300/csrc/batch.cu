@@ -62,8 +62,8 @@ struct erx_batch {
   int n_stats = 0;
   BItem* ema_items = nullptr;
   int n_ema = 0;
-  BItem* solve_items[4] = {nullptr, nullptr, nullptr, nullptr};
-  int n_solve[4] = {0, 0, 0, 0};
+  BItem* solve_items[kRoutes] = {};
+  int n_solve[kRoutes] = {};
   unsigned long long* err = nullptr;
   // graph
   cudaGraph_t graph = nullptr;
@@ -106,17 +106,24 @@ bool route_allowed(int form, int route) {
     case ERX_FORM_FP32: return route == 1;
     case ERX_FORM_TF32: return route == 1 || route == 2;
     case ERX_FORM_BF16: return route == 1 || route == 3;
+    case ERX_FORM_TF32X3: return route == 1 || route == 4;
   }
   return false;
 }
 
 int native_route(int form) {
-  return form == ERX_FORM_FP64 ? 0 : form == ERX_FORM_FP32 ? 1 : form == ERX_FORM_TF32 ? 2 : 3;
+  return form == ERX_FORM_FP64 ? 0 : form == ERX_FORM_FP32 ? 1 : form == ERX_FORM_TF32 ? 2
+         : form == ERX_FORM_BF16 ? 3 : 4;
+}
+
+// operand format of a tensor-core route: 2 TF32, 1 BF16, 3 3xTF32
+int route_format(int route) {
+  return route == 2 ? 2 : route == 3 ? 1 : 3;
 }
 
 // (Re)build the score-kernel work lists from the routes in the host table.
 erx_status build_solve_items(erx_batch* b) {
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < kRoutes; ++r) {
     std::vector<BItem> items;
     for (int s = 0; s < b->n; ++s)
       if (b->host[s].route == r)
@@ -167,10 +174,10 @@ void enqueue_step(erx_batch* b, cudaStream_t st) {
   launch_batch_ema(b->table, b->ema_items, b->n_ema, st);
   launch_batch_chol(b->table, b->n, b->dmax, !fp64, b->err, st);
   if (!fp64) launch_batch_trinv32(b->table, b->n, b->dmax, st);
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < kRoutes; ++r) {
     if (!b->n_solve[r]) continue;
     if (r <= 1) launch_batch_solve_simt(r, b->table, b->solve_items[r], b->n_solve[r], b->dmax, st);
-    else launch_batch_solve_tc(r == 2 ? 2 : 1, b->table, b->solve_items[r], b->n_solve[r],
+    else launch_batch_solve_tc(route_format(r), b->table, b->solve_items[r], b->n_solve[r],
                                b->dmax, b->err, st);
   }
   launch_batch_normalise(b->table, b->n, fp64, st);
@@ -204,7 +211,7 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
   if (!out || n < 1 || !cfgs) return ERX_EINVAL;
   *out = nullptr;
   const int form = cfgs[0].form;
-  if (form < ERX_FORM_FP64 || form > ERX_FORM_BF16) return ERX_EINVAL;
+  if (form < ERX_FORM_FP64 || form > ERX_FORM_TF32X3) return ERX_EINVAL;
   for (int i = 0; i < n; ++i) {
     const erx_config& c = cfgs[i];
     if (c.bands < 1 || c.width < 2 || !(c.momentum > 0.0 && c.momentum <= 1.0) ||
@@ -439,7 +446,7 @@ erx_status erx_batch_tune(erx_batch* b, int32_t reps, const char* cache_path) {
   std::map<int, std::vector<int>> classes;
   for (int s = 0; s < b->n; ++s) classes[b->host[s].d].push_back(s);
   std::vector<int> routes;
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < kRoutes; ++r)
     if (route_allowed(b->form, r)) routes.push_back(r);
   if (routes.size() < 2) return ERX_OK;
   char dev_name[256] = "gpu";
@@ -509,7 +516,7 @@ erx_status erx_batch_tune(erx_batch* b, int32_t reps, const char* cache_path) {
           continue;
         }
         cudaMemcpy(dit, it.data(), it.size() * sizeof(BItem), cudaMemcpyHostToDevice);
-        // the route's score type must match the table's: route 1 vs 2/3 all write float
+        // the route's score type must match the table's: routes 1 to 4 all write float
         std::vector<BStream> tmp = b->host;
         for (int s : kv.second) tmp[s].route = r;
         cudaMemcpy(b->table, tmp.data(), sizeof(BStream) * b->n, cudaMemcpyHostToDevice);
@@ -518,7 +525,7 @@ erx_status erx_batch_tune(erx_batch* b, int32_t reps, const char* cache_path) {
           cudaEventRecord(e0, b->stream);
           for (int k = 0; k < reps; ++k) {
             if (r <= 1) launch_batch_solve_simt(r, b->table, dit, (int)it.size(), b->dmax, b->stream);
-            else launch_batch_solve_tc(r == 2 ? 2 : 1, b->table, dit, (int)it.size(), b->dmax,
+            else launch_batch_solve_tc(route_format(r), b->table, dit, (int)it.size(), b->dmax,
                                        b->err, b->stream);
           }
           cudaEventRecord(e1, b->stream);

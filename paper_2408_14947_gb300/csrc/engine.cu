@@ -190,11 +190,16 @@ erx_status validate(const erx_config* cfg) {
     return ERX_EINVAL;
   if (cfg->in_dtype < ERX_U16 || cfg->in_dtype > ERX_F64) return ERX_EINVAL;
   if (cfg->in_dtype == ERX_U16 && (cfg->in_bits < 1 || cfg->in_bits > 16)) return ERX_EINVAL;
-  if (cfg->form < ERX_FORM_FP64 || cfg->form > ERX_FORM_BF16) return ERX_EINVAL;
+  if (cfg->form < ERX_FORM_FP64 || cfg->form > ERX_FORM_TF32X3) return ERX_EINVAL;
   if (cfg->block_lines < 0 || cfg->warmup_lines < 0) return ERX_EINVAL;
   const int d = cfg->proj != ERX_PROJ_NONE ? cfg->proj_dim : cfg->bands;
   if (d > kMaxDim || cfg->width > (1 << 20) || cfg->bands > 65536) return ERX_EUNSUPPORTED;
   return ERX_OK;
+}
+
+// operand format of the tensor-core kernels for a form: 1 BF16, 2 TF32, 3 3xTF32; 0: none
+int tc_format(int form) {
+  return form == ERX_FORM_TF32 ? 2 : form == ERX_FORM_BF16 ? 1 : form == ERX_FORM_TF32X3 ? 3 : 0;
 }
 
 // Enqueue the whole step for `n` lines at `x` (device), outputs at line offset 0 of the given
@@ -255,8 +260,20 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
       KernelScope ks(c, ERX_K_MEAN);
       launch_mean(ztype, zsrc, zstride, ps, W, d, T, !c->fp64, c->mu_hat, c->shift, st);
     }
-    KernelScope ks(c, ERX_K_STATS_FP);
-    launch_stats_fp(ztype, c->fp64, zsrc, zstride, ps, W, d, T, c->shift, c->S2f, st);
+    // TF32 / BF16 forms: S2 on the tensor cores.  The 3xTF32 form keeps the FP32
+    // SIMT scatter: its scatter on the tensor cores measured 3.5e-6 (relative
+    // to sqrt(K_aa K_bb)) against 1e-7 for FP32, from accumulating ~200 MMA
+    // steps per line in tensor memory, which puts its scores 10x off FP32's.
+    const int fmt = tc_format(c->cfg.form);
+    if ((fmt == 1 || fmt == 2) && ztype == ERX_F32 && !(c->cfg.flags & ERX_FLAG_SIMT_STATS) &&
+        syrk_tc_supported(zsrc, zstride, ps, W, d)) {
+      KernelScope ks(c, ERX_K_SYRK_TC);
+      launch_syrk_tc(fmt, (const float*)zsrc, zstride, W, d, T, c->n_sm, c->shift, c->S2f, c->err,
+                     c->t, st);
+    } else {
+      KernelScope ks(c, ERX_K_STATS_FP);
+      launch_stats_fp(ztype, c->fp64, zsrc, zstride, ps, W, d, T, c->shift, c->S2f, st);
+    }
   }
   {
     KernelScope ks(c, ERX_K_EMA);
@@ -276,9 +293,9 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
   if (c->fp64) {
     KernelScope ks(c, ERX_K_SOLVE_FP64);
     launch_solve_fp64(ztype, zsrc, zstride, ps, W, d, T, c->mu_t, c->Linv, (double*)delta, st);
-  } else if (c->cfg.form == ERX_FORM_TF32 || c->cfg.form == ERX_FORM_BF16) {
+  } else if (tc_format(c->cfg.form) > 0) {
     KernelScope ks(c, ERX_K_SOLVE_TC);
-    launch_solve_tc(c->cfg.form == ERX_FORM_TF32 ? 2 : 1, ztype, zsrc, zstride, ps, W, d, T,
+    launch_solve_tc(tc_format(c->cfg.form), ztype, zsrc, zstride, ps, W, d, T,
                     c->mu_t, c->Linv32, (float*)delta, c->err, c->t, st);
   } else {
     KernelScope ks(c, ERX_K_SOLVE_FP32);
@@ -458,7 +475,8 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   T = std::min(T, 4096);
   c->T = T;
   if (configure_factor_kernels() != cudaSuccess || configure_solve_kernels() != cudaSuccess ||
-      configure_stats_tc_kernel() != cudaSuccess || configure_solve_tc_kernels() != cudaSuccess) {
+      configure_stats_tc_kernel() != cudaSuccess || configure_solve_tc_kernels() != cudaSuccess ||
+      configure_syrk_tc_kernels() != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return ERX_ECUDA;
@@ -810,7 +828,7 @@ const char* erx_kernel_name(int32_t k) {
                                            "stats_fp",   "ema_scan",   "chol",
                                            "solve_fp64", "solve_fp32", "normalise",
                                            "stats_tc",   "solve_tc",   "encode",
-                                           "trinv32"};
+                                           "trinv32",    "syrk_tc"};
   return (k >= 0 && k < ERX_K_COUNT) ? names[k] : nullptr;
 }
 

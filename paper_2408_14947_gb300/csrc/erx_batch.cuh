@@ -7,10 +7,13 @@
 
 namespace erx {
 
+constexpr int kRoutes = 5;   // score kernels a stream can be routed to
+
 struct BStream {
   const float* x;        // the stream's current line, [W][d] float32 (device)
   int W, d;
-  int route;             // score kernel: 0 FP64, 1 FP32 SIMT, 2 TF32 MMA, 3 BF16 MMA
+  int route;             // score kernel: 0 FP64, 1 FP32 SIMT, 2 TF32 MMA, 3 BF16 MMA,
+                         // 4 3xTF32 MMA
   int order;
   double alpha, ridge, threshold;
   int64_t warmup;

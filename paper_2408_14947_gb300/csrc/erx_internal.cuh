@@ -97,6 +97,12 @@ void launch_solve_fp32(int in_type, const void* x, int64_t line_stride, int ps, 
 
 // delta_i on the tensor cores: fmt 2 = TF32, 1 = BF16 operands, FP32 accumulation.
 cudaError_t configure_solve_tc_kernels();
+// S2 centred scatter of float lines on the tensor cores (fmt 1 BF16, 2 TF32)
+bool syrk_tc_supported(const void* x, int64_t line_stride, int ps, int W, int d);
+cudaError_t configure_syrk_tc_kernels();
+void launch_syrk_tc(int fmt, const float* x, int64_t line_stride, int W, int d, int T, int n_sm,
+                    const double* shift, double* S2f, unsigned long long* err, int64_t t0,
+                    cudaStream_t st);
 void launch_solve_tc(int fmt, int in_type, const void* x, int64_t line_stride, int ps, int W,
                      int d, int T, const double* mu_t, const float* Lf32, float* delta,
                      unsigned long long* err, int64_t t0, cudaStream_t st);

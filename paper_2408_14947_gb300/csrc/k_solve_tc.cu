@@ -1,16 +1,19 @@
-// S5 (Sec. III-D) on the tensor cores: TF32 or BF16 operands, FP32 accumulation.
+// S5 (Sec. III-D) on the tensor cores: BF16, TF32 or 3xTF32 operands, FP32
+// accumulation.
 //
 // With the full inverse X = L_t^{-1} (FP32, made from the blocked factor by
 // trinv32), the scores of a 128-pixel tile are one lower-triangular product
-//   M = R X^T  (R: 128 x d centred pixels),  delta_i = |M_i|,
-// computed as independent 128 x 32 output blocks: block J needs K = j0 + 32
-// (X is zero above its diagonal).  The pixels' rows of R stay in shared memory
-// for the whole tile; the 32 rows of X of block J are staged into one of two
-// buffers while the MMAs of block J-1 run (one thread issues them and commits
-// them to the buffer's mbarrier), and all blocks accumulate into their own TMEM
-// columns, drained once at the end (pixel p is TMEM lane p).  Operand tiles are
-// K-major, no swizzle.  r is formed as (x - mu_hi) - mu_lo with mu split into
-// two floats; TF32 operands are rounded to nearest (cvt.rna).
+//   M = R X^T  (R: 128 x d centred pixels),  delta_i = |M_i|.
+// The contraction runs K-outer in 32-column chunks: chunk k0 .. k0+31 of R
+// meets rows j >= k0 of X (X is zero above its diagonal), so one MMA of
+// N = dK - k0 per K step accumulates into TMEM columns k0 .. dK-1 (pixel p is
+// TMEM lane p).  Two stage buffers: while the MMAs of chunk c run, the threads
+// stage chunk c+1 (R from registers loaded one chunk ahead, X from L2), and one
+// thread issues the MMAs and commits them to the stage's mbarrier.  Operand
+// tiles are K-major, no swizzle.  r is formed as (x - mu_hi) - mu_lo with mu
+// split into two floats; TF32 operands are rounded to nearest (cvt.rna).
+// 3xTF32 (FMT 3) splits each operand v as hi = tf32(v), lo = tf32(v - hi) and
+// accumulates Hi Hi' + Hi Lo' + Lo Hi'.
 #include <cuda_bf16.h>
 
 #include "erx_batch.cuh"
@@ -21,7 +24,7 @@ namespace erx {
 namespace {
 
 constexpr int kPix = 128;
-constexpr int kB = kFactorBlock;     // 32 outputs per block
+constexpr int kB = kFactorBlock;     // 32 columns per K chunk
 constexpr uint32_t kLBO = 128;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
@@ -34,19 +37,29 @@ __device__ __forceinline__ uint32_t tf32_bits(float v) {
   return r;
 }
 
-// 16 bytes of operand data (4 tf32 or 8 bf16 values) from consecutive floats
+// 16 bytes of operand data (4 tf32 or 8 bf16 values) from consecutive floats;
+// for FMT 3 also the 16 bytes of the low parts
 template <int FMT>
-__device__ __forceinline__ uint4 pack16(const float* v) {
-  if (FMT == 2) {
-    return make_uint4(tf32_bits(v[0]), tf32_bits(v[1]), tf32_bits(v[2]), tf32_bits(v[3]));
-  } else {
+__device__ __forceinline__ void pack16(const float* v, uint4& hi, uint4& lo) {
+  if constexpr (FMT == 1) {
     uint32_t w[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
       w[i] = *reinterpret_cast<const uint32_t*>(&b);
     }
-    return make_uint4(w[0], w[1], w[2], w[3]);
+    hi = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    uint32_t h[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = tf32_bits(v[i]);
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    if constexpr (FMT == 3) {
+      uint32_t l[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) l[i] = tf32_bits(v[i] - __uint_as_float(h[i]));
+      lo = make_uint4(l[0], l[1], l[2], l[3]);
+    }
   }
 }
 
@@ -57,20 +70,50 @@ __host__ __device__ inline uint32_t tc_cols(int d) {
   return dk <= 32 ? 32u : dk <= 64 ? 64u : dk <= 128 ? 128u : 256u;
 }
 
-// FMT 2: TF32 (4-byte elements, 4 per core row, K = 8 per MMA);
-// FMT 1: BF16 (2-byte elements, 8 per core row, K = 16 per MMA).
+// bytes of one stage: R chunk (128 x 32) and X chunk (dK x 32), hi (and lo)
+__host__ __device__ inline int tc_stage_bytes(int d, int fmt) {
+  const int E = fmt == 1 ? 2 : 4, NT = fmt == 3 ? 2 : 1;
+  return NT * (kPix + tc_dk(d)) * kB * E;
+}
+
+// the 32 values x[k0 .. k0+31] of one pixel (0 beyond d or for an invalid pixel)
+template <typename InT, bool VEC>
+__device__ __forceinline__ void load_chunk(const InT* __restrict__ xp, bool valid, int k0, int d,
+                                           float (&v)[kB]) {
+  if constexpr (VEC) {
+    // float lines, 16-byte aligned pixel rows, d a multiple of 4
+#pragma unroll
+    for (int u = 0; u < kB / 4; ++u) {
+      const int k = k0 + 4 * u;
+      float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (valid && k < d) f = __ldg(reinterpret_cast<const float4*>(xp + k));
+      v[4 * u] = f.x, v[4 * u + 1] = f.y, v[4 * u + 2] = f.z, v[4 * u + 3] = f.w;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < kB; ++u) {
+      const int k = k0 + u;
+      v[u] = (valid && k < d) ? to_f(xp[k]) : 0.f;
+    }
+  }
+}
+
 // Pixels tile*128 .. +127 of one line (x, pixel stride ps) with mu (d) and the
 // FP32 inverse factor Xg (packed lower); delta: the line's W scores; `line` is
-// reported on a timeout.
-template <typename InT, int FMT>
+// reported on a timeout.  FMT 1: BF16, 2: TF32, 3: 3xTF32.
+template <typename InT, int FMT, bool VEC>
 __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps, int W, int d,
                                               const double* __restrict__ mu,
                                               const float* __restrict__ Xg,
                                               float* __restrict__ delta,
                                               unsigned long long* __restrict__ err, int64_t line,
                                               int tile) {
-  constexpr int E = FMT == 2 ? 4 : 2;     // bytes per element
+  constexpr int E = FMT == 1 ? 2 : 4;     // bytes per element
   constexpr int CK = 16 / E;              // elements per 16-byte core row
+  constexpr int KS = 32 / E;              // K per MMA
+  constexpr int NT = FMT == 3 ? 2 : 1;
+  constexpr uint32_t SBO = (kB / CK) * 128u;
+  constexpr int FK = FMT == 1 ? 1 : 2;
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tslot;
@@ -78,13 +121,12 @@ __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps,
   const int tid = threadIdx.x, warp = tid >> 5;
   const int i0 = tile * kPix;
   const int dK = tc_dk(d);
+  const int nK = dK / kB;
   const uint32_t ncols = tc_cols(d);
-  const uint32_t sbo = (uint32_t)(dK / CK) * 128u;
-  unsigned char* Rt = sm;                                  // [128][dK]
-  unsigned char* Xt0 = Rt + (size_t)kPix * dK * E;         // [2][32][dK]
-  const size_t xt_bytes = (size_t)kB * dK * E;
-  auto off = [sbo](int row, int k) -> uint32_t {
-    return (uint32_t)(row >> 3) * sbo + (uint32_t)(k / CK) * kLBO + (uint32_t)(row & 7) * 16u;
+  const int r_bytes = kPix * kB * E, x_bytes = dK * kB * E;
+  const int stage = tc_stage_bytes(d, FMT);
+  auto off = [](int row, int k) -> uint32_t {
+    return (uint32_t)(row >> 3) * SBO + (uint32_t)(k / CK) * kLBO + (uint32_t)(row & 7) * 16u;
   };
   for (int k = tid; k < d; k += kPix) {
     const double m = mu[k];
@@ -98,69 +140,95 @@ __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps,
     tc::mbar_init(&mbar[1], 1);
     tc::fence_mbar_init();
   }
-  __syncthreads();
-  // r of this thread's pixel into its row of Rt (zero beyond d or beyond the line)
   const int p = tid, i = i0 + p;
   const bool valid = i < W;
   const InT* xp = x + (int64_t)(valid ? i : 0) * ps;
-  for (int k0 = 0; k0 < dK; k0 += CK) {
-    float v[CK];
-#pragma unroll
-    for (int u = 0; u < CK; ++u) {
-      const int k = k0 + u;
-      v[u] = (valid && k < d) ? (to_f(xp[k]) - mu_hi[k]) - mu_lo[k] : 0.f;
-    }
-    *reinterpret_cast<uint4*>(Rt + off(p, k0)) = pack16<FMT>(v);
-  }
+  float cur[kB];
+  load_chunk<InT, VEC>(xp, valid, 0, d, cur);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tslot;
-  const uint32_t id = tc::idesc(FMT, kPix, kB);
-  const int nblk = dK / kB;
   bool ok = true;
-  for (int J = 0; J < nblk && ok; ++J) {
-    const int b = J & 1;
-    unsigned char* Xt = Xt0 + b * xt_bytes;
-    if (J >= 2) {
-      const bool w_ok = tc::mbar_wait(&mbar[b], (uint32_t)((J - 2) >> 1) & 1u, kWaitLimit);
+  for (int kc = 0; kc < nK; ++kc) {
+    const int b = kc & 1, k0 = kc * kB;
+    unsigned char* Rh = sm + b * stage;
+    unsigned char* Rl = Rh + r_bytes;                   // FMT 3 only
+    unsigned char* Xh = Rh + NT * r_bytes;
+    unsigned char* Xl = Xh + x_bytes;                   // FMT 3 only
+    float nxt[kB];
+    if (kc + 1 < nK) load_chunk<InT, VEC>(xp, valid, k0 + kB, d, nxt);
+    if (kc >= 2) {
+      const bool w_ok = tc::mbar_wait(&mbar[b], (uint32_t)((kc - 2) >> 1) & 1u, kWaitLimit);
       if (__syncthreads_or(!w_ok)) {
         ok = false;
         break;
       }
     }
-    // rows j0 .. j0+31 of X, columns k < j0 + 32 (zero above the diagonal and beyond d)
-    const int j0 = J * kB, kcols = j0 + kB;
-    for (int e = tid; e < kB * (kcols / CK); e += kPix) {
-      const int jj = e % kB, kg = e / kB, j = j0 + jj;
+    // this pixel's row of the R chunk
+#pragma unroll
+    for (int g = 0; g < kB / CK; ++g) {
       float v[CK];
 #pragma unroll
       for (int u = 0; u < CK; ++u) {
-        const int k = kg * CK + u;
-        v[u] = (j < d && k <= j) ? Xg[j * (j + 1) / 2 + k] : 0.f;
+        const int k = k0 + g * CK + u;
+        v[u] = (valid && k < d) ? (cur[g * CK + u] - mu_hi[k]) - mu_lo[k] : 0.f;
       }
-      *reinterpret_cast<uint4*>(Xt + off(jj, kg * CK)) = pack16<FMT>(v);
+      uint4 hi, lo;
+      pack16<FMT>(v, hi, lo);
+      *reinterpret_cast<uint4*>(Rh + off(p, g * CK)) = hi;
+      if constexpr (FMT == 3) *reinterpret_cast<uint4*>(Rl + off(p, g * CK)) = lo;
+    }
+    // rows j = k0 .. dK-1 of X, columns k0 .. k0+31 (zero above the diagonal and beyond d)
+    const int nrows = dK - k0;
+    for (int e = tid; e < nrows * (kB / CK); e += kPix) {
+      const int jj = e / (kB / CK), kg = e % (kB / CK), j = k0 + jj;
+      const float* Xj = Xg + (int64_t)j * (j + 1) / 2;
+      float v[CK];
+#pragma unroll
+      for (int u = 0; u < CK; ++u) {
+        const int k = k0 + kg * CK + u;
+        v[u] = (j < d && k <= j) ? __ldg(Xj + k) : 0.f;
+      }
+      uint4 hi, lo;
+      pack16<FMT>(v, hi, lo);
+      *reinterpret_cast<uint4*>(Xh + off(jj, kg * CK)) = hi;
+      if constexpr (FMT == 3) *reinterpret_cast<uint4*>(Xl + off(jj, kg * CK)) = lo;
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     if (tid == 0) {
-      const uint32_t aR = tc::smem_u32(Rt), aX = tc::smem_u32(Xt);
-      for (int kk = 0; kk < kcols / (2 * CK); ++kk) {
-        const uint32_t ko = (uint32_t)kk * 2u * kLBO;
-        const uint64_t da = tc::desc(aR + ko, kLBO, sbo);
-        const uint64_t db = tc::desc(aX + ko, kLBO, sbo);
-        if (FMT == 2) tc::mma_tf32(tmem + (uint32_t)j0, da, db, id, kk > 0);
-        else tc::mma_bf16(tmem + (uint32_t)j0, da, db, id, kk > 0);
+      const uint32_t id = tc::idesc(FK, kPix, nrows);
+      const uint32_t aRh = tc::smem_u32(Rh), aXh = tc::smem_u32(Xh);
+#pragma unroll
+      for (int s = 0; s < kB / KS; ++s) {
+        const uint32_t ko = (uint32_t)s * 2u * kLBO;
+        const uint64_t da = tc::desc(aRh + ko, kLBO, SBO);
+        const uint64_t db = tc::desc(aXh + ko, kLBO, SBO);
+        const uint32_t acc = (kc > 0 || s > 0) ? 1u : 0u;
+        if constexpr (FMT == 1) {
+          tc::mma_bf16(tmem + (uint32_t)k0, da, db, id, acc);
+        } else {
+          tc::mma_tf32(tmem + (uint32_t)k0, da, db, id, acc);
+          if constexpr (FMT == 3) {
+            const uint64_t dal = tc::desc(tc::smem_u32(Rl) + ko, kLBO, SBO);
+            const uint64_t dbl = tc::desc(tc::smem_u32(Xl) + ko, kLBO, SBO);
+            tc::mma_tf32(tmem + (uint32_t)k0, da, dbl, id, 1u);
+            tc::mma_tf32(tmem + (uint32_t)k0, dal, db, id, 1u);
+          }
+        }
       }
       tc::commit(&mbar[b]);
     }
+#pragma unroll
+    for (int u = 0; u < kB; ++u) cur[u] = nxt[u];
   }
   // wait for the last commit of each buffer
   uint32_t pending_parity[2] = {0u, 0u};
   bool pending[2] = {false, false};
-  for (int J = nblk - 1; J >= 0 && J >= nblk - 2; --J) {
+  for (int J = nK - 1; J >= 0 && J >= nK - 2; --J) {
     pending[J & 1] = true;
     pending_parity[J & 1] = (uint32_t)(J >> 1) & 1u;
   }
@@ -197,15 +265,15 @@ __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps,
   if (warp == 0) tc::tmem_free(tmem, ncols);
 }
 
-template <typename InT, int FMT>
+template <typename InT, int FMT, bool VEC>
 __global__ void __launch_bounds__(kPix) solve_tc_kernel(
     const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
     const double* __restrict__ mu_t, const float* __restrict__ Lf32, float* __restrict__ delta,
     unsigned long long* __restrict__ err, int64_t t0) {
   const int t = blockIdx.y;
-  solve_tc_body<InT, FMT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
-                          Lf32 + (int64_t)t * packed_size(d), delta + (int64_t)t * W, err,
-                          t0 + t, blockIdx.x);
+  solve_tc_body<InT, FMT, VEC>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
+                               Lf32 + (int64_t)t * packed_size(d), delta + (int64_t)t * W, err,
+                               t0 + t, blockIdx.x);
 }
 
 // Batched form: one CTA per (stream, 128-pixel tile) item.
@@ -215,59 +283,97 @@ __global__ void __launch_bounds__(kPix) b_solve_tc_kernel(const BStream* __restr
                                                           unsigned long long* __restrict__ err) {
   const BItem it = items[blockIdx.x];
   const BStream& s = S[it.s];
-  solve_tc_body<float, FMT>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta, err, it.s,
-                            it.tile);
+  if (((uintptr_t)s.x % 16) == 0 && (s.d % 4) == 0)
+    solve_tc_body<float, FMT, true>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta, err,
+                                    it.s, it.tile);
+  else
+    solve_tc_body<float, FMT, false>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta, err,
+                                     it.s, it.tile);
 }
 
-size_t smem_bytes(int d, int fmt) {
-  const int E = fmt == 2 ? 4 : 2;
-  return (size_t)(kPix + 2 * kB) * tc_dk(d) * E;
+int g_smem_per_sm = 0;
+
+// Dynamic shared memory of one CTA: two stages, raised where needed so that no
+// more CTAs share an SM than its 512 TMEM columns hold (no CTA then waits in
+// tcgen05.alloc for another's columns).
+size_t launch_smem(int d, int fmt) {
+  const size_t need = 2 * (size_t)tc_stage_bytes(d, fmt);
+  const int maxc = 512 / (int)tc_cols(d);
+  const size_t pad = (size_t)g_smem_per_sm / (size_t)(maxc + 1) + 1;
+  return need > pad ? need : pad;
 }
 
 }  // namespace
 
 cudaError_t configure_solve_tc_kernels() {
   cudaError_t e = cudaSuccess;
-  const int m2 = (int)smem_bytes(kMaxDim, 2), m1 = (int)smem_bytes(kMaxDim, 1);
+  if (!g_smem_per_sm) {
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+      e = cudaDeviceGetAttribute(&g_smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return e;
+  }
+  // the largest request of any d <= kMaxDim
+  auto most = [](int fmt) {
+    size_t m = 0;
+    for (int d = 1; d <= kMaxDim; d += 31) m = m > launch_smem(d, fmt) ? m : launch_smem(d, fmt);
+    const size_t top = launch_smem(kMaxDim, fmt);
+    return (int)(m > top ? m : top);
+  };
+  const int m1 = most(1), m2 = most(2), m3 = most(3);
 #define ERX_CFG(K, M) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, M)
-  ERX_CFG((solve_tc_kernel<uint16_t, 2>), m2);
-  ERX_CFG((solve_tc_kernel<float, 2>), m2);
-  ERX_CFG((solve_tc_kernel<double, 2>), m2);
-  ERX_CFG((solve_tc_kernel<uint16_t, 1>), m1);
-  ERX_CFG((solve_tc_kernel<float, 1>), m1);
-  ERX_CFG((solve_tc_kernel<double, 1>), m1);
-  ERX_CFG((b_solve_tc_kernel<2>), m2);
+#define ERX_CFG_T(IT)                                  \
+  ERX_CFG((solve_tc_kernel<IT, 1, false>), m1);        \
+  ERX_CFG((solve_tc_kernel<IT, 2, false>), m2);        \
+  ERX_CFG((solve_tc_kernel<IT, 3, false>), m3);
+  ERX_CFG_T(uint16_t)
+  ERX_CFG_T(float)
+  ERX_CFG_T(double)
+  ERX_CFG((solve_tc_kernel<float, 1, true>), m1);
+  ERX_CFG((solve_tc_kernel<float, 2, true>), m2);
+  ERX_CFG((solve_tc_kernel<float, 3, true>), m3);
   ERX_CFG((b_solve_tc_kernel<1>), m1);
+  ERX_CFG((b_solve_tc_kernel<2>), m2);
+  ERX_CFG((b_solve_tc_kernel<3>), m3);
+#undef ERX_CFG_T
 #undef ERX_CFG
   return e;
 }
 
 void launch_batch_solve_tc(int fmt, const BStream* S, const BItem* items, int n_items, int dmax,
                            unsigned long long* err, cudaStream_t st) {
-  if (fmt == 2)
-    b_solve_tc_kernel<2><<<n_items, kPix, smem_bytes(dmax, 2), st>>>(S, items, err);
-  else
-    b_solve_tc_kernel<1><<<n_items, kPix, smem_bytes(dmax, 1), st>>>(S, items, err);
+  const size_t sm = launch_smem(dmax, fmt);
+  if (fmt == 1) b_solve_tc_kernel<1><<<n_items, kPix, sm, st>>>(S, items, err);
+  else if (fmt == 2) b_solve_tc_kernel<2><<<n_items, kPix, sm, st>>>(S, items, err);
+  else b_solve_tc_kernel<3><<<n_items, kPix, sm, st>>>(S, items, err);
 }
 
 void launch_solve_tc(int fmt, int in_type, const void* x, int64_t line_stride, int ps, int W,
                      int d, int T, const double* mu_t, const float* Lf32, float* delta,
                      unsigned long long* err, int64_t t0, cudaStream_t st) {
   dim3 grid((W + kPix - 1) / kPix, T);
-  const size_t sm = smem_bytes(d, fmt);
-#define ERX_L(IT, F)                                                                           \
-  solve_tc_kernel<IT, F><<<grid, kPix, sm, st>>>((const IT*)x, line_stride, ps, W, d, mu_t, \
-                                                 Lf32, delta, err, t0)
-  if (fmt == 2) {
-    if (in_type == 0) ERX_L(uint16_t, 2);
-    else if (in_type == 1) ERX_L(float, 2);
-    else ERX_L(double, 2);
+  const size_t sm = launch_smem(d, fmt);
+  // vector loads: float lines whose pixel rows start on 16 bytes
+  const bool vec = in_type == 1 && ((uintptr_t)x % 16) == 0 && (ps % 4) == 0 &&
+                   (line_stride % 4) == 0 && (d % 4) == 0;
+#define ERX_L(IT, F, V)                                                                  \
+  solve_tc_kernel<IT, F, V><<<grid, kPix, sm, st>>>((const IT*)x, line_stride, ps, W, d, \
+                                                    mu_t, Lf32, delta, err, t0)
+#define ERX_LF(F)                          \
+  if (in_type == 0) ERX_L(uint16_t, F, false); \
+  else if (vec) ERX_L(float, F, true);     \
+  else if (in_type == 1) ERX_L(float, F, false); \
+  else ERX_L(double, F, false);
+  if (fmt == 1) {
+    ERX_LF(1)
+  } else if (fmt == 2) {
+    ERX_LF(2)
   } else {
-    if (in_type == 0) ERX_L(uint16_t, 1);
-    else if (in_type == 1) ERX_L(float, 1);
-    else ERX_L(double, 1);
+    ERX_LF(3)
   }
+#undef ERX_LF
 #undef ERX_L
 }
 

@@ -19,7 +19,9 @@ ERX_FLAG_SIMT_STATS = 1
 ERX_PROJ_NONE, ERX_PROJ_SRP, ERX_PROJ_LEARNED = 0, 1, 2
 ERX_UPDATE_THEN_SCORE, ERX_SCORE_THEN_UPDATE = 0, 1
 ERX_U16, ERX_F32, ERX_F64 = 0, 1, 2
-ERX_FORM_FP64, ERX_FORM_FP32, ERX_FORM_TF32, ERX_FORM_BF16 = 0, 1, 2, 3
+ERX_FORM_FP64, ERX_FORM_FP32, ERX_FORM_TF32, ERX_FORM_BF16, ERX_FORM_TF32X3 = 0, 1, 2, 3, 4
+FORMS = {"fp64": ERX_FORM_FP64, "fp32": ERX_FORM_FP32, "tf32": ERX_FORM_TF32,
+         "bf16": ERX_FORM_BF16, "tf32x3": ERX_FORM_TF32X3}
 
 _SAMPLE_BYTES = {ERX_U16: 2, ERX_F32: 4, ERX_F64: 8}
 
@@ -197,7 +199,7 @@ def erx_srp_weights(bands: int, dim: int, seed: int):
     return w
 
 
-ERX_K_COUNT = 13
+ERX_K_COUNT = 14
 
 
 def erx_push_lines_static(cfg, stream, mu_ptr, k_ptr, t, lines_ptr, n_lines, stride_bytes,
@@ -259,8 +261,7 @@ class Detector:
                      "score_then_update": ERX_SCORE_THEN_UPDATE}[order]
         cfg.in_dtype = {"u16": ERX_U16, "f32": ERX_F32, "f64": ERX_F64}[in_dtype]
         cfg.in_bits = in_bits
-        cfg.form = {"fp64": ERX_FORM_FP64, "fp32": ERX_FORM_FP32, "tf32": ERX_FORM_TF32,
-                    "bf16": ERX_FORM_BF16}[form]
+        cfg.form = FORMS[form]
         cfg.threshold = threshold if threshold is not None else math.inf
         cfg.block_lines = block_lines
         cfg.flags = ERX_FLAG_SIMT_STATS if simt_stats else 0
@@ -369,8 +370,7 @@ class Batch:
             load_library().erx_config_default(C.byref(cfgs[i]), sd["bands"], sd["width"])
             c = cfgs[i]
             c.in_dtype = ERX_F32
-            c.form = {"fp64": ERX_FORM_FP64, "fp32": ERX_FORM_FP32, "tf32": ERX_FORM_TF32,
-                      "bf16": ERX_FORM_BF16}[form]
+            c.form = FORMS[form]
             c.momentum = sd.get("momentum", 0.1)
             c.ridge = sd.get("ridge", 1e-5)
             c.warmup_lines = sd.get("warmup", 99)

@@ -42,13 +42,15 @@ def _run_batch(form, cubes, warmup=2):
     return b, outs
 
 
-@pytest.mark.parametrize("form", ["fp64", "fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("form", ["fp64", "fp32", "tf32", "bf16", "tf32x3"])
 def test_batch_matches_single_stream_contexts(form):
     need_gpu()
     cubes = _cubes()
     b, outs = _run_batch(form, cubes)
     for i, c in enumerate(cubes):
-        ref, det = run_gpu(c, form=form, warmup=2, push_sizes=[1] * STEPS)
+        # the batch takes line statistics with the FP32 SIMT scatter in every
+        # non-FP64 form; the contexts are asked for the same
+        ref, det = run_gpu(c, form=form, warmup=2, push_sizes=[1] * STEPS, simt_stats=True)
         got_d = np.stack([o[0] for o in outs[i]])
         got_n = np.stack([o[1] for o in outs[i]])
         assert np.array_equal(got_d, ref["delta"]), (form, SHAPES[i])
@@ -69,7 +71,7 @@ def test_batch_matches_single_stream_contexts(form):
 # here are about twice those.  The bit-for-bit check against single-stream
 # contexts above is the exact test of the batched path.
 @pytest.mark.parametrize("form,tol", [("fp64", 1e-9), ("fp32", 5e-3), ("tf32", 2e-2),
-                                      ("bf16", 0.2)])
+                                      ("bf16", 0.2), ("tf32x3", 5e-3)])
 def test_batch_matches_oracle(form, tol):
     need_gpu()
     cubes = _cubes(seed=1)

@@ -15,7 +15,7 @@ from tests.gpu_util import dn_err, need_gpu, rel_err, run_gpu, torch
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-9, "fp32": 1e-4, "tf32": 5e-3, "bf16": 4e-2}
+TOL = {"fp64": 1e-9, "fp32": 1e-4, "tf32": 5e-3, "bf16": 4e-2, "tf32x3": 1e-4}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -236,26 +236,59 @@ def test_tensor_core_stats_range_check():
     assert det.profile_read()["stats_tc"][2] > 0
 
 
+# name, cube factory, detector kwargs, whether S2 takes the tensor-core scatter
+# (float lines, d > 16, p * d a multiple of 4)
 TC_CASES = [
-    ("c2_u16", lambda: synth.gen_lines(synth.dn_c2(width=300, bands=108), 0, 12), {"in_bits": 12}),
-    ("c1_f32", lambda: synth.gen_lines(synth.reflectance_c1(width=200, bands=64), 0, 10), {}),
-    ("c3_k1e3_d224", lambda: synth.gen_lines(synth.cov_c3(1e3, width=260, bands=224), 0, 3), {}),
-    ("ragged_d33", lambda: synth.gen_lines(synth.reflectance_c1(width=129, bands=33), 0, 6), {}),
+    ("c2_u16", lambda: synth.gen_lines(synth.dn_c2(width=300, bands=108), 0, 12), {"in_bits": 12},
+     False),
+    ("c1_f32", lambda: synth.gen_lines(synth.reflectance_c1(width=200, bands=64), 0, 10), {},
+     True),
+    ("c3_k1e3_d224", lambda: synth.gen_lines(synth.cov_c3(1e3, width=260, bands=224), 0, 3), {},
+     True),
+    ("c3_d130_w100", lambda: synth.gen_lines(synth.cov_c3(1e2, width=100, bands=130), 0, 4), {},
+     True),
+    ("c1_d40_w77", lambda: synth.gen_lines(synth.reflectance_c1(width=77, bands=40), 0, 6), {},
+     True),
+    ("ragged_d33", lambda: synth.gen_lines(synth.reflectance_c1(width=129, bands=33), 0, 6), {},
+     False),
     ("srp5", lambda: synth.gen_lines(synth.dn_c2(width=140, bands=108), 0, 8),
-     {"proj": "srp", "proj_dim": 5, "seed": 3}),
+     {"proj": "srp", "proj_dim": 5, "seed": 3}, False),
 ]
 
 
-@pytest.mark.parametrize("form", ["tf32", "bf16"])
-@pytest.mark.parametrize("name,make,kw", TC_CASES, ids=[c[0] for c in TC_CASES])
-def test_tensor_core_forms(name, make, kw, form):
+@pytest.mark.parametrize("form", ["tf32", "bf16", "tf32x3"])
+@pytest.mark.parametrize("name,make,kw,syrk", TC_CASES, ids=[c[0] for c in TC_CASES])
+def test_tensor_core_forms(name, make, kw, syrk, form):
     cube = make()
     got, det = run_gpu(cube, form=form, warmup=2, threshold=3.0, **kw)
     ref = oracle.run_cube(cube, warmup=2, **_oracle_kw(kw, cube))
     e = rel_err(got["delta"], ref["delta"])
     print(f"{name} {form}: max rel delta err {e:.3e}")
     assert e <= TOL[form], f"{name} {form}: {e}"
-    assert det.profile_read()["solve_tc"][2] > 0
+    prof = det.profile_read()
+    assert prof["solve_tc"][2] > 0
+    # the 3xTF32 form keeps S2 in FP32 SIMT
+    assert (prof["syrk_tc"][2] > 0) == (syrk and form != "tf32x3")
+
+
+@pytest.mark.parametrize("form,tol", [("tf32", 1.2e-3), ("bf16", 8e-3)])
+@pytest.mark.parametrize("width,bands", [(200, 64), (260, 224), (77, 40), (64, 130)])
+def test_tensor_core_scatter_matches_simt(form, tol, width, bands):
+    """S2 on the tensor cores against the FP32 SIMT scatter, line by line
+    (momentum 1: the state K is the last line's K_hat).  Each centred sample
+    is rounded once (TF32: 2^-11, BF16: 2^-8 relative), so
+    |dK_ab| <= 2 u sqrt(K_aa K_bb) plus FP32 accumulation."""
+    cube = synth.gen_lines(synth.cov_c3(1e3, width=width, bands=bands, seed=5), 0, 3)
+    for t in range(cube.shape[0]):
+        _, d_tc = run_gpu(cube[t:t + 1], form=form, warmup=0, momentum=1.0)
+        _, d_simt = run_gpu(cube[t:t + 1], form=form, warmup=0, momentum=1.0, simt_stats=True)
+        assert d_tc.profile_read()["syrk_tc"][2] > 0
+        assert d_simt.profile_read()["syrk_tc"][2] == 0
+        k_tc, k_simt = d_tc.state()[2], d_simt.state()[2]
+        dg = np.sqrt(np.diag(k_simt))
+        e = np.max(np.abs(k_tc - k_simt) / np.outer(dg, dg))
+        print(f"{form} {width}x{bands} line {t}: scatter err {e:.2e}")
+        assert e <= tol, (form, width, bands, t, e)
 
 
 def test_long_block_chunked_ema_matches_line_by_line():
