@@ -8,13 +8,19 @@
 // d/32 small inverses (d * 32^2 / 6 DFMA) instead of the full d^3/6.
 //
 // The packed factor (d(d+1)/2 doubles, 197 KiB at d = 224) lives in shared
-// memory; each pivot takes one reciprocal square root (l_jj = a_jj rsqrt(a_jj)).  Right-looking Cholesky: per column j the pivot is checked and
-// square-rooted, the column scaled, and the trailing triangle updated
-// A_ik -= l_ij l_kj with its elements spread evenly over all threads (the FP64
-// pipe is 2 lanes/clk/SM on GB300, so idle lanes of a partial warp cost as
-// much as busy ones).  Each diagonal block is then inverted by one warp, one
-// column per lane, with the block in registers.  A pivot that is not positive
-// and finite records the line in the error slot and poisons its scores (NaN).
+// memory.  Right-looking Cholesky in panels of kPB = 8 columns:
+//  * panel: thread r owns row j0 + r and keeps its kPB panel entries in
+//    registers.  Per column: every row scales its entry by 1/l_jj (the panel
+//    rows publish theirs), barrier; every row updates its later panel entries
+//    and the next pivot's row takes l_jj = a_jj rsqrt(a_jj), barrier.  No
+//    multiply is repeated across threads (the FP64 pipe is the bottleneck);
+//  * trailing update A22 -= L21 L21^T as a rank-kPB step in 4 x 4 register
+//    tiles over the lower triangle, reading L21 from a column-major copy.
+// Every element receives the same multiply-adds in the same order as in the
+// column-by-column algorithm (a_ik = fma(-l_ij, l_kj, a_ik), j ascending).
+// Each diagonal block is then inverted by one warp, one column per lane.  A
+// pivot that is not positive and finite records the line in the error slot
+// and poisons its scores (NaN).
 #include <cmath>
 
 #include "erx_batch.cuh"
@@ -25,56 +31,131 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kNB = kFactorBlock;
+constexpr int kPB = 8;             // panel width
 
 __device__ __forceinline__ int pidx(int i, int k) { return i * (i + 1) / 2 + k; }
 
+// rows of the column-major L21 copy (a multiple of 4: whole register tiles of 2 or 4)
+__host__ __device__ inline int lp_stride(int d) { return (d + 3) & ~3; }
+// shared memory: A (packed, padded to 16 bytes) | L21 copy [kPB][lp_stride] | 1/l_jj [d]
+__host__ __device__ inline size_t chol_smem(int d) {
+  return (size_t)(((packed_size(d) + 1) & ~1) + kPB * lp_stride(d) + d) * sizeof(double);
+}
+
 // Factor one line's K (packed, src) into the blocked factor (dst, dst32);
-// `line` is the global line index reported on a bad pivot.
+// `line` is the global line index reported on a bad pivot.  TS: edge of the
+// trailing update's register tiles (4 where one CTA fills an SM, 2 where four
+// CTAs share it and each thread has 64 registers).
+template <int TS>
 __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d, double ridge,
                                           double* __restrict__ dst, float* __restrict__ d32,
                                           unsigned long long* __restrict__ err, int64_t line) {
   extern __shared__ __align__(16) double sm[];
+  __shared__ double Pl[kPB][kPB];   // Pl[r][c] = l_{j0+r, j0+c}: the panel rows' scaled entries
+  __shared__ double s_ri[kPB];      // 1 / l_jj of the panel's columns
   const int P = d * (d + 1) / 2;
+  const int ls = lp_stride(d);
   double* A = sm;
-  double* col = sm + P;          // scaled column of the current step
-  double* rdiag = col + d;       // 1 / l_jj
-  __shared__ double s_inv;
-  for (int q = threadIdx.x; q < P; q += kThreads) A[q] = src[q];
+  double* Lp = sm + ((P + 1) & ~1);
+  double* rdiag = Lp + kPB * ls;    // 1 / l_jj
+  const int tid = threadIdx.x;
+  for (int q = tid; q < P; q += kThreads) A[q] = src[q];
   __syncthreads();
-  for (int j = threadIdx.x; j < d; j += kThreads) A[pidx(j, j)] += ridge;
+  for (int j = tid; j < d; j += kThreads) A[pidx(j, j)] += ridge;
   __syncthreads();
+  // pivot of column j (its updated diagonal a): l_jj = a rsqrt(a), published
+  auto pivot = [&](double& a, int jj, int j) {
+    if (!(a > 0.0) || !isfinite(a)) {
+      atomicMin(&err[kErrNotPD], (unsigned long long)line);
+      a = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    const double ri = rsqrt(a);
+    s_ri[jj] = ri;
+    rdiag[j] = ri;
+    a = a * ri;
+  };
 
-  for (int j = 0; j < d; ++j) {
-    if (threadIdx.x == 0) {
-      double ajj = A[pidx(j, j)];
-      if (!(ajj > 0.0) || !isfinite(ajj)) {
-        atomicMin(&err[kErrNotPD], (unsigned long long)line);
-        ajj = __longlong_as_double(0x7ff8000000000000ll);
+  for (int j0 = 0; j0 < d; j0 += kPB) {
+    const int jb = min(kPB, d - j0);
+    const int rl = tid, i = j0 + rl;          // this thread's row (d - j0 <= kThreads)
+    const bool own = i < d;
+    double a[kPB];
+#pragma unroll
+    for (int c = 0; c < kPB; ++c) a[c] = (own && c < jb && c <= rl) ? A[pidx(i, j0 + c)] : 0.0;
+    if (own && rl == 0) pivot(a[0], 0, j0);
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < kPB; ++jj) {
+      if (jj >= jb) break;
+      // scale this row's entry of column jj; panel rows publish theirs
+      double lij = 0.0;
+      if (own && rl > jj) {
+        lij = a[jj] * s_ri[jj];
+        a[jj] = lij;
+        if (rl < jb) Pl[rl][jj] = lij;
       }
-      const double ri = rsqrt(ajj);                   // 1 / l_jj
-      A[pidx(j, j)] = ajj * ri;                       // l_jj
-      s_inv = ri;
-      rdiag[j] = ri;
+      __syncthreads();
+      // update this row's later panel entries; the next pivot's row takes its pivot
+      if (own && rl > jj) {
+#pragma unroll
+        for (int c = jj + 1; c < kPB; ++c)
+          if (c < jb && c <= rl) a[c] = fma(-lij, Pl[c][jj], a[c]);
+        if (rl == jj + 1 && rl < jb) pivot(a[min(jj + 1, kPB - 1)], jj + 1, i);
+      }
+      __syncthreads();
+    }
+    // the panel's final entries back into A; L21 (rows below the panel) into
+    // its column-major copy, zero-padded to whole 4-row tiles
+    if (own) {
+#pragma unroll
+      for (int c = 0; c < kPB; ++c)
+        if (c < jb && c <= rl) A[pidx(i, j0 + c)] = a[c];
+    }
+    const int m = d - j0 - jb;                 // trailing rows
+    const int r2 = rl - jb;
+    if (r2 >= 0 && r2 < ((m + TS - 1) / TS) * TS) {
+#pragma unroll
+      for (int c = 0; c < kPB; ++c) Lp[c * ls + r2] = (r2 < m && c < jb) ? a[c] : 0.0;
     }
     __syncthreads();
-    const double inv = s_inv;
-    for (int i = j + 1 + threadIdx.x; i < d; i += kThreads) {
-      const double v = A[pidx(i, j)] * inv;
-      A[pidx(i, j)] = v;
-      col[i] = v;
-    }
-    __syncthreads();
-    // trailing triangle rows/cols j+1 .. d-1: m(m+1)/2 elements, enumerated evenly
-    const int m = d - 1 - j;
-    const int n = m * (m + 1) / 2;
-    for (int q = threadIdx.x; q < n; q += kThreads) {
-      int r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-      while (r * (r + 1) / 2 > q) --r;
-      while ((r + 1) * (r + 2) / 2 <= q) ++r;
-      const int c = q - r * (r + 1) / 2;
-      const int i = j + 1 + r, k = j + 1 + c;
-      const int p = pidx(i, k);
-      A[p] = fma(-col[i], col[k], A[p]);
+    if (m > 0) {
+      const int nt = (m + TS - 1) / TS;
+      const int ntile = nt * (nt + 1) / 2;
+      const int g0 = j0 + jb;
+      for (int q = tid; q < ntile; q += kThreads) {
+        int I = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+        while (I * (I + 1) / 2 > q) --I;
+        while ((I + 1) * (I + 2) / 2 <= q) ++I;
+        const int J = q - I * (I + 1) / 2;
+        double acc[TS][TS];
+#pragma unroll
+        for (int u = 0; u < TS; ++u)
+#pragma unroll
+          for (int v = 0; v < TS; ++v) {
+            const int gi = g0 + TS * I + u, gk = g0 + TS * J + v;
+            acc[u][v] = (gi < d && gk <= gi) ? A[pidx(gi, gk)] : 0.0;
+          }
+        for (int c = 0; c < jb; ++c) {
+          double av[TS], bv[TS];
+#pragma unroll
+          for (int h = 0; h < TS; h += 2) {
+            const double2 x = *reinterpret_cast<const double2*>(Lp + c * ls + TS * I + h);
+            const double2 y = *reinterpret_cast<const double2*>(Lp + c * ls + TS * J + h);
+            av[h] = x.x, av[h + 1] = x.y, bv[h] = y.x, bv[h + 1] = y.y;
+          }
+#pragma unroll
+          for (int u = 0; u < TS; ++u)
+#pragma unroll
+            for (int v = 0; v < TS; ++v) acc[u][v] = fma(-av[u], bv[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < TS; ++u)
+#pragma unroll
+          for (int v = 0; v < TS; ++v) {
+            const int gi = g0 + TS * I + u, gk = g0 + TS * J + v;
+            if (gi < d && gk <= gi) A[pidx(gi, gk)] = acc[u][v];
+          }
+      }
     }
     __syncthreads();
   }
@@ -110,14 +191,16 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) chol_kernel(const double* __restrict__ K_t, int d,
-                                                       double ridge, double* __restrict__ Lf,
-                                                       float* __restrict__ Lf32,
-                                                       unsigned long long* __restrict__ err,
-                                                       int64_t t0) {
+template <int TS, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) chol_kernel(const double* __restrict__ K_t,
+                                                          int d, double ridge,
+                                                          double* __restrict__ Lf,
+                                                          float* __restrict__ Lf32,
+                                                          unsigned long long* __restrict__ err,
+                                                          int64_t t0) {
   const int t = blockIdx.x;
   const int64_t P = packed_size(d);
-  chol_body(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err, t0 + t);
+  chol_body<TS>(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err, t0 + t);
 }
 
 // Batched form: one CTA per stream.
@@ -125,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 4) b_chol_kernel(const BStream* __re
                                                          bool want32,
                                                          unsigned long long* __restrict__ err) {
   const BStream& s = S[blockIdx.x];
-  chol_body(s.K_t, s.d, s.ridge, s.Lf, want32 ? s.Lf32 : nullptr, err, blockIdx.x);
+  chol_body<2>(s.K_t, s.d, s.ridge, s.Lf, want32 ? s.Lf32 : nullptr, err, blockIdx.x);
 }
 
 // Full inverse X = L^{-1} in FP32 from the float blocked factor, for the FP32,
@@ -196,8 +279,11 @@ void launch_batch_trinv32(const BStream* S, int n, int dmax, cudaStream_t st) {
 }
 
 cudaError_t configure_factor_kernels() {
-  const int m = (int)((packed_size(kMaxDim) + 2 * kMaxDim) * sizeof(double));
-  cudaError_t e = cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+  const int m = (int)chol_smem(kMaxDim);
+  cudaError_t e =
+      cudaFuncSetAttribute(chol_kernel<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chol_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(b_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   const int m32 = (int)(packed_size(kMaxDim) * sizeof(float));
@@ -210,14 +296,16 @@ cudaError_t configure_factor_kernels() {
 
 void launch_batch_chol(const BStream* S, int n, int dmax, bool want32, unsigned long long* err,
                        cudaStream_t st) {
-  const size_t smem = (size_t)(packed_size(dmax) + 2 * dmax) * sizeof(double);
-  b_chol_kernel<<<n, kThreads, smem, st>>>(S, want32, err);
+  b_chol_kernel<<<n, kThreads, chol_smem(dmax), st>>>(S, want32, err);
 }
 
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, float* Lf32,
                      unsigned long long* err, int64_t t0, cudaStream_t st) {
-  const size_t smem = (size_t)(packed_size(d) + 2 * d) * sizeof(double);
-  chol_kernel<<<T, kThreads, smem, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
+  // above 128 dimensions the factor fills an SM's shared memory: one CTA per SM
+  if (d > 128)
+    chol_kernel<4, 1><<<T, kThreads, chol_smem(d), st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
+  else
+    chol_kernel<2, 4><<<T, kThreads, chol_smem(d), st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
 }
 
 }  // namespace erx
