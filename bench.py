@@ -451,9 +451,9 @@ def run_ours(args):
     else:
         peak, unit, bound = FP64_PEAK_GFLOPS, "GFLOP/s", "alu"
     # DRAM bytes (read + write) of one solve_fp64 launch from the ncu capture in
-    # profiles/solve_fp64_c2_2000x640x108.md: 271.5 MB for 1405 lines, scaled to
-    # this run's average lines per launch (traffic grows with the lines).
-    traffic = 271.5e6 * lines_per_launch / 1405.0 if dom == "solve_fp64" else None
+    # profiles/solve_fp64_c2_2000x640x108.md: 383.9 MB for a 2000-line launch,
+    # scaled to this run's average lines per launch (traffic grows with the lines).
+    traffic = 383.88e6 * lines_per_launch / 2000.0 if dom == "solve_fp64" else None
     roof = {"bound": bound, "pipe": "fp64" if dom != "stats_int" else "int32", "kernel": dom,
             "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
             "traffic": traffic, "algorithmic_bytes": (WIDTH * BANDS * 2 + WIDTH * 8 +
@@ -554,6 +554,42 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile_case(args):
+    """One block of a named workload through one form, for profiler captures:
+    a warm-up push, then one push of `--lines` lines (its kernels are the ones
+    to capture: skip the warm-up push's launches)."""
+    import numpy as np
+    import torch
+
+    from paper_2408_14947_gb300 import Detector, _build
+    _build.build()
+    kind, form = args.profile_case.split("_", 1)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    if kind == "c2":
+        cube = make_cube(args.lines, seed=0)
+        x = torch.from_numpy(cube.view(np.int16)).to(dev)
+        det = Detector(BANDS, WIDTH, in_dtype="u16", in_bits=BITS, form=form, stream=stream,
+                       block_lines=args.lines)
+    else:
+        cube = make_cube(args.lines, seed=1, kind="c3", width=1024, bands=224, kappa=1e3)
+        x = torch.from_numpy(cube).to(dev)
+        det = Detector(224, 1024, in_dtype="f32", form=form, stream=stream,
+                       block_lines=args.lines)
+    del cube
+    det.push(x)
+    det.sync()
+    det.reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    det.push(x)
+    e1.record(stream)
+    det.sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "lines": args.lines,
+                      "ms": e0.elapsed_time(e1)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -566,9 +602,17 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip latency, forms, e2e, baseline")
     ap.add_argument("--lines", type=int, default=LINES,
                     help="lines of the workload cube (smaller cubes for profiler captures)")
+    ap.add_argument("--profile-case", default=None,
+                    choices=["c2_fp64", "c2_fp32", "c2_tf32", "c2_bf16", "c3_fp64", "c3_fp32",
+                             "c3_tf32", "c3_bf16", "c3_tf32x3"],
+                    help="push one block of --lines lines of a workload (c2: 640 px x 108 "
+                         "bands u16; c3: 1024 px x 224 bands f32, kappa 1e3) through one "
+                         "form, after one warm-up push, for profiler captures; no bench line")
     args = ap.parse_args()
     globals()["LINES"] = args.lines
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

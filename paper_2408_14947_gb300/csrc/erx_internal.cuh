@@ -30,8 +30,9 @@ __host__ __device__ inline int64_t packed_size(int d) { return (int64_t)d * (d +
 // the state produce the same bits.
 #ifdef __CUDACC__
 // K_hat_ab from the scatter S_ab about shift c: (S_ab - p e_a e_b) / (p - 1), e = mu_hat - c
-__device__ __forceinline__ double ema_khat(double S, double ea, double eb, double Wd) {
-  return __dmul_rn(__dsub_rn(S, __dmul_rn(__dmul_rn(Wd, ea), eb)), __drcp_rn(__dsub_rn(Wd, 1.0)));
+// rw1 = 1 / (W - 1), correctly rounded (W - 1 is exact)
+__device__ __forceinline__ double ema_khat(double S, double ea, double eb, double Wd, double rw1) {
+  return __dmul_rn(__dsub_rn(S, __dmul_rn(__dmul_rn(Wd, ea), eb)), rw1);
 }
 // (1 - a) s + a x, both products rounded before the sum (as written in Sec. III-C)
 __device__ __forceinline__ double ema_mix(double s, double x, double alpha, double beta) {

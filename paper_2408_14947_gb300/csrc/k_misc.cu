@@ -40,6 +40,8 @@ struct EmaSrc {
   const double* S2f;
   int d, W;
   int64_t P;
+  double rw1;    // 1 / (W - 1), correctly rounded
+  double rw12;   // 1 / (W (W - 1)), correctly rounded
 };
 
 // line statistic of element (a, b) (b < 0: the mean of band a) at line t of the block
@@ -54,11 +56,11 @@ __device__ __forceinline__ double ema_stat(const EmaSrc& s, int64_t t, int a, in
     const int64_t s1a = (int64_t)__ldg(s.S1i + t * s.d + a);
     const int64_t s1b = (int64_t)__ldg(s.S1i + t * s.d + b);
     const int64_t s2 = (int64_t)__ldg(s.S2i + t * dd + ab);
-    return (double)((int64_t)s.W * s2 - s1a * s1b) * (1.0 / (Wd * (Wd - 1.0)));
+    return (double)((int64_t)s.W * s2 - s1a * s1b) * s.rw12;
   }
   const double ea = __dsub_rn(__ldg(s.mu_hat + t * s.d + a), __ldg(s.shift + t * s.d + a));
   const double eb = __dsub_rn(__ldg(s.mu_hat + t * s.d + b), __ldg(s.shift + t * s.d + b));
-  return ema_khat(__ldg(s.S2f + t * dd + ab), ea, eb, Wd);
+  return ema_khat(__ldg(s.S2f + t * dd + ab), ea, eb, Wd, s.rw1);
 }
 
 __device__ __forceinline__ void ema_element(const EmaSrc& s, int64_t q, int& a, int& b) {
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(128) b_ema_kernel(BStream* __restrict__ S,
     const int b = (int)(q - (int64_t)a * (a + 1) / 2);
     const double ea = __dsub_rn(s.mu_hat[a], s.shift[a]);
     const double eb = __dsub_rn(s.mu_hat[b], s.shift[b]);
-    const double kh = ema_khat(s.S2f[(int64_t)a * d + b], ea, eb, Wd);
+    const double kh = ema_khat(s.S2f[(int64_t)a * d + b], ea, eb, Wd, __drcp_rn(Wd - 1.0));
     const double prev = s.K_state[q];
     const double post = first ? kh : ema_mix(prev, kh, alpha, beta);
     s.K_t[q] = (s.order == 0 || first) ? post : prev;
@@ -274,7 +276,11 @@ void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      int W, double alpha, int64_t t0, int order, double* mu_state,
                      double* K_state, double* mu_t, double* K_t, double* scratch,
                      cudaStream_t st) {
-  EmaSrc s{int_stats, S1i, S2i, mu_hat, shift, S2f, d, W, packed_size(d)};
+  // both reciprocals correctly rounded on the host (IEEE division), as
+  // __drcp_rn and the device's double division would give
+  const double Wd = (double)W;
+  EmaSrc s{int_stats, S1i,    S2i, mu_hat, shift, S2f, d, W, packed_size(d),
+           1.0 / (Wd - 1.0), 1.0 / (Wd * (Wd - 1.0))};
   const int64_t n = s.P + d;
   const unsigned bx = (unsigned)((n + 127) / 128);
   const int G = (T + kEmaChunk - 1) / kEmaChunk;
