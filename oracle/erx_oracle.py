@@ -21,6 +21,10 @@ so the code can be checked against it):
   population standard deviation, and a line with zero spread gets delta_N = 0.
 * Warm-up: the 99-line buffer of Sec. IV-B is a warm-up; those lines are
   scored like any other and flagged not-detecting.
+* IMC (the ablation of Sec. IV-C that replaces the EMAs): a batch version of
+  Welford's update (the paper cites Schubert and Gertz 2018), so the state is
+  the mean and the 1/(n-1) covariance of all n pixels seen so far, every line
+  weighed equally; the momentum is not used.
 """
 from __future__ import annotations
 
@@ -55,6 +59,19 @@ def ema_update(mu, k, mu_hat, k_hat, alpha: float):
     return (1.0 - alpha) * mu + alpha * mu_hat, (1.0 - alpha) * k + alpha * k_hat
 
 
+def imc_update(mu, k, n_a: int, mu_hat, k_hat, n_b: int):
+    """Sec. IV-C's IMC, batch Welford (Schubert and Gertz 2018): merge the n_a
+    pixels summarised by (mu, k) with a line of n_b pixels (mu_hat, k_hat).
+    With the scatter M = (n - 1) K of each part and delta = mu_hat - mu:
+    mu' = mu + delta n_b / n,  M' = M_a + M_b + delta delta^T n_a n_b / n,
+    n = n_a + n_b.  Returns (mu', K' = M' / (n - 1))."""
+    n = n_a + n_b
+    delta = mu_hat - mu
+    mu_new = mu + delta * (n_b / n)
+    m = k * (n_a - 1) + k_hat * (n_b - 1) + np.outer(delta, delta) * (n_a * n_b / n)
+    return mu_new, m / (n - 1)
+
+
 def cholesky_ridge(k: np.ndarray, ridge: float) -> np.ndarray:
     """Sec. III-D: lower L with L L^T = K_t + ridge * I."""
     d = k.shape[0]
@@ -86,19 +103,23 @@ class ERXOracle:
     Sec. III-B), ``ridge`` = 1e-5 (Sec. III-D), ``warmup`` = 99 lines (Sec. IV-B),
     ``threshold`` = tau_N (Sec. III-E; None for no mask).
     ``proj`` is "none" (all bands), "srp" (matrix drawn from ``seed``) or an
-    explicit b x d array.
+    explicit b x d array.  ``averaging`` is "ema" (Sec. III-C) or "imc" (the
+    equal-weight ablation of Sec. IV-C).
     """
 
     def __init__(self, bands: int, width: int, momentum: float = 0.1, proj="none",
                  proj_dim: int = 5, seed: int = 0, ridge: float = 1e-5,
                  warmup: int = 99, order: str = "update_then_score",
-                 threshold: float | None = None):
+                 threshold: float | None = None, averaging: str = "ema"):
         if not (0.0 < momentum <= 1.0):
             raise ValueError("momentum must be in (0, 1]")
         if width < 2:
             raise ValueError("a line needs at least 2 pixels for its covariance")
         if order not in ("update_then_score", "score_then_update"):
             raise ValueError(order)
+        if averaging not in ("ema", "imc"):
+            raise ValueError(averaging)
+        self.averaging = averaging
         self.bands, self.width = bands, width
         self.alpha, self.ridge = float(momentum), float(ridge)
         self.warmup, self.order, self.threshold = warmup, order, threshold
@@ -118,6 +139,9 @@ class ERXOracle:
     def _update(self, mu_hat, k_hat):
         if self.t == 0:                       # Sec. III-C: start from the first line
             self.mu, self.k = mu_hat.copy(), k_hat.copy()
+        elif self.averaging == "imc":         # all lines so far have width pixels each
+            self.mu, self.k = imc_update(self.mu, self.k, self.t * self.width, mu_hat, k_hat,
+                                         self.width)
         else:
             self.mu, self.k = ema_update(self.mu, self.k, mu_hat, k_hat, self.alpha)
 

@@ -203,6 +203,31 @@ def check_srp_projection():
     return rel(r1["delta"], r2["delta"])
 
 
+def check_imc_pooled(order="update_then_score"):
+    """IMC (Sec. IV-C) weighs every pixel seen so far equally: after line t the
+    state is the mean and the 1/(n-1) covariance (numpy.cov) of all pixels of
+    lines 0..t, and each line is scored (textbook RX, explicit inverse) against
+    the pooled statistics of the lines its order prescribes."""
+    p, b, T, ridge = 9, 4, 7, 1e-3
+    r = np.random.default_rng(21)
+    # lines with different means, so the between-line term of the pooled covariance matters
+    cube = np.stack([r.standard_normal((p, b)) + 3.0 * r.standard_normal(b) for _ in range(T)])
+    det = eo.ERXOracle(b, p, averaging="imc", ridge=ridge, order=order)
+    worst = 0.0
+    for t in range(T):
+        out = det.push(cube[t])
+        seen = cube[: t + 1].reshape(-1, b)
+        worst = max(worst, rel(det.mu, seen.mean(axis=0)))
+        worst = max(worst, rel(det.k, np.cov(seen.T, ddof=1)))
+        ref = cube[: t + 1] if (order == "update_then_score" or t == 0) else cube[:t]
+        ref = ref.reshape(-1, b)
+        vi = np.linalg.inv(np.cov(ref.T, ddof=1) + ridge * np.eye(b))
+        mu = ref.mean(axis=0)
+        want = [scipy.spatial.distance.mahalanobis(x, mu, vi) for x in cube[t]]
+        worst = max(worst, rel(out["delta"], want))
+    return worst
+
+
 ALL_CHECKS = {
     "exact_golden": (check_exact_golden, 1e-11),
     "hand_1d": (check_hand_1d, 1e-14),
@@ -218,4 +243,6 @@ ALL_CHECKS = {
     "stationary": (check_stationary, 1e-12),
     "score_then_update_alpha1": (check_score_then_update_alpha1, 1e-9),
     "srp_projection": (check_srp_projection, 1e-9),
+    "imc_pooled": (check_imc_pooled, 1e-9),
+    "imc_pooled_stu": (lambda: check_imc_pooled("score_then_update"), 1e-9),
 }

@@ -44,7 +44,21 @@ def _stats_uncentred(z):
     return mu, (z.T @ z) / (p - 1)
 
 
+def _imc_no_between(mu, k, n_a, mu_hat, k_hat, n_b):
+    n = n_a + n_b
+    m = k * (n_a - 1) + k_hat * (n_b - 1)
+    return mu + (mu_hat - mu) * (n_b / n), m / (n - 1)
+
+
+def _imc_weights_by_line(mu, k, n_a, mu_hat, k_hat, n_b):
+    # equal weight per line count instead of per pixel, and no between-line term
+    t = n_a // n_b
+    return (t * mu + mu_hat) / (t + 1), (t * k + k_hat) / (t + 1)
+
+
 MUTATIONS = {
+    "imc_between_term_dropped": ("imc_update", _imc_no_between),
+    "imc_average_of_covariances": ("imc_update", _imc_weights_by_line),
     "cov_over_p": ("line_stats", _stats_over_p),
     "ema_weights_swapped": ("ema_update", _ema_swapped),
     "ridge_dropped": ("cholesky_ridge", _chol_no_ridge),
