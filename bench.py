@@ -498,6 +498,7 @@ def run_ours(args):
         forms = {}
         for name, kw in (("fp32", {"form": "fp32"}), ("tf32", {"form": "tf32"}),
                          ("bf16", {"form": "bf16"}), ("tf32x3", {"form": "tf32x3"}),
+                         ("fp64_imc", {"form": "fp64", "averaging": "imc"}),
                          ("fp64_srp5", {"form": "fp64", "proj": "srp", "proj_dim": 5}),
                          ("fp32_srp5", {"form": "fp32", "proj": "srp", "proj_dim": 5})):
             forms[name] = time_form(lambda **k: Detector(BANDS, WIDTH, in_dtype="u16",
@@ -564,18 +565,21 @@ def run_profile_case(args):
     from paper_2408_14947_gb300 import Detector, _build
     _build.build()
     kind, form = args.profile_case.split("_", 1)
+    avg = "ema"
+    if form.endswith("_imc"):
+        form, avg = form[: -len("_imc")], "imc"
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(device=dev)
     if kind == "c2":
         cube = make_cube(args.lines, seed=0)
         x = torch.from_numpy(cube.view(np.int16)).to(dev)
         det = Detector(BANDS, WIDTH, in_dtype="u16", in_bits=BITS, form=form, stream=stream,
-                       block_lines=args.lines)
+                       block_lines=args.lines, averaging=avg)
     else:
         cube = make_cube(args.lines, seed=1, kind="c3", width=1024, bands=224, kappa=1e3)
         x = torch.from_numpy(cube).to(dev)
         det = Detector(224, 1024, in_dtype="f32", form=form, stream=stream,
-                       block_lines=args.lines)
+                       block_lines=args.lines, averaging=avg)
     del cube
     det.push(x)
     det.sync()
@@ -603,11 +607,12 @@ def main():
     ap.add_argument("--lines", type=int, default=LINES,
                     help="lines of the workload cube (smaller cubes for profiler captures)")
     ap.add_argument("--profile-case", default=None,
-                    choices=["c2_fp64", "c2_fp32", "c2_tf32", "c2_bf16", "c3_fp64", "c3_fp32",
-                             "c3_tf32", "c3_bf16", "c3_tf32x3"],
+                    choices=["c2_fp64", "c2_fp32", "c2_tf32", "c2_bf16", "c2_fp64_imc", "c3_fp64",
+                             "c3_fp32", "c3_tf32", "c3_bf16", "c3_tf32x3"],
                     help="push one block of --lines lines of a workload (c2: 640 px x 108 "
                          "bands u16; c3: 1024 px x 224 bands f32, kappa 1e3) through one "
-                         "form, after one warm-up push, for profiler captures; no bench line")
+                         "form (_imc: IMC averaging), after one warm-up push, for profiler "
+                         "captures; no bench line")
     args = ap.parse_args()
     globals()["LINES"] = args.lines
     if args.profile_case:

@@ -56,6 +56,11 @@ typedef enum {
 enum { ERX_PROJ_NONE = 0, ERX_PROJ_SRP = 1, ERX_PROJ_LEARNED = 2 };
 /* order of update and scoring (Sec. III-C/III-D: the paper scores with mu_t, L_t) */
 enum { ERX_UPDATE_THEN_SCORE = 0, ERX_SCORE_THEN_UPDATE = 1 };
+/* background averaging: ERX_AVG_EMA, the exponentially moving averages of
+ * Sec. III-C (momentum alpha); ERX_AVG_IMC, the equal-weight ablation of
+ * Sec. IV-C, a batch version of Welford's update: the state is the mean and the
+ * 1/(n-1) covariance of all n pixels seen (momentum unused) */
+enum { ERX_AVG_EMA = 0, ERX_AVG_IMC = 1 };
 /* input sample type, lines laid out [pixel][band] (band-interleaved-by-pixel) */
 enum { ERX_U16 = 0, ERX_F32 = 1, ERX_F64 = 2 };
 /* flags: ERX_FLAG_SIMT_STATS keeps S2 off the tensor cores: exact integer
@@ -96,6 +101,8 @@ typedef struct {
   int32_t block_lines;  /* lines processed per internal block; 0 = automatic */
   int32_t flags;        /* ERX_FLAG_* bits */
   const double* srp_weights; /* optional b x d row-major host matrix replacing the drawn SRP */
+  int32_t averaging;    /* ERX_AVG_EMA (paper) or ERX_AVG_IMC; the batch and the
+                         * no-allocation entry point take ERX_AVG_EMA only */
 } erx_config;
 
 /* Fill *cfg with the paper's defaults for a b-band, p-pixel line:

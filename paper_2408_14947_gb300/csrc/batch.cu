@@ -219,6 +219,7 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
         (c.order != ERX_UPDATE_THEN_SCORE && c.order != ERX_SCORE_THEN_UPDATE) ||
         c.form != form)
       return ERX_EINVAL;
+    if (c.averaging != ERX_AVG_EMA) return ERX_EUNSUPPORTED;
     if (c.in_dtype != ERX_F32 || c.proj != ERX_PROJ_NONE || c.bands > kMaxDim ||
         c.width > (1 << 20))
       return ERX_EUNSUPPORTED;

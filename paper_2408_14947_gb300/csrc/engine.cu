@@ -48,6 +48,7 @@ struct erx_ctx {
   double* vals = nullptr;
   unsigned long long* err = nullptr;
   double* ema_scratch = nullptr;
+  double* imc_mprev = nullptr;   // IMC: per-line deltas, constants and chunk sums of a block
   // host staging for erx_push_lines_host
   void* h_in[2] = {nullptr, nullptr};
   void* d_in[2] = {nullptr, nullptr};
@@ -188,6 +189,7 @@ erx_status validate(const erx_config* cfg) {
     return ERX_EINVAL;
   if (cfg->order != ERX_UPDATE_THEN_SCORE && cfg->order != ERX_SCORE_THEN_UPDATE)
     return ERX_EINVAL;
+  if (cfg->averaging != ERX_AVG_EMA && cfg->averaging != ERX_AVG_IMC) return ERX_EINVAL;
   if (cfg->in_dtype < ERX_U16 || cfg->in_dtype > ERX_F64) return ERX_EINVAL;
   if (cfg->in_dtype == ERX_U16 && (cfg->in_bits < 1 || cfg->in_bits > 16)) return ERX_EINVAL;
   if (cfg->form < ERX_FORM_FP64 || cfg->form > ERX_FORM_TF32X3) return ERX_EINVAL;
@@ -275,7 +277,12 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
       launch_stats_fp(ztype, c->fp64, zsrc, zstride, ps, W, d, T, c->shift, c->S2f, st);
     }
   }
-  {
+  if (c->cfg.averaging == ERX_AVG_IMC) {
+    KernelScope ks(c, ERX_K_EMA);
+    launch_imc_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W, c->t,
+                    c->cfg.order, c->mu_state, c->K_state, c->mu_t, c->K_t, c->imc_mprev,
+                    c->ema_scratch, st);
+  } else {
     KernelScope ks(c, ERX_K_EMA);
     launch_ema_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W,
                   c->cfg.momentum, c->t, c->cfg.order, c->mu_state, c->K_state, c->mu_t, c->K_t,
@@ -402,6 +409,7 @@ void erx_config_default(erx_config* cfg, int32_t bands, int32_t width) {
   cfg->ridge = 1e-5;
   cfg->warmup_lines = 99;
   cfg->order = ERX_UPDATE_THEN_SCORE;
+  cfg->averaging = ERX_AVG_EMA;
   cfg->in_dtype = ERX_F32;
   cfg->in_bits = 16;
   cfg->form = ERX_FORM_FP64;
@@ -500,6 +508,7 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   }
   ERX_A(err, kErrSlots);
   if (ema_scratch_doubles(d, T) > 0) ERX_A(ema_scratch, ema_scratch_doubles(d, T));
+  if (cfg->averaging == ERX_AVG_IMC) ERX_A(imc_mprev, imc_work_doubles(d, T));
 #undef ERX_A
   if (s == ERX_OK && learned) {
     float* zp = nullptr;

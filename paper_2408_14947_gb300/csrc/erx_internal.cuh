@@ -79,6 +79,15 @@ void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      double* K_state, double* mu_t, double* K_t, double* scratch,
                      cudaStream_t st);
 
+// IMC (equal-weight ablation, batch Welford) in place of the EMA scan: same
+// outputs; `work` holds imc_work_doubles(d, T) doubles.
+size_t imc_work_doubles(int d, int T);
+void launch_imc_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
+                     const double* mu_hat, const double* shift, const double* S2f, int T, int d,
+                     int W, int64_t t0, int order, double* mu_state, double* K_state,
+                     double* mu_t, double* K_t, double* work, double* scratch,
+                     cudaStream_t st);
+
 // Cholesky of K_t + ridge I, diagonal blocks inverted, one CTA per line.
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Linv, float* Linv32,
                      unsigned long long* err, int64_t t0, cudaStream_t st);

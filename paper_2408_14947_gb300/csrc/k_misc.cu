@@ -152,6 +152,146 @@ __global__ void __launch_bounds__(128) ema_pass_c(EmaSrc s, int T, double alpha,
   if (!Cin) *st = v;
 }
 
+// ---- IMC: the equal-weight ablation of Sec. IV-C (batch Welford) ----------
+// After global line g (p pixels each) the state is the mean and the 1/(n-1)
+// covariance of all n = (g+1)p pixels seen.  With delta_g = mu_hat_g - mu_{g-1}:
+//   mu_g = mu_{g-1} + delta_g / (g+1)   (the mean of the line means: S_g / (g+1),
+//                                        S_g = sum_{s <= g} mu_hat_s),
+//   M_g  = M_{g-1} + (p-1) K_hat_g + (g p^2 / ((g+1) p)) delta_g delta_g^T,
+//   K_g  = M_g / ((g+1)p - 1),
+// (M = (n-1) K, the scatter).  Both are prefix sums over the block's lines,
+// computed in 32-line chunks: chunk sums, a carry over chunks, per-line values.
+// Per-line constants come from a table (one thread per line), so no element
+// divides per line.
+
+// per-line table, 4 x T: weight of delta delta^T, 1/((g+1)p - 1), 1/(gp - 1), 1/(g+1)
+__global__ void __launch_bounds__(128) imc_table_kernel(int T, int W, int64_t t0,
+                                                        double* __restrict__ tab) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  const int64_t g = t0 + t;
+  const double na = (double)g * W, n = na + W;
+  tab[t] = na * W / n;
+  tab[T + t] = 1.0 / (n - 1.0);
+  tab[2 * T + t] = g > 0 ? 1.0 / (na - 1.0) : 0.0;
+  tab[3 * T + t] = 1.0 / (double)(g + 1);
+}
+
+// means, pass A: E1[c][a] = sum of the line means of chunk c
+__global__ void __launch_bounds__(128) imc_mean_a(EmaSrc s, int T, double* __restrict__ E1) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= s.d) return;
+  const int c = blockIdx.y;
+  const int tb = c * kEmaChunk, te = min(T, tb + kEmaChunk);
+  double u = 0.0;
+  for (int t = tb; t < te; ++t) u += ema_stat(s, t, a, -1);
+  E1[(int64_t)c * s.d + a] = u;
+}
+
+// means, pass C: per line mu_t (the order's) and delta_g; the state is left to imc_mean_state
+__global__ void __launch_bounds__(128) imc_mean_c(EmaSrc s, int T, int64_t t0, int order,
+                                                  const double* __restrict__ mu_state,
+                                                  const double* __restrict__ E1,
+                                                  const double* __restrict__ tab,
+                                                  double* __restrict__ mu_t,
+                                                  double* __restrict__ dlt) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= s.d) return;
+  const int c = blockIdx.y;
+  const int tb = c * kEmaChunk, te = min(T, tb + kEmaChunk);
+  double S = t0 > 0 ? mu_state[a] * (double)t0 : 0.0;
+  for (int cc = 0; cc < c; ++cc) S += E1[(int64_t)cc * s.d + a];
+  const int64_t g0 = t0 + tb;
+  double prev = g0 == 0 ? 0.0 : (tb == 0 ? mu_state[a] : S * (1.0 / (double)g0));
+  for (int t = tb; t < te; ++t) {
+    const int64_t g = t0 + t;
+    const double mh = ema_stat(s, t, a, -1);
+    S += mh;
+    const double post = g == 0 ? mh : S * tab[3 * T + t];
+    dlt[(int64_t)t * s.d + a] = g == 0 ? 0.0 : mh - prev;
+    mu_t[(int64_t)t * s.d + a] = (order == 0 || g == 0) ? post : prev;
+    prev = post;
+  }
+}
+
+__global__ void __launch_bounds__(128) imc_mean_state(int d, int G, int T, int64_t t0,
+                                                      const double* __restrict__ E1,
+                                                      double* __restrict__ mu_state) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= d) return;
+  double S = t0 > 0 ? mu_state[a] * (double)t0 : 0.0;
+  for (int c = 0; c < G; ++c) S += E1[(int64_t)c * d + a];
+  mu_state[a] = S / (double)(t0 + T);
+}
+
+// scatter increment of element (a, b) at line t of the block
+__device__ __forceinline__ double imc_inc(const EmaSrc& s, int64_t t, int a, int b,
+                                          const double* __restrict__ dlt,
+                                          const double* __restrict__ tab) {
+  const double kh = ema_stat(s, t, a, b);
+  return kh * ((double)s.W - 1.0) +
+         __ldg(dlt + t * s.d + a) * __ldg(dlt + t * s.d + b) * __ldg(tab + t);
+}
+
+// pass A: the chunk's sum of increments, E[c][q]
+__global__ void __launch_bounds__(128) imc_pass_a(EmaSrc s, int T,
+                                                  const double* __restrict__ dlt,
+                                                  const double* __restrict__ tab,
+                                                  double* __restrict__ E) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= s.P) return;
+  const int c = blockIdx.y;
+  int a, b;
+  ema_element(s, q, a, b);
+  const int tb = c * kEmaChunk, te = min(T, tb + kEmaChunk);
+  double u = 0.0;
+  for (int t = tb; t < te; ++t) u += imc_inc(s, t, a, b, dlt, tab);
+  E[(int64_t)c * s.P + q] = u;
+}
+
+// pass B: scatter entering each chunk, Cin[c][q]; the state's K becomes the
+// covariance after the block
+__global__ void __launch_bounds__(128) imc_pass_b(int64_t P, int T, int G, int W, int64_t t0,
+                                                  const double* __restrict__ E,
+                                                  double* __restrict__ Cin,
+                                                  double* __restrict__ Kst) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= P) return;
+  double m = t0 > 0 ? Kst[q] * ((double)t0 * W - 1.0) : 0.0;
+  for (int c = 0; c < G; ++c) {
+    Cin[(int64_t)c * P + q] = m;
+    m += E[(int64_t)c * P + q];
+  }
+  Kst[q] = m / ((double)(t0 + T) * W - 1.0);
+}
+
+// pass C: per-line covariances from each chunk's carried-in scatter (or, with
+// no carry, from the state: the whole block as one chunk, state updated here)
+__global__ void __launch_bounds__(128) imc_pass_c(EmaSrc s, int T, int64_t t0, int order,
+                                                  const double* __restrict__ dlt,
+                                                  const double* __restrict__ tab,
+                                                  const double* __restrict__ Cin,
+                                                  double* __restrict__ Kst,
+                                                  double* __restrict__ K_t) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= s.P) return;
+  const int c = blockIdx.y;
+  int a, b;
+  ema_element(s, q, a, b);
+  const double Wd = (double)s.W;
+  double m = Cin ? Cin[(int64_t)c * s.P + q] : (t0 > 0 ? Kst[q] * ((double)t0 * Wd - 1.0) : 0.0);
+  const int tb = c * kEmaChunk, te = Cin ? min(T, tb + kEmaChunk) : T;
+  for (int t = tb; t < te; ++t) {
+    const int64_t g = t0 + t;
+    const double post = m + imc_inc(s, t, a, b, dlt, tab);
+    const double out = (order == 0 || g == 0) ? post * __ldg(tab + T + t)
+                                              : m * __ldg(tab + 2 * T + t);
+    K_t[(int64_t)t * s.P + q] = out;
+    m = post;
+  }
+  if (!Cin) Kst[q] = m / ((double)(t0 + T) * Wd - 1.0);
+}
+
 // ---- S6: line-by-line normalisation (Sec. III-E) -------------------------
 __device__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -295,6 +435,40 @@ void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
   ema_pass_b<<<bx, 128, 0, st>>>(n, T, G, alpha, t0, E, Cin, K_state, mu_state, s.P);
   ema_pass_c<<<dim3(bx, G), 128, 0, st>>>(s, T, alpha, t0, order, Cin, K_state, mu_state, mu_t,
                                          K_t);
+}
+
+void launch_imc_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
+                     const double* mu_hat, const double* shift, const double* S2f, int T, int d,
+                     int W, int64_t t0, int order, double* mu_state, double* K_state,
+                     double* mu_t, double* K_t, double* work, double* scratch,
+                     cudaStream_t st) {
+  const double Wd = (double)W;
+  EmaSrc s{int_stats, S1i,    S2i, mu_hat, shift, S2f, d, W, packed_size(d),
+           1.0 / (Wd - 1.0), 1.0 / (Wd * (Wd - 1.0))};
+  const int G = (T + kEmaChunk - 1) / kEmaChunk;
+  double* dlt = work;                         // T x d
+  double* tab = work + (int64_t)T * d;        // 4 x T
+  double* E1 = tab + 4 * (int64_t)T;          // G x d
+  const unsigned bd = (unsigned)((d + 127) / 128);
+  imc_table_kernel<<<(T + 127) / 128, 128, 0, st>>>(T, W, t0, tab);
+  imc_mean_a<<<dim3(bd, G), 128, 0, st>>>(s, T, E1);
+  imc_mean_c<<<dim3(bd, G), 128, 0, st>>>(s, T, t0, order, mu_state, E1, tab, mu_t, dlt);
+  imc_mean_state<<<bd, 128, 0, st>>>(d, G, T, t0, E1, mu_state);
+  const unsigned bx = (unsigned)((s.P + 127) / 128);
+  if (G <= 1 || !scratch) {
+    imc_pass_c<<<dim3(bx, 1), 128, 0, st>>>(s, T, t0, order, dlt, tab, nullptr, K_state, K_t);
+    return;
+  }
+  double* E = scratch;
+  double* Cin = scratch + (int64_t)G * s.P;
+  imc_pass_a<<<dim3(bx, G), 128, 0, st>>>(s, T, dlt, tab, E);
+  imc_pass_b<<<bx, 128, 0, st>>>(s.P, T, G, W, t0, E, Cin, K_state);
+  imc_pass_c<<<dim3(bx, G), 128, 0, st>>>(s, T, t0, order, dlt, tab, Cin, K_state, K_t);
+}
+
+size_t imc_work_doubles(int d, int T) {
+  const int G = (T + kEmaChunk - 1) / kEmaChunk;
+  return (size_t)T * d + 4 * (size_t)T + (size_t)G * d;
 }
 
 size_t ema_scratch_doubles(int d, int T) {

@@ -104,8 +104,9 @@ extern "C" erx_status erx_push_lines_static(const erx_config* cfg, void* cuda_st
       (cfg->form != ERX_FORM_FP64 && cfg->form != ERX_FORM_FP32) || cfg->warmup_lines < 0 ||
       (cfg->proj != ERX_PROJ_NONE && cfg->proj != ERX_PROJ_SRP))
     return ERX_EINVAL;
-  // limits of the fixed scratch: no projection, d = b <= 224, p <= 2^20
-  if (cfg->proj != ERX_PROJ_NONE || cfg->bands > kStaticMaxDim || cfg->width > (1 << 20))
+  // limits of the fixed scratch: no projection, d = b <= 224, p <= 2^20; EMA averaging
+  if (cfg->proj != ERX_PROJ_NONE || cfg->bands > kStaticMaxDim || cfg->width > (1 << 20) ||
+      cfg->averaging != ERX_AVG_EMA)
     return ERX_EUNSUPPORTED;
   const size_t es = sample_bytes(cfg->in_dtype);
   const int W = cfg->width, d = cfg->bands;

@@ -18,6 +18,7 @@ ERX_OK, ERX_EINVAL, ERX_ENOMEM, ERX_ECUDA, ERX_ENOTPD, ERX_ERANGE, ERX_ESTATE, \
 ERX_FLAG_SIMT_STATS = 1
 ERX_PROJ_NONE, ERX_PROJ_SRP, ERX_PROJ_LEARNED = 0, 1, 2
 ERX_UPDATE_THEN_SCORE, ERX_SCORE_THEN_UPDATE = 0, 1
+ERX_AVG_EMA, ERX_AVG_IMC = 0, 1
 ERX_U16, ERX_F32, ERX_F64 = 0, 1, 2
 ERX_FORM_FP64, ERX_FORM_FP32, ERX_FORM_TF32, ERX_FORM_BF16, ERX_FORM_TF32X3 = 0, 1, 2, 3, 4
 FORMS = {"fp64": ERX_FORM_FP64, "fp32": ERX_FORM_FP32, "tf32": ERX_FORM_TF32,
@@ -33,7 +34,7 @@ class ErxConfig(C.Structure):
         ("ridge", C.c_double), ("warmup_lines", C.c_int32), ("order", C.c_int32),
         ("in_dtype", C.c_int32), ("in_bits", C.c_int32), ("form", C.c_int32),
         ("threshold", C.c_double), ("block_lines", C.c_int32), ("flags", C.c_int32),
-        ("srp_weights", C.POINTER(C.c_double)),
+        ("srp_weights", C.POINTER(C.c_double)), ("averaging", C.c_int32),
     ]
 
 
@@ -244,7 +245,8 @@ class Detector:
     def __init__(self, bands, width, momentum=0.1, proj="none", proj_dim=5, seed=0, ridge=1e-5,
                  warmup=99, order="update_then_score", in_dtype="f32", in_bits=16,
                  form="fp64", threshold=3.0, block_lines=0, srp_weights=None, stream=None,
-                 simt_stats=False, encoder=None, audit_every=0, min_rank_corr=0.0):
+                 simt_stats=False, encoder=None, audit_every=0, min_rank_corr=0.0,
+                 averaging="ema"):
         import torch
         self.torch = torch
         cfg = erx_config_default(bands, width)
@@ -265,6 +267,7 @@ class Detector:
         cfg.threshold = threshold if threshold is not None else math.inf
         cfg.block_lines = block_lines
         cfg.flags = ERX_FLAG_SIMT_STATS if simt_stats else 0
+        cfg.averaging = {"ema": ERX_AVG_EMA, "imc": ERX_AVG_IMC}[averaging]
         self._w = None
         if srp_weights is not None:
             import numpy as np

@@ -307,3 +307,32 @@ def test_long_block_chunked_ema_matches_line_by_line():
         c, _ = run_gpu(cube, block_lines=150, order=order)
         refc = oracle.run_cube(cube, order=order)
         assert rel_err(c["delta"], refc["delta"]) < 1e-9
+
+
+@pytest.mark.parametrize("form,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
+@pytest.mark.parametrize("order", ["update_then_score", "score_then_update"])
+def test_imc_matches_oracle(form, tol, order):
+    """IMC averaging (Sec. IV-C ablation): a 70-line block (three chunks of the
+    prefix sum), one single line and a 9-line block, against the oracle; the
+    state is the pooled mean and covariance of every pixel seen."""
+    cube = synth.gen_lines(synth.reflectance_c1(width=96, bands=24, seed=4), 0, 80)
+    kw = {"averaging": "imc", "order": order}
+    ref = oracle.run_cube(cube, warmup=3, threshold=3.0, **kw)
+    got, det = run_gpu(cube, form=form, warmup=3, threshold=3.0, push_sizes=[70, 1, 9], **kw)
+    _compare(got, ref, tol)
+    t, mu, k = det.state()
+    _, mu_o, k_o = ref["state"]
+    assert t == 80
+    # the FP32 form's line means sum runs of 8 samples in FP32 (relative 1e-7)
+    tol_s = 1e-10 if form == "fp64" else 1e-6
+    assert rel_err(mu, mu_o) < tol_s and rel_err(k, k_o) < tol_s
+
+
+def test_imc_integer_statistics():
+    """IMC on u16 lines through the exact integer statistics."""
+    cube = synth.gen_lines(synth.dn_c2(width=64, bands=16, seed=2), 0, 40)
+    ref = oracle.run_cube(cube, warmup=2, threshold=3.0, averaging="imc")
+    got, det = run_gpu(cube, warmup=2, threshold=3.0, in_bits=12, averaging="imc",
+                       push_sizes=[40])
+    _compare(got, ref, 1e-9)
+    assert det.profile_read()["stats_tc"][2] > 0
