@@ -371,6 +371,32 @@ def bench_learned(dev, stream, n_train: int = 2000, n_test: int = 200):
     return out
 
 
+LATENCY_PERIOD_S = 1e-3   # lines arriving every millisecond (1000 lines/s)
+
+
+def paced_latency(det, x, out, stream, n, period_s, offset=200):
+    """p50/p99 of enqueue -> delta_N written for single-line pushes arriving every
+    period_s (host-paced, so each push finds the GPU idle, as lines from a
+    sensor would): CUDA events on the detector's stream around each push."""
+    import torch
+    lines = x.shape[0]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(n)]
+    t_next = time.perf_counter()
+    for i, (a, b) in enumerate(ev):
+        while time.perf_counter() < t_next:
+            pass
+        t_next += period_s
+        j = offset + i % (lines - offset)
+        a.record(stream)
+        det.push(x[j:j + 1], out)
+        b.record(stream)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    return {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * len(lat))], "lines": len(lat),
+            "mode": f"one line per push, a line every {period_s * 1e3:g} ms"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -492,7 +518,20 @@ def run_ours(args):
         torch.cuda.synchronize()
         lat = sorted(a.elapsed_time(b) for a, b in ev)
         result["latency_ms"] = {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * len(lat))],
-                                "lines": len(lat), "mode": "one line per push"}
+                                "lines": len(lat), "mode": "one line per push, back to back"}
+        result["latency_paced_ms"] = paced_latency(det, x, one, stream, args.latency_lines,
+                                                   LATENCY_PERIOD_S)
+        # score-then-update with the update deferred to a second stream (the
+        # line is scored against the factor made at the end of the previous push)
+        dpl = detector(form="fp64", order="score_then_update", pipeline=True)
+        for i in range(200):
+            dpl.push(x[i:i + 1], one)
+        dpl.sync()
+        result["latency_pipelined_ms"] = {
+            "order": "score_then_update, ERX_FLAG_PIPELINE",
+            "paced": paced_latency(dpl, x, one, stream, args.latency_lines, LATENCY_PERIOD_S)}
+        dpl.sync()
+        dpl.close()
 
         # other forms on the same cube, same step definition
         forms = {}

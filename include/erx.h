@@ -65,8 +65,16 @@ enum { ERX_AVG_EMA = 0, ERX_AVG_IMC = 1 };
 enum { ERX_U16 = 0, ERX_F32 = 1, ERX_F64 = 2 };
 /* flags: ERX_FLAG_SIMT_STATS keeps S2 off the tensor cores: exact integer
  * sums by 32-bit integer multiply-adds for u16 lines (identical results), the
- * FP32 SIMT scatter for floating-point lines in the tensor-core forms */
-enum { ERX_FLAG_SIMT_STATS = 1 };
+ * FP32 SIMT scatter for floating-point lines in the tensor-core forms.
+ * ERX_FLAG_PIPELINE (score-then-update order only; not with a learned
+ * projection): a single-line push scores its line against the factor of the
+ * state made at the end of the previous push, writes delta / delta_N on the
+ * context's stream, and defers the line's statistics, the state update and
+ * the next factor to a second stream, so a line's latency is its score and
+ * normalisation alone.  Results are identical to score-then-update without
+ * the flag.  The line's buffer is free once the context's stream has passed
+ * the push; erx_sync, erx_get_state and erx_destroy wait for both streams. */
+enum { ERX_FLAG_SIMT_STATS = 1, ERX_FLAG_PIPELINE = 2 };
 /* arithmetic form of S5 (and of S2 for floating input); S3 and S4 are FP64 in
  * every form, and u16 input without projection always gets exact integer S2.
  * FP64: FP64 arithmetic.  FP32: FP32 SIMT arithmetic.  TF32 / BF16: tensor-core

@@ -49,6 +49,15 @@ struct erx_ctx {
   unsigned long long* err = nullptr;
   double* ema_scratch = nullptr;
   double* imc_mprev = nullptr;   // IMC: per-line deltas, constants and chunk sums of a block
+  // ERX_FLAG_PIPELINE: the factor of the current state, made ahead for the next
+  // single-line push, and the second stream that defers each line's update
+  bool pipeline = false;
+  bool have_pre = false;
+  double* mu_pre = nullptr;
+  double* Lf_pre = nullptr;
+  float* Lf32_pre = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_stats = nullptr, ev_scored = nullptr, ev_ready = nullptr;
   // host staging for erx_push_lines_host
   void* h_in[2] = {nullptr, nullptr};
   void* d_in[2] = {nullptr, nullptr};
@@ -105,6 +114,9 @@ void free_all(erx_ctx* c) {
   }
   if (c->h_out) cudaFreeHost(c->h_out);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  for (cudaEvent_t* e : {&c->ev_start, &c->ev_stats, &c->ev_scored, &c->ev_ready})
+    if (*e) cudaEventDestroy(*e), *e = nullptr;
+  if (c->side) cudaStreamDestroy(c->side), c->side = nullptr;
   if (c->audit) erx_destroy(c->audit), c->audit = nullptr;
   for (auto& p : c->pending) cudaEventDestroy(p.a), cudaEventDestroy(p.b);
   for (auto e : c->spare_events) cudaEventDestroy(e);
@@ -127,19 +139,21 @@ cudaEvent_t take_event(erx_ctx* c) {
 struct KernelScope {
   erx_ctx* c;
   int k;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  KernelScope(erx_ctx* c_, int k_) : c(c_), k(k_) {
+  KernelScope(erx_ctx* c_, int k_, cudaStream_t s_ = nullptr)
+      : c(c_), k(k_), st(s_ ? s_ : c_->stream) {
     c->launches[k]++;
     if (c->profiling) {
       a = take_event(c);
-      if (a) cudaEventRecord(a, c->stream);
+      if (a) cudaEventRecord(a, st);
     }
   }
   ~KernelScope() {
     if (a) {
       cudaEvent_t b = take_event(c);
       if (b) {
-        cudaEventRecord(b, c->stream);
+        cudaEventRecord(b, st);
         c->pending.push_back({k, a, b});
       } else {
         c->spare_events.push_back(a);
@@ -190,6 +204,9 @@ erx_status validate(const erx_config* cfg) {
   if (cfg->order != ERX_UPDATE_THEN_SCORE && cfg->order != ERX_SCORE_THEN_UPDATE)
     return ERX_EINVAL;
   if (cfg->averaging != ERX_AVG_EMA && cfg->averaging != ERX_AVG_IMC) return ERX_EINVAL;
+  if ((cfg->flags & ERX_FLAG_PIPELINE) &&
+      (cfg->order != ERX_SCORE_THEN_UPDATE || cfg->proj == ERX_PROJ_LEARNED))
+    return ERX_EINVAL;
   if (cfg->in_dtype < ERX_U16 || cfg->in_dtype > ERX_F64) return ERX_EINVAL;
   if (cfg->in_dtype == ERX_U16 && (cfg->in_bits < 1 || cfg->in_bits > 16)) return ERX_EINVAL;
   if (cfg->form < ERX_FORM_FP64 || cfg->form > ERX_FORM_TF32X3) return ERX_EINVAL;
@@ -207,6 +224,13 @@ int tc_format(int form) {
 // Enqueue the whole step for `n` lines at `x` (device), outputs at line offset 0 of the given
 // pointers.
 erx_status audit_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems, void* delta);
+
+void enqueue_stats(erx_ctx* c, const void* x, int64_t stride_elems, const void* zsrc, int ztype,
+                   int64_t zstride, int ps, int T, cudaStream_t st);
+void enqueue_update(erx_ctx* c, int T, cudaStream_t st);
+void enqueue_score(erx_ctx* c, const void* zsrc, int ztype, int64_t zstride, int ps, int T,
+                   const double* mu, const double* Lf, const float* Lf32, void* delta, void* dn,
+                   uint8_t* mask, uint8_t* det, cudaStream_t st);
 
 erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems, void* delta,
                      void* dn, uint8_t* mask, uint8_t* det) {
@@ -249,45 +273,8 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
     zstride = (int64_t)W * d;
     ps = d;
   }
-  if (c->int_stats && c->tc_stats) {
-    KernelScope ks(c, ERX_K_STATS_TC);
-    launch_stats_tc((const uint16_t*)x, stride_elems, W, d, (1u << c->cfg.in_bits) - 1u, T,
-                    c->n_sm, c->S1i, c->S2i, c->err, c->t, st);
-  } else if (c->int_stats) {
-    KernelScope ks(c, ERX_K_STATS_INT);
-    launch_stats_int((const uint16_t*)x, stride_elems, W, d, (1u << c->cfg.in_bits) - 1u, T,
-                     c->S1i, c->S2i, c->err, c->t, st);
-  } else {
-    {
-      KernelScope ks(c, ERX_K_MEAN);
-      launch_mean(ztype, zsrc, zstride, ps, W, d, T, !c->fp64, c->mu_hat, c->shift, st);
-    }
-    // TF32 / BF16 forms: S2 on the tensor cores.  The 3xTF32 form keeps the FP32
-    // SIMT scatter: its scatter on the tensor cores measured 3.5e-6 (relative
-    // to sqrt(K_aa K_bb)) against 1e-7 for FP32, from accumulating ~200 MMA
-    // steps per line in tensor memory, which puts its scores 10x off FP32's.
-    const int fmt = tc_format(c->cfg.form);
-    if ((fmt == 1 || fmt == 2) && ztype == ERX_F32 && !(c->cfg.flags & ERX_FLAG_SIMT_STATS) &&
-        syrk_tc_supported(zsrc, zstride, ps, W, d)) {
-      KernelScope ks(c, ERX_K_SYRK_TC);
-      launch_syrk_tc(fmt, (const float*)zsrc, zstride, W, d, T, c->n_sm, c->shift, c->S2f, c->err,
-                     c->t, st);
-    } else {
-      KernelScope ks(c, ERX_K_STATS_FP);
-      launch_stats_fp(ztype, c->fp64, zsrc, zstride, ps, W, d, T, c->shift, c->S2f, st);
-    }
-  }
-  if (c->cfg.averaging == ERX_AVG_IMC) {
-    KernelScope ks(c, ERX_K_EMA);
-    launch_imc_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W, c->t,
-                    c->cfg.order, c->mu_state, c->K_state, c->mu_t, c->K_t, c->imc_mprev,
-                    c->ema_scratch, st);
-  } else {
-    KernelScope ks(c, ERX_K_EMA);
-    launch_ema_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W,
-                  c->cfg.momentum, c->t, c->cfg.order, c->mu_state, c->K_state, c->mu_t, c->K_t,
-                  c->ema_scratch, st);
-  }
+  enqueue_stats(c, x, stride_elems, zsrc, ztype, zstride, ps, T, st);
+  enqueue_update(c, T, st);
   {
     KernelScope ks(c, ERX_K_CHOL);
     launch_chol_inv(c->K_t, d, T, c->cfg.ridge, c->Linv, c->fp64 ? nullptr : c->Linv32, c->err,
@@ -297,22 +284,8 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
     KernelScope ks(c, ERX_K_TRINV);
     launch_trinv32(c->Linv32, d, T, st);
   }
-  if (c->fp64) {
-    KernelScope ks(c, ERX_K_SOLVE_FP64);
-    launch_solve_fp64(ztype, zsrc, zstride, ps, W, d, T, c->mu_t, c->Linv, (double*)delta, st);
-  } else if (tc_format(c->cfg.form) > 0) {
-    KernelScope ks(c, ERX_K_SOLVE_TC);
-    launch_solve_tc(tc_format(c->cfg.form), ztype, zsrc, zstride, ps, W, d, T,
-                    c->mu_t, c->Linv32, (float*)delta, c->err, c->t, st);
-  } else {
-    KernelScope ks(c, ERX_K_SOLVE_FP32);
-    launch_solve_fp32(ztype, zsrc, zstride, ps, W, d, T, c->mu_t, c->Linv32, (float*)delta, st);
-  }
-  {
-    KernelScope ks(c, ERX_K_NORMALISE);
-    launch_normalise(c->fp64, delta, W, T, c->cfg.threshold, c->t, c->cfg.warmup_lines, dn,
-                     mask, det, st);
-  }
+  enqueue_score(c, zsrc, ztype, zstride, ps, T, c->mu_t, c->Linv, c->Linv32, delta, dn, mask,
+                det, st);
   const erx_status rs = check_cuda(c, cudaGetLastError());
   if (rs == ERX_OK && learned && c->audit_every > 0) {
     const erx_status as = audit_block(c, x, n, stride_elems, delta);
@@ -321,6 +294,161 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
   }
   c->t += n;
   return rs;
+}
+
+// S2 of T lines (x: the raw lines; z: what S2 takes, the lines or their projection)
+void enqueue_stats(erx_ctx* c, const void* x, int64_t stride_elems, const void* zsrc, int ztype,
+                   int64_t zstride, int ps, int T, cudaStream_t st) {
+  const int W = c->W, d = c->d;
+  if (c->int_stats && c->tc_stats) {
+    KernelScope ks(c, ERX_K_STATS_TC, st);
+    launch_stats_tc((const uint16_t*)x, stride_elems, W, d, (1u << c->cfg.in_bits) - 1u, T,
+                    c->n_sm, c->S1i, c->S2i, c->err, c->t, st);
+  } else if (c->int_stats) {
+    KernelScope ks(c, ERX_K_STATS_INT, st);
+    launch_stats_int((const uint16_t*)x, stride_elems, W, d, (1u << c->cfg.in_bits) - 1u, T,
+                     c->S1i, c->S2i, c->err, c->t, st);
+  } else {
+    {
+      KernelScope ks(c, ERX_K_MEAN, st);
+      launch_mean(ztype, zsrc, zstride, ps, W, d, T, !c->fp64, c->mu_hat, c->shift, st);
+    }
+    // TF32 / BF16 forms: S2 on the tensor cores.  The 3xTF32 form keeps the FP32
+    // SIMT scatter: its scatter on the tensor cores measured 3.5e-6 (relative
+    // to sqrt(K_aa K_bb)) against 1e-7 for FP32, from accumulating ~200 MMA
+    // steps per line in tensor memory, which puts its scores 10x off FP32's.
+    const int fmt = tc_format(c->cfg.form);
+    if ((fmt == 1 || fmt == 2) && ztype == ERX_F32 && !(c->cfg.flags & ERX_FLAG_SIMT_STATS) &&
+        syrk_tc_supported(zsrc, zstride, ps, W, d)) {
+      KernelScope ks(c, ERX_K_SYRK_TC, st);
+      launch_syrk_tc(fmt, (const float*)zsrc, zstride, W, d, T, c->n_sm, c->shift, c->S2f, c->err,
+                     c->t, st);
+    } else {
+      KernelScope ks(c, ERX_K_STATS_FP, st);
+      launch_stats_fp(ztype, c->fp64, zsrc, zstride, ps, W, d, T, c->shift, c->S2f, st);
+    }
+  }
+}
+
+// S3 over T lines: per-line statistics to score with (mu_t, K_t) and the state advanced
+void enqueue_update(erx_ctx* c, int T, cudaStream_t st) {
+  const int W = c->W, d = c->d;
+  if (c->cfg.averaging == ERX_AVG_IMC) {
+    KernelScope ks(c, ERX_K_EMA, st);
+    launch_imc_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W, c->t,
+                    c->cfg.order, c->mu_state, c->K_state, c->mu_t, c->K_t, c->imc_mprev,
+                    c->ema_scratch, st);
+  } else {
+    KernelScope ks(c, ERX_K_EMA, st);
+    launch_ema_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W,
+                    c->cfg.momentum, c->t, c->cfg.order, c->mu_state, c->K_state, c->mu_t,
+                    c->K_t, c->ema_scratch, st);
+  }
+}
+
+// S5 and S6 of T lines against (mu_t, factor) per line
+void enqueue_score(erx_ctx* c, const void* zsrc, int ztype, int64_t zstride, int ps, int T,
+                   const double* mu, const double* Lf, const float* Lf32, void* delta, void* dn,
+                   uint8_t* mask, uint8_t* det, cudaStream_t st) {
+  const int W = c->W, d = c->d;
+  if (c->fp64) {
+    KernelScope ks(c, ERX_K_SOLVE_FP64, st);
+    launch_solve_fp64(ztype, zsrc, zstride, ps, W, d, T, mu, Lf, (double*)delta, st);
+  } else if (tc_format(c->cfg.form) > 0) {
+    KernelScope ks(c, ERX_K_SOLVE_TC, st);
+    launch_solve_tc(tc_format(c->cfg.form), ztype, zsrc, zstride, ps, W, d, T, mu, Lf32,
+                    (float*)delta, c->err, c->t, st);
+  } else {
+    KernelScope ks(c, ERX_K_SOLVE_FP32, st);
+    launch_solve_fp32(ztype, zsrc, zstride, ps, W, d, T, mu, Lf32, (float*)delta, st);
+  }
+  {
+    KernelScope ks(c, ERX_K_NORMALISE, st);
+    launch_normalise(c->fp64, delta, W, T, c->cfg.threshold, c->t, c->cfg.warmup_lines, dn,
+                     mask, det, st);
+  }
+}
+
+// ERX_FLAG_PIPELINE: the factor of the current state (the one the next line is
+// scored with in score-then-update order), on stream st
+void enqueue_prefactor(erx_ctx* c, cudaStream_t st) {
+  const int d = c->d;
+  {
+    KernelScope ks(c, ERX_K_CHOL, st);
+    launch_chol_inv(c->K_state, d, 1, c->cfg.ridge, c->Lf_pre, c->fp64 ? nullptr : c->Lf32_pre,
+                    c->err, c->t, st);
+  }
+  if (!c->fp64) {
+    KernelScope ks(c, ERX_K_TRINV, st);
+    launch_trinv32(c->Lf32_pre, d, 1, st);
+  }
+  cudaMemcpyAsync(c->mu_pre, c->mu_state, sizeof(double) * d, cudaMemcpyDeviceToDevice, st);
+}
+
+// One line in score-then-update order with the update deferred (ERX_FLAG_PIPELINE).
+// On the context's stream: the line is scored against the factor made at the
+// end of the previous push, and its delta_N written.  On the second stream,
+// concurrently: the line's statistics and the state's update, then (once the
+// score has read the old factor) the factor of the new state for the next
+// line.  The next push's score waits for that factor; the context's stream
+// waits for the statistics (so the line's buffer is free once it passes).
+erx_status run_line_pipelined(erx_ctx* c, const void* x, int64_t stride_elems, void* delta,
+                              void* dn, uint8_t* mask, uint8_t* det) {
+  const int W = c->W, d = c->d, B = c->B;
+  cudaStream_t st = c->stream, sd = c->side;
+  cudaStreamWaitEvent(st, c->ev_ready, 0);
+  const void* zsrc = x;
+  int ztype = c->cfg.in_dtype;
+  int64_t zstride = stride_elems;
+  int ps = B;
+  if (!c->w_host.empty()) {
+    KernelScope ks(c, ERX_K_PROJECT, st);
+    launch_project(c->cfg.in_dtype, x, stride_elems, B, W, d, 1, c->colptr, c->rows, c->vals,
+                   c->fp64, c->Z, st);
+    zsrc = c->Z;
+    ztype = c->fp64 ? ERX_F64 : ERX_F32;
+    zstride = (int64_t)W * d;
+    ps = d;
+  }
+  cudaEventRecord(c->ev_start, st);
+  enqueue_score(c, zsrc, ztype, zstride, ps, 1, c->mu_pre, c->Lf_pre, c->Lf32_pre, delta, dn,
+                mask, det, st);
+  cudaStreamWaitEvent(sd, c->ev_start, 0);
+  enqueue_stats(c, x, stride_elems, zsrc, ztype, zstride, ps, 1, sd);
+  cudaEventRecord(c->ev_stats, sd);
+  enqueue_update(c, 1, sd);
+  cudaStreamWaitEvent(st, c->ev_stats, 0);
+  cudaEventRecord(c->ev_scored, st);
+  cudaStreamWaitEvent(sd, c->ev_scored, 0);
+  c->t += 1;
+  enqueue_prefactor(c, sd);
+  cudaEventRecord(c->ev_ready, sd);
+  return check_cuda(c, cudaGetLastError());
+}
+
+// ERX_FLAG_PIPELINE, around pushes that take the ordinary path: first the
+// deferred update of the last pipelined line must be done (join), afterwards
+// the factor of the new state is made for the next single-line push (refresh).
+void pipeline_join(erx_ctx* c) {
+  if (c->pipeline) cudaStreamWaitEvent(c->stream, c->ev_ready, 0);
+}
+
+erx_status pipeline_refresh(erx_ctx* c) {
+  if (!c->pipeline) return ERX_OK;
+  c->have_pre = false;
+  if (c->t == 0) return ERX_OK;
+  enqueue_prefactor(c, c->stream);
+  cudaEventRecord(c->ev_ready, c->stream);
+  const erx_status s = check_cuda(c, cudaGetLastError());
+  c->have_pre = s == ERX_OK;
+  return s;
+}
+
+// every stream of the context idle
+cudaError_t sync_all(erx_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess && c->side) e = cudaStreamSynchronize(c->side);
+  return e;
 }
 
 double spearman(const double* a, const double* b, int n) {
@@ -509,6 +637,19 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   ERX_A(err, kErrSlots);
   if (ema_scratch_doubles(d, T) > 0) ERX_A(ema_scratch, ema_scratch_doubles(d, T));
   if (cfg->averaging == ERX_AVG_IMC) ERX_A(imc_mprev, imc_work_doubles(d, T));
+  c->pipeline = (cfg->flags & ERX_FLAG_PIPELINE) != 0;
+  if (c->pipeline) {
+    ERX_A(mu_pre, d);
+    ERX_A(Lf_pre, P);
+    if (!c->fp64) ERX_A(Lf32_pre, P);
+    if (s == ERX_OK &&
+        (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_stats, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_scored, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess))
+      s = ERX_ECUDA;
+  }
 #undef ERX_A
   if (s == ERX_OK && learned) {
     float* zp = nullptr;
@@ -570,6 +711,9 @@ erx_status erx_push_lines(erx_ctx* c, const void* lines, int64_t n, int64_t stri
   if (stride_bytes < line_elems * (int64_t)es || stride_bytes % (int64_t)es) return ERX_EINVAL;
   const int64_t stride = stride_bytes / (int64_t)es;
   const size_t ss = c->fp64 ? 8 : 4;
+  if (c->pipeline && n == 1 && c->have_pre)
+    return run_line_pipelined(c, lines, stride, delta, dn, mask, det);
+  pipeline_join(c);
   for (int64_t b = 0; b < n; b += c->T) {
     const int64_t m = std::min<int64_t>(c->T, n - b);
     const char* x = (const char*)lines + b * stride_bytes;
@@ -578,7 +722,7 @@ erx_status erx_push_lines(erx_ctx* c, const void* lines, int64_t n, int64_t stri
                              mask ? mask + (size_t)b * c->W : nullptr, det ? det + b : nullptr);
     if (s != ERX_OK) return s;
   }
-  return ERX_OK;
+  return pipeline_refresh(c);
 }
 
 erx_status erx_push_lines_host(erx_ctx* c, const void* lines, int64_t n, int64_t stride_bytes,
@@ -616,6 +760,7 @@ erx_status erx_push_lines_host(erx_ctx* c, const void* lines, int64_t n, int64_t
       return s;
     }
   }
+  pipeline_join(c);
   // Input: pinned caller memory is copied directly; pageable memory through h_in.
   cudaPointerAttributes pa{};
   const bool pinned = cudaPointerGetAttributes(&pa, lines) == cudaSuccess &&
@@ -684,8 +829,9 @@ erx_status erx_push_lines_host(erx_ctx* c, const void* lines, int64_t n, int64_t
       e = cudaMemcpyAsync(det + off, d_det, (size_t)m, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return check_cuda(c, e);
   }
-  erx_status s = check_cuda(c, cudaStreamSynchronize(c->copy_stream));
-  if (s == ERX_OK) s = check_cuda(c, cudaStreamSynchronize(c->stream));
+  erx_status s = pipeline_refresh(c);
+  if (s == ERX_OK) s = check_cuda(c, cudaStreamSynchronize(c->copy_stream));
+  if (s == ERX_OK) s = check_cuda(c, sync_all(c));
   return s;
 }
 
@@ -694,7 +840,7 @@ erx_status erx_sync(erx_ctx* c, int64_t* bad_line) {
   if (!c) return ERX_EINVAL;
   if (c->failed) return ERX_ECUDA;
   unsigned long long e[kErrSlots];
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+  if (sync_all(c) != cudaSuccess ||
       cudaMemcpy(e, c->err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess)
     return check_cuda(c, cudaGetLastError());
   if (cudaMemset(c->err, 0xff, sizeof(e)) != cudaSuccess) return check_cuda(c, cudaGetLastError());
@@ -717,6 +863,7 @@ erx_status erx_reset(erx_ctx* c) {
   if (!c) return ERX_EINVAL;
   if (c->failed) return ERX_ECUDA;
   c->t = 0;
+  c->have_pre = false;
   return ERX_OK;
 }
 
@@ -726,7 +873,7 @@ erx_status erx_get_state(erx_ctx* c, int64_t* t, double* mu, double* K) {
   const int d = c->d;
   const int64_t P = packed_size(d);
   std::vector<double> kp((size_t)P);
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, cudaGetLastError());
+  if (sync_all(c) != cudaSuccess) return check_cuda(c, cudaGetLastError());
   if (mu && cudaMemcpy(mu, c->mu_state, sizeof(double) * d, cudaMemcpyDeviceToHost) != cudaSuccess)
     return check_cuda(c, cudaGetLastError());
   if (K) {
@@ -753,13 +900,14 @@ erx_status erx_set_state(erx_ctx* c, int64_t t, const double* mu, const double* 
     std::vector<double> kp((size_t)P);
     for (int a = 0; a < d; ++a)
       for (int b = 0; b <= a; ++b) kp[(size_t)a * (a + 1) / 2 + b] = K[(size_t)a * d + b];
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+    if (sync_all(c) != cudaSuccess ||
         cudaMemcpy(c->mu_state, mu, sizeof(double) * d, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->K_state, kp.data(), sizeof(double) * P, cudaMemcpyHostToDevice) !=
             cudaSuccess)
       return check_cuda(c, cudaGetLastError());
   }
   c->t = t;
+  c->have_pre = false;   // the next push takes the ordinary path and refactors
   return ERX_OK;
 }
 
@@ -821,7 +969,7 @@ erx_status erx_profile_read(erx_ctx* c, int32_t k, int32_t reset, double* total_
                             int64_t* timed, int64_t* launches) {
   if (!c || k < 0 || k >= ERX_K_COUNT) return ERX_EINVAL;
   if (c->failed) return ERX_ECUDA;
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return check_cuda(c, cudaGetLastError());
+  if (sync_all(c) != cudaSuccess) return check_cuda(c, cudaGetLastError());
   resolve_pending(c);
   if (total_ms) *total_ms = c->total_ms[k];
   if (timed) *timed = c->timed[k];
@@ -843,7 +991,7 @@ const char* erx_kernel_name(int32_t k) {
 
 erx_status erx_destroy(erx_ctx* c) {
   if (!c) return ERX_OK;
-  cudaStreamSynchronize(c->stream);
+  sync_all(c);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   cudaGetLastError();
   free_all(c);

@@ -46,7 +46,7 @@ __host__ __device__ inline size_t chol_smem(int d) {
 // `line` is the global line index reported on a bad pivot.  TS: edge of the
 // trailing update's register tiles (4 where one CTA fills an SM, 2 where four
 // CTAs share it and each thread has 64 registers).
-template <int TS>
+template <int TS, int NT = kThreads>
 __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d, double ridge,
                                           double* __restrict__ dst, float* __restrict__ d32,
                                           unsigned long long* __restrict__ err, int64_t line) {
@@ -59,9 +59,9 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   double* Lp = sm + ((P + 1) & ~1);
   double* rdiag = Lp + kPB * ls;    // 1 / l_jj
   const int tid = threadIdx.x;
-  for (int q = tid; q < P; q += kThreads) A[q] = src[q];
+  for (int q = tid; q < P; q += NT) A[q] = src[q];
   __syncthreads();
-  for (int j = tid; j < d; j += kThreads) A[pidx(j, j)] += ridge;
+  for (int j = tid; j < d; j += NT) A[pidx(j, j)] += ridge;
   __syncthreads();
   // pivot of column j (its updated diagonal a): l_jj = a rsqrt(a), published
   auto pivot = [&](double& a, int jj, int j) {
@@ -77,7 +77,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
 
   for (int j0 = 0; j0 < d; j0 += kPB) {
     const int jb = min(kPB, d - j0);
-    const int rl = tid, i = j0 + rl;          // this thread's row (d - j0 <= kThreads)
+    const int rl = tid, i = j0 + rl;          // this thread's row (d - j0 <= NT)
     const bool own = i < d;
     double a[kPB];
 #pragma unroll
@@ -122,7 +122,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
       const int nt = (m + TS - 1) / TS;
       const int ntile = nt * (nt + 1) / 2;
       const int g0 = j0 + jb;
-      for (int q = tid; q < ntile; q += kThreads) {
+      for (int q = tid; q < ntile; q += NT) {
         int I = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
         while (I * (I + 1) / 2 > q) --I;
         while ((I + 1) * (I + 2) / 2 <= q) ++I;
@@ -167,7 +167,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   // per-lane arrays are needed and the kernel keeps few registers.
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = (d + kNB - 1) / kNB;
-  for (int bk = warp; bk < nblk; bk += kThreads / 32) {
+  for (int bk = warp; bk < nblk; bk += NT / 32) {
     const int j0 = bk * kNB;
     const int nb = min(kNB, d - j0);
     for (int j = nb - 1; j >= 0; --j) {
@@ -185,22 +185,22 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
     }
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < P; q += kThreads) dst[q] = A[q];
+  for (int q = threadIdx.x; q < P; q += NT) dst[q] = A[q];
   if (d32) {
-    for (int q = threadIdx.x; q < P; q += kThreads) d32[q] = (float)A[q];
+    for (int q = threadIdx.x; q < P; q += NT) d32[q] = (float)A[q];
   }
 }
 
-template <int TS, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) chol_kernel(const double* __restrict__ K_t,
-                                                          int d, double ridge,
-                                                          double* __restrict__ Lf,
-                                                          float* __restrict__ Lf32,
-                                                          unsigned long long* __restrict__ err,
-                                                          int64_t t0) {
+template <int TS, int MINB, int NT = kThreads>
+__global__ void __launch_bounds__(NT, MINB) chol_kernel(const double* __restrict__ K_t, int d,
+                                                    double ridge, double* __restrict__ Lf,
+                                                    float* __restrict__ Lf32,
+                                                    unsigned long long* __restrict__ err,
+                                                    int64_t t0) {
   const int t = blockIdx.x;
   const int64_t P = packed_size(d);
-  chol_body<TS>(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err, t0 + t);
+  chol_body<TS, NT>(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err,
+                    t0 + t);
 }
 
 // Batched form: one CTA per stream.
@@ -285,6 +285,12 @@ cudaError_t configure_factor_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(chol_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chol_kernel<2, 1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             m);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(chol_kernel<4, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             m);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(b_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   const int m32 = (int)(packed_size(kMaxDim) * sizeof(float));
   if (e == cudaSuccess)
@@ -301,11 +307,26 @@ void launch_batch_chol(const BStream* S, int n, int dmax, bool want32, unsigned 
 
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, float* Lf32,
                      unsigned long long* err, int64_t t0, cudaStream_t st) {
-  // above 128 dimensions the factor fills an SM's shared memory: one CTA per SM
-  if (d > 128)
-    chol_kernel<4, 1><<<T, kThreads, chol_smem(d), st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
+  // above 128 dimensions the factor fills an SM's shared memory: one CTA per SM.
+  // Fewer lines than SMs (a line or a few pushed alone): one CTA per SM anyway,
+  // so each takes more threads (as many as its registers allow) to hide the
+  // latency of its barriers and DFMA chains.
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (n_sm <= 0) n_sm = 1;
+  }
+  const size_t sm = chol_smem(d);
+  if (T < n_sm && d > 128)
+    chol_kernel<4, 1, 512><<<T, 512, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
+  else if (T < n_sm)
+    chol_kernel<2, 1, 1024><<<T, 1024, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
+  else if (d > 128)
+    chol_kernel<4, 1><<<T, kThreads, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
   else
-    chol_kernel<2, 4><<<T, kThreads, chol_smem(d), st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
+    chol_kernel<2, 4><<<T, kThreads, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
 }
 
 }  // namespace erx

@@ -87,36 +87,40 @@ __device__ __forceinline__ void solve_fp64_body(const InT* __restrict__ x, int p
   delta[i] = sqrt(d2);
 }
 
-// Large d (> 128): a 64-pixel tile holds 113 KiB of residuals, so two CTAs fit
-// on an SM; with one thread per pixel that is four warps, one per SMSP, too
-// few to cover the latency of the dependent DFMA chains and the L2 reads of L.
-// Here two threads share each pixel (128 threads, eight warps per SM): per
-// 32-row block they take the even and the odd rows of y_J (written in place
-// of r_J), then the even and the odd rows of m_J = D_J y_J, held in registers
-// until both have read y_J.  No shared memory beyond the residual tile; every
-// sum is taken in the same order as in the one-thread body, so both give the
-// same bits.
-template <typename InT>
-__device__ __forceinline__ void solve_fp64_pair_body(const InT* __restrict__ x, int ps, int W,
-                                                     int d, const double* __restrict__ mu,
-                                                     const double* __restrict__ L,
-                                                     double* __restrict__ delta, int tile) {
+// H threads per pixel, NPX pixels per tile (H * NPX threads).  Per 32-row
+// block the H threads of a pixel take the rows jj = H u + h of y_J (written in
+// place of r_J), then the same rows of m_J = D_J y_J, held in registers until
+// all have read y_J; the squares are summed in row order by one thread.  Every
+// sum is taken in the same order as in the one-thread body, so all variants
+// give the same bits.  Uses:
+//  * large d (> 128), H = 2, NPX = 64: a 64-pixel tile holds 113 KiB of
+//    residuals, two CTAs fit on an SM, and one thread per pixel would be four
+//    warps per SM, too few to cover the DFMA chains and the L2 reads of L;
+//  * launches with fewer 64-pixel tiles than SMs (a line or a few pushed
+//    alone), H = 16, NPX = 8: the line's pixels spread over up to 8x as many
+//    SMs, four warps each, so a single line's score takes a few tens of
+//    microseconds instead of the 10 SMs' worth of FP64 time.
+template <typename InT, int H, int NPX>
+__device__ __forceinline__ void solve_fp64_multi_body(const InT* __restrict__ x, int ps, int W,
+                                                      int d, const double* __restrict__ mu,
+                                                      const double* __restrict__ L,
+                                                      double* __restrict__ delta, int tile) {
   extern __shared__ __align__(16) double r[];
   const int dp = d | 1;
-  const int i0 = tile * kPixF64;
-  for (int e = threadIdx.x; e < kPixF64 * d; e += 2 * kPixF64) {
+  const int i0 = tile * NPX;
+  for (int e = threadIdx.x; e < NPX * d; e += H * NPX) {
     const int p = e / d, k = e - p * d, i = i0 + p;
     r[p * dp + k] = i < W ? to_d(x[(int64_t)i * ps + k]) - mu[k] : 0.0;
   }
   __syncthreads();
-  const int p = threadIdx.x % kPixF64, h = threadIdx.x / kPixF64;   // pixel, row parity
+  const int p = threadIdx.x % NPX, h = threadIdx.x / NPX;   // pixel, row phase
   const int i = i0 + p;
   double* rr = r + p * dp;
   for (int j0 = 0; j0 < d; j0 += kNB) {
     const int nb = min(kNB, d - j0);
 #pragma unroll
-    for (int u = 0; u < kNB / 2; ++u) {
-      const int jj = 2 * u + h;
+    for (int u = 0; u < kNB / H; ++u) {
+      const int jj = H * u + h;
       if (jj < nb) {
         const int j = j0 + jj;
         const double* Lj = L + j * (j + 1) / 2;
@@ -126,27 +130,26 @@ __device__ __forceinline__ void solve_fp64_pair_body(const InT* __restrict__ x, 
       }
     }
     __syncthreads();
-    double m[kNB / 2];
+    double m[kNB / H];
 #pragma unroll
-    for (int u = 0; u < kNB / 2; ++u) {
-      const int jj = 2 * u + h;
+    for (int u = 0; u < kNB / H; ++u) {
+      const int jj = H * u + h;
       double s = 0.0;
       if (jj < nb) {
         const double* Dj = L + (j0 + jj) * (j0 + jj + 1) / 2 + j0;
         const double* yj = rr + j0;
 #pragma unroll
-        for (int kk = 0; kk <= 2 * u; ++kk) s = fma(__ldg(Dj + kk), yj[kk], s);
-        if (h) s = fma(__ldg(Dj + 2 * u + 1), yj[2 * u + 1], s);
+        for (int kk = 0; kk < H * u + H; ++kk)
+          if (kk <= jj) s = fma(__ldg(Dj + kk), yj[kk], s);
       }
       m[u] = s;
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < kNB / 2; ++u)
-      if (2 * u + h < nb) rr[j0 + 2 * u + h] = m[u];
+    for (int u = 0; u < kNB / H; ++u)
+      if (H * u + h < nb) rr[j0 + H * u + h] = m[u];
     __syncthreads();
   }
-  // the squares are summed in row order by one thread, as in the one-thread body
   if (h == 0 && i < W) {
     double d2 = 0.0;
     for (int j = 0; j < d; ++j) d2 = fma(rr[j], rr[j], d2);
@@ -155,23 +158,24 @@ __device__ __forceinline__ void solve_fp64_pair_body(const InT* __restrict__ x, 
 }
 
 // Persistent grid (a whole number of waves): CTA c takes tiles c, c + grid, ...
-// of the T x ntiles (line, tile) pairs.
-template <typename InT, bool PAIR>
-__global__ void __launch_bounds__(PAIR ? 2 * kPixF64 : kPixF64) solve_fp64_kernel(
+// of the T x ntiles (line, tile) pairs.  H = 1: one thread per pixel.
+template <typename InT, int H, int NPX>
+__global__ void __launch_bounds__(H * NPX) solve_fp64_kernel(
     const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
     const double* __restrict__ mu_t, const double* __restrict__ Lf, double* __restrict__ delta,
     int T) {
-  const int ntiles = (W + kPixF64 - 1) / kPixF64;
+  const int ntiles = (W + NPX - 1) / NPX;
   const int64_t total = (int64_t)T * ntiles;
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
     const int t = (int)(w / ntiles), tile = (int)(w % ntiles);
     __syncthreads();          // the previous tile's threads are done with shared memory
-    if (PAIR)
-      solve_fp64_pair_body<InT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
-                                Lf + (int64_t)t * packed_size(d), delta + (int64_t)t * W, tile);
-    else
+    if constexpr (H == 1)
       solve_fp64_body<InT>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
                            Lf + (int64_t)t * packed_size(d), delta + (int64_t)t * W, tile);
+    else
+      solve_fp64_multi_body<InT, H, NPX>(X + (int64_t)t * line_stride, ps, W, d,
+                                         mu_t + (int64_t)t * d, Lf + (int64_t)t * packed_size(d),
+                                         delta + (int64_t)t * W, tile);
   }
 }
 
@@ -292,23 +296,25 @@ cudaError_t configure_solve_kernels() {
   const int m64 = (int)smem_fp64(kMaxDim), m32 = (int)smem_fp32(kMaxDim);
 #define ERX_CFG(K, M) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, M)
-  ERX_CFG((solve_fp64_kernel<uint16_t, false>), m64);
-  ERX_CFG((solve_fp64_kernel<float, false>), m64);
-  ERX_CFG((solve_fp64_kernel<double, false>), m64);
-  ERX_CFG((solve_fp64_kernel<uint16_t, true>), m64);
-  ERX_CFG((solve_fp64_kernel<float, true>), m64);
-  ERX_CFG((solve_fp64_kernel<double, true>), m64);
+#define ERX_CFG3(IT)                                 \
+  ERX_CFG((solve_fp64_kernel<IT, 1, kPixF64>), m64); \
+  ERX_CFG((solve_fp64_kernel<IT, 2, kPixF64>), m64); \
+  ERX_CFG((solve_fp64_kernel<IT, 16, 8>), m64);
+  ERX_CFG3(uint16_t)
+  ERX_CFG3(float)
+  ERX_CFG3(double)
+#undef ERX_CFG3
   // residual tiles take nearly all of the SM's shared memory (two 113 KiB
   // tiles at d = 224); L streams through L2
 #define ERX_CARVE(K)     \
   if (e == cudaSuccess) \
   e = cudaFuncSetAttribute(K, cudaFuncAttributePreferredSharedMemoryCarveout, 100)
-  ERX_CARVE((solve_fp64_kernel<uint16_t, false>));
-  ERX_CARVE((solve_fp64_kernel<float, false>));
-  ERX_CARVE((solve_fp64_kernel<double, false>));
-  ERX_CARVE((solve_fp64_kernel<uint16_t, true>));
-  ERX_CARVE((solve_fp64_kernel<float, true>));
-  ERX_CARVE((solve_fp64_kernel<double, true>));
+  ERX_CARVE((solve_fp64_kernel<uint16_t, 1, kPixF64>));
+  ERX_CARVE((solve_fp64_kernel<float, 1, kPixF64>));
+  ERX_CARVE((solve_fp64_kernel<double, 1, kPixF64>));
+  ERX_CARVE((solve_fp64_kernel<uint16_t, 2, kPixF64>));
+  ERX_CARVE((solve_fp64_kernel<float, 2, kPixF64>));
+  ERX_CARVE((solve_fp64_kernel<double, 2, kPixF64>));
 #undef ERX_CARVE
   ERX_CFG(solve_fp32_kernel<uint16_t>, m32);
   ERX_CFG(solve_fp32_kernel<float>, m32);
@@ -332,14 +338,28 @@ void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, in
     b_solve_fp32_kernel<<<n_items, 128, smem_fp32(dmax), st>>>(S, items);
 }
 
-constexpr int kPairMinD = 129;   // the paired kernel from here on
+constexpr int kPairMinD = 129;   // two threads per pixel from here on
 
-template <typename InT, bool PAIR>
+template <typename InT, int H, int NPX>
 void launch_fp64_t(const InT* x, int64_t line_stride, int ps, int W, int d, int T,
-                   const double* mu_t, const double* Linv, double* delta, cudaStream_t st) {
-  const int threads = PAIR ? 2 * kPixF64 : kPixF64;
-  const size_t sm = smem_fp64(d);
+                   const double* mu_t, const double* Linv, double* delta, int n_sm,
+                   cudaStream_t st) {
+  const int threads = H * NPX;
+  const size_t sm = (size_t)NPX * (d | 1) * sizeof(double);
   // a whole number of waves: resident CTAs per SM times the SM count
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fp64_kernel<InT, H, NPX>, threads,
+                                                sm);
+  per_sm = std::max(1, per_sm);
+  const int64_t total = (int64_t)T * ((W + NPX - 1) / NPX);
+  const int grid = (int)std::min<int64_t>(total, (int64_t)n_sm * per_sm);
+  solve_fp64_kernel<InT, H, NPX><<<grid, threads, sm, st>>>(x, line_stride, ps, W, d, mu_t,
+                                                             Linv, delta, T);
+}
+
+template <typename InT>
+void launch_fp64_in(const InT* x, int64_t line_stride, int ps, int W, int d, int T,
+                    const double* mu_t, const double* Linv, double* delta, cudaStream_t st) {
   static int n_sm = 0;
   if (!n_sm) {
     int dev = 0;
@@ -347,33 +367,24 @@ void launch_fp64_t(const InT* x, int64_t line_stride, int ps, int W, int d, int 
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (n_sm <= 0) n_sm = 1;
   }
-  int per_sm = 1;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_fp64_kernel<InT, PAIR>, threads,
-                                                sm);
-  per_sm = std::max(1, per_sm);
-  const int64_t total = (int64_t)T * ((W + kPixF64 - 1) / kPixF64);
-  const int grid = (int)std::min<int64_t>(total, (int64_t)n_sm * per_sm);
-  solve_fp64_kernel<InT, PAIR><<<grid, threads, sm, st>>>(x, line_stride, ps, W, d, mu_t, Linv,
-                                                          delta, T);
+  const int64_t tiles64 = (int64_t)T * ((W + kPixF64 - 1) / kPixF64);
+  if (tiles64 < n_sm)
+    launch_fp64_t<InT, 16, 8>(x, line_stride, ps, W, d, T, mu_t, Linv, delta, n_sm, st);
+  else if (d >= kPairMinD)
+    launch_fp64_t<InT, 2, kPixF64>(x, line_stride, ps, W, d, T, mu_t, Linv, delta, n_sm, st);
+  else
+    launch_fp64_t<InT, 1, kPixF64>(x, line_stride, ps, W, d, T, mu_t, Linv, delta, n_sm, st);
 }
 
 void launch_solve_fp64(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,
                        int T, const double* mu_t, const double* Linv, double* delta,
                        cudaStream_t st) {
-  const bool pair = d >= kPairMinD;
-#define ERX_F64(IT)                                                                          \
-  if (pair)                                                                                  \
-    launch_fp64_t<IT, true>((const IT*)x, line_stride, ps, W, d, T, mu_t, Linv, delta, st); \
-  else                                                                                       \
-    launch_fp64_t<IT, false>((const IT*)x, line_stride, ps, W, d, T, mu_t, Linv, delta, st)
-  if (in_type == 0) {
-    ERX_F64(uint16_t);
-  } else if (in_type == 1) {
-    ERX_F64(float);
-  } else {
-    ERX_F64(double);
-  }
-#undef ERX_F64
+  if (in_type == 0)
+    launch_fp64_in((const uint16_t*)x, line_stride, ps, W, d, T, mu_t, Linv, delta, st);
+  else if (in_type == 1)
+    launch_fp64_in((const float*)x, line_stride, ps, W, d, T, mu_t, Linv, delta, st);
+  else
+    launch_fp64_in((const double*)x, line_stride, ps, W, d, T, mu_t, Linv, delta, st);
 }
 
 void launch_solve_fp32(int in_type, const void* x, int64_t line_stride, int ps, int W, int d,

@@ -15,9 +15,9 @@ lib_path = os.path.join(_PKG, "_lib", "liberx.so")
 
 ERX_OK, ERX_EINVAL, ERX_ENOMEM, ERX_ECUDA, ERX_ENOTPD, ERX_ERANGE, ERX_ESTATE, \
     ERX_EUNSUPPORTED, ERX_ETIMEOUT = range(9)
-ERX_FLAG_SIMT_STATS = 1
 ERX_PROJ_NONE, ERX_PROJ_SRP, ERX_PROJ_LEARNED = 0, 1, 2
 ERX_UPDATE_THEN_SCORE, ERX_SCORE_THEN_UPDATE = 0, 1
+ERX_FLAG_SIMT_STATS, ERX_FLAG_PIPELINE = 1, 2
 ERX_AVG_EMA, ERX_AVG_IMC = 0, 1
 ERX_U16, ERX_F32, ERX_F64 = 0, 1, 2
 ERX_FORM_FP64, ERX_FORM_FP32, ERX_FORM_TF32, ERX_FORM_BF16, ERX_FORM_TF32X3 = 0, 1, 2, 3, 4
@@ -246,7 +246,7 @@ class Detector:
                  warmup=99, order="update_then_score", in_dtype="f32", in_bits=16,
                  form="fp64", threshold=3.0, block_lines=0, srp_weights=None, stream=None,
                  simt_stats=False, encoder=None, audit_every=0, min_rank_corr=0.0,
-                 averaging="ema"):
+                 averaging="ema", pipeline=False):
         import torch
         self.torch = torch
         cfg = erx_config_default(bands, width)
@@ -266,7 +266,8 @@ class Detector:
         cfg.form = FORMS[form]
         cfg.threshold = threshold if threshold is not None else math.inf
         cfg.block_lines = block_lines
-        cfg.flags = ERX_FLAG_SIMT_STATS if simt_stats else 0
+        cfg.flags = (ERX_FLAG_SIMT_STATS if simt_stats else 0) | \
+            (ERX_FLAG_PIPELINE if pipeline else 0)
         cfg.averaging = {"ema": ERX_AVG_EMA, "imc": ERX_AVG_IMC}[averaging]
         self._w = None
         if srp_weights is not None:

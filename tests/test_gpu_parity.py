@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import dn_err, need_gpu, rel_err, run_gpu, torch
+from tests.gpu_util import dn_err, need_gpu, rel_err, run_gpu, to_dev, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -336,3 +336,39 @@ def test_imc_integer_statistics():
                        push_sizes=[40])
     _compare(got, ref, 1e-9)
     assert det.profile_read()["stats_tc"][2] > 0
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32", "tf32"])
+def test_pipelined_score_then_update_is_bitwise_plain(form):
+    """ERX_FLAG_PIPELINE: single-line pushes scored against the factor made at
+    the end of the previous push, the update deferred to a second stream, give
+    the same bits as score-then-update without it; interleaved block pushes and
+    a set_state in mid-stream take the ordinary path and refactor."""
+    cube = synth.gen_lines(synth.reflectance_c1(width=96, bands=24, seed=6), 0, 40)
+    sizes = [1] * 12 + [5] + [1] * 23
+    kw = dict(form=form, warmup=2, threshold=3.0, order="score_then_update")
+    plain, dp = run_gpu(cube, push_sizes=sizes, **kw)
+    piped, dq = run_gpu(cube, push_sizes=sizes, pipeline=True, **kw)
+    for k in ("delta", "delta_n", "mask", "detecting"):
+        assert np.array_equal(plain[k], piped[k]), k
+    sp, sq = dp.state(), dq.state()
+    assert sp[0] == sq[0] == 40 and np.array_equal(sp[1], sq[1]) and np.array_equal(sp[2], sq[2])
+    ref = oracle.run_cube(cube, warmup=2, threshold=3.0, order="score_then_update")
+    # the first lines are scored against one line's covariance, kappa 2.4e4 here:
+    # above the range of the FP32 and TF32 bars (1e4); the kappa sweep gives
+    # FP32 2.6e-4 and TF32 4.3e-3 at 1e5 (tolerances as in the batched tests)
+    _compare(piped, ref, {"fp64": 1e-9, "fp32": 5e-4, "tf32": 2e-2}[form])
+    # resume from a saved state: the next line takes the ordinary path
+    x = to_dev(cube)
+    dq.set_state(*sp)
+    dp.set_state(*sp)
+    for t in range(35, 40):
+        a, b = dp.push(x[t:t + 1]), dq.push(x[t:t + 1])
+        dp.sync(), dq.sync()
+        assert torch.equal(a[0], b[0])
+
+
+def test_pipeline_flag_needs_score_then_update():
+    from paper_2408_14947_gb300 import Detector, ErxError
+    with pytest.raises(ErxError):
+        Detector(8, 16, order="update_then_score", pipeline=True)
