@@ -25,6 +25,10 @@ so the code can be checked against it):
   Welford's update (the paper cites Schubert and Gertz 2018), so the state is
   the mean and the 1/(n-1) covariance of all n pixels seen so far, every line
   weighed equally; the momentum is not used.
+* "pooled": the other reading of the 99-line buffer (Sec. IV-B): the warm-up
+  lines are pooled with equal weight (the IMC update) into the estimate the
+  EMAs start from; from the first line after the warm-up on, the EMAs of
+  Sec. III-C.
 """
 from __future__ import annotations
 
@@ -103,8 +107,9 @@ class ERXOracle:
     Sec. III-B), ``ridge`` = 1e-5 (Sec. III-D), ``warmup`` = 99 lines (Sec. IV-B),
     ``threshold`` = tau_N (Sec. III-E; None for no mask).
     ``proj`` is "none" (all bands), "srp" (matrix drawn from ``seed``) or an
-    explicit b x d array.  ``averaging`` is "ema" (Sec. III-C) or "imc" (the
-    equal-weight ablation of Sec. IV-C).
+    explicit b x d array.  ``averaging`` is "ema" (Sec. III-C), "imc" (the
+    equal-weight ablation of Sec. IV-C) or "pooled" (IMC over the ``warmup``
+    lines, the EMAs afterwards).
     """
 
     def __init__(self, bands: int, width: int, momentum: float = 0.1, proj="none",
@@ -117,7 +122,7 @@ class ERXOracle:
             raise ValueError("a line needs at least 2 pixels for its covariance")
         if order not in ("update_then_score", "score_then_update"):
             raise ValueError(order)
-        if averaging not in ("ema", "imc"):
+        if averaging not in ("ema", "imc", "pooled"):
             raise ValueError(averaging)
         self.averaging = averaging
         self.bands, self.width = bands, width
@@ -139,7 +144,8 @@ class ERXOracle:
     def _update(self, mu_hat, k_hat):
         if self.t == 0:                       # Sec. III-C: start from the first line
             self.mu, self.k = mu_hat.copy(), k_hat.copy()
-        elif self.averaging == "imc":         # all lines so far have width pixels each
+        elif self.averaging == "imc" or (self.averaging == "pooled" and self.t < self.warmup):
+            # all lines so far have width pixels each
             self.mu, self.k = imc_update(self.mu, self.k, self.t * self.width, mu_hat, k_hat,
                                          self.width)
         else:

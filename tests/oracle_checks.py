@@ -228,6 +228,33 @@ def check_imc_pooled(order="update_then_score"):
     return worst
 
 
+def check_pooled_warmup(alpha=0.2, warmup=5, extra=4):
+    """The pooled reading of the warm-up buffer: after the warm-up lines the
+    state is their pooled mean and 1/(n-1) covariance (numpy.cov of all their
+    pixels); after k more lines it is the closed form of the EMA started from
+    there, mu = (1-a)^k mu_pool + sum_j a (1-a)^(k-1-j) mu_hat_j (same for K)."""
+    p, b = 8, 3
+    r = np.random.default_rng(33)
+    cube = np.stack([r.standard_normal((p, b)) + 2.0 * r.standard_normal(b)
+                     for _ in range(warmup + extra)])
+    det = eo.ERXOracle(b, p, momentum=alpha, averaging="pooled", warmup=warmup, ridge=1e-3)
+    for t in range(warmup):
+        det.push(cube[t])
+    pool = cube[:warmup].reshape(-1, b)
+    worst = max(rel(det.mu, pool.mean(axis=0)), rel(det.k, np.cov(pool.T, ddof=1)))
+    for t in range(warmup, warmup + extra):
+        det.push(cube[t])
+    k = extra
+    mu = (1 - alpha) ** k * pool.mean(axis=0)
+    kk = (1 - alpha) ** k * np.cov(pool.T, ddof=1)
+    for j in range(k):
+        z = cube[warmup + j]
+        w = alpha * (1 - alpha) ** (k - 1 - j)
+        mu = mu + w * z.mean(axis=0)
+        kk = kk + w * np.cov(z.T, ddof=1)
+    return max(worst, rel(det.mu, mu), rel(det.k, kk))
+
+
 ALL_CHECKS = {
     "exact_golden": (check_exact_golden, 1e-11),
     "hand_1d": (check_hand_1d, 1e-14),
@@ -245,4 +272,5 @@ ALL_CHECKS = {
     "srp_projection": (check_srp_projection, 1e-9),
     "imc_pooled": (check_imc_pooled, 1e-9),
     "imc_pooled_stu": (lambda: check_imc_pooled("score_then_update"), 1e-9),
+    "pooled_warmup": (check_pooled_warmup, 1e-11),
 }

@@ -109,3 +109,19 @@ def test_order_swap_is_caught(monkeypatch):
     monkeypatch.setattr(eo.ERXOracle, "__init__", swapped)
     errs = {k: fn() for k, (fn, tol) in oc.ALL_CHECKS.items()}
     assert any(errs[k] > oc.ALL_CHECKS[k][1] for k in errs)
+
+
+def test_pooled_boundary_off_by_one_is_caught(monkeypatch):
+    # the pooled reading switching to the EMAs one line late
+    def late(self, mu_hat, k_hat):
+        if self.t == 0:
+            self.mu, self.k = mu_hat.copy(), k_hat.copy()
+        elif self.averaging == "imc" or (self.averaging == "pooled" and self.t <= self.warmup):
+            self.mu, self.k = eo.imc_update(self.mu, self.k, self.t * self.width, mu_hat, k_hat,
+                                            self.width)
+        else:
+            self.mu, self.k = eo.ema_update(self.mu, self.k, mu_hat, k_hat, self.alpha)
+
+    monkeypatch.setattr(eo.ERXOracle, "_update", late)
+    errs = {k: fn() for k, (fn, tol) in oc.ALL_CHECKS.items()}
+    assert any(errs[k] > oc.ALL_CHECKS[k][1] for k in errs)
