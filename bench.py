@@ -397,6 +397,53 @@ def paced_latency(det, x, out, stream, n, period_s, offset=200):
             "mode": f"one line per push, a line every {period_s * 1e3:g} ms"}
 
 
+def bench_paper_speed(dev, stream, n_lines=3000, reps=2):
+    """The paper's speed experiments (Sec. IV-C) on this GPU, ERX as the paper
+    runs it (SRP d = 5, alpha 0.1, 99-line warm-up; FP64 form): uniform random
+    cubes of 3000 lines, bands 10..200 at 500 px and pixels 100..1500 at 50
+    bands; the SRP dimension sweep of the ablation (d = 1..50 and no SRP) and
+    the three datasets' shapes (random data of the same size), with the
+    paper's Jetson Xavier NX lines/s beside them (context only)."""
+    import torch
+
+    from paper_2408_14947_gb300 import Detector
+    g = torch.Generator(device=dev)
+    g.manual_seed(2408)
+
+    def lps(width, bands, lines, **kw):
+        x = torch.rand((lines, width, bands), generator=g, device=dev, dtype=torch.float32)
+        det = Detector(bands, width, in_dtype="f32", stream=stream, form="fp64", momentum=0.1,
+                       warmup=99, **kw)
+        det.push(x)
+        det.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            det.reset()
+            det.push(x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        det.sync()
+        det.close()
+        return lines * reps / (e0.elapsed_time(e1) / 1000.0)
+
+    srp5 = {"proj": "srp", "proj_dim": 5}
+    out = {"form": "fp64", "config": "SRP d = 5, alpha 0.1, warm-up 99 lines, uniform f32"}
+    out["bands_sweep_500px"] = {b: lps(500, b, n_lines, **srp5) for b in range(10, 201, 10)}
+    out["pixels_sweep_50b"] = {p: lps(p, 50, n_lines, **srp5) for p in range(100, 1501, 100)}
+    paper_d = {1: 610, 3: 580, 5: 566, 10: 525, 20: 446, 30: 379, 50: 287, "none": 243}
+    dsw = {}
+    for d in (1, 3, 5, 10, 20, 30, 50, "none"):
+        kw = {} if d == "none" else {"proj": "srp", "proj_dim": d}
+        dsw[d] = {"lines_per_s": lps(600, 90, 2400, **kw), "paper_jetson": paper_d[d]}
+    out["d_sweep_600px_90b"] = dsw
+    shapes = {"beach_452x108": (452, 108, 3072, 561), "synthetic_600x90": (600, 90, 2400, 508),
+              "snp_1116x13": (1116, 13, 2499, 561)}
+    out["dataset_shapes"] = {k: {"lines_per_s": lps(w, b, n, **srp5), "paper_jetson": pj}
+                             for k, (w, b, n, pj) in shapes.items()}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -558,6 +605,9 @@ def run_ours(args):
         result["forms_224"] = {"workload": f"{n224} lines x 1024 px x 224 bands f32, "
                                            "Gaussian background, kappa 1e3", **forms224}
         del x224
+
+        # the paper's speed experiments and SRP dimension sweep at its shapes
+        result["paper_speed_tests"] = bench_paper_speed(dev, stream)
 
         # batched form: 256 streams, widths U{128..2048}, bands from {8,16,64,108,224}
         result["batched"] = bench_batched(dev, stream)

@@ -59,8 +59,11 @@ enum { ERX_UPDATE_THEN_SCORE = 0, ERX_SCORE_THEN_UPDATE = 1 };
 /* background averaging: ERX_AVG_EMA, the exponentially moving averages of
  * Sec. III-C (momentum alpha); ERX_AVG_IMC, the equal-weight ablation of
  * Sec. IV-C, a batch version of Welford's update: the state is the mean and the
- * 1/(n-1) covariance of all n pixels seen (momentum unused) */
-enum { ERX_AVG_EMA = 0, ERX_AVG_IMC = 1 };
+ * 1/(n-1) covariance of all n pixels seen (momentum unused); ERX_AVG_POOLED,
+ * the other reading of the warm-up buffer of Sec. IV-B: the warmup_lines first
+ * lines are pooled with equal weight (as IMC) into the estimate the EMAs start
+ * from, the EMAs of Sec. III-C afterwards */
+enum { ERX_AVG_EMA = 0, ERX_AVG_IMC = 1, ERX_AVG_POOLED = 2 };
 /* input sample type, lines laid out [pixel][band] (band-interleaved-by-pixel) */
 enum { ERX_U16 = 0, ERX_F32 = 1, ERX_F64 = 2 };
 /* flags: ERX_FLAG_SIMT_STATS keeps S2 off the tensor cores: exact integer
@@ -109,8 +112,9 @@ typedef struct {
   int32_t block_lines;  /* lines processed per internal block; 0 = automatic */
   int32_t flags;        /* ERX_FLAG_* bits */
   const double* srp_weights; /* optional b x d row-major host matrix replacing the drawn SRP */
-  int32_t averaging;    /* ERX_AVG_EMA (paper) or ERX_AVG_IMC; the batch and the
-                         * no-allocation entry point take ERX_AVG_EMA only */
+  int32_t averaging;    /* ERX_AVG_EMA (paper), ERX_AVG_IMC or ERX_AVG_POOLED; the
+                         * batch and the no-allocation entry point take
+                         * ERX_AVG_EMA only */
 } erx_config;
 
 /* Fill *cfg with the paper's defaults for a b-band, p-pixel line:

@@ -203,7 +203,9 @@ erx_status validate(const erx_config* cfg) {
     return ERX_EINVAL;
   if (cfg->order != ERX_UPDATE_THEN_SCORE && cfg->order != ERX_SCORE_THEN_UPDATE)
     return ERX_EINVAL;
-  if (cfg->averaging != ERX_AVG_EMA && cfg->averaging != ERX_AVG_IMC) return ERX_EINVAL;
+  if (cfg->averaging != ERX_AVG_EMA && cfg->averaging != ERX_AVG_IMC &&
+      cfg->averaging != ERX_AVG_POOLED)
+    return ERX_EINVAL;
   if ((cfg->flags & ERX_FLAG_PIPELINE) &&
       (cfg->order != ERX_SCORE_THEN_UPDATE || cfg->proj == ERX_PROJ_LEARNED))
     return ERX_EINVAL;
@@ -330,19 +332,31 @@ void enqueue_stats(erx_ctx* c, const void* x, int64_t stride_elems, const void* 
   }
 }
 
-// S3 over T lines: per-line statistics to score with (mu_t, K_t) and the state advanced
+// S3 over T lines: per-line statistics to score with (mu_t, K_t) and the state
+// advanced.  EMA; IMC; or pooled: IMC over the warm-up lines, EMA afterwards (a
+// block that straddles the end of the warm-up is scanned in two parts).
 void enqueue_update(erx_ctx* c, int T, cudaStream_t st) {
   const int W = c->W, d = c->d;
-  if (c->cfg.averaging == ERX_AVG_IMC) {
+  const int64_t P = packed_size(d);
+  int k = 0;   // leading lines of the block averaged with equal weight
+  if (c->cfg.averaging == ERX_AVG_IMC)
+    k = T;
+  else if (c->cfg.averaging == ERX_AVG_POOLED && c->t < c->cfg.warmup_lines)
+    k = (int)std::min<int64_t>(T, c->cfg.warmup_lines - c->t);
+  if (k > 0) {
     KernelScope ks(c, ERX_K_EMA, st);
-    launch_imc_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W, c->t,
+    launch_imc_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, k, d, W, c->t,
                     c->cfg.order, c->mu_state, c->K_state, c->mu_t, c->K_t, c->imc_mprev,
                     c->ema_scratch, st);
-  } else {
+  }
+  if (k < T) {
+    const int64_t dd = (int64_t)d * d;
     KernelScope ks(c, ERX_K_EMA, st);
-    launch_ema_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, T, d, W,
-                    c->cfg.momentum, c->t, c->cfg.order, c->mu_state, c->K_state, c->mu_t,
-                    c->K_t, c->ema_scratch, st);
+    launch_ema_scan(c->int_stats, c->S1i ? c->S1i + k * d : nullptr,
+                    c->S2i ? c->S2i + k * dd : nullptr, c->mu_hat ? c->mu_hat + k * d : nullptr,
+                    c->shift ? c->shift + k * d : nullptr, c->S2f ? c->S2f + k * dd : nullptr,
+                    T - k, d, W, c->cfg.momentum, c->t + k, c->cfg.order, c->mu_state,
+                    c->K_state, c->mu_t + k * d, c->K_t + k * P, c->ema_scratch, st);
   }
 }
 
@@ -636,7 +650,7 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   }
   ERX_A(err, kErrSlots);
   if (ema_scratch_doubles(d, T) > 0) ERX_A(ema_scratch, ema_scratch_doubles(d, T));
-  if (cfg->averaging == ERX_AVG_IMC) ERX_A(imc_mprev, imc_work_doubles(d, T));
+  if (cfg->averaging != ERX_AVG_EMA) ERX_A(imc_mprev, imc_work_doubles(d, T));
   c->pipeline = (cfg->flags & ERX_FLAG_PIPELINE) != 0;
   if (c->pipeline) {
     ERX_A(mu_pre, d);

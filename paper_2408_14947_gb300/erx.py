@@ -18,7 +18,7 @@ ERX_OK, ERX_EINVAL, ERX_ENOMEM, ERX_ECUDA, ERX_ENOTPD, ERX_ERANGE, ERX_ESTATE, \
 ERX_PROJ_NONE, ERX_PROJ_SRP, ERX_PROJ_LEARNED = 0, 1, 2
 ERX_UPDATE_THEN_SCORE, ERX_SCORE_THEN_UPDATE = 0, 1
 ERX_FLAG_SIMT_STATS, ERX_FLAG_PIPELINE = 1, 2
-ERX_AVG_EMA, ERX_AVG_IMC = 0, 1
+ERX_AVG_EMA, ERX_AVG_IMC, ERX_AVG_POOLED = 0, 1, 2
 ERX_U16, ERX_F32, ERX_F64 = 0, 1, 2
 ERX_FORM_FP64, ERX_FORM_FP32, ERX_FORM_TF32, ERX_FORM_BF16, ERX_FORM_TF32X3 = 0, 1, 2, 3, 4
 FORMS = {"fp64": ERX_FORM_FP64, "fp32": ERX_FORM_FP32, "tf32": ERX_FORM_TF32,
@@ -268,7 +268,8 @@ class Detector:
         cfg.block_lines = block_lines
         cfg.flags = (ERX_FLAG_SIMT_STATS if simt_stats else 0) | \
             (ERX_FLAG_PIPELINE if pipeline else 0)
-        cfg.averaging = {"ema": ERX_AVG_EMA, "imc": ERX_AVG_IMC}[averaging]
+        cfg.averaging = {"ema": ERX_AVG_EMA, "imc": ERX_AVG_IMC,
+                         "pooled": ERX_AVG_POOLED}[averaging]
         self._w = None
         if srp_weights is not None:
             import numpy as np

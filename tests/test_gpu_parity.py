@@ -372,3 +372,19 @@ def test_pipeline_flag_needs_score_then_update():
     from paper_2408_14947_gb300 import Detector, ErxError
     with pytest.raises(ErxError):
         Detector(8, 16, order="update_then_score", pipeline=True)
+
+
+@pytest.mark.parametrize("order", ["update_then_score", "score_then_update"])
+def test_pooled_warmup_matches_oracle(order):
+    """Pooled reading of the warm-up buffer: IMC over the 40 warm-up lines, the
+    EMAs afterwards; the second push straddles the switch (its 20 lines are
+    scanned in two parts), the first spans two 32-line chunks."""
+    cube = synth.gen_lines(synth.reflectance_c1(width=80, bands=20, seed=8), 0, 80)
+    kw = {"averaging": "pooled", "order": order}
+    ref = oracle.run_cube(cube, warmup=40, threshold=3.0, momentum=0.2, **kw)
+    got, det = run_gpu(cube, warmup=40, threshold=3.0, momentum=0.2, push_sizes=[33, 20, 1, 26],
+                       **kw)
+    _compare(got, ref, 1e-9)
+    _, mu, k = det.state()
+    _, mu_o, k_o = ref["state"]
+    assert rel_err(mu, mu_o) < 1e-10 and rel_err(k, k_o) < 1e-10
