@@ -391,6 +391,32 @@ erx_status erx_destroy(erx_ctx* ctx);
 /* Static string naming a status code. */
 const char* erx_status_str(erx_status s);
 
+
+/* ---- Detection quality (Sec. IV-B), a tooling call outside the per-line step ----
+ * Scores a detection map (n scores, device, float or double) against anomaly
+ * labels (n bytes, device, nonzero = anomaly):
+ *   auc          area under the ROC curve (TPR against FPR over all thresholds),
+ *                of the map min-max normalised in FP64, v = (s - min) / (max - min),
+ *                and quantised to `bins` levels, q = min(floor(v * bins), bins - 1):
+ *                the Mann-Whitney statistic, ties within a level counting one half
+ *                (|auc - exact| <= 1 / bins for a continuous map);
+ *   auc_tpr_tau  area under TPR against the threshold tau in [0, 1] of the
+ *                normalised map (= the anomalies' mean normalised score);
+ *   auc_fpr_tau  the same for FPR (= the background's mean normalised score);
+ *   auc_td = (auc + auc_tpr_tau) / 2,  auc_bs = (auc - auc_fpr_tau + 1) / 2;
+ *   u2           2U, the exact integer statistic behind auc.
+ * A non-finite score counts in level 0 (the sums then carry it).
+ * Synchronous on cuda_stream; allocates its scratch (cudaMalloc) per call.
+ * ERX_EINVAL if n <= 0, bins outside [2, 2^24], score_dtype not ERX_F32 / ERX_F64,
+ * or the labels hold no anomaly or no background pixel. */
+typedef struct {
+  double auc, auc_tpr_tau, auc_fpr_tau, auc_td, auc_bs;
+  int64_t positives, negatives;
+  uint64_t u2;
+} erx_roc;
+erx_status erx_roc_metrics(const void* scores_dev, int32_t score_dtype, const uint8_t* labels_dev,
+                           int64_t n, int32_t bins, void* cuda_stream, erx_roc* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -38,6 +38,12 @@ class ErxConfig(C.Structure):
     ]
 
 
+class ErxRoc(C.Structure):
+    _fields_ = [("auc", C.c_double), ("auc_tpr_tau", C.c_double), ("auc_fpr_tau", C.c_double),
+                ("auc_td", C.c_double), ("auc_bs", C.c_double), ("positives", C.c_int64),
+                ("negatives", C.c_int64), ("u2", C.c_uint64)]
+
+
 class ErxTrainOpts(C.Structure):
     _fields_ = [("momentum", C.c_double), ("ridge", C.c_double), ("lr", C.c_float),
                 ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
@@ -82,6 +88,7 @@ def load_library() -> C.CDLL:
         "erx_profile_read": (C.c_int, [P, I32, I32, C.POINTER(D), C.POINTER(I64),
                                        C.POINTER(I64)]),
         "erx_kernel_name": (C.c_char_p, [I32]),
+        "erx_roc_metrics": (C.c_int, [P, I32, P, I64, I32, P, C.POINTER(ErxRoc)]),
         "erx_train_opts_default": (None, [C.POINTER(ErxTrainOpts)]),
         "erx_encoder_create": (C.c_int, [I32, I32, I32, U64, P, C.POINTER(P)]),
         "erx_encoder_set_norm": (C.c_int, [P, P, P]),
@@ -212,6 +219,23 @@ def erx_push_lines_static(cfg, stream, mu_ptr, k_ptr, t, lines_ptr, n_lines, str
                                                 delta_ptr, dn_ptr or None, mask_ptr or None,
                                                 det_ptr or None), "erx_push_lines_static")
     return tt.value
+
+
+def roc_metrics(scores, labels, bins: int = 1 << 16, stream=None) -> dict:
+    """Detection quality of a score map (Sec. IV-B) on the GPU: ROC AUC of the
+    map quantised to `bins` levels, AUC_TPR,tau, AUC_FPR,tau, AUC_TD, AUC_BS.
+    scores: CUDA float32/float64 tensor; labels: CUDA bool/uint8 tensor (same
+    number of elements, nonzero = anomaly)."""
+    import torch
+    s = scores.contiguous()
+    y = labels.contiguous().to(torch.uint8)
+    assert s.is_cuda and y.is_cuda and s.numel() == y.numel()
+    dt = {torch.float32: ERX_F32, torch.float64: ERX_F64}[s.dtype]
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = ErxRoc()
+    _check(load_library().erx_roc_metrics(s.data_ptr(), dt, y.data_ptr(), s.numel(), bins,
+                                          st.cuda_stream, C.byref(out)), "erx_roc_metrics")
+    return {k: getattr(out, k) for k, _ in ErxRoc._fields_}
 
 
 def erx_kernel_name(k: int) -> str:
