@@ -226,7 +226,7 @@ def time_form(make, x, kw, dev, stream, reps: int = 2):
     import torch
     n, p, _ = x.shape
     det = make(**kw)
-    sdt = torch.float64 if kw.get("form", "fp64") == "fp64" else torch.float32
+    sdt = torch.float64 if kw.get("form", "fp64") in ("fp64", "fp64e") else torch.float32
     out = (torch.empty((n, p), dtype=sdt, device=dev), torch.empty((n, p), dtype=sdt, device=dev),
            torch.empty((n, p), dtype=torch.uint8, device=dev),
            torch.empty((n,), dtype=torch.uint8, device=dev))
@@ -616,7 +616,8 @@ def run_ours(args):
 
         # other forms on the same cube, same step definition
         forms = {}
-        for name, kw in (("fp32", {"form": "fp32"}), ("tf32", {"form": "tf32"}),
+        for name, kw in (("fp64e", {"form": "fp64e"}), ("fp32", {"form": "fp32"}),
+                         ("tf32", {"form": "tf32"}),
                          ("bf16", {"form": "bf16"}), ("tf32x3", {"form": "tf32x3"}),
                          ("fp64_imc", {"form": "fp64", "averaging": "imc"}),
                          ("fp64_srp5", {"form": "fp64", "proj": "srp", "proj_dim": 5}),
@@ -632,7 +633,7 @@ def run_ours(args):
         x224 = torch.from_numpy(cube224).to(dev)
         del cube224
         forms224 = {}
-        for name in ("fp64", "fp32", "tf32", "bf16", "tf32x3"):
+        for name in ("fp64", "fp64e", "fp32", "tf32", "bf16", "tf32x3"):
             forms224[name] = time_form(lambda **k: Detector(224, 1024, in_dtype="f32",
                                                             stream=stream, **k),
                                        x224, {"form": name}, dev, stream)
@@ -733,7 +734,7 @@ def main():
     ap.add_argument("--lines", type=int, default=LINES,
                     help="lines of the workload cube (smaller cubes for profiler captures)")
     ap.add_argument("--profile-case", default=None,
-                    choices=["c2_fp64", "c2_fp32", "c2_tf32", "c2_bf16", "c2_fp64_imc", "c3_fp64",
+                    choices=["c2_fp64", "c2_fp64e", "c2_fp32", "c2_tf32", "c2_bf16", "c2_fp64_imc", "c3_fp64",
                              "c3_fp32", "c3_tf32", "c3_bf16", "c3_tf32x3"],
                     help="push one block of --lines lines of a workload (c2: 640 px x 108 "
                          "bands u16; c3: 1024 px x 224 bands f32, kappa 1e3) through one "

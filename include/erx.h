@@ -86,13 +86,18 @@ enum { ERX_FLAG_SIMT_STATS = 1, ERX_FLAG_PIPELINE = 2 };
  * hi hi' + hi lo' + lo hi' in FP32 (near-FP32 products at three MMAs each).
  * In the tensor-core forms, S2 of floating-point lines runs on the tensor
  * cores too (unless ERX_FLAG_SIMT_STATS is set, or the lines are not 16-byte
- * aligned with p * d a multiple of 4: then FP32 SIMT). */
+ * aligned with p * d a multiple of 4: then FP32 SIMT).  FP64E: as FP64
+ * (statistics, state, factor and delta in FP64), but S5 in double-float
+ * arithmetic on the FP32 pipe (each value a sum of two floats, about 48
+ * significant bits, error-free sums and products), held to the FP64 form's
+ * error bar; u16 or f32 lines without projection (ERX_EUNSUPPORTED otherwise). */
 enum {
   ERX_FORM_FP64 = 0,
   ERX_FORM_FP32 = 1,
   ERX_FORM_TF32 = 2,
   ERX_FORM_BF16 = 3,
-  ERX_FORM_TF32X3 = 4
+  ERX_FORM_TF32X3 = 4,
+  ERX_FORM_FP64E = 5
 };
 
 typedef struct {
@@ -135,7 +140,8 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out);
  * each p x b samples of in_dtype, row-major [pixel][band]; line_stride_bytes
  * = 0 means p*b*sizeof(sample).  Outputs (device, caller-owned, row-major
  * [line][pixel]):
- *   delta_dev       delta (Sec. III-D); double for ERX_FORM_FP64, float for the other forms
+ *   delta_dev       delta (Sec. III-D); double for ERX_FORM_FP64 and ERX_FORM_FP64E, float
+ *                   for the other forms
  *   delta_norm_dev  delta_N (Sec. III-E), same type as delta; may be NULL
  *   mask_dev        uint8 delta_N >= threshold; may be NULL
  *   detecting_dev   uint8 per line, 1 once the warm-up lines have passed; may be NULL
@@ -368,7 +374,8 @@ enum {
   ERX_K_ENCODE = 11,    /* S1 learned band encoder (codes) */
   ERX_K_TRINV = 12,     /* S4 full inverse of the factor in FP32 (non-FP64 forms) */
   ERX_K_SYRK_TC = 13,   /* S2 centred scatter of floating lines on the tensor cores */
-  ERX_K_COUNT = 14
+  ERX_K_SOLVE_DF = 14,  /* S5 scores in double-float (FP64E form) */
+  ERX_K_COUNT = 15
 };
 
 /* Per-kernel timing.  While enabled (on != 0), every kernel the context

@@ -49,6 +49,8 @@ struct erx_ctx {
   unsigned long long* err = nullptr;
   double* ema_scratch = nullptr;
   double* imc_mprev = nullptr;   // IMC: per-line deltas, constants and chunk sums of a block
+  float2* L2 = nullptr;          // FP64E: the blocked factor and mu_t as hi/lo floats
+  float2* mu2 = nullptr;
   // ERX_FLAG_PIPELINE: the factor of the current state, made ahead for the next
   // single-line push, and the second stream that defers each line's update
   bool pipeline = false;
@@ -211,7 +213,10 @@ erx_status validate(const erx_config* cfg) {
     return ERX_EINVAL;
   if (cfg->in_dtype < ERX_U16 || cfg->in_dtype > ERX_F64) return ERX_EINVAL;
   if (cfg->in_dtype == ERX_U16 && (cfg->in_bits < 1 || cfg->in_bits > 16)) return ERX_EINVAL;
-  if (cfg->form < ERX_FORM_FP64 || cfg->form > ERX_FORM_TF32X3) return ERX_EINVAL;
+  if (cfg->form < ERX_FORM_FP64 || cfg->form > ERX_FORM_FP64E) return ERX_EINVAL;
+  if (cfg->form == ERX_FORM_FP64E &&
+      (cfg->proj != ERX_PROJ_NONE || (cfg->in_dtype != ERX_U16 && cfg->in_dtype != ERX_F32)))
+    return ERX_EUNSUPPORTED;
   if (cfg->block_lines < 0 || cfg->warmup_lines < 0) return ERX_EINVAL;
   const int d = cfg->proj != ERX_PROJ_NONE ? cfg->proj_dim : cfg->bands;
   if (d > kMaxDim || cfg->width > (1 << 20) || cfg->bands > 65536) return ERX_EUNSUPPORTED;
@@ -365,7 +370,11 @@ void enqueue_score(erx_ctx* c, const void* zsrc, int ztype, int64_t zstride, int
                    const double* mu, const double* Lf, const float* Lf32, void* delta, void* dn,
                    uint8_t* mask, uint8_t* det, cudaStream_t st) {
   const int W = c->W, d = c->d;
-  if (c->fp64) {
+  if (c->cfg.form == ERX_FORM_FP64E) {
+    KernelScope ks(c, ERX_K_SOLVE_DF, st);
+    launch_solve_df(ztype, zsrc, zstride, ps, W, d, T, mu, Lf, c->mu2, c->L2, (double*)delta,
+                    st);
+  } else if (c->fp64) {
     KernelScope ks(c, ERX_K_SOLVE_FP64, st);
     launch_solve_fp64(ztype, zsrc, zstride, ps, W, d, T, mu, Lf, (double*)delta, st);
   } else if (tc_format(c->cfg.form) > 0) {
@@ -588,7 +597,7 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   c->W = cfg->width;
   c->d = cfg->proj != ERX_PROJ_NONE ? cfg->proj_dim : cfg->bands;
   c->stream = (cudaStream_t)cuda_stream;
-  c->fp64 = cfg->form == ERX_FORM_FP64;
+  c->fp64 = cfg->form == ERX_FORM_FP64 || cfg->form == ERX_FORM_FP64E;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -626,7 +635,7 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   c->T = T;
   if (configure_factor_kernels() != cudaSuccess || configure_solve_kernels() != cudaSuccess ||
       configure_stats_tc_kernel() != cudaSuccess || configure_solve_tc_kernels() != cudaSuccess ||
-      configure_syrk_tc_kernels() != cudaSuccess) {
+      configure_syrk_tc_kernels() != cudaSuccess || configure_solve_df_kernels() != cudaSuccess) {
     cudaGetLastError();
     delete c;
     return ERX_ECUDA;
@@ -651,6 +660,10 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
   ERX_A(err, kErrSlots);
   if (ema_scratch_doubles(d, T) > 0) ERX_A(ema_scratch, ema_scratch_doubles(d, T));
   if (cfg->averaging != ERX_AVG_EMA) ERX_A(imc_mprev, imc_work_doubles(d, T));
+  if (cfg->form == ERX_FORM_FP64E) {
+    ERX_A(L2, (size_t)T * P);
+    ERX_A(mu2, (size_t)T * d);
+  }
   c->pipeline = (cfg->flags & ERX_FLAG_PIPELINE) != 0;
   if (c->pipeline) {
     ERX_A(mu_pre, d);
@@ -999,7 +1012,7 @@ const char* erx_kernel_name(int32_t k) {
                                            "stats_fp",   "ema_scan",   "chol",
                                            "solve_fp64", "solve_fp32", "normalise",
                                            "stats_tc",   "solve_tc",   "encode",
-                                           "trinv32",    "syrk_tc"};
+                                           "trinv32",    "syrk_tc",    "solve_df"};
   return (k >= 0 && k < ERX_K_COUNT) ? names[k] : nullptr;
 }
 

@@ -107,6 +107,12 @@ void launch_solve_fp32(int in_type, const void* x, int64_t line_stride, int ps, 
 
 // delta_i on the tensor cores: fmt 2 = TF32, 1 = BF16 operands, FP32 accumulation.
 cudaError_t configure_solve_tc_kernels();
+// S5 in double-float (FP64E form): splits the blocked factor and mu_t into
+// hi/lo floats (L2: T x P, mu2: T x d), then scores; in_type 0 (u16) or 1 (f32)
+cudaError_t configure_solve_df_kernels();
+void launch_solve_df(int in_type, const void* x, int64_t line_stride, int ps, int W, int d, int T,
+                     const double* mu_t, const double* Lf, float2* mu2, float2* L2,
+                     double* delta, cudaStream_t st);
 // S2 centred scatter of float lines on the tensor cores (fmt 1 BF16, 2 TF32)
 bool syrk_tc_supported(const void* x, int64_t line_stride, int ps, int W, int d);
 cudaError_t configure_syrk_tc_kernels();

@@ -20,9 +20,10 @@ ERX_UPDATE_THEN_SCORE, ERX_SCORE_THEN_UPDATE = 0, 1
 ERX_FLAG_SIMT_STATS, ERX_FLAG_PIPELINE = 1, 2
 ERX_AVG_EMA, ERX_AVG_IMC, ERX_AVG_POOLED = 0, 1, 2
 ERX_U16, ERX_F32, ERX_F64 = 0, 1, 2
-ERX_FORM_FP64, ERX_FORM_FP32, ERX_FORM_TF32, ERX_FORM_BF16, ERX_FORM_TF32X3 = 0, 1, 2, 3, 4
+ERX_FORM_FP64, ERX_FORM_FP32, ERX_FORM_TF32, ERX_FORM_BF16, ERX_FORM_TF32X3, ERX_FORM_FP64E = \
+    0, 1, 2, 3, 4, 5
 FORMS = {"fp64": ERX_FORM_FP64, "fp32": ERX_FORM_FP32, "tf32": ERX_FORM_TF32,
-         "bf16": ERX_FORM_BF16, "tf32x3": ERX_FORM_TF32X3}
+         "bf16": ERX_FORM_BF16, "tf32x3": ERX_FORM_TF32X3, "fp64e": ERX_FORM_FP64E}
 
 _SAMPLE_BYTES = {ERX_U16: 2, ERX_F32: 4, ERX_F64: 8}
 
@@ -207,7 +208,7 @@ def erx_srp_weights(bands: int, dim: int, seed: int):
     return w
 
 
-ERX_K_COUNT = 14
+ERX_K_COUNT = 15
 
 
 def erx_push_lines_static(cfg, stream, mu_ptr, k_ptr, t, lines_ptr, n_lines, stride_bytes,
@@ -304,7 +305,7 @@ class Detector:
         self.cfg = cfg
         self.bands, self.width = bands, width
         self.in_dtype = cfg.in_dtype
-        self.score_dtype = torch.float64 if form == "fp64" else torch.float32
+        self.score_dtype = torch.float64 if form in ("fp64", "fp64e") else torch.float32
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = erx_create(cfg, self.stream.cuda_stream)
         self.dim = erx_dim(self.ctx)
@@ -465,7 +466,7 @@ class Batch:
         torch = self.torch
         line, dl, dn, mk, dt = self.buffers(i)
         w, bands = self.streams[i]["width"], self.streams[i]["bands"]
-        st = "<f8" if self.form == "fp64" else "<f4"
+        st = "<f8" if self.form in ("fp64", "fp64e") else "<f4"
         return (_device_view(line, (w, bands), "<f4"), _device_view(dl, (w,), st),
                 _device_view(dn, (w,), st), _device_view(mk, (w,), "|u1"),
                 _device_view(dt, (1,), "|u1"))

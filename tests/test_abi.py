@@ -49,7 +49,7 @@ def test_config_defaults(lib):
 
 @pytest.mark.parametrize("field,value", [("width", 1), ("bands", 0), ("momentum", 0.0),
                                          ("momentum", 1.5), ("ridge", -1.0), ("order", 7),
-                                         ("in_dtype", 9), ("form", 5), ("proj", 4)])
+                                         ("in_dtype", 9), ("form", 99), ("proj", 4)])
 def test_invalid_config_rejected_before_any_cuda_call(lib, field, value):
     c = erx.erx_config_default(8, 16)
     setattr(c, field, value)

@@ -15,7 +15,7 @@ from tests.gpu_util import dn_err, need_gpu, rel_err, run_gpu, to_dev, torch
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-9, "fp32": 1e-4, "tf32": 5e-3, "bf16": 4e-2, "tf32x3": 1e-4}
+TOL = {"fp64": 1e-9, "fp64e": 1e-9, "fp32": 1e-4, "tf32": 5e-3, "bf16": 4e-2, "tf32x3": 1e-4}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -388,3 +388,45 @@ def test_pooled_warmup_matches_oracle(order):
     _, mu, k = det.state()
     _, mu_o, k_o = ref["state"]
     assert rel_err(mu, mu_o) < 1e-10 and rel_err(k, k_o) < 1e-10
+
+
+
+FP64E_CASES = [
+    ("c2_u16_108", lambda: synth.gen_lines(synth.dn_c2(width=200, bands=108), 0, 24),
+     {"in_bits": 12}),
+    ("c1_f32_ragged", lambda: synth.gen_lines(synth.reflectance_c1(width=77, bands=41), 0, 12), {}),
+    ("c3_k1e4_d224", lambda: synth.gen_lines(synth.cov_c3(1e4, width=100, bands=224), 0, 3), {}),
+    ("tiny_w2_b1", lambda: synth.gen_lines(synth.reflectance_c1(width=2, bands=1), 0, 7), {}),
+    ("stu_order", lambda: synth.gen_lines(synth.reflectance_c1(width=65, bands=12), 0, 11),
+     {"order": "score_then_update"}),
+]
+
+
+@pytest.mark.parametrize("name,make,kw", FP64E_CASES, ids=[c[0] for c in FP64E_CASES])
+def test_fp64e_matches_oracle(name, make, kw):
+    """FP64E: FP64 statistics, state and factor, the score in double-float on
+    the FP32 pipe, held to the FP64 bar; blocks and single lines."""
+    cube = make()
+    ref = oracle.run_cube(cube, warmup=3, **_oracle_kw(kw, cube))
+    for sizes in (None, [1] * cube.shape[0]):
+        got, det = run_gpu(cube, form="fp64e", warmup=3, threshold=3.0, push_sizes=sizes, **kw)
+        _compare(got, ref, TOL["fp64e"])
+        assert det.profile_read()["solve_df"][2] > 0
+
+
+def test_fp64e_pipelined():
+    cube = synth.gen_lines(synth.dn_c2(width=96, bands=40, seed=4), 0, 20)
+    kw = dict(form="fp64e", warmup=2, threshold=3.0, order="score_then_update", in_bits=12,
+              push_sizes=[1] * 20)
+    a, _ = run_gpu(cube, **kw)
+    b, _ = run_gpu(cube, pipeline=True, **kw)
+    assert np.array_equal(a["delta"], b["delta"])
+    _compare(b, oracle.run_cube(cube, warmup=2, threshold=3.0, order="score_then_update"), 1e-9)
+
+
+def test_fp64e_rejects_projection_and_f64():
+    from paper_2408_14947_gb300 import Detector, ErxError
+    with pytest.raises(ErxError):
+        Detector(16, 32, form="fp64e", proj="srp", proj_dim=4)
+    with pytest.raises(ErxError):
+        Detector(16, 32, form="fp64e", in_dtype="f64")
