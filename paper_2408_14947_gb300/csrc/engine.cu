@@ -51,6 +51,16 @@ struct erx_ctx {
   double* imc_mprev = nullptr;   // IMC: per-line deltas, constants and chunk sums of a block
   float2* L2 = nullptr;          // FP64E: the blocked factor and mu_t as hi/lo floats
   float2* mu2 = nullptr;
+  // pushes of several blocks: block b+1's statistics, update and factor (stream A,
+  // the context's stream) overlap block b's score (stream B); the buffers that
+  // pass from A to B have one copy per slot (b & 1)
+  bool overlap = false;
+  cudaStream_t sB = nullptr;
+  cudaEvent_t ev_fac[2] = {}, ev_fin[2] = {}, ev_join = nullptr;
+  double* mu_t_s[2] = {};
+  double* Linv_s[2] = {};
+  float* Linv32_s[2] = {};
+  void* Z_s[2] = {};
   // ERX_FLAG_PIPELINE: the factor of the current state, made ahead for the next
   // single-line push, and the second stream that defers each line's update
   bool pipeline = false;
@@ -116,8 +126,10 @@ void free_all(erx_ctx* c) {
   }
   if (c->h_out) cudaFreeHost(c->h_out);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
-  for (cudaEvent_t* e : {&c->ev_start, &c->ev_stats, &c->ev_scored, &c->ev_ready})
+  for (cudaEvent_t* e : {&c->ev_start, &c->ev_stats, &c->ev_scored, &c->ev_ready, &c->ev_fac[0],
+                        &c->ev_fac[1], &c->ev_fin[0], &c->ev_fin[1], &c->ev_join})
     if (*e) cudaEventDestroy(*e), *e = nullptr;
+  if (c->sB) cudaStreamDestroy(c->sB), c->sB = nullptr;
   if (c->side) cudaStreamDestroy(c->side), c->side = nullptr;
   if (c->audit) erx_destroy(c->audit), c->audit = nullptr;
   for (auto& p : c->pending) cudaEventDestroy(p.a), cudaEventDestroy(p.b);
@@ -240,8 +252,17 @@ void enqueue_score(erx_ctx* c, const void* zsrc, int ztype, int64_t zstride, int
                    uint8_t* mask, uint8_t* det, cudaStream_t st);
 
 erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems, void* delta,
-                     void* dn, uint8_t* mask, uint8_t* det) {
+                     void* dn, uint8_t* mask, uint8_t* det, int slot = -1) {
   const int T = (int)n, W = c->W, d = c->d, B = c->B;
+  if (slot >= 0) {
+    // this block's copies of the buffers stream B reads; wait until B is done
+    // with them (block b-2)
+    c->mu_t = c->mu_t_s[slot];
+    c->Linv = c->Linv_s[slot];
+    c->Linv32 = c->Linv32_s[slot];
+    c->Z = c->Z_s[slot];
+    cudaStreamWaitEvent(c->stream, c->ev_fin[slot], 0);
+  }
   const bool learned = c->cfg.proj == ERX_PROJ_LEARNED;
   if (learned && !c->enc) return ERX_ESTATE;
   if (learned && c->fallback) {
@@ -287,12 +308,19 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
     launch_chol_inv(c->K_t, d, T, c->cfg.ridge, c->Linv, c->fp64 ? nullptr : c->Linv32, c->err,
                     c->t, st);
   }
+  cudaStream_t sb = st;
+  if (slot >= 0) {
+    cudaEventRecord(c->ev_fac[slot], st);
+    sb = c->sB;
+    cudaStreamWaitEvent(sb, c->ev_fac[slot], 0);
+  }
   if (!c->fp64) {
-    KernelScope ks(c, ERX_K_TRINV);
-    launch_trinv32(c->Linv32, d, T, st);
+    KernelScope ks(c, ERX_K_TRINV, sb);
+    launch_trinv32(c->Linv32, d, T, sb);
   }
   enqueue_score(c, zsrc, ztype, zstride, ps, T, c->mu_t, c->Linv, c->Linv32, delta, dn, mask,
-                det, st);
+                det, sb);
+  if (slot >= 0) cudaEventRecord(c->ev_fin[slot], sb);
   const erx_status rs = check_cuda(c, cudaGetLastError());
   if (rs == ERX_OK && learned && c->audit_every > 0) {
     const erx_status as = audit_block(c, x, n, stride_elems, delta);
@@ -471,6 +499,7 @@ erx_status pipeline_refresh(erx_ctx* c) {
 cudaError_t sync_all(erx_ctx* c) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess && c->side) e = cudaStreamSynchronize(c->side);
+  if (e == cudaSuccess && c->sB) e = cudaStreamSynchronize(c->sB);
   return e;
 }
 
@@ -677,6 +706,26 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
          cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess))
       s = ERX_ECUDA;
   }
+  // block overlap (stream B): second copies of what passes from A to B.  Not in
+  // the FP64 form: both halves are bound by the same FP64 pipe there, and the
+  // overlap only adds contention.
+  c->overlap = !learned && cfg->form != ERX_FORM_FP64;
+  c->mu_t_s[0] = c->mu_t;
+  c->Linv_s[0] = c->Linv;
+  c->Linv32_s[0] = c->Linv32;
+  if (c->overlap) {
+    if (s == ERX_OK) s = dalloc(c, &c->mu_t_s[1], (size_t)T * d);
+    if (s == ERX_OK) s = dalloc(c, &c->Linv_s[1], (size_t)T * P);
+    if (s == ERX_OK && !c->fp64) s = dalloc(c, &c->Linv32_s[1], (size_t)T * P);
+    if (s == ERX_OK &&
+        (cudaStreamCreateWithFlags(&c->sB, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_fac[0], cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_fac[1], cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_fin[0], cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_fin[1], cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
+      s = ERX_ECUDA;
+  }
 #undef ERX_A
   if (s == ERX_OK && learned) {
     float* zp = nullptr;
@@ -701,6 +750,12 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
       s = c->fp64 ? dalloc(c, (double**)&zp, (size_t)T * W * d)
                   : dalloc(c, (float**)&zp, (size_t)T * W * d);
       c->Z = zp;
+      c->Z_s[0] = zp;
+    }
+    if (s == ERX_OK && c->overlap) {
+      s = c->fp64 ? dalloc(c, (double**)&zp, (size_t)T * W * d)
+                  : dalloc(c, (float**)&zp, (size_t)T * W * d);
+      c->Z_s[1] = zp;
     }
     if (s == ERX_OK) {
       cudaMemcpy(c->colptr, cp.data(), cp.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -741,12 +796,26 @@ erx_status erx_push_lines(erx_ctx* c, const void* lines, int64_t n, int64_t stri
   if (c->pipeline && n == 1 && c->have_pre)
     return run_line_pipelined(c, lines, stride, delta, dn, mask, det);
   pipeline_join(c);
+  const bool two = c->overlap && n > c->T;
   for (int64_t b = 0; b < n; b += c->T) {
     const int64_t m = std::min<int64_t>(c->T, n - b);
     const char* x = (const char*)lines + b * stride_bytes;
     erx_status s = run_block(c, x, m, stride, (char*)delta + (size_t)b * c->W * ss,
                              dn ? (char*)dn + (size_t)b * c->W * ss : nullptr,
-                             mask ? mask + (size_t)b * c->W : nullptr, det ? det + b : nullptr);
+                             mask ? mask + (size_t)b * c->W : nullptr, det ? det + b : nullptr,
+                             two ? (int)((b / c->T) & 1) : -1);
+    if (s != ERX_OK) return s;
+  }
+  if (two) {
+    // the context's stream waits for the last scores; slot 0's buffers are the
+    // ones the single-stream path uses
+    cudaEventRecord(c->ev_join, c->sB);
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    c->mu_t = c->mu_t_s[0];
+    c->Linv = c->Linv_s[0];
+    c->Linv32 = c->Linv32_s[0];
+    c->Z = c->Z_s[0];
+    const erx_status s = check_cuda(c, cudaGetLastError());
     if (s != ERX_OK) return s;
   }
   return pipeline_refresh(c);

@@ -430,3 +430,22 @@ def test_fp64e_rejects_projection_and_f64():
         Detector(16, 32, form="fp64e", proj="srp", proj_dim=4)
     with pytest.raises(ErxError):
         Detector(16, 32, form="fp64e", in_dtype="f64")
+
+
+@pytest.mark.parametrize("form,kw", [("fp64", {}), ("fp64e", {}), ("fp32", {}), ("tf32", {}),
+                                     ("bf16", {}), ("tf32x3", {}),
+                                     ("fp64", {"proj": "srp", "proj_dim": 6}),
+                                     ("fp32", {"averaging": "imc"})])
+def test_overlapped_blocks_are_bitwise_block_pushes(form, kw):
+    """One push of 40 lines in 7-line blocks runs block b+1's statistics,
+    update and factor on the context's stream while a second stream scores
+    block b; it gives the same bits as pushing the same blocks one call at a
+    time (one stream)."""
+    cube = synth.gen_lines(synth.reflectance_c1(width=96, bands=40, seed=9), 0, 40)
+    kw = dict(form=form, warmup=2, threshold=3.0, block_lines=7, **kw)
+    one, d1 = run_gpu(cube, **kw)
+    sep, d2 = run_gpu(cube, push_sizes=[7, 7, 7, 7, 7, 5], **kw)
+    for k in ("delta", "delta_n", "mask", "detecting"):
+        assert np.array_equal(one[k], sep[k]), k
+    s1, s2 = d1.state(), d2.state()
+    assert np.array_equal(s1[1], s2[1]) and np.array_equal(s1[2], s2[2])
