@@ -24,6 +24,7 @@
 
 #include "../../include/erx.h"
 #include "erx_internal.cuh"
+#include "tc_util.cuh"
 
 using namespace erx;
 
@@ -103,6 +104,200 @@ __global__ void __launch_bounds__(kThreads) enc_fwd_kernel(
       if (i < n) codes[i * k + c] = acc[a];
     }
   }
+}
+
+// ---- forward on the tensor cores (inference) --------------------------------
+// Both layers are dense contractions over a 128-pixel tile (M = 128):
+//   layer 1: A = xn (pixels x bands, bf16), B = W1 (hidden x bands, bf16), N = h;
+//   layer 2: A = relu(a + b1) (pixels x hidden, bf16), B = W2 (codes x hidden), N = k;
+// FP32 accumulation in tensor memory (layer 1 at column 0, layer 2 at column
+// 256).  Operand tiles are K-major, no swizzle (8-row x 16-byte core matrices);
+// band, hidden and code counts are padded to multiples of 16 with zero weights
+// (a padded hidden unit has zero weights and bias, so relu gives 0).  One
+// persistent CTA per SM keeps W1 and W2 in shared memory and walks the tiles:
+// stage xn = (x - shift) * scale as bf16, layer-1 MMAs, epilogue (bias, relu,
+// bf16 into the layer-2 operand), layer-2 MMAs, epilogue (bias, FP32 codes).
+// Activations are rounded to bf16 here; training uses the FP32 forward above.
+constexpr int kFT = 256;                    // threads
+constexpr uint32_t kFLBO = 128;
+constexpr uint32_t kFWait = 1u << 26;
+
+__host__ __device__ inline int pad16(int v) { return (v + 15) & ~15; }
+__host__ __device__ inline size_t fwd_tc_smem(int b, int h, int k) {
+  const int bK = pad16(b), hP = pad16(h), kP = pad16(k);
+  return (size_t)2 * ((size_t)128 * bK + (size_t)hP * bK + (size_t)128 * hP + (size_t)kP * hP) +
+         (size_t)4 * (2 * bK + hP + kP);
+}
+
+__device__ __forceinline__ uint32_t fwd_off(int row, int kk, uint32_t sbo) {
+  return (uint32_t)(row >> 3) * sbo + (uint32_t)(kk >> 3) * kFLBO + (uint32_t)(row & 7) * 16u;
+}
+
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__global__ void __launch_bounds__(kFT, 1) enc_fwd_tc_kernel(
+    const float* __restrict__ x, int64_t n, int b, int h, int k, const float* __restrict__ shift,
+    const float* __restrict__ scale, const __nv_bfloat16* __restrict__ W1,
+    const float* __restrict__ b1, const __nv_bfloat16* __restrict__ W2,
+    const float* __restrict__ b2, float* __restrict__ codes, unsigned long long* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smtc[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int bK = pad16(b), hP = pad16(h), kP = pad16(k);
+  const uint32_t sbo1 = (uint32_t)(bK / 8) * 128u, sbo2 = (uint32_t)(hP / 8) * 128u;
+  unsigned char* A1 = smtc;                                // [128][bK]
+  unsigned char* B1 = A1 + (size_t)128 * bK * 2;           // [hP][bK]
+  unsigned char* A2 = B1 + (size_t)hP * bK * 2;            // [128][hP]
+  unsigned char* B2 = A2 + (size_t)128 * hP * 2;           // [kP][hP]
+  float* s_shift = reinterpret_cast<float*>(B2 + (size_t)kP * hP * 2);
+  float* s_scale = s_shift + bK;
+  float* s_b1 = s_scale + bK;
+  float* s_b2 = s_b1 + hP;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // weights, biases and the normalisation, once per CTA (zero padding)
+  for (int it = tid; it < hP * (bK / 8); it += kFT) {
+    const int j = it / (bK / 8), g = it % (bK / 8);
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q0 = 8 * g + 2 * u;
+      const float v0 = (j < h && q0 < b) ? __bfloat162float(W1[(size_t)j * b + q0]) : 0.f;
+      const float v1 = (j < h && q0 + 1 < b) ? __bfloat162float(W1[(size_t)j * b + q0 + 1]) : 0.f;
+      w[u] = pack_bf2(v0, v1);
+    }
+    *reinterpret_cast<uint4*>(B1 + fwd_off(j, 8 * g, sbo1)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  for (int it = tid; it < kP * (hP / 8); it += kFT) {
+    const int c = it / (hP / 8), g = it % (hP / 8);
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j0 = 8 * g + 2 * u;
+      const float v0 = (c < k && j0 < h) ? __bfloat162float(W2[(size_t)c * h + j0]) : 0.f;
+      const float v1 = (c < k && j0 + 1 < h) ? __bfloat162float(W2[(size_t)c * h + j0 + 1]) : 0.f;
+      w[u] = pack_bf2(v0, v1);
+    }
+    *reinterpret_cast<uint4*>(B2 + fwd_off(c, 8 * g, sbo2)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  for (int q = tid; q < bK; q += kFT) {
+    s_shift[q] = q < b ? shift[q] : 0.f;
+    s_scale[q] = q < b ? scale[q] : 0.f;
+  }
+  for (int j = tid; j < hP; j += kFT) s_b1[j] = j < h ? b1[j] : 0.f;
+  for (int c = tid; c < kP; c += kFT) s_b2[c] = c < k ? b2[c] : 0.f;
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  const uint32_t id1 = tc::idesc(1, 128, hP), id2 = tc::idesc(1, 128, kP);
+  const int64_t ntile = (n + 127) / 128;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x) {
+    const int64_t i0 = tile * 128;
+    // xn of the tile's pixels as bf16 (rows beyond n and bands beyond b: 0)
+    for (int it = tid; it < 128 * (bK / 8); it += kFT) {
+      const int p = it / (bK / 8), g = it % (bK / 8);
+      const int64_t i = i0 + p;
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q0 = 8 * g + 2 * u;
+        const float v0 = (i < n && q0 < b) ? (x[i * b + q0] - s_shift[q0]) * s_scale[q0] : 0.f;
+        const float v1 =
+            (i < n && q0 + 1 < b) ? (x[i * b + q0 + 1] - s_shift[q0 + 1]) * s_scale[q0 + 1] : 0.f;
+        w[u] = pack_bf2(v0, v1);
+      }
+      *reinterpret_cast<uint4*>(A1 + fwd_off(p, 8 * g, sbo1)) =
+          make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t a = tc::smem_u32(A1), bb = tc::smem_u32(B1);
+      for (int s = 0; s < bK / 16; ++s) {
+        const uint32_t ko = (uint32_t)s * 2u * kFLBO;
+        tc::mma_bf16(tmem, tc::desc(a + ko, kFLBO, sbo1), tc::desc(bb + ko, kFLBO, sbo1), id1,
+                     s > 0);
+      }
+      tc::commit(&mbar);
+    }
+    ok = tc::mbar_wait(&mbar, phase, kFWait);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) break;
+    tc::fence_after_sync();
+    // epilogue 1: warp w reads TMEM lanes 32 (w % 4) .. (pixels), 16-column chunks
+    {
+      const int p = 32 * (warp & 3) + lane;
+      const uint32_t lb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+      for (int c0 = (warp >> 2) * 16; c0 < hP; c0 += 32) {
+        uint32_t v[16];
+        tc::tmem_ld16(lb + (uint32_t)c0, v);
+        tc::tmem_ld_wait();
+        uint32_t w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          w[u] = pack_bf2(fmaxf(__uint_as_float(v[2 * u]) + s_b1[c0 + 2 * u], 0.f),
+                          fmaxf(__uint_as_float(v[2 * u + 1]) + s_b1[c0 + 2 * u + 1], 0.f));
+        *reinterpret_cast<uint4*>(A2 + fwd_off(p, c0, sbo2)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(A2 + fwd_off(p, c0 + 8, sbo2)) =
+            make_uint4(w[4], w[5], w[6], w[7]);
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+      const uint32_t a = tc::smem_u32(A2), bb = tc::smem_u32(B2);
+      for (int s = 0; s < hP / 16; ++s) {
+        const uint32_t ko = (uint32_t)s * 2u * kFLBO;
+        tc::mma_bf16(tmem + 256u, tc::desc(a + ko, kFLBO, sbo2), tc::desc(bb + ko, kFLBO, sbo2),
+                     id2, s > 0);
+      }
+      tc::commit(&mbar);
+    }
+    ok = tc::mbar_wait(&mbar, phase, kFWait);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) break;
+    tc::fence_after_sync();
+    // epilogue 2: codes of the tile's pixels
+    if (warp < 4) {
+      const int p = 32 * warp + lane;
+      const int64_t i = i0 + p;
+      const uint32_t lb = tmem + 256u + ((uint32_t)(32 * warp) << 16);
+      for (int c0 = 0; c0 < kP; c0 += 16) {
+        uint32_t v[16];
+        tc::tmem_ld16(lb + (uint32_t)c0, v);
+        tc::tmem_ld_wait();
+        if (i < n) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (c0 + u < k) codes[i * k + c0 + u] = __uint_as_float(v[u]) + s_b2[c0 + u];
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  }
+  if (!ok) {
+    if (tid == 0) atomicMin(&err[kErrTimeout], 0ull);
+    tc::mbar_wait(&mbar, phase, kFWait);   // one more bounded wait for MMAs in flight
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_free(tmem, 512);
 }
 
 // ---- loss and dL/dc -------------------------------------------------------
@@ -346,6 +541,22 @@ void forward(erx_encoder* e, const float* x, int64_t n, float* codes, __nv_bfloa
       e->theta + e->off_b2, codes, hout);
 }
 
+// inference forward on the tensor cores (bf16 activations): one persistent CTA per SM
+void forward_tc(erx_encoder* e, const float* x, int64_t n, float* codes, cudaStream_t st) {
+  static int n_sm = 0;
+  if (!n_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (n_sm <= 0) n_sm = 1;
+  }
+  const int64_t tiles = (n + 127) / 128;
+  const int grid = (int)std::min<int64_t>(tiles, n_sm);
+  enc_fwd_tc_kernel<<<grid, kFT, fwd_tc_smem(e->b, e->h, e->k), st>>>(
+      x, n, e->b, e->h, e->k, e->shift, e->scale, e->w1b, e->theta + e->off_b1, e->w2b,
+      e->theta + e->off_b2, codes, e->err);
+}
+
 // One line: forward, code statistics (update then score), loss, backward and,
 // when `apply`, the AdamW step.  grad_out (device, nparam) receives the gradient.
 erx_status train_line(erx_encoder* e, const float* line, int p, const double* target,
@@ -388,7 +599,7 @@ namespace erx {
 int encoder_k(const erx_encoder* e) { return e->k; }
 int encoder_bands(const erx_encoder* e) { return e->b; }
 void encoder_forward_on(erx_encoder* e, const float* x, int64_t n, float* codes, cudaStream_t st) {
-  forward(e, x, n, codes, nullptr, st);
+  forward_tc(e, x, n, codes, st);
 }
 }  // namespace erx
 
@@ -450,11 +661,14 @@ erx_status erx_encoder_create(int32_t bands, int32_t hidden, int32_t k, uint64_t
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (fwd_smem(bands, hidden, k) > (size_t)optin || bwd_smem(bands, hidden, k) > (size_t)optin)
+    if (fwd_smem(bands, hidden, k) > (size_t)optin || bwd_smem(bands, hidden, k) > (size_t)optin ||
+        fwd_tc_smem(bands, hidden, k) > (size_t)optin)
       s = ERX_EUNSUPPORTED;
     else if (configure_factor_kernels() != cudaSuccess ||
              cudaFuncSetAttribute(enc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)fwd_smem(bands, hidden, k)) != cudaSuccess ||
+             cudaFuncSetAttribute(enc_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fwd_tc_smem(bands, hidden, k)) != cudaSuccess ||
              cudaFuncSetAttribute(enc_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)bwd_smem(bands, hidden, k)) != cudaSuccess)
       s = ERX_ECUDA;
@@ -536,7 +750,7 @@ erx_status erx_encoder_forward(erx_encoder* e, const float* x_dev, int64_t n_pix
   if (!e || n_pix < 0 || (n_pix > 0 && (!x_dev || !codes_dev))) return ERX_EINVAL;
   if (e->failed) return ERX_ECUDA;
   if (n_pix == 0) return ERX_OK;
-  forward(e, x_dev, n_pix, codes_dev, nullptr, e->stream);
+  forward_tc(e, x_dev, n_pix, codes_dev, e->stream);
   return ecuda(e, cudaGetLastError());
 }
 
