@@ -24,10 +24,12 @@
 using namespace erx;
 
 namespace erx {
-int batch_stats_tiles(int d);
+int batch_stats_tiles(int d, bool fp64);
 int batch_solve_tiles(int route, int W);
 void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, int n_items,
                              int dmax, cudaStream_t st);
+void launch_batch_solve_fp64(const BStream* S, const BItem* items, int n_hi, int n_items,
+                             int dmax, int dmax_lo, cudaStream_t st);
 void launch_batch_solve_tc(int fmt, const BStream* S, const BItem* items, int n_items, int dmax,
                            unsigned long long* err, cudaStream_t st);
 }  // namespace erx
@@ -64,6 +66,7 @@ struct erx_batch {
   int n_ema = 0;
   BItem* solve_items[kRoutes] = {};
   int n_solve[kRoutes] = {};
+  int n_hi0 = 0, dmax_lo0 = 1;   // FP64 route: items of streams with d > 128; largest other d
   unsigned long long* err = nullptr;
   // graph
   cudaGraph_t graph = nullptr;
@@ -133,6 +136,14 @@ erx_status build_solve_items(erx_batch* b) {
       return b->host[x.s].d > b->host[y.s].d;
     });
     b->n_solve[r] = (int)items.size();
+    if (r == 0) {
+      b->n_hi0 = 0;
+      b->dmax_lo0 = 1;
+      for (const BItem& it : items) {
+        if (b->host[it.s].d > 128) ++b->n_hi0;
+        else b->dmax_lo0 = std::max(b->dmax_lo0, b->host[it.s].d);
+      }
+    }
     if (!b->solve_items[r]) {
       // capacity: every stream's tiles for this route
       size_t cap = 0;
@@ -176,9 +187,14 @@ void enqueue_step(erx_batch* b, cudaStream_t st) {
   if (!fp64) launch_batch_trinv32(b->table, b->n, b->dmax, st);
   for (int r = 0; r < kRoutes; ++r) {
     if (!b->n_solve[r]) continue;
-    if (r <= 1) launch_batch_solve_simt(r, b->table, b->solve_items[r], b->n_solve[r], b->dmax, st);
-    else launch_batch_solve_tc(route_format(r), b->table, b->solve_items[r], b->n_solve[r],
-                               b->dmax, b->err, st);
+    if (r == 0)
+      launch_batch_solve_fp64(b->table, b->solve_items[0], b->n_hi0, b->n_solve[0], b->dmax,
+                              b->dmax_lo0, st);
+    else if (r == 1)
+      launch_batch_solve_simt(r, b->table, b->solve_items[r], b->n_solve[r], b->dmax, st);
+    else
+      launch_batch_solve_tc(route_format(r), b->table, b->solve_items[r], b->n_solve[r],
+                            b->dmax, b->err, st);
   }
   launch_batch_normalise(b->table, b->n, fp64, st);
 }
@@ -299,7 +315,8 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
       e.dn = adn + ow * ss;
       e.mask = amk + ow;
       e.det = adt + i;
-      for (int k = 0; k < batch_stats_tiles(d); ++k) st_items.push_back({i, k});
+      for (int k = 0; k < batch_stats_tiles(d, form == ERX_FORM_FP64); ++k)
+        st_items.push_back({i, k});
       const int64_t ne = packed_size(d) + d;
       for (int k = 0; k < (int)((ne + 127) / 128); ++k) ema_items.push_back({i, k});
       ox += (size_t)W * d;

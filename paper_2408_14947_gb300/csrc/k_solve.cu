@@ -179,6 +179,20 @@ __global__ void __launch_bounds__(H * NPX) solve_fp64_kernel(
   }
 }
 
+// Batched form: one CTA per (stream, pixel tile) item; H = 2 for streams with
+// more than 128 dimensions (two threads per pixel, as the single-stream path).
+template <int H>
+__global__ void __launch_bounds__(H * kPixF64) b_solve_fp64_kernel(
+    const BStream* __restrict__ S, const BItem* __restrict__ items) {
+  const BItem it = items[blockIdx.x];
+  const BStream& s = S[it.s];
+  if constexpr (H == 1)
+    solve_fp64_body<float>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf, (double*)s.delta, it.tile);
+  else
+    solve_fp64_multi_body<float, H, kPixF64>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf, (double*)s.delta,
+                                             it.tile);
+}
+
 constexpr int kPixF32 = 64;   // pixels per CTA
 constexpr int kOutB = kNB;    // outputs per block of the factor
 
@@ -269,13 +283,7 @@ __global__ void __launch_bounds__(128) solve_fp32_kernel(
                        Lf32 + (int64_t)t * packed_size(d), delta + (int64_t)t * W, blockIdx.x);
 }
 
-// Batched form: one CTA per (stream, pixel tile) item.
-__global__ void __launch_bounds__(kPixF64) b_solve_fp64_kernel(const BStream* __restrict__ S,
-                                                               const BItem* __restrict__ items) {
-  const BItem it = items[blockIdx.x];
-  const BStream& s = S[it.s];
-  solve_fp64_body<float>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf, (double*)s.delta, it.tile);
-}
+
 
 __global__ void __launch_bounds__(128) b_solve_fp32_kernel(const BStream* __restrict__ S,
                                                            const BItem* __restrict__ items) {
@@ -319,7 +327,8 @@ cudaError_t configure_solve_kernels() {
   ERX_CFG(solve_fp32_kernel<uint16_t>, m32);
   ERX_CFG(solve_fp32_kernel<float>, m32);
   ERX_CFG(solve_fp32_kernel<double>, m32);
-  ERX_CFG(b_solve_fp64_kernel, m64);
+  ERX_CFG(b_solve_fp64_kernel<1>, m64);
+  ERX_CFG(b_solve_fp64_kernel<2>, m64);
   ERX_CFG(b_solve_fp32_kernel, m32);
 #undef ERX_CFG
   return e;
@@ -333,9 +342,19 @@ int batch_solve_tiles(int route, int W) {
 void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, int n_items,
                              int dmax, cudaStream_t st) {
   if (route == 0)
-    b_solve_fp64_kernel<<<n_items, kPixF64, smem_fp64(dmax), st>>>(S, items);
+    b_solve_fp64_kernel<1><<<n_items, kPixF64, smem_fp64(dmax), st>>>(S, items);
   else
     b_solve_fp32_kernel<<<n_items, 128, smem_fp32(dmax), st>>>(S, items);
+}
+
+// FP64 route with its items sorted by dimension, largest first: the first n_hi
+// (d > 128) with two threads per pixel and shared memory for dmax, the rest
+// with one thread per pixel and shared memory for their own largest d
+void launch_batch_solve_fp64(const BStream* S, const BItem* items, int n_hi, int n_items,
+                             int dmax, int dmax_lo, cudaStream_t st) {
+  if (n_hi > 0) b_solve_fp64_kernel<2><<<n_hi, 2 * kPixF64, smem_fp64(dmax), st>>>(S, items);
+  if (n_items > n_hi)
+    b_solve_fp64_kernel<1><<<n_items - n_hi, kPixF64, smem_fp64(dmax_lo), st>>>(S, items + n_hi);
 }
 
 constexpr int kPairMinD = 129;   // two threads per pixel from here on

@@ -21,6 +21,7 @@ namespace {
 constexpr int SB = 64;    // output block edge
 constexpr int KCI = 64;   // pixels per shared-memory chunk, integer route
 constexpr int KCF = 32;   // pixels per chunk, floating route
+constexpr int kMeanThreads = 1024;   // line mean: threads per line
 
 __device__ __forceinline__ void block_pair(int q, int& I, int& J) {
   int i = 0;
@@ -116,7 +117,8 @@ __global__ void __launch_bounds__(256) stats_int_kernel(
   }
 }
 
-// Line mean of one line (x: its first sample, pixel stride ps): 256 threads.
+// Line mean of one line (x: its first sample, pixel stride ps): kMeanThreads
+// threads, G = kMeanThreads / d of them per band, each summing every G-th pixel.
 // FP64 form (float_shift false): every sample added in FP64.  Other forms:
 // runs of 8 samples summed in FP32 first (relative error <= 7 * 2^-24 of the
 // run, far below those forms' tolerances), an eighth of the FP64 adds.
@@ -124,7 +126,7 @@ template <typename InT>
 __device__ __forceinline__ void mean_body(const InT* __restrict__ x, int ps, int W, int d,
                                           bool float_shift, double* __restrict__ mu_hat,
                                           double* __restrict__ shift) {
-  __shared__ double part[256];
+  __shared__ double part[kMeanThreads];
   const int G = max(1, (int)blockDim.x / d);
   const int g = threadIdx.x / d, b = threadIdx.x % d;
   double s = 0.0;
@@ -153,7 +155,7 @@ __device__ __forceinline__ void mean_body(const InT* __restrict__ x, int ps, int
 }
 
 template <typename InT>
-__global__ void __launch_bounds__(256) mean_kernel(const InT* __restrict__ X, int64_t line_stride,
+__global__ void __launch_bounds__(kMeanThreads) mean_kernel(const InT* __restrict__ X, int64_t line_stride,
                                                    int ps, int W, int d, bool float_shift,
                                                    double* __restrict__ mu_hat,
                                                    double* __restrict__ shift) {
@@ -280,7 +282,7 @@ int n_pairs(int d, int sb = SB) {
 }
 
 // Batched form: one CTA per stream (mean) / per (stream, block pair) item.
-__global__ void __launch_bounds__(256) b_mean_kernel(const BStream* __restrict__ S,
+__global__ void __launch_bounds__(kMeanThreads) b_mean_kernel(const BStream* __restrict__ S,
                                                      bool float_shift) {
   const BStream& s = S[blockIdx.x];
   mean_body<float>(s.x, s.d, s.W, s.d, float_shift, s.mu_hat, s.shift);
@@ -293,16 +295,19 @@ __global__ void __launch_bounds__(256) b_stats_kernel(const BStream* __restrict_
   const BStream& s = S[it.s];
   if (s.d <= kSmallD)
     stats_small_body<float, AccT>(s.x, s.d, s.W, s.d, s.shift, s.S2f);
-  else
-    stats_fp_body<float, AccT>(s.x, s.d, s.W, s.d, s.shift, s.S2f, it.tile);
+  else   // FP64: 32 x 32 blocks, as the single-stream path
+    stats_fp_body<float, AccT, sizeof(AccT) == 8 ? 32 : SB>(s.x, s.d, s.W, s.d, s.shift, s.S2f,
+                                                          it.tile);
 }
 
 }  // namespace
 
-int batch_stats_tiles(int d) { return d <= kSmallD ? 1 : n_pairs(d); }
+int batch_stats_tiles(int d, bool fp64) {
+  return d <= kSmallD ? 1 : n_pairs(d, fp64 ? 32 : SB);
+}
 
 void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t st) {
-  b_mean_kernel<<<n, 256, 0, st>>>(S, float_shift);
+  b_mean_kernel<<<n, kMeanThreads, 0, st>>>(S, float_shift);
 }
 
 void launch_batch_stats(const BStream* S, const BItem* items, int n_items, bool fp64,
@@ -325,13 +330,13 @@ void launch_stats_int(const uint16_t* x, int64_t line_stride, int W, int d, uint
 void launch_mean(int in_type, const void* x, int64_t line_stride, int ps, int W, int d, int T,
                  bool float_shift, double* mu_hat, double* shift, cudaStream_t st) {
   if (in_type == 0)
-    mean_kernel<uint16_t><<<T, 256, 0, st>>>((const uint16_t*)x, line_stride, ps, W, d,
+    mean_kernel<uint16_t><<<T, kMeanThreads, 0, st>>>((const uint16_t*)x, line_stride, ps, W, d,
                                              float_shift, mu_hat, shift);
   else if (in_type == 1)
-    mean_kernel<float><<<T, 256, 0, st>>>((const float*)x, line_stride, ps, W, d, float_shift,
+    mean_kernel<float><<<T, kMeanThreads, 0, st>>>((const float*)x, line_stride, ps, W, d, float_shift,
                                           mu_hat, shift);
   else
-    mean_kernel<double><<<T, 256, 0, st>>>((const double*)x, line_stride, ps, W, d, float_shift,
+    mean_kernel<double><<<T, kMeanThreads, 0, st>>>((const double*)x, line_stride, ps, W, d, float_shift,
                                            mu_hat, shift);
 }
 
