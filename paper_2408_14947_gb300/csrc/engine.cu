@@ -306,7 +306,7 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
   {
     KernelScope ks(c, ERX_K_CHOL);
     launch_chol_inv(c->K_t, d, T, c->cfg.ridge, c->Linv, c->fp64 ? nullptr : c->Linv32, c->err,
-                    c->t, st);
+                    c->t, st, c->fp64);
   }
   cudaStream_t sb = st;
   if (slot >= 0) {
@@ -427,7 +427,7 @@ void enqueue_prefactor(erx_ctx* c, cudaStream_t st) {
   {
     KernelScope ks(c, ERX_K_CHOL, st);
     launch_chol_inv(c->K_state, d, 1, c->cfg.ridge, c->Lf_pre, c->fp64 ? nullptr : c->Lf32_pre,
-                    c->err, c->t, st);
+                    c->err, c->t, st, c->fp64);
   }
   if (!c->fp64) {
     KernelScope ks(c, ERX_K_TRINV, st);

@@ -89,8 +89,11 @@ void launch_imc_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      cudaStream_t st);
 
 // Cholesky of K_t + ridge I, diagonal blocks inverted, one CTA per line.
+// invert: replace the 32 x 32 diagonal blocks by their inverses in FP64 (the
+// FP64 score kernels and the encoder's loss need them; the FP32 routes invert
+// them in trinv32 instead)
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Linv, float* Linv32,
-                     unsigned long long* err, int64_t t0, cudaStream_t st);
+                     unsigned long long* err, int64_t t0, cudaStream_t st, bool invert = true);
 
 // In place: the float blocked factor of T lines becomes the full L^{-1} (FP32).
 void launch_trinv32(float* Lf32, int d, int T, cudaStream_t st);

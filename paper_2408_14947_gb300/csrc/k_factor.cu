@@ -49,7 +49,8 @@ __host__ __device__ inline size_t chol_smem(int d) {
 template <int TS, int NT = kThreads>
 __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d, double ridge,
                                           double* __restrict__ dst, float* __restrict__ d32,
-                                          unsigned long long* __restrict__ err, int64_t line) {
+                                          unsigned long long* __restrict__ err, int64_t line,
+                                          bool inv) {
   extern __shared__ __align__(16) double sm[];
   __shared__ double Pl[kPB][kPB];   // Pl[r][c] = l_{j0+r, j0+c}: the panel rows' scaled entries
   __shared__ double s_ri[kPB];      // 1 / l_jj of the panel's columns
@@ -166,7 +167,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   // block, column j becomes -(1/l_jj) T l_col (lane i computes row i), so no
   // per-lane arrays are needed and the kernel keeps few registers.
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nblk = (d + kNB - 1) / kNB;
+  const int nblk = inv ? (d + kNB - 1) / kNB : 0;
   for (int bk = warp; bk < nblk; bk += NT / 32) {
     const int j0 = bk * kNB;
     const int nb = min(kNB, d - j0);
@@ -196,11 +197,11 @@ __global__ void __launch_bounds__(NT, MINB) chol_kernel(const double* __restrict
                                                     double ridge, double* __restrict__ Lf,
                                                     float* __restrict__ Lf32,
                                                     unsigned long long* __restrict__ err,
-                                                    int64_t t0) {
+                                                    int64_t t0, bool inv) {
   const int t = blockIdx.x;
   const int64_t P = packed_size(d);
   chol_body<TS, NT>(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err,
-                    t0 + t);
+                    t0 + t, inv);
 }
 
 // Batched form: one CTA per stream.
@@ -208,11 +209,13 @@ __global__ void __launch_bounds__(kThreads, 4) b_chol_kernel(const BStream* __re
                                                          bool want32,
                                                          unsigned long long* __restrict__ err) {
   const BStream& s = S[blockIdx.x];
-  chol_body<2>(s.K_t, s.d, s.ridge, s.Lf, want32 ? s.Lf32 : nullptr, err, blockIdx.x);
+  // the FP32 routes invert the diagonal blocks in trinv32 (FP32)
+  chol_body<2>(s.K_t, s.d, s.ridge, s.Lf, want32 ? s.Lf32 : nullptr, err, blockIdx.x, !want32);
 }
 
-// Full inverse X = L^{-1} in FP32 from the float blocked factor, for the FP32,
-// TF32 and BF16 forms (their score kernels then apply X with one triangular
+// Full inverse X = L^{-1} in FP32 from the float factor (plain diagonal blocks:
+// the FP32 routes skip the FP64 block inversion), for the FP32, TF32, BF16 and
+// 3xTF32 forms (their score kernels then apply X with one triangular
 // product instead of a block-by-block solve).  One CTA per line, in place in
 // shared memory and in the caller's buffer.  Column blocks left to right, row
 // blocks top to bottom:  X_KK = D_K (already stored),
@@ -226,6 +229,29 @@ __device__ __forceinline__ void trinv32_body(float* __restrict__ Lf32, int d) {
   for (int q = threadIdx.x; q < P; q += kThreads) S[q] = Lf32[q];
   __syncthreads();
   const int nblk = (d + kNB - 1) / kNB;
+  // the factor comes with plain diagonal blocks L_KK: D_K = L_KK^{-1} first, in
+  // FP32, one warp per block, columns right to left (column j becomes
+  // -(1/l_jj) T l_col with T the already inverted trailing part; lane i: row i)
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int bk = warp; bk < nblk; bk += kThreads / 32) {
+      const int j0 = bk * kNB, nb = min(kNB, d - j0);
+      for (int j = nb - 1; j >= 0; --j) {
+        const float rjj = 1.0f / S[pidx(j0 + j, j0 + j)];
+        const int i = lane;
+        float acc = 0.f;
+        if (i > j && i < nb) {
+          const float* Ti = S + pidx(j0 + i, j0);
+          for (int k = j + 1; k <= i; ++k) acc = fmaf(Ti[k], S[pidx(j0 + k, j0 + j)], acc);
+        }
+        __syncwarp();
+        if (i > j && i < nb) S[pidx(j0 + i, j0 + j)] = -rjj * acc;
+        if (i == j) S[pidx(j0 + j, j0 + j)] = rjj;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
   for (int K = 0; K < nblk; ++K) {
     const int k0 = K * kNB, k1 = min(d, k0 + kNB);
     for (int J = K + 1; J < nblk; ++J) {
@@ -281,9 +307,7 @@ void launch_batch_trinv32(const BStream* S, int n, int dmax, cudaStream_t st) {
 cudaError_t configure_factor_kernels() {
   const int m = (int)chol_smem(kMaxDim);
   cudaError_t e =
-      cudaFuncSetAttribute(chol_kernel<4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(chol_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+      cudaFuncSetAttribute(chol_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(chol_kernel<2, 1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              m);
@@ -306,7 +330,7 @@ void launch_batch_chol(const BStream* S, int n, int dmax, bool want32, unsigned 
 }
 
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, float* Lf32,
-                     unsigned long long* err, int64_t t0, cudaStream_t st) {
+                     unsigned long long* err, int64_t t0, cudaStream_t st, bool invert) {
   // above 128 dimensions the factor fills an SM's shared memory: one CTA per SM.
   // Fewer lines than SMs (a line or a few pushed alone): one CTA per SM anyway,
   // so each takes more threads (as many as its registers allow) to hide the
@@ -319,14 +343,12 @@ void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, 
     if (n_sm <= 0) n_sm = 1;
   }
   const size_t sm = chol_smem(d);
-  if (T < n_sm && d > 128)
-    chol_kernel<4, 1, 512><<<T, 512, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
+  if (d > 128)   // one CTA per SM: 512 threads to cover its barriers and DFMA latency
+    chol_kernel<4, 1, 512><<<T, 512, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
   else if (T < n_sm)
-    chol_kernel<2, 1, 1024><<<T, 1024, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
-  else if (d > 128)
-    chol_kernel<4, 1><<<T, kThreads, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
+    chol_kernel<2, 1, 1024><<<T, 1024, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
   else
-    chol_kernel<2, 4><<<T, kThreads, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0);
+    chol_kernel<2, 4><<<T, kThreads, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
 }
 
 }  // namespace erx
