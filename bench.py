@@ -702,11 +702,21 @@ def run_profile_case(args):
         x = torch.from_numpy(cube.view(np.int16)).to(dev)
         det = Detector(BANDS, WIDTH, in_dtype="u16", in_bits=BITS, form=form, stream=stream,
                        block_lines=args.lines, averaging=avg)
-    else:
+    elif kind == "c3":
         cube = make_cube(args.lines, seed=1, kind="c3", width=1024, bands=224, kappa=1e3)
         x = torch.from_numpy(cube).to(dev)
         det = Detector(224, 1024, in_dtype="f32", form=form, stream=stream,
                        block_lines=args.lines, averaging=avg)
+    else:
+        # learned codes 224 -> 128 -> 32 (untrained weights: the kernels' work is the same)
+        from paper_2408_14947_gb300 import Encoder
+        cube = make_cube(args.lines, seed=1, kind="c3", width=1024, bands=224, kappa=1e3)
+        x = torch.from_numpy(cube).to(dev)
+        enc = Encoder(224, 128, 32, seed=0, stream=stream)
+        flat = cube[: min(len(cube), 64)].reshape(-1, 224)
+        enc.set_norm(flat.mean(0), 1.0 / (flat.std(0) + 1e-3))
+        det = Detector(224, 1024, in_dtype="f32", form=form, stream=stream,
+                       block_lines=args.lines, encoder=enc)
     del cube
     det.push(x)
     det.sync()
@@ -735,10 +745,10 @@ def main():
                     help="lines of the workload cube (smaller cubes for profiler captures)")
     ap.add_argument("--profile-case", default=None,
                     choices=["c2_fp64", "c2_fp64e", "c2_fp32", "c2_tf32", "c2_bf16", "c2_fp64_imc", "c3_fp64",
-                             "c3_fp32", "c3_tf32", "c3_bf16", "c3_tf32x3"],
+                             "c3_fp32", "c3_tf32", "c3_bf16", "c3_tf32x3", "c5_fp32", "c5_fp64"],
                     help="push one block of --lines lines of a workload (c2: 640 px x 108 "
-                         "bands u16; c3: 1024 px x 224 bands f32, kappa 1e3) through one "
-                         "form (_imc: IMC averaging), after one warm-up push, for profiler "
+                         "bands u16; c3: 1024 px x 224 bands f32, kappa 1e3; c5: c3 lines "
+                         "through learned 32-dim codes) through one form (_imc: IMC averaging), after one warm-up push, for profiler "
                          "captures; no bench line")
     args = ap.parse_args()
     globals()["LINES"] = args.lines

@@ -8,19 +8,35 @@
 // d/32 small inverses (d * 32^2 / 6 DFMA) instead of the full d^3/6.
 //
 // The packed factor (d(d+1)/2 doubles, 197 KiB at d = 224) lives in shared
-// memory.  Right-looking Cholesky in panels of kPB = 8 columns:
-//  * panel: thread r owns row j0 + r and keeps its kPB panel entries in
-//    registers.  Per column: every row scales its entry by 1/l_jj (the panel
-//    rows publish theirs), barrier; every row updates its later panel entries
-//    and the next pivot's row takes l_jj = a_jj rsqrt(a_jj), barrier.  No
-//    multiply is repeated across threads (the FP64 pipe is the bottleneck);
-//  * trailing update A22 -= L21 L21^T as a rank-kPB step in 4 x 4 register
-//    tiles over the lower triangle, reading L21 from a column-major copy.
-// Every element receives the same multiply-adds in the same order as in the
-// column-by-column algorithm (a_ik = fma(-l_ij, l_kj, a_ik), j ascending).
-// Each diagonal block is then inverted by one warp, one column per lane.  A
-// pivot that is not positive and finite records the line in the error slot
-// and poisons its scores (NaN).
+// memory.  Right-looking Cholesky in panels of kPB = 8 columns; the trailing
+// update A22 -= L21 L21^T is a rank-kPB step in TS x TS FP64 register tiles
+// over the lower triangle, reading L21 from a column-major copy.  Two panel
+// schedules:
+//  * column schedule (several CTAs per SM, d <= 128): thread r owns row
+//    j0 + r and keeps its panel entries in registers; per column every row
+//    scales its entry by 1/l_jj (the panel rows publish theirs), barrier, then
+//    updates its later panel entries while the next pivot's row takes
+//    l_jj = a_jj rsqrt(a_jj), barrier; then the whole trailing update.  The
+//    other resident CTAs fill the FP64 pipe during the barriers;
+//  * look-ahead schedule (one CTA per SM: d > 128, or fewer lines than SMs),
+//    three barriers per panel:
+//    (1) warp 0 factors the panel's 8 x 8 diagonal block while the other warps
+//        apply the previous panel's update to the trailing triangle right of
+//        this panel, tiles handed out 32 at a time from a shared counter
+//        (warp 0 joins when its block is done);
+//    (2) each row below the block computes its panel entries against the block
+//        (one thread per row) into A and the L21 copy;
+//    (3) the panel's update of the next panel's columns only, so the next
+//        block can start at once.
+//    The chain of pivots (a reciprocal square root per column) thus runs beside
+//    the bulk of the multiply-adds instead of between barriers.
+// In both, every element receives the same multiply-adds in the same order as
+// in the column-by-column algorithm (a_ik = fma(-l_ij, l_kj, a_ik), j
+// ascending), so all variants give the same bits.
+// Each diagonal block is then inverted by one warp, one column per lane (the
+// FP64 forms; the FP32 routes invert them in FP32 in trinv32).  A pivot that is
+// not positive and finite records the line in the error slot and poisons its
+// scores (NaN).
 #include <cmath>
 
 #include "erx_batch.cuh"
@@ -44,9 +60,13 @@ __host__ __device__ inline size_t chol_smem(int d) {
 
 // Factor one line's K (packed, src) into the blocked factor (dst, dst32);
 // `line` is the global line index reported on a bad pivot.  TS: edge of the
-// trailing update's register tiles (4 where one CTA fills an SM, 2 where four
-// CTAs share it and each thread has 64 registers).
-template <int TS, int NT = kThreads>
+// trailing update's register tiles (2 x 2 everywhere: 4 x 4 tiles need fewer
+// shared-memory loads per DFMA, but their 8k-cycle chunks leave a long uneven
+// tail at every barrier; measured 12 % slower at d = 224).  LA: the look-ahead schedule (one CTA per SM, where
+// barriers cannot be hidden by other CTAs); else the column schedule (several
+// CTAs per SM, where the look-ahead's one-warp block factor costs more FP64
+// issue slots than the barriers it saves).
+template <int TS, int NT = kThreads, bool LA = false>
 __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d, double ridge,
                                           double* __restrict__ dst, float* __restrict__ d32,
                                           unsigned long long* __restrict__ err, int64_t line,
@@ -54,16 +74,61 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   extern __shared__ __align__(16) double sm[];
   __shared__ double Pl[kPB][kPB];   // Pl[r][c] = l_{j0+r, j0+c}: the panel rows' scaled entries
   __shared__ double s_ri[kPB];      // 1 / l_jj of the panel's columns
+  __shared__ int s_next;            // next trailing tile to hand out (look-ahead)
   const int P = d * (d + 1) / 2;
   const int ls = lp_stride(d);
   double* A = sm;
   double* Lp = sm + ((P + 1) & ~1);
   double* rdiag = Lp + kPB * ls;    // 1 / l_jj
   const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   for (int q = tid; q < P; q += NT) A[q] = src[q];
+  if (tid == 0) s_next = 0;
   __syncthreads();
   for (int j = tid; j < d; j += NT) A[pidx(j, j)] += ridge;
   __syncthreads();
+
+  // rank-jbp update of the TS x TS tile (I, J) of the lower triangle whose tile
+  // grid starts at row and column g; Lp row r holds l_{g+r, c} of the panel
+  auto tile = [&](int g, int I, int J, int jbp) {
+    double acc[TS][TS];
+#pragma unroll
+    for (int u = 0; u < TS; ++u)
+#pragma unroll
+      for (int v = 0; v < TS; ++v) {
+        const int gi = g + TS * I + u, gk = g + TS * J + v;
+        acc[u][v] = (gi < d && gk <= gi) ? A[pidx(gi, gk)] : 0.0;
+      }
+    constexpr int kU = TS == 4 ? 2 : kPB;   // 4 x 4 tiles: no room to hoist more loads
+#pragma unroll kU
+    for (int c = 0; c < jbp; ++c) {
+      double av[TS], bv[TS];
+#pragma unroll
+      for (int h = 0; h < TS; h += 2) {
+        const double2 x = *reinterpret_cast<const double2*>(Lp + c * ls + TS * I + h);
+        const double2 y = *reinterpret_cast<const double2*>(Lp + c * ls + TS * J + h);
+        av[h] = x.x, av[h + 1] = x.y, bv[h] = y.x, bv[h + 1] = y.y;
+      }
+#pragma unroll
+      for (int u = 0; u < TS; ++u)
+#pragma unroll
+        for (int v = 0; v < TS; ++v) acc[u][v] = fma(-av[u], bv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < TS; ++u)
+#pragma unroll
+      for (int v = 0; v < TS; ++v) {
+        const int gi = g + TS * I + u, gk = g + TS * J + v;
+        if (gi < d && gk <= gi) A[pidx(gi, gk)] = acc[u][v];
+      }
+  };
+  // tile q of a triangle of tiles -> (I, J), J <= I
+  auto tri = [](int q, int& I, int& J) {
+    I = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+    while (I * (I + 1) / 2 > q) --I;
+    while ((I + 1) * (I + 2) / 2 <= q) ++I;
+    J = q - I * (I + 1) / 2;
+  };
   // pivot of column j (its updated diagonal a): l_jj = a rsqrt(a), published
   auto pivot = [&](double& a, int jj, int j) {
     if (!(a > 0.0) || !isfinite(a)) {
@@ -76,89 +141,145 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
     a = a * ri;
   };
 
-  for (int j0 = 0; j0 < d; j0 += kPB) {
-    const int jb = min(kPB, d - j0);
-    const int rl = tid, i = j0 + rl;          // this thread's row (d - j0 <= NT)
-    const bool own = i < d;
-    double a[kPB];
-#pragma unroll
-    for (int c = 0; c < kPB; ++c) a[c] = (own && c < jb && c <= rl) ? A[pidx(i, j0 + c)] : 0.0;
-    if (own && rl == 0) pivot(a[0], 0, j0);
-    __syncthreads();
-#pragma unroll
-    for (int jj = 0; jj < kPB; ++jj) {
-      if (jj >= jb) break;
-      // scale this row's entry of column jj; panel rows publish theirs
-      double lij = 0.0;
-      if (own && rl > jj) {
-        lij = a[jj] * s_ri[jj];
-        a[jj] = lij;
-        if (rl < jb) Pl[rl][jj] = lij;
+  if constexpr (LA) {
+    constexpr int J0 = kPB / TS;      // tile columns of one panel
+    static_assert(NT >= kMaxDim, "step (2) takes one row per thread");
+    for (int j0 = 0; j0 < d; j0 += kPB) {
+      const int jb = min(kPB, d - j0);
+      // (1) warp 0 factors the panel's diagonal block in Pl (lane r owns row r)
+      //     while the other warps, and warp 0 once done, apply the previous
+      //     panel's update to the columns right of this panel
+      if (warp == 0) {
+        const int r = lane;
+        if (r < jb)
+          for (int c = 0; c <= r; ++c) Pl[r][c] = A[pidx(j0 + r, j0 + c)];
+        __syncwarp();
+        for (int jj = 0; jj < jb; ++jj) {
+          if (r == jj) pivot(Pl[jj][jj], jj, j0 + jj);
+          __syncwarp();
+          if (r > jj && r < jb) Pl[r][jj] = Pl[r][jj] * s_ri[jj];
+          __syncwarp();
+          if (r > jj && r < jb) {
+            const double l = Pl[r][jj];
+            for (int c = jj + 1; c <= r; ++c) Pl[r][c] = fma(-l, Pl[c][jj], Pl[r][c]);
+          }
+          __syncwarp();
+        }
+        if (r < jb)
+          for (int c = 0; c <= r; ++c) A[pidx(j0 + r, j0 + c)] = Pl[r][c];
+      }
+      if (j0 > 0) {
+        const int nt = (d - j0 + TS - 1) / TS, n2 = nt - J0;
+        const int ntile = n2 > 0 ? n2 * (n2 + 1) / 2 : 0;
+        for (;;) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&s_next, 32);
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (base >= ntile) break;
+          const int q = base + lane;
+          if (q < ntile) {
+            int I, J;
+            tri(q, I, J);
+            tile(j0, I + J0, J + J0, kPB);
+          }
+        }
       }
       __syncthreads();
-      // update this row's later panel entries; the next pivot's row takes its pivot
-      if (own && rl > jj) {
+      // (2) the rows below the block: their panel entries against the block,
+      //     into A and the column-major copy (zero rows pad whole tiles)
+      const int g = j0 + jb, m = d - g;
+      const int mr = ((m + TS - 1) / TS) * TS;
+      if (tid == 0) s_next = 0;
+      if (const int t = tid; t < mr) {
+        const int i = g + t;
+        double a[kPB];
 #pragma unroll
-        for (int c = jj + 1; c < kPB; ++c)
-          if (c < jb && c <= rl) a[c] = fma(-lij, Pl[c][jj], a[c]);
-        if (rl == jj + 1 && rl < jb) pivot(a[min(jj + 1, kPB - 1)], jj + 1, i);
-      }
-      __syncthreads();
-    }
-    // the panel's final entries back into A; L21 (rows below the panel) into
-    // its column-major copy, zero-padded to whole 4-row tiles
-    if (own) {
+        for (int c = 0; c < kPB; ++c) a[c] = (t < m && c < jb) ? A[pidx(i, j0 + c)] : 0.0;
+        if (t < m) {
 #pragma unroll
-      for (int c = 0; c < kPB; ++c)
-        if (c < jb && c <= rl) A[pidx(i, j0 + c)] = a[c];
-    }
-    const int m = d - j0 - jb;                 // trailing rows
-    const int r2 = rl - jb;
-    if (r2 >= 0 && r2 < ((m + TS - 1) / TS) * TS) {
+          for (int c = 0; c < kPB; ++c) {
+            if (c >= jb) break;
+            const double l = a[c] * s_ri[c];
+            a[c] = l;
 #pragma unroll
-      for (int c = 0; c < kPB; ++c) Lp[c * ls + r2] = (r2 < m && c < jb) ? a[c] : 0.0;
-    }
-    __syncthreads();
-    if (m > 0) {
-      const int nt = (m + TS - 1) / TS;
-      const int ntile = nt * (nt + 1) / 2;
-      const int g0 = j0 + jb;
-      for (int q = tid; q < ntile; q += NT) {
-        int I = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
-        while (I * (I + 1) / 2 > q) --I;
-        while ((I + 1) * (I + 2) / 2 <= q) ++I;
-        const int J = q - I * (I + 1) / 2;
-        double acc[TS][TS];
-#pragma unroll
-        for (int u = 0; u < TS; ++u)
-#pragma unroll
-          for (int v = 0; v < TS; ++v) {
-            const int gi = g0 + TS * I + u, gk = g0 + TS * J + v;
-            acc[u][v] = (gi < d && gk <= gi) ? A[pidx(gi, gk)] : 0.0;
-          }
-        for (int c = 0; c < jb; ++c) {
-          double av[TS], bv[TS];
-#pragma unroll
-          for (int h = 0; h < TS; h += 2) {
-            const double2 x = *reinterpret_cast<const double2*>(Lp + c * ls + TS * I + h);
-            const double2 y = *reinterpret_cast<const double2*>(Lp + c * ls + TS * J + h);
-            av[h] = x.x, av[h + 1] = x.y, bv[h] = y.x, bv[h + 1] = y.y;
+            for (int c2 = c + 1; c2 < kPB; ++c2)
+              if (c2 < jb) a[c2] = fma(-l, Pl[c2][c], a[c2]);
           }
 #pragma unroll
-          for (int u = 0; u < TS; ++u)
-#pragma unroll
-            for (int v = 0; v < TS; ++v) acc[u][v] = fma(-av[u], bv[v], acc[u][v]);
+          for (int c = 0; c < kPB; ++c)
+            if (c < jb) A[pidx(i, j0 + c)] = a[c];
         }
 #pragma unroll
-        for (int u = 0; u < TS; ++u)
-#pragma unroll
-          for (int v = 0; v < TS; ++v) {
-            const int gi = g0 + TS * I + u, gk = g0 + TS * J + v;
-            if (gi < d && gk <= gi) A[pidx(gi, gk)] = acc[u][v];
-          }
+        for (int c = 0; c < kPB; ++c) Lp[c * ls + t] = a[c];
       }
+      __syncthreads();
+      // (3) this panel's update of the next panel's columns (rows >= g)
+      if (m > 0) {
+        const int nt = mr / TS, jn = min(J0, nt);
+        const int ntile = jn * nt - jn * (jn - 1) / 2;   // sum over J < jn of (nt - J)
+        for (int q = tid; q < ntile; q += NT) {
+          int J = 0, rem = q;
+          while (rem >= nt - J) rem -= nt - J, ++J;
+          tile(g, J + rem, J, jb);
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
+  } else {
+    for (int j0 = 0; j0 < d; j0 += kPB) {
+      const int jb = min(kPB, d - j0);
+      const int rl = tid, i = j0 + rl;          // this thread's row (d - j0 <= NT)
+      const bool own = i < d;
+      double a[kPB];
+#pragma unroll
+      for (int c = 0; c < kPB; ++c) a[c] = (own && c < jb && c <= rl) ? A[pidx(i, j0 + c)] : 0.0;
+      if (own && rl == 0) pivot(a[0], 0, j0);
+      __syncthreads();
+#pragma unroll
+      for (int jj = 0; jj < kPB; ++jj) {
+        if (jj >= jb) break;
+        // scale this row's entry of column jj; panel rows publish theirs
+        double lij = 0.0;
+        if (own && rl > jj) {
+          lij = a[jj] * s_ri[jj];
+          a[jj] = lij;
+          if (rl < jb) Pl[rl][jj] = lij;
+        }
+        __syncthreads();
+        // update this row's later panel entries; the next pivot's row takes its pivot
+        if (own && rl > jj) {
+#pragma unroll
+          for (int c = jj + 1; c < kPB; ++c)
+            if (c < jb && c <= rl) a[c] = fma(-lij, Pl[c][jj], a[c]);
+          if (rl == jj + 1 && rl < jb) pivot(a[min(jj + 1, kPB - 1)], jj + 1, i);
+        }
+        __syncthreads();
+      }
+      // the panel's final entries back into A; L21 (rows below the panel) into
+      // its column-major copy, zero-padded to whole tiles
+      if (own) {
+#pragma unroll
+        for (int c = 0; c < kPB; ++c)
+          if (c < jb && c <= rl) A[pidx(i, j0 + c)] = a[c];
+      }
+      const int m = d - j0 - jb;                 // trailing rows
+      const int r2 = rl - jb;
+      if (r2 >= 0 && r2 < ((m + TS - 1) / TS) * TS) {
+#pragma unroll
+        for (int c = 0; c < kPB; ++c) Lp[c * ls + r2] = (r2 < m && c < jb) ? a[c] : 0.0;
+      }
+      __syncthreads();
+      if (m > 0) {
+        const int nt = (m + TS - 1) / TS;
+        const int ntile = nt * (nt + 1) / 2;
+        for (int q = tid; q < ntile; q += NT) {
+          int I, J;
+          tri(q, I, J);
+          tile(j0 + jb, I, J, jb);
+        }
+      }
+      __syncthreads();
+    }
   }
 
   __syncthreads();
@@ -166,7 +287,6 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   // columns right to left; with T = the already inverted trailing part of the
   // block, column j becomes -(1/l_jj) T l_col (lane i computes row i), so no
   // per-lane arrays are needed and the kernel keeps few registers.
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nblk = inv ? (d + kNB - 1) / kNB : 0;
   for (int bk = warp; bk < nblk; bk += NT / 32) {
     const int j0 = bk * kNB;
@@ -200,7 +320,7 @@ __global__ void __launch_bounds__(NT, MINB) chol_kernel(const double* __restrict
                                                     int64_t t0, bool inv) {
   const int t = blockIdx.x;
   const int64_t P = packed_size(d);
-  chol_body<TS, NT>(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err,
+  chol_body<TS, NT, MINB == 1>(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err,
                     t0 + t, inv);
 }
 
@@ -312,7 +432,7 @@ cudaError_t configure_factor_kernels() {
     e = cudaFuncSetAttribute(chol_kernel<2, 1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              m);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(chol_kernel<4, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(chol_kernel<2, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              m);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(b_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
@@ -343,8 +463,8 @@ void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, 
     if (n_sm <= 0) n_sm = 1;
   }
   const size_t sm = chol_smem(d);
-  if (d > 128)   // one CTA per SM: 512 threads to cover its barriers and DFMA latency
-    chol_kernel<4, 1, 512><<<T, 512, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
+  if (d > 128)   // one CTA per SM: look-ahead, 2 x 2 tiles (a finer dynamic tail than 4 x 4)
+    chol_kernel<2, 1, 512><<<T, 512, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
   else if (T < n_sm)
     chol_kernel<2, 1, 1024><<<T, 1024, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
   else
