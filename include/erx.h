@@ -311,18 +311,22 @@ erx_status erx_get_drift(erx_ctx* ctx, double* last_corr, double* min_corr, int6
  * A step is six phase kernels launched once for the whole batch (line means,
  * centred scatter, EMA update, FP64 factor, scores, normalisation) with work
  * lists mapping CTAs to (stream, tile); it is captured once in a CUDA graph and
- * replayed.  Limits: float32 input, no projection, bands <= 224, one form for
- * the whole batch. */
+ * replayed.  Limits: float32 input, bands <= 224, one form for the whole batch.
+ * Projection: none, or the learned codes of one encoder shared by the batch
+ * (streams with proj ERX_PROJ_LEARNED; see erx_batch_set_encoder). */
 typedef struct erx_batch erx_batch;
 
 /* Create a batch of n streams from cfgs[0..n-1] (all with the same form and
- * in_dtype ERX_F32, proj ERX_PROJ_NONE).  Allocates per-stream state, one
- * input line and one output line per stream on the current device. */
+ * in_dtype ERX_F32; proj ERX_PROJ_NONE, or ERX_PROJ_LEARNED with proj_dim = the
+ * encoder's code count k, every learned stream with the same bands and k).
+ * Allocates per-stream state, one input line and one output line per stream on
+ * the current device; learned streams also get a codes line (width x k). */
 erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream,
                             erx_batch** out);
 
 /* The batch-owned device buffers of stream i: the input line (width x bands
- * float, written by the caller or by erx_batch_push) and the scores of the
+ * float, written by the caller or by erx_batch_push; the raw spectra for a
+ * learned stream) and the scores of the
  * last step (delta and delta_N: double for ERX_FORM_FP64, float otherwise;
  * mask: width bytes; detecting: 1 byte).  Any out pointer may be NULL. */
 erx_status erx_batch_buffers(erx_batch* b, int32_t i, float** line_dev, void** delta_dev,
@@ -332,6 +336,17 @@ erx_status erx_batch_buffers(erx_batch* b, int32_t i, float** line_dev, void** d
  * n device pointers (an entry may be NULL) whose lines are first copied into
  * the streams' input buffers by one gather kernel.  Asynchronous. */
 erx_status erx_batch_push(erx_batch* b, const float* const* lines_dev);
+
+/* Attach the band encoder of the batch's learned streams (Sec. V names learned
+ * band reduction as future work; the encoder is this library's extension):
+ * each step first maps every learned stream's line to its codes with one
+ * encoder forward over all of them (tensor cores, BF16 operands, FP32
+ * results), and ERX then runs on the codes.  enc must have bands and k equal to
+ * the learned streams' bands and proj_dim (ERX_EINVAL otherwise, and when the
+ * batch has no learned stream) and must outlive the batch or be replaced.
+ * Re-captures the step.  A batch with learned streams returns ERX_ESTATE from
+ * erx_batch_push until an encoder is attached. */
+erx_status erx_batch_set_encoder(erx_batch* b, erx_encoder* enc);
 
 /* Wait for the batch's stream; report ERX_ENOTPD / ERX_ETIMEOUT raised since
  * the last call, with the index of the first offending stream. */

@@ -7,7 +7,9 @@
 // per-stream parameters, including the line count, live in a device table, so
 // the step is captured once in a CUDA graph and replayed.  The score kernel of
 // each band count is chosen by an autotuner that times the candidate kernels
-// on the batch itself.
+// on the batch itself.  Streams on learned codes share one encoder: their raw
+// lines sit in one contiguous buffer and their codes in another, so a single
+// encoder forward over all their pixels opens the step.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -40,8 +42,8 @@ __global__ void gather_kernel(const float* const* __restrict__ src, const BStrea
   const BStream& s = S[blockIdx.y];
   const float* p = src[blockIdx.y];
   if (!p) return;
-  float* dst = const_cast<float*>(s.x);
-  const int64_t n = (int64_t)s.W * s.d;
+  float* dst = s.xin ? s.xin : const_cast<float*>(s.x);
+  const int64_t n = (int64_t)s.W * (s.xin ? s.b_in : s.d);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     dst[i] = p[i];
@@ -68,6 +70,12 @@ struct erx_batch {
   int n_solve[kRoutes] = {};
   int n_hi0 = 0, dmax_lo0 = 1;   // FP64 route: items of streams with d > 128; largest other d
   unsigned long long* err = nullptr;
+  // learned streams: raw lines [sum W][b_in] and codes [sum W][k], stream order
+  int n_learned = 0, learned_b = 0, learned_k = 0;
+  int64_t learned_pix = 0;
+  float* xin = nullptr;
+  float* codes = nullptr;
+  erx_encoder* enc = nullptr;
   // graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -180,6 +188,8 @@ erx_status upload_table(erx_batch* b) {
 
 void enqueue_step(erx_batch* b, cudaStream_t st) {
   const bool fp64 = b->form == ERX_FORM_FP64;
+  if (b->enc && b->learned_pix > 0)
+    encoder_forward_on(b->enc, b->xin, b->learned_pix, b->codes, st);
   launch_batch_mean(b->table, b->n, !fp64, st);
   launch_batch_stats(b->table, b->stats_items, b->n_stats, fp64, st);
   launch_batch_ema(b->table, b->ema_items, b->n_ema, st);
@@ -236,9 +246,17 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
         c.form != form)
       return ERX_EINVAL;
     if (c.averaging != ERX_AVG_EMA) return ERX_EUNSUPPORTED;
-    if (c.in_dtype != ERX_F32 || c.proj != ERX_PROJ_NONE || c.bands > kMaxDim ||
-        c.width > (1 << 20))
+    if (c.proj == ERX_PROJ_LEARNED) {
+      // one encoder for the batch: all learned streams share bands and k
+      if (c.proj_dim < 1 || c.proj_dim > kMaxDim || c.bands > (1 << 16)) return ERX_EINVAL;
+      for (int j = 0; j < i; ++j)
+        if (cfgs[j].proj == ERX_PROJ_LEARNED &&
+            (cfgs[j].bands != c.bands || cfgs[j].proj_dim != c.proj_dim))
+          return ERX_EINVAL;
+    } else if (c.proj != ERX_PROJ_NONE || c.bands > kMaxDim) {
       return ERX_EUNSUPPORTED;
+    }
+    if (c.in_dtype != ERX_F32 || c.width > (1 << 20)) return ERX_EUNSUPPORTED;
   }
   erx_batch* b = new (std::nothrow) erx_batch();
   if (!b) return ERX_ENOMEM;
@@ -248,9 +266,18 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
   b->cfg.assign(cfgs, cfgs + n);
   b->host.resize(n);
   size_t nx = 0, nd = 0, np = 0, ndd = 0, nw = 0;
+  auto dim = [&](int i) {   // ERX dimension of stream i
+    return cfgs[i].proj == ERX_PROJ_LEARNED ? cfgs[i].proj_dim : cfgs[i].bands;
+  };
   for (int i = 0; i < n; ++i) {
-    const int d = cfgs[i].bands, W = cfgs[i].width;
+    const int d = dim(i), W = cfgs[i].width;
     b->dmax = std::max(b->dmax, d);
+    if (cfgs[i].proj == ERX_PROJ_LEARNED) {
+      b->n_learned += 1;
+      b->learned_b = cfgs[i].bands;
+      b->learned_k = d;
+      b->learned_pix += W;
+    }
     nx += (size_t)W * d;
     nd += d;
     np += (size_t)packed_size(d);
@@ -268,6 +295,7 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
 #define BA(p, cnt) \
   if (s == ERX_OK) s = balloc(b, &p, cnt)
   BA(ax, nx);
+  if (b->n_learned) BA(b->xin, (size_t)b->learned_pix * b->learned_b);
   BA(amu, nd);
   BA(amh, nd);
   BA(ash, nd);
@@ -286,13 +314,28 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
   BA(b->ptr_dev, (size_t)n);
 #undef BA
   if (s == ERX_OK) {
-    size_t ox = 0, od = 0, op = 0, odd = 0, ow = 0;
+    // line buffers: the learned streams' codes first, contiguous in stream
+    // order (one encoder forward writes them all), then the other streams
+    size_t ox = (size_t)b->learned_pix * b->learned_k, oc = 0, oin = 0;
+    size_t od = 0, op = 0, odd = 0, ow = 0;
+    b->codes = ax;
     std::vector<BItem> st_items, ema_items;
     for (int i = 0; i < n; ++i) {
       const erx_config& c = cfgs[i];
-      const int d = c.bands, W = c.width;
+      const int d = dim(i), W = c.width;
       BStream& e = b->host[i];
-      e.x = ax + ox;
+      if (c.proj == ERX_PROJ_LEARNED) {
+        e.x = ax + oc;
+        e.xin = b->xin + oin;
+        e.b_in = c.bands;
+        oc += (size_t)W * d;
+        oin += (size_t)W * c.bands;
+      } else {
+        e.x = ax + ox;
+        e.xin = nullptr;
+        e.b_in = 0;
+        ox += (size_t)W * d;
+      }
       e.W = W;
       e.d = d;
       e.route = native_route(form);
@@ -319,7 +362,6 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
         st_items.push_back({i, k});
       const int64_t ne = packed_size(d) + d;
       for (int k = 0; k < (int)((ne + 127) / 128); ++k) ema_items.push_back({i, k});
-      ox += (size_t)W * d;
       od += d;
       op += (size_t)packed_size(d);
       odd += (size_t)d * d;
@@ -350,7 +392,8 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
                           cudaSuccess ||
                       cudaDeviceSynchronize() != cudaSuccess))
     s = ERX_ECUDA;
-  if (s == ERX_OK) s = capture(b);
+  // a batch with learned streams is captured when its encoder is attached
+  if (s == ERX_OK && !b->n_learned) s = capture(b);
   if (s != ERX_OK) {
     cudaGetLastError();
     bfree(b);
@@ -361,11 +404,25 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
   return ERX_OK;
 }
 
+erx_status erx_batch_set_encoder(erx_batch* b, erx_encoder* enc) {
+  if (!b || !enc || !b->n_learned || encoder_bands(enc) != b->learned_b ||
+      encoder_k(enc) != b->learned_k)
+    return ERX_EINVAL;
+  if (b->failed) return ERX_ECUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    b->failed = true;
+    return ERX_ECUDA;
+  }
+  b->enc = enc;
+  return capture(b);
+}
+
 erx_status erx_batch_buffers(erx_batch* b, int32_t i, float** line_dev, void** delta_dev,
                              void** delta_norm_dev, uint8_t** mask_dev, uint8_t** detecting_dev) {
   if (!b || i < 0 || i >= b->n) return ERX_EINVAL;
   const BStream& e = b->host[i];
-  if (line_dev) *line_dev = const_cast<float*>(e.x);
+  if (line_dev) *line_dev = e.xin ? e.xin : const_cast<float*>(e.x);
   if (delta_dev) *delta_dev = e.delta;
   if (delta_norm_dev) *delta_norm_dev = e.dn;
   if (mask_dev) *mask_dev = e.mask;
@@ -376,6 +433,7 @@ erx_status erx_batch_buffers(erx_batch* b, int32_t i, float** line_dev, void** d
 erx_status erx_batch_push(erx_batch* b, const float* const* lines_dev) {
   if (!b) return ERX_EINVAL;
   if (b->failed) return ERX_ECUDA;
+  if (b->n_learned && !b->enc) return ERX_ESTATE;
   if (lines_dev) {
     const int slot = b->ptr_slot;
     b->ptr_slot ^= 1;
@@ -386,8 +444,10 @@ erx_status erx_batch_push(erx_batch* b, const float* const* lines_dev) {
     }
     std::memcpy(b->ptr_host[slot], lines_dev, sizeof(float*) * b->n);
     int wmax = 1;
-    for (int i = 0; i < b->n; ++i)
-      wmax = std::max<int64_t>(wmax, ((int64_t)b->host[i].W * b->host[i].d + 255) / 256);
+    for (int i = 0; i < b->n; ++i) {
+      const BStream& h = b->host[i];
+      wmax = std::max<int64_t>(wmax, ((int64_t)h.W * (h.xin ? h.b_in : h.d) + 255) / 256);
+    }
     if (cudaMemcpyAsync(b->ptr_dev, b->ptr_host[slot], sizeof(float*) * b->n,
                         cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
         cudaEventRecord(b->ptr_ev[slot], b->stream) != cudaSuccess) {

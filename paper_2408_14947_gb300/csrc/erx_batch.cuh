@@ -10,7 +10,9 @@ namespace erx {
 constexpr int kRoutes = 5;   // score kernels a stream can be routed to
 
 struct BStream {
-  const float* x;        // the stream's current line, [W][d] float32 (device)
+  const float* x;        // the stream's current line, [W][d] float32 (device); codes if learned
+  float* xin;            // learned streams: the raw line [W][b_in] the gather writes; else null
+  int b_in;
   int W, d;
   int route;             // score kernel: 0 FP64, 1 FP32 SIMT, 2 TF32 MMA, 3 BF16 MMA,
                          // 4 3xTF32 MMA

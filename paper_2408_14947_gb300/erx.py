@@ -112,6 +112,7 @@ def load_library() -> C.CDLL:
         "erx_batch_get_state": (C.c_int, [P, I32, C.POINTER(I64), P, P]),
         "erx_batch_route": (C.c_int, [P, I32, C.POINTER(I32)]),
         "erx_batch_tune": (C.c_int, [P, I32, C.c_char_p]),
+        "erx_batch_set_encoder": (C.c_int, [P, P]),
         "erx_batch_destroy": (C.c_int, [P]),
         "erx_push_lines_static": (C.c_int, [C.POINTER(ErxConfig), P, P, P, C.POINTER(I64), P,
                                             I64, I64, P, P, P, P]),
@@ -387,11 +388,12 @@ class Batch:
     """A batch of independent streams (erx_batch_*), one line each per step.
 
     ``streams`` is a list of dicts with ``bands`` and ``width`` (and optional
-    momentum, ridge, warmup, order, threshold); ``form`` is shared.  Inputs and
-    outputs are batch-owned device buffers exposed as torch tensors.
+    momentum, ridge, warmup, order, threshold, and ``learned``: run ERX on the
+    codes of ``encoder``, shared by all learned streams); ``form`` is shared.
+    Inputs and outputs are batch-owned device buffers exposed as torch tensors.
     """
 
-    def __init__(self, streams, form="fp64", stream=None):
+    def __init__(self, streams, form="fp64", stream=None, encoder=None):
         import torch
         self.torch = torch
         n = len(streams)
@@ -408,7 +410,13 @@ class Batch:
                        "score_then_update": ERX_SCORE_THEN_UPDATE}[sd.get("order",
                                                                       "update_then_score")]
             c.threshold = sd.get("threshold", 3.0)
+            if sd.get("learned"):
+                if encoder is None:
+                    raise ValueError("learned streams need an encoder")
+                c.proj = ERX_PROJ_LEARNED
+                c.proj_dim = encoder.k
         self.n = n
+        self.encoder = encoder
         self.streams = streams
         self.form = form
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -417,6 +425,13 @@ class Batch:
                                                C.byref(h)), "erx_batch_create")
         self.b = h.value
         self._ptrs = (C.c_void_p * n)()
+        if any(sd.get("learned") for sd in streams):
+            _check(load_library().erx_batch_set_encoder(self.b, C.c_void_p(encoder.e)),
+                   "erx_batch_set_encoder")
+
+    def dim(self, i):
+        """ERX dimension of stream i: its bands, or the encoder's k if learned."""
+        return self.encoder.k if self.streams[i].get("learned") else self.streams[i]["bands"]
 
     def buffers(self, i):
         """Raw device pointers (line, delta, delta_n, mask, detecting) of stream i."""
@@ -443,7 +458,7 @@ class Batch:
 
     def state(self, i):
         import numpy as np
-        d = self.streams[i]["bands"]
+        d = self.dim(i)
         t = C.c_int64()
         mu, k = np.zeros(d), np.zeros((d, d))
         _check(load_library().erx_batch_get_state(self.b, i, C.byref(t), mu.ctypes.data,

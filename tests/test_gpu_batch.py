@@ -115,3 +115,77 @@ def test_batch_autotune_and_cache(tmp_path):
     assert [b2.route(i) for i in range(len(SHAPES))] == routes
     b.close()
     b2.close()
+
+
+# Learned streams (codes of one shared encoder) mixed with plain streams: the
+# batch runs one encoder forward over all learned streams' pixels, then the
+# same phase kernels on the codes.
+LEARNED = [(130, 40, True), (96, 16, False), (77, 40, True), (256, 40, True), (50, 64, False)]
+
+
+def _learned_setup(seed=3):
+    from paper_2408_14947_gb300 import Encoder
+    enc = Encoder(40, 24, 8, seed=seed)
+    cubes = []
+    for s, (w, bb, _) in enumerate(LEARNED):
+        cfg = synth.SceneConfig(bands=bb, width=w, seed=seed, stream=s, n_end=(3, 5),
+                                noise=0.01, scene_lines=3, drift=0.05)
+        cubes.append(synth.gen_lines(cfg, 0, STEPS))
+    flat = np.concatenate([c.reshape(-1, 40) for c, (_, bb, lr) in zip(cubes, LEARNED) if lr])
+    enc.set_norm(flat.mean(0), 1.0 / (flat.std(0) + 1e-3))
+    return enc, cubes
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32", "bf16"])
+def test_batch_learned_streams_match_contexts(form):
+    need_gpu()
+    from paper_2408_14947_gb300 import Batch
+    enc, cubes = _learned_setup()
+    b = Batch([{"bands": bb, "width": w, "warmup": 2, "learned": lr} for (w, bb, lr) in LEARNED],
+              form=form, encoder=enc)
+    assert [b.dim(i) for i in range(len(LEARNED))] == [8, 16, 8, 8, 64]
+    dev = [torch.from_numpy(c).cuda() for c in cubes]
+    got = [[] for _ in LEARNED]
+    for t in range(STEPS):
+        b.push([x[t] for x in dev])
+        b.sync()
+        for i in range(len(LEARNED)):
+            v = b.views(i)
+            got[i].append([v[1].cpu().numpy().copy(), v[2].cpu().numpy().copy()])
+    for i, (c, (w, bb, lr)) in enumerate(zip(cubes, LEARNED)):
+        kw = {"encoder": enc} if lr else {}
+        ref, det = run_gpu(c, form=form, warmup=2, push_sizes=[1] * STEPS, simt_stats=True, **kw)
+        assert np.array_equal(np.stack([g[0] for g in got[i]]), ref["delta"]), (form, i)
+        assert np.array_equal(np.stack([g[1] for g in got[i]]), ref["delta_n"]), (form, i)
+        tb, mub, kb = b.state(i)
+        td, mud, kd = det.state()
+        assert tb == td == STEPS and kb.shape == kd.shape and np.array_equal(kb, kd)
+        det.close()
+        if lr and form == "fp64":
+            # and the oracle on the codes the encoder gives for these lines
+            codes = enc.forward(torch.from_numpy(c.reshape(-1, bb)).cuda()).cpu().numpy()
+            ref_o = oracle.run_cube(codes.astype(np.float64).reshape(STEPS, w, -1), warmup=2)
+            assert rel_err(np.stack([g[0] for g in got[i]]), ref_o["delta"]) < 1e-9
+    b.close()
+    enc.close()
+
+
+def test_batch_learned_needs_matching_encoder():
+    need_gpu()
+    import ctypes as C
+
+    from paper_2408_14947_gb300 import Batch, Encoder, ERX_EINVAL
+    from paper_2408_14947_gb300.erx import load_library
+    enc, cubes = _learned_setup()
+    lib = load_library()
+    b = Batch([{"bands": 40, "width": 64, "learned": True}], form="fp32", encoder=enc)
+    for other in (Encoder(40, 24, 6, seed=1), Encoder(32, 24, 8, seed=1)):
+        # another code count or band count than the batch's learned streams
+        assert lib.erx_batch_set_encoder(C.c_void_p(b.b), C.c_void_p(other.e)) == ERX_EINVAL
+        other.close()
+    b.close()
+    # a batch without learned streams takes no encoder
+    p = Batch([{"bands": 16, "width": 64}], form="fp32")
+    assert lib.erx_batch_set_encoder(C.c_void_p(p.b), C.c_void_p(enc.e)) == ERX_EINVAL
+    p.close()
+    enc.close()
