@@ -12,13 +12,14 @@
 // update A22 -= L21 L21^T is a rank-kPB step in TS x TS FP64 register tiles
 // over the lower triangle, reading L21 from a column-major copy.  Two panel
 // schedules:
-//  * column schedule (several CTAs per SM, d <= 128): thread r owns row
+//  * column schedule (d <= 128: several CTAs per SM, or one 1024-thread CTA
+//    per line when fewer lines than SMs are factored): thread r owns row
 //    j0 + r and keeps its panel entries in registers; per column every row
 //    scales its entry by 1/l_jj (the panel rows publish theirs), barrier, then
 //    updates its later panel entries while the next pivot's row takes
 //    l_jj = a_jj rsqrt(a_jj), barrier; then the whole trailing update.  The
 //    other resident CTAs fill the FP64 pipe during the barriers;
-//  * look-ahead schedule (one CTA per SM: d > 128, or fewer lines than SMs),
+//  * look-ahead schedule (d > 128, where one CTA fills an SM),
 //    three barriers per panel:
 //    (1) warp 0 factors the panel's 8 x 8 diagonal block while the other warps
 //        apply the previous panel's update to the trailing triangle right of
@@ -62,10 +63,11 @@ __host__ __device__ inline size_t chol_smem(int d) {
 // `line` is the global line index reported on a bad pivot.  TS: edge of the
 // trailing update's register tiles (2 x 2 everywhere: 4 x 4 tiles need fewer
 // shared-memory loads per DFMA, but their 8k-cycle chunks leave a long uneven
-// tail at every barrier; measured 12 % slower at d = 224).  LA: the look-ahead schedule (one CTA per SM, where
-// barriers cannot be hidden by other CTAs); else the column schedule (several
-// CTAs per SM, where the look-ahead's one-warp block factor costs more FP64
-// issue slots than the barriers it saves).
+// tail at every barrier; measured 12 % slower at d = 224).  LA: the look-ahead
+// schedule (d > 128, one CTA per SM, where barriers cannot be hidden by other
+// CTAs); else the column schedule (several CTAs per SM, where the look-ahead's
+// one-warp block factor costs more FP64 issue slots than the barriers it
+// saves, and single lines at d <= 128, where its block chain is the longer).
 template <int TS, int NT = kThreads, bool LA = false>
 __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d, double ridge,
                                           double* __restrict__ dst, float* __restrict__ d32,
@@ -312,7 +314,7 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   }
 }
 
-template <int TS, int MINB, int NT = kThreads>
+template <int TS, int MINB, int NT = kThreads, bool LA = false>
 __global__ void __launch_bounds__(NT, MINB) chol_kernel(const double* __restrict__ K_t, int d,
                                                     double ridge, double* __restrict__ Lf,
                                                     float* __restrict__ Lf32,
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(NT, MINB) chol_kernel(const double* __restrict
                                                     int64_t t0, bool inv) {
   const int t = blockIdx.x;
   const int64_t P = packed_size(d);
-  chol_body<TS, NT, MINB == 1>(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err,
+  chol_body<TS, NT, LA>(K_t + t * P, d, ridge, Lf + t * P, Lf32 ? Lf32 + t * P : nullptr, err,
                     t0 + t, inv);
 }
 
@@ -432,8 +434,8 @@ cudaError_t configure_factor_kernels() {
     e = cudaFuncSetAttribute(chol_kernel<2, 1, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              m);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(chol_kernel<2, 1, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             m);
+    e = cudaFuncSetAttribute(chol_kernel<2, 1, 512, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(b_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   const int m32 = (int)(packed_size(kMaxDim) * sizeof(float));
@@ -463,8 +465,12 @@ void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, 
     if (n_sm <= 0) n_sm = 1;
   }
   const size_t sm = chol_smem(d);
-  if (d > 128)   // one CTA per SM: look-ahead, 2 x 2 tiles (a finer dynamic tail than 4 x 4)
-    chol_kernel<2, 1, 512><<<T, 512, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
+  // d > 128: one CTA per SM, look-ahead schedule.  Fewer lines than SMs at
+  // d <= 128 (a line pushed alone): the column schedule with 1024 threads, whose
+  // pivot chain is shorter than the look-ahead's one-warp block chain there
+  // (measured: 27 us more per line with the look-ahead at d = 108).
+  if (d > 128)
+    chol_kernel<2, 1, 512, true><<<T, 512, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
   else if (T < n_sm)
     chol_kernel<2, 1, 1024><<<T, 1024, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
   else
