@@ -380,7 +380,7 @@ void enqueue_update(erx_ctx* c, int T, cudaStream_t st) {
     KernelScope ks(c, ERX_K_EMA, st);
     launch_imc_scan(c->int_stats, c->S1i, c->S2i, c->mu_hat, c->shift, c->S2f, k, d, W, c->t,
                     c->cfg.order, c->mu_state, c->K_state, c->mu_t, c->K_t, c->imc_mprev,
-                    c->ema_scratch, st);
+                    c->ema_scratch, st, (c->int_stats ? (1u << c->cfg.in_bits) - 1u : 0xffffu));
   }
   if (k < T) {
     const int64_t dd = (int64_t)d * d;
@@ -389,7 +389,8 @@ void enqueue_update(erx_ctx* c, int T, cudaStream_t st) {
                     c->S2i ? c->S2i + k * dd : nullptr, c->mu_hat ? c->mu_hat + k * d : nullptr,
                     c->shift ? c->shift + k * d : nullptr, c->S2f ? c->S2f + k * dd : nullptr,
                     T - k, d, W, c->cfg.momentum, c->t + k, c->cfg.order, c->mu_state,
-                    c->K_state, c->mu_t + k * d, c->K_t + k * P, c->ema_scratch, st);
+                    c->K_state, c->mu_t + k * d, c->K_t + k * P, c->ema_scratch, st,
+                    (c->int_stats ? (1u << c->cfg.in_bits) - 1u : 0xffffu));
   }
 }
 

@@ -73,11 +73,12 @@ void launch_stats_fp(int in_type, bool fp64, const void* x, int64_t line_stride,
 // statistics each line is scored with and advances the state.  `scratch`
 // holds ema_scratch_doubles(d, T) doubles (NULL: sequential scan).
 size_t ema_scratch_doubles(int d, int T);
+// maxv: the largest sample of integer statistics (it bounds their sums)
 void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      const double* mu_hat, const double* shift, const double* S2f, int T, int d,
                      int W, double alpha, int64_t t0, int order, double* mu_state,
                      double* K_state, double* mu_t, double* K_t, double* scratch,
-                     cudaStream_t st);
+                     cudaStream_t st, uint32_t maxv = 0xffffu);
 
 // IMC (equal-weight ablation, batch Welford) in place of the EMA scan: same
 // outputs; `work` holds imc_work_doubles(d, T) doubles.
@@ -86,7 +87,7 @@ void launch_imc_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      const double* mu_hat, const double* shift, const double* S2f, int T, int d,
                      int W, int64_t t0, int order, double* mu_state, double* K_state,
                      double* mu_t, double* K_t, double* work, double* scratch,
-                     cudaStream_t st);
+                     cudaStream_t st, uint32_t maxv = 0xffffu);
 
 // Cholesky of K_t + ridge I, diagonal blocks inverted, one CTA per line.
 // invert: replace the 32 x 32 diagonal blocks by their inverses in FP64 (the

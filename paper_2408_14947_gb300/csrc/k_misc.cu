@@ -30,9 +30,11 @@ __device__ __forceinline__ double to_d(T v) { return (double)v; }
 // the sequential recursion only by rounding.  Blocks of at most kEmaChunk lines
 // run pass C alone on the state (purely sequential).
 constexpr int kEmaChunk = 32;
+constexpr int kEmaPre = 8;     // line statistics in flight per thread
 
 struct EmaSrc {
   bool int_stats;
+  bool small_ints;   // |W s2 - s1a s1b| <= (W maxv)^2 < 2^51: the exact short conversion applies
   const uint64_t* S1i;
   const uint64_t* S2i;
   const double* mu_hat;
@@ -43,6 +45,20 @@ struct EmaSrc {
   double rw1;    // 1 / (W - 1), correctly rounded
   double rw12;   // 1 / (W (W - 1)), correctly rounded
 };
+
+// v as a double, exactly, for |v| < 2^51: v added to the bits of 1.5 * 2^52 (whose
+// last mantissa bit is worth 1) gives the double 1.5 * 2^52 + v; one exact
+// subtraction removes the offset.  An integer add and one DADD, where the
+// general 64-bit conversion is slower on this part.
+__device__ __forceinline__ double i2d_exact(int64_t v) {
+  return __dsub_rn(__longlong_as_double(0x4338000000000000ll + v), 6755399441055744.0);
+}
+
+// (W maxv)^2 < 2^51 bounds |W s2 - s1a s1b| for samples <= maxv
+inline bool small_ints(int W, uint32_t maxv) {
+  const double m = (double)W * (double)maxv;
+  return m * m < 2251799813685248.0;
+}
 
 // line statistic of element (a, b) (b < 0: the mean of band a) at line t of the block
 __device__ __forceinline__ double ema_stat(const EmaSrc& s, int64_t t, int a, int b) {
@@ -56,7 +72,8 @@ __device__ __forceinline__ double ema_stat(const EmaSrc& s, int64_t t, int a, in
     const int64_t s1a = (int64_t)__ldg(s.S1i + t * s.d + a);
     const int64_t s1b = (int64_t)__ldg(s.S1i + t * s.d + b);
     const int64_t s2 = (int64_t)__ldg(s.S2i + t * dd + ab);
-    return (double)((int64_t)s.W * s2 - s1a * s1b) * s.rw12;
+    const int64_t v = (int64_t)s.W * s2 - s1a * s1b;
+    return (s.small_ints ? i2d_exact(v) : (double)v) * s.rw12;
   }
   const double ea = __dsub_rn(__ldg(s.mu_hat + t * s.d + a), __ldg(s.shift + t * s.d + a));
   const double eb = __dsub_rn(__ldg(s.mu_hat + t * s.d + b), __ldg(s.shift + t * s.d + b));
@@ -88,9 +105,15 @@ __global__ void __launch_bounds__(128) ema_pass_a(EmaSrc s, int T, double alpha,
   const double beta = 1.0 - alpha;
   const int tb = g * kEmaChunk, te = min(T, tb + kEmaChunk);
   double u = 0.0;
-  for (int t = tb; t < te; ++t) {
-    const double kh = ema_stat(s, t, a, b);
-    u = (t0 + t == 0) ? kh : ema_mix(u, kh, alpha, beta);
+  // the line statistics are loaded kEmaPre lines ahead of the recursion, so
+  // their loads overlap instead of each waiting on the last
+  for (int t8 = tb; t8 < te; t8 += kEmaPre) {
+    double kh[kEmaPre];
+#pragma unroll
+    for (int j = 0; j < kEmaPre; ++j) kh[j] = t8 + j < te ? ema_stat(s, t8 + j, a, b) : 0.0;
+#pragma unroll
+    for (int j = 0; j < kEmaPre; ++j)
+      if (t8 + j < te) u = (t0 + t8 + j == 0) ? kh[j] : ema_mix(u, kh[j], alpha, beta);
   }
   E[(int64_t)g * n + q] = u;
 }
@@ -140,14 +163,21 @@ __global__ void __launch_bounds__(128) ema_pass_c(EmaSrc s, int T, double alpha,
   double* st = q < s.P ? Kst + q : must + (q - s.P);
   double v = Cin ? Cin[(int64_t)g * n + q] : *st;
   const int tb = g * kEmaChunk, te = Cin ? min(T, tb + kEmaChunk) : T;
-  for (int t = tb; t < te; ++t) {
-    const double kh = ema_stat(s, t, a, b);
-    const bool first = (t0 + t == 0);
-    const double post = first ? kh : ema_mix(v, kh, alpha, beta);
-    const double out = (order == 0 || first) ? post : v;
-    if (b < 0) mu_t[(int64_t)t * s.d + a] = out;
-    else K_t[(int64_t)t * s.P + q] = out;
-    v = post;
+  for (int t8 = tb; t8 < te; t8 += kEmaPre) {
+    double kh[kEmaPre];
+#pragma unroll
+    for (int j = 0; j < kEmaPre; ++j) kh[j] = t8 + j < te ? ema_stat(s, t8 + j, a, b) : 0.0;
+#pragma unroll
+    for (int j = 0; j < kEmaPre; ++j) {
+      const int t = t8 + j;
+      if (t >= te) break;
+      const bool first = (t0 + t == 0);
+      const double post = first ? kh[j] : ema_mix(v, kh[j], alpha, beta);
+      const double out = (order == 0 || first) ? post : v;
+      if (b < 0) mu_t[(int64_t)t * s.d + a] = out;
+      else K_t[(int64_t)t * s.P + q] = out;
+      v = post;
+    }
   }
   if (!Cin) *st = v;
 }
@@ -415,11 +445,11 @@ void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      const double* mu_hat, const double* shift, const double* S2f, int T, int d,
                      int W, double alpha, int64_t t0, int order, double* mu_state,
                      double* K_state, double* mu_t, double* K_t, double* scratch,
-                     cudaStream_t st) {
+                     cudaStream_t st, uint32_t maxv) {
   // both reciprocals correctly rounded on the host (IEEE division), as
   // __drcp_rn and the device's double division would give
   const double Wd = (double)W;
-  EmaSrc s{int_stats, S1i,    S2i, mu_hat, shift, S2f, d, W, packed_size(d),
+  EmaSrc s{int_stats, small_ints(W, maxv), S1i, S2i, mu_hat, shift, S2f, d, W, packed_size(d),
            1.0 / (Wd - 1.0), 1.0 / (Wd * (Wd - 1.0))};
   const int64_t n = s.P + d;
   const unsigned bx = (unsigned)((n + 127) / 128);
@@ -441,9 +471,9 @@ void launch_imc_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      const double* mu_hat, const double* shift, const double* S2f, int T, int d,
                      int W, int64_t t0, int order, double* mu_state, double* K_state,
                      double* mu_t, double* K_t, double* work, double* scratch,
-                     cudaStream_t st) {
+                     cudaStream_t st, uint32_t maxv) {
   const double Wd = (double)W;
-  EmaSrc s{int_stats, S1i,    S2i, mu_hat, shift, S2f, d, W, packed_size(d),
+  EmaSrc s{int_stats, small_ints(W, maxv), S1i, S2i, mu_hat, shift, S2f, d, W, packed_size(d),
            1.0 / (Wd - 1.0), 1.0 / (Wd * (Wd - 1.0))};
   const int G = (T + kEmaChunk - 1) / kEmaChunk;
   double* dlt = work;                         // T x d

@@ -80,7 +80,7 @@ __host__ __device__ inline int tc_stage_bytes(int d, int fmt) {
 template <typename InT, bool VEC>
 __device__ __forceinline__ void load_chunk(const InT* __restrict__ xp, bool valid, int k0, int d,
                                            float (&v)[kB]) {
-  if constexpr (VEC) {
+  if constexpr (VEC && sizeof(InT) == 4) {
     // float lines, 16-byte aligned pixel rows, d a multiple of 4
 #pragma unroll
     for (int u = 0; u < kB / 4; ++u) {
@@ -88,6 +88,16 @@ __device__ __forceinline__ void load_chunk(const InT* __restrict__ xp, bool vali
       float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
       if (valid && k < d) f = __ldg(reinterpret_cast<const float4*>(xp + k));
       v[4 * u] = f.x, v[4 * u + 1] = f.y, v[4 * u + 2] = f.z, v[4 * u + 3] = f.w;
+    }
+  } else if constexpr (VEC) {
+    // u16 lines, 8-byte aligned pixel rows, d a multiple of 4: four samples per load
+#pragma unroll
+    for (int u = 0; u < kB / 4; ++u) {
+      const int k = k0 + 4 * u;
+      uint2 w = make_uint2(0u, 0u);
+      if (valid && k < d) w = __ldg(reinterpret_cast<const uint2*>(xp + k));
+      v[4 * u] = (float)(w.x & 0xffffu), v[4 * u + 1] = (float)(w.x >> 16);
+      v[4 * u + 2] = (float)(w.y & 0xffffu), v[4 * u + 3] = (float)(w.y >> 16);
     }
   } else {
 #pragma unroll
@@ -331,6 +341,9 @@ cudaError_t configure_solve_tc_kernels() {
   ERX_CFG_T(uint16_t)
   ERX_CFG_T(float)
   ERX_CFG_T(double)
+  ERX_CFG((solve_tc_kernel<uint16_t, 1, true>), m1);
+  ERX_CFG((solve_tc_kernel<uint16_t, 2, true>), m2);
+  ERX_CFG((solve_tc_kernel<uint16_t, 3, true>), m3);
   ERX_CFG((solve_tc_kernel<float, 1, true>), m1);
   ERX_CFG((solve_tc_kernel<float, 2, true>), m2);
   ERX_CFG((solve_tc_kernel<float, 3, true>), m3);
@@ -355,14 +368,18 @@ void launch_solve_tc(int fmt, int in_type, const void* x, int64_t line_stride, i
                      unsigned long long* err, int64_t t0, cudaStream_t st) {
   dim3 grid((W + kPix - 1) / kPix, T);
   const size_t sm = launch_smem(d, fmt);
-  // vector loads: float lines whose pixel rows start on 16 bytes
+  // vector loads: float lines whose pixel rows start on 16 bytes, u16 lines
+  // whose pixel rows start on 8 bytes (four samples per load either way)
   const bool vec = in_type == 1 && ((uintptr_t)x % 16) == 0 && (ps % 4) == 0 &&
                    (line_stride % 4) == 0 && (d % 4) == 0;
+  const bool vec16 = in_type == 0 && ((uintptr_t)x % 8) == 0 && (ps % 4) == 0 &&
+                     (line_stride % 4) == 0 && (d % 4) == 0;
 #define ERX_L(IT, F, V)                                                                  \
   solve_tc_kernel<IT, F, V><<<grid, kPix, sm, st>>>((const IT*)x, line_stride, ps, W, d, \
                                                     mu_t, Lf32, delta, err, t0)
 #define ERX_LF(F)                          \
-  if (in_type == 0) ERX_L(uint16_t, F, false); \
+  if (vec16) ERX_L(uint16_t, F, true);     \
+  else if (in_type == 0) ERX_L(uint16_t, F, false); \
   else if (vec) ERX_L(float, F, true);     \
   else if (in_type == 1) ERX_L(float, F, false); \
   else ERX_L(double, F, false);

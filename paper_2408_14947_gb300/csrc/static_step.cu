@@ -156,7 +156,8 @@ extern "C" erx_status erx_push_lines_static(const erx_config* cfg, void* cuda_st
       launch_stats_fp(cfg->in_dtype, fp64, x, stride, d, W, d, 1, shift, S2f, st);
     }
     launch_ema_scan(int_stats, S1i, S2i, mu_hat, shift, S2f, 1, d, W, cfg->momentum, t,
-                    cfg->order, mu_dev, K_dev, mu_t, K_t, nullptr, st);
+                    cfg->order, mu_dev, K_dev, mu_t, K_t, nullptr, st,
+                    int_stats ? (1u << cfg->in_bits) - 1u : 0xffffu);
     launch_chol_inv(K_t, d, 1, cfg->ridge, Linv, fp64 ? nullptr : Linv32, err, t, st, fp64);
     if (!fp64) launch_trinv32(Linv32, d, 1, st);
     if (fp64)
