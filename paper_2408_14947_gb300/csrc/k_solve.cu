@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(H * kPixF64) b_solve_fp64_kernel(
 
 constexpr int kPixF32 = 64;   // pixels per CTA
 constexpr int kOutB = kNB;    // outputs per block of the factor
+constexpr int kLS = kOutB + 4;   // row pitch of the staged factor band (16-byte multiple)
 
 template <typename InT>
 __device__ __forceinline__ void solve_fp32_body(const InT* __restrict__ x, int ps, int W, int d,
@@ -203,7 +204,7 @@ __device__ __forceinline__ void solve_fp32_body(const InT* __restrict__ x, int p
                                                 float* __restrict__ delta, int tile) {
   extern __shared__ __align__(16) float smf[];
   float* rT = smf;                          // [d][kPixF32]: r, k-major
-  float* LT = smf + d * kPixF32;            // [d][kOutB]: rows of L^{-1}, k-major
+  float* LT = smf + d * kPixF32;            // [d][kLS]: rows of L^{-1}, k-major
   __shared__ float mu_hi[kMaxDim], mu_lo[kMaxDim];
   __shared__ float d2w[2][kPixF32];
   const int i0 = tile * kPixF32;
@@ -214,11 +215,39 @@ __device__ __forceinline__ void solve_fp32_body(const InT* __restrict__ x, int p
     mu_lo[k] = (float)(m - (double)h);
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kPixF32 * d; e += 128) {
-    const int p = e / d, k = e - p * d, i = i0 + p;
-    float v = 0.f;
-    if (i < W) v = (to_f(x[(int64_t)i * ps + k]) - mu_hi[k]) - mu_lo[k];
-    rT[k * kPixF32 + p] = v;
+  // pixel-fastest, so the transposed stores hit distinct banks.  Where pixel
+  // rows allow it, four consecutive bands per load (16 bytes of float, 8 of u16)
+  constexpr bool kVecIn = sizeof(InT) <= 4;
+  const bool vec = kVecIn && (d % 4) == 0 && (ps % 4) == 0 &&
+                   ((uintptr_t)x % (4 * sizeof(InT))) == 0;
+  if (vec) {
+    const int p = threadIdx.x & (kPixF32 - 1), i = i0 + p;
+    const InT* xp = x + (int64_t)(i < W ? i : 0) * ps;
+#pragma unroll 4
+    for (int k4 = (threadIdx.x / kPixF32) * 4; k4 < d; k4 += 8) {
+      float v[4] = {0.f, 0.f, 0.f, 0.f};
+      if (i < W) {
+        if constexpr (sizeof(InT) == 4) {
+          const float4 f = __ldg(reinterpret_cast<const float4*>(xp + k4));
+          v[0] = f.x, v[1] = f.y, v[2] = f.z, v[3] = f.w;
+        } else if constexpr (sizeof(InT) == 2) {
+          const uint2 w = __ldg(reinterpret_cast<const uint2*>(xp + k4));
+          v[0] = (float)(w.x & 0xffffu), v[1] = (float)(w.x >> 16);
+          v[2] = (float)(w.y & 0xffffu), v[3] = (float)(w.y >> 16);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = (v[u] - mu_hi[k4 + u]) - mu_lo[k4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) rT[(k4 + u) * kPixF32 + p] = v[u];
+    }
+  } else {
+    for (int e = threadIdx.x; e < kPixF32 * d; e += 128) {
+      const int k = e / kPixF32, p = e - k * kPixF32, i = i0 + p;
+      float v = 0.f;
+      if (i < W) v = (to_f(x[(int64_t)i * ps + k]) - mu_hi[k]) - mu_lo[k];
+      rT[k * kPixF32 + p] = v;
+    }
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ph = warp & 1, oh = warp >> 1;
@@ -229,9 +258,11 @@ __device__ __forceinline__ void solve_fp32_body(const InT* __restrict__ x, int p
   for (int j0 = 0; j0 < d; j0 += kOutB) {
     const int j1 = min(d, j0 + kOutB);
     __syncthreads();
-    for (int e = threadIdx.x; e < j1 * kOutB; e += 128) {
-      const int k = e / kOutB, jj = e % kOutB, j = j0 + jj;
-      LT[k * kOutB + jj] = (j < d && k <= j) ? Lg[j * (j + 1) / 2 + k] : 0.f;
+    // one warp per row of the band, lanes along k: each row is read contiguously
+    for (int jj = warp; jj < kOutB; jj += 4) {
+      const int j = j0 + jj;
+      const float* Lj = Lg + j * (j + 1) / 2;
+      for (int k = lane; k < j1; k += 32) LT[k * kLS + jj] = (j < d && k <= j) ? Lj[k] : 0.f;
     }
     __syncthreads();
     // m_J = X_{J, k < j1} r (X = L^{-1}: lower triangular, zeros above the diagonal)
@@ -243,7 +274,7 @@ __device__ __forceinline__ void solve_fp32_body(const InT* __restrict__ x, int p
 #pragma unroll 4
     for (int k = 0; k < j1; ++k) {
       const float4 rv = *reinterpret_cast<const float4*>(rT + k * kPixF32 + pcol);
-      const float4 lv = *reinterpret_cast<const float4*>(LT + k * kOutB + ocol);
+      const float4 lv = *reinterpret_cast<const float4*>(LT + k * kLS + ocol);
       const float ra[4] = {rv.x, rv.y, rv.z, rv.w};
       const float la[4] = {lv.x, lv.y, lv.z, lv.w};
 #pragma unroll
@@ -294,7 +325,7 @@ __global__ void __launch_bounds__(128) b_solve_fp32_kernel(const BStream* __rest
 
 size_t smem_fp64(int d) { return (size_t)kPixF64 * (d | 1) * sizeof(double); }
 size_t smem_fp32(int d) {
-  return (size_t)d * (kPixF32 + kOutB) * sizeof(float);
+  return (size_t)d * (kPixF32 + kLS) * sizeof(float);
 }
 
 }  // namespace
