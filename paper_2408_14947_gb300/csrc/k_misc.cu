@@ -351,8 +351,9 @@ __device__ __forceinline__ void normalise_body(const ST* __restrict__ dl, int W,
     v = __fma_rn(e, e, v);
   }
   const double sd = sqrt(block_sum(v, sh) / (double)W);
+  const double rsd = sd > 0.0 ? 1.0 / sd : 0.0;   // one division per line, not per pixel
   for (int i = threadIdx.x; i < W; i += blockDim.x) {
-    const double z = sd > 0.0 ? (to_d(dl[i]) - mean) / sd : 0.0;
+    const double z = (to_d(dl[i]) - mean) * rsd;
     if (dn) dn[i] = (ST)z;
     if (mask) mask[i] = (uint8_t)(z >= threshold);
   }
