@@ -306,7 +306,10 @@ erx_status run_block(erx_ctx* c, const void* x, int64_t n, int64_t stride_elems,
   {
     KernelScope ks(c, ERX_K_CHOL);
     launch_chol_inv(c->K_t, d, T, c->cfg.ridge, c->Linv, c->fp64 ? nullptr : c->Linv32, c->err,
-                    c->t, st, c->fp64);
+                    c->t, st, c->fp64,
+                    // FP64E: the previous block's score runs on the FP32 pipe beside the
+                    // FP64 factor (measured +7 %); the other forms gain nothing from it
+                    slot >= 0 && c->cfg.form == ERX_FORM_FP64E);
   }
   cudaStream_t sb = st;
   if (slot >= 0) {

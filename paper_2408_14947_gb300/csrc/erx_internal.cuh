@@ -94,7 +94,8 @@ void launch_imc_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
 // FP64 score kernels and the encoder's loss need them; the FP32 routes invert
 // them in trinv32 instead)
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Linv, float* Linv32,
-                     unsigned long long* err, int64_t t0, cudaStream_t st, bool invert = true);
+                     unsigned long long* err, int64_t t0, cudaStream_t st, bool invert = true,
+                     bool leave_room = false);
 
 // In place: the float blocked factor of T lines becomes the full L^{-1} (FP32).
 void launch_trinv32(float* Lf32, int d, int T, cudaStream_t st);

@@ -452,16 +452,18 @@ void launch_batch_chol(const BStream* S, int n, int dmax, bool want32, unsigned 
 }
 
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, float* Lf32,
-                     unsigned long long* err, int64_t t0, cudaStream_t st, bool invert) {
+                     unsigned long long* err, int64_t t0, cudaStream_t st, bool invert,
+                     bool leave_room) {
   // above 128 dimensions the factor fills an SM's shared memory: one CTA per SM.
   // Fewer lines than SMs (a line or a few pushed alone): one CTA per SM anyway,
   // so each takes more threads (as many as its registers allow) to hide the
   // latency of its barriers and DFMA chains.
-  static int n_sm = 0;
+  static int n_sm = 0, smem_sm = 0;
   if (!n_sm) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (n_sm <= 0) n_sm = 1;
   }
   const size_t sm = chol_smem(d);
@@ -473,8 +475,14 @@ void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, 
     chol_kernel<2, 1, 512, true><<<T, 512, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
   else if (T < n_sm)
     chol_kernel<2, 1, 1024><<<T, 1024, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
-  else
-    chol_kernel<2, 4><<<T, kThreads, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
+  else {
+    // leave_room: at most three CTAs per SM (a quarter of the SM's shared memory
+    // requested), so the score kernels of the previous block, on another
+    // stream, find registers and shared memory beside the factor
+    const size_t room = smem_sm > 0 ? (size_t)smem_sm / 4 + 1024 : sm;
+    const size_t smr = leave_room && room > sm ? room : sm;
+    chol_kernel<2, 4><<<T, kThreads, smr, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
+  }
 }
 
 }  // namespace erx
