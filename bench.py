@@ -361,6 +361,7 @@ def bench_learned(dev, stream, n_train: int = 2000, n_test: int = 200):
     for name, kw in (("learned_fp32", {"form": "fp32", "encoder": enc}),
                      ("learned_fp64", {"form": "fp64", "encoder": enc}),
                      ("srp32_fp32", {"form": "fp32", "proj": "srp", "proj_dim": 32, "seed": 5}),
+                     ("srp5_fp32", {"form": "fp32", "proj": "srp", "proj_dim": 5, "seed": 5}),
                      ("full_fp64", {"form": "fp64"}), ("full_fp32", {"form": "fp32"}),
                      ("full_bf16", {"form": "bf16"})):
         speed = time_form(lambda **k: Detector(B, W, in_dtype="f32", warmup=0, stream=stream, **k),
@@ -412,6 +413,29 @@ def bench_learned_batched(enc, xt, stream, n_streams: int = 64, steps: int = 30)
 
 
 LATENCY_PERIOD_S = 1e-3   # lines arriving every millisecond (1000 lines/s)
+
+
+def push_size_throughput(det, x, out, stream, sizes=(1, 64, 256), lines=(2000, 8192, 8192)):
+    """lines/s of the FP64 form when the cube arrives n lines per push, pushes
+    queued back to back (CUDA events on the detector's stream)."""
+    import torch
+    res = {}
+    for n, m in zip(sizes, lines):
+        m = min(m, x.shape[0]) // n * n
+        det.reset()
+        for j in range(0, min(m, 4 * n), n):      # warm-up pushes
+            det.push(x[j:j + n], tuple(o[j:j + n] for o in out))
+        det.sync()
+        det.reset()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for j in range(0, m, n):
+            det.push(x[j:j + n], tuple(o[j:j + n] for o in out))
+        b.record(stream)
+        det.sync()
+        torch.cuda.synchronize()
+        res[str(n)] = {"lines_per_s": m / (a.elapsed_time(b) * 1e-3), "lines": m}
+    return res
 
 
 def paced_latency(det, x, out, stream, n, period_s, offset=200):
@@ -642,6 +666,9 @@ def run_ours(args):
                                 "lines": len(lat), "mode": "one line per push, back to back"}
         result["latency_paced_ms"] = paced_latency(det, x, one, stream, args.latency_lines,
                                                    LATENCY_PERIOD_S)
+        # throughput by push size: stream mode (one line per push, pushes queued
+        # back to back) and block mode (64 and 256 lines per push)
+        result["throughput_by_push_lines"] = push_size_throughput(det, x, out, stream)
         # score-then-update with the update deferred to a second stream (the
         # line is scored against the factor made at the end of the previous push)
         dpl = detector(form="fp64", order="score_then_update", pipeline=True)
@@ -712,6 +739,10 @@ def run_ours(args):
         result["e2e"] = {"value": LINES / statistics.median(ts), "unit": UNIT,
                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
         result["cpu_baseline"] = cpu_baseline(args.cpu_lines)
+        one_t = cpu_baseline(args.cpu_lines // 10, one_thread=True)
+        result["cpu_baseline"]["value_1thread"] = one_t["value"]
+        result["cpu_baseline"]["sample_1thread"] = one_t["sample"] + ", 1 BLAS thread"
+        result["pixel_spectra_per_s"] = value * WIDTH
     elif rank == 0:
         result["e2e"] = None
         result["cpu_baseline"] = None
@@ -779,7 +810,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-lines", type=int, default=3000)
     ap.add_argument("--ref-lines", type=int, default=1000)
-    ap.add_argument("--latency-lines", type=int, default=5000)
+    ap.add_argument("--latency-lines", type=int, default=10000)
     ap.add_argument("--quick", action="store_true", help="skip latency, forms, e2e, baseline")
     ap.add_argument("--lines", type=int, default=LINES,
                     help="lines of the workload cube (smaller cubes for profiler captures)")

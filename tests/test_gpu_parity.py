@@ -204,6 +204,29 @@ def test_planted_anomaly_ranking_fp32_matches_fp64():
         assert np.all(same | close | np.roll(close, 1))
 
 
+# relative gap below which two planted anomalies count as tied: a few times
+# each form's stated error bar
+RANK_TIES = [("fp64e", 1e-6), ("tf32x3", 1e-3), ("tf32", 2e-2), ("bf16", 0.15)]
+
+
+@pytest.mark.parametrize("form,tie", RANK_TIES)
+def test_planted_anomaly_ranking_every_form(form, tie):
+    """For every pair of planted anomalies that the oracle orders clearly (delta_N
+    apart by more than `tie` relative), the form orders them the same way: the
+    ranking is the oracle's up to ties."""
+    cfg = synth.dn_c2(width=256, bands=64, seed=5)
+    cube = synth.gen_lines(cfg, 0, 60)
+    m = synth.anomaly_mask(cfg, 0, 60)
+    ref = oracle.run_cube(cube)["delta_n"][m]
+    got = run_gpu(cube, form=form, in_bits=12)[0]["delta_n"][m].astype(np.float64)
+    assert m.sum() >= 10
+    gap = ref[:, None] - ref[None, :]
+    scale = np.maximum(np.maximum(np.abs(ref[:, None]), np.abs(ref[None, :])), 1.0)
+    clear = gap > tie * scale                       # oracle: i clearly above j
+    agree = (got[:, None] - got[None, :]) > 0
+    assert np.all(agree[clear]), (form, int((~agree[clear]).sum()))
+
+
 @pytest.mark.parametrize("width,bands", [(640, 108), (2048, 127), (65, 1), (130, 16), (1, 5)])
 def test_tensor_core_stats_match_integer_route_bitwise(width, bands):
     """The tcgen05 exact-integer SYRK (bf16 6-bit split, FP32 accumulation in
