@@ -47,7 +47,7 @@ typedef enum {
   ERX_ENOTPD = 4,       /* K_t + ridge I was not positive definite at some line */
   ERX_ERANGE = 5,       /* an integer input sample exceeded 2^in_bits - 1 */
   ERX_ESTATE = 6,       /* call not valid in the context's current state */
-  ERX_EUNSUPPORTED = 7, /* valid request this build does not implement */
+  ERX_EUNSUPPORTED = 7, /* valid request this library does not implement */
   ERX_ETIMEOUT = 8      /* a bounded wait inside a kernel gave up; results of the call are invalid */
 } erx_status;
 

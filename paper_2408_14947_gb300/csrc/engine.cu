@@ -1108,7 +1108,7 @@ const char* erx_status_str(erx_status s) {
     case ERX_ENOTPD: return "ERX_ENOTPD: K_t + ridge I not positive definite";
     case ERX_ERANGE: return "ERX_ERANGE: input sample above 2^in_bits - 1";
     case ERX_ESTATE: return "ERX_ESTATE: call not valid in this state";
-    case ERX_EUNSUPPORTED: return "ERX_EUNSUPPORTED: beyond this build's limits";
+    case ERX_EUNSUPPORTED: return "ERX_EUNSUPPORTED: beyond this library's limits";
     case ERX_ETIMEOUT: return "ERX_ETIMEOUT: a bounded wait in a kernel gave up";
   }
   return "ERX_?: unknown status";
