@@ -543,13 +543,7 @@ void forward(erx_encoder* e, const float* x, int64_t n, float* codes, __nv_bfloa
 
 // inference forward on the tensor cores (bf16 activations): one persistent CTA per SM
 void forward_tc(erx_encoder* e, const float* x, int64_t n, float* codes, cudaStream_t st) {
-  static int n_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (n_sm <= 0) n_sm = 1;
-  }
+  const int n_sm = device_shape().n_sm;
   const int64_t tiles = (n + 127) / 128;
   const int grid = (int)std::min<int64_t>(tiles, n_sm);
   enc_fwd_tc_kernel<<<grid, kFT, fwd_tc_smem(e->b, e->h, e->k), st>>>(

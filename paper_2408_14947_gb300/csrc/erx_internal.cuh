@@ -73,6 +73,14 @@ void launch_stats_fp(int in_type, bool fp64, const void* x, int64_t line_stride,
 // statistics each line is scored with and advances the state.  `scratch`
 // holds ema_scratch_doubles(d, T) doubles (NULL: sequential scan).
 size_t ema_scratch_doubles(int d, int T);
+// SM count and shared memory per SM of the current device, queried once
+// (thread-safe initialisation; one device per process)
+struct DeviceShape {
+  int n_sm;
+  int smem_per_sm;
+};
+const DeviceShape& device_shape();
+
 // maxv: the largest sample of integer statistics (it bounds their sums)
 void launch_ema_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
                      const double* mu_hat, const double* shift, const double* S2f, int T, int d,

@@ -458,14 +458,7 @@ void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, 
   // Fewer lines than SMs (a line or a few pushed alone): one CTA per SM anyway,
   // so each takes more threads (as many as its registers allow) to hide the
   // latency of its barriers and DFMA chains.
-  static int n_sm = 0, smem_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (n_sm <= 0) n_sm = 1;
-  }
+  const int n_sm = device_shape().n_sm, smem_sm = device_shape().smem_per_sm;
   const size_t sm = chol_smem(d);
   // d > 128: one CTA per SM, look-ahead schedule.  Fewer lines than SMs at
   // d <= 128 (a line pushed alone): the column schedule with 1024 threads, whose

@@ -547,4 +547,19 @@ void launch_project(int in_type, const void* x, int64_t line_stride, int B, int 
 #undef ERX_PRJ
 }
 
+const DeviceShape& device_shape() {
+  static const DeviceShape shape = [] {
+    DeviceShape r{1, 0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      cudaDeviceGetAttribute(&r.n_sm, cudaDevAttrMultiProcessorCount, dev);
+      cudaDeviceGetAttribute(&r.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    }
+    cudaGetLastError();
+    if (r.n_sm <= 0) r.n_sm = 1;
+    return r;
+  }();
+  return shape;
+}
+
 }  // namespace erx

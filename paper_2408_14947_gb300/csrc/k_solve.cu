@@ -410,13 +410,7 @@ void launch_fp64_t(const InT* x, int64_t line_stride, int ps, int W, int d, int 
 template <typename InT>
 void launch_fp64_in(const InT* x, int64_t line_stride, int ps, int W, int d, int T,
                     const double* mu_t, const double* Linv, double* delta, cudaStream_t st) {
-  static int n_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (n_sm <= 0) n_sm = 1;
-  }
+  const int n_sm = device_shape().n_sm;
   const int64_t tiles64 = (int64_t)T * ((W + kPixF64 - 1) / kPixF64);
   if (tiles64 < n_sm)
     launch_fp64_t<InT, 16, 8>(x, line_stride, ps, W, d, T, mu_t, Linv, delta, n_sm, st);

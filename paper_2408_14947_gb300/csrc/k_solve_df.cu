@@ -215,13 +215,7 @@ size_t smem_df(int d, int npx) {
 template <typename InT, int H, int NPX>
 void launch_df_t(const InT* x, int64_t line_stride, int ps, int W, int d, int T,
                  const float2* mu2, const float2* L2, double* delta, cudaStream_t st) {
-  static int n_sm = 0;
-  if (!n_sm) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (n_sm <= 0) n_sm = 1;
-  }
+  const int n_sm = device_shape().n_sm;
   const int threads = H * NPX;
   const size_t sm = smem_df(d, NPX);
   int per_sm = 1;

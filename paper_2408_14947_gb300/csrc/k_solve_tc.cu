@@ -301,15 +301,13 @@ __global__ void __launch_bounds__(kPix) b_solve_tc_kernel(const BStream* __restr
                                      it.s, it.tile);
 }
 
-int g_smem_per_sm = 0;
-
 // Dynamic shared memory of one CTA: two stages, raised where needed so that no
 // more CTAs share an SM than its 512 TMEM columns hold (no CTA then waits in
 // tcgen05.alloc for another's columns).
 size_t launch_smem(int d, int fmt) {
   const size_t need = 2 * (size_t)tc_stage_bytes(d, fmt);
   const int maxc = 512 / (int)tc_cols(d);
-  const size_t pad = (size_t)g_smem_per_sm / (size_t)(maxc + 1) + 1;
+  const size_t pad = (size_t)device_shape().smem_per_sm / (size_t)(maxc + 1) + 1;
   return need > pad ? need : pad;
 }
 
@@ -317,13 +315,8 @@ size_t launch_smem(int d, int fmt) {
 
 cudaError_t configure_solve_tc_kernels() {
   cudaError_t e = cudaSuccess;
-  if (!g_smem_per_sm) {
-    int dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess)
-      e = cudaDeviceGetAttribute(&g_smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e != cudaSuccess) return e;
-  }
+  // the TMEM padding of launch_smem needs the SM's shared memory size
+  if (device_shape().smem_per_sm <= 0) return cudaErrorInvalidDevice;
   // the largest request of any d <= kMaxDim
   auto most = [](int fmt) {
     size_t m = 0;
