@@ -415,7 +415,9 @@ erx_status erx_batch_set_encoder(erx_batch* b, erx_encoder* enc) {
     return ERX_ECUDA;
   }
   b->enc = enc;
-  return capture(b);
+  const erx_status s = capture(b);
+  if (s != ERX_OK) b->failed = true;   // no step graph: the batch cannot run
+  return s;
 }
 
 erx_status erx_batch_buffers(erx_batch* b, int32_t i, float** line_dev, void** delta_dev,
