@@ -199,25 +199,51 @@ __global__ void __launch_bounds__(kFT, 1) enc_fwd_tc_kernel(
   const uint32_t tmem = tslot;
   const uint32_t id1 = tc::idesc(1, 128, hP), id2 = tc::idesc(1, 128, kP);
   const int64_t ntile = (n + 127) / 128;
+  const bool vec8 = (b % 8) == 0 && ((uintptr_t)x % 16) == 0;   // pixel rows start on 32 bytes
   uint32_t phase = 0;
   bool ok = true;
   for (int64_t tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x) {
     const int64_t i0 = tile * 128;
     // xn of the tile's pixels as bf16 (rows beyond n and bands beyond b: 0)
-    for (int it = tid; it < 128 * (bK / 8); it += kFT) {
-      const int p = it / (bK / 8), g = it % (bK / 8);
-      const int64_t i = i0 + p;
-      uint32_t w[4];
+    if (vec8) {
+      // eight bands per item in two 16-byte loads, two items in flight per thread
+#pragma unroll 2
+      for (int it = tid; it < 128 * (bK / 8); it += kFT) {
+        const int p = it / (bK / 8), g = it % (bK / 8);
+        const int64_t i = i0 + p;
+        float v[8];
+        if (i < n && 8 * g < b) {
+          const float4 f0 = __ldg(reinterpret_cast<const float4*>(x + i * b + 8 * g));
+          const float4 f1 = __ldg(reinterpret_cast<const float4*>(x + i * b + 8 * g + 4));
+          v[0] = f0.x, v[1] = f0.y, v[2] = f0.z, v[3] = f0.w;
+          v[4] = f1.x, v[5] = f1.y, v[6] = f1.z, v[7] = f1.w;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int q0 = 8 * g + 2 * u;
-        const float v0 = (i < n && q0 < b) ? (x[i * b + q0] - s_shift[q0]) * s_scale[q0] : 0.f;
-        const float v1 =
-            (i < n && q0 + 1 < b) ? (x[i * b + q0 + 1] - s_shift[q0 + 1]) * s_scale[q0 + 1] : 0.f;
-        w[u] = pack_bf2(v0, v1);
+          for (int u = 0; u < 8; ++u) v[u] = (v[u] - s_shift[8 * g + u]) * s_scale[8 * g + u];
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = 0.f;
+        }
+        *reinterpret_cast<uint4*>(A1 + fwd_off(p, 8 * g, sbo1)) =
+            make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                       pack_bf2(v[6], v[7]));
       }
-      *reinterpret_cast<uint4*>(A1 + fwd_off(p, 8 * g, sbo1)) =
-          make_uint4(w[0], w[1], w[2], w[3]);
+    } else {
+      for (int it = tid; it < 128 * (bK / 8); it += kFT) {
+        const int p = it / (bK / 8), g = it % (bK / 8);
+        const int64_t i = i0 + p;
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q0 = 8 * g + 2 * u;
+          const float v0 = (i < n && q0 < b) ? (x[i * b + q0] - s_shift[q0]) * s_scale[q0] : 0.f;
+          const float v1 = (i < n && q0 + 1 < b)
+                               ? (x[i * b + q0 + 1] - s_shift[q0 + 1]) * s_scale[q0 + 1]
+                               : 0.f;
+          w[u] = pack_bf2(v0, v1);
+        }
+        *reinterpret_cast<uint4*>(A1 + fwd_off(p, 8 * g, sbo1)) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+      }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
