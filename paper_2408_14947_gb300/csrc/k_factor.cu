@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(kThreads, 4) b_chol_kernel(const BStream* __re
 // which reads only L entries of rows >= J and X entries of column block K
 // above row block J, so X_JK can overwrite L_JK.  d^3/6 FP32 multiply-adds.
 __device__ __forceinline__ void trinv32_body(float* __restrict__ Lf32, int d) {
+  static_assert(kThreads == 256 && kNB == 32, "one 2 x 2 tile per thread covers a 32 x 32 block");
   extern __shared__ __align__(16) float S[];
   __shared__ float Tm[kNB * kNB];
   const int P = d * (d + 1) / 2;
@@ -378,28 +379,59 @@ __device__ __forceinline__ void trinv32_body(float* __restrict__ Lf32, int d) {
     const int k0 = K * kNB, k1 = min(d, k0 + kNB);
     for (int J = K + 1; J < nblk; ++J) {
       const int j0 = J * kNB, j1 = min(d, j0 + kNB);
+      // each thread a 2 x 2 tile: rows j, j+1 and columns k, k+1 of the pair
+      // (kThreads = 256 tiles = 32 x 32 entries); every entry keeps its own
+      // chain of multiply-adds in the order of the one-entry loop
+      const int jj = 2 * (threadIdx.x >> 4), kk = 2 * (threadIdx.x & 15);
+      const int j = j0 + jj, k = k0 + kk;
+      const bool vj = j < j1, vj1 = j + 1 < j1, vk = k < k1, vk1 = k + 1 < k1;
       // T = sum_M L_JM X_MK over columns m in [k0, j0)
-      for (int e = threadIdx.x; e < kNB * kNB; e += kThreads) {
-        const int jj = e / kNB, kk = e % kNB;
-        const int j = j0 + jj, k = k0 + kk;
-        float acc = 0.f;
-        if (j < j1 && k < k1) {
-          const float* Lj = S + pidx(j, 0);
-          for (int m = k; m < j0; ++m) acc = fmaf(Lj[m], S[pidx(m, k)], acc);
+      {
+        float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+        if (vj && vk) {
+          const float* L0 = S + pidx(j, 0);
+          const float* L1 = vj1 ? S + pidx(j + 1, 0) : L0;
+          // m = k: column k only (X_{k, k+1} lies above the diagonal)
+          const float xkk = S[pidx(k, k)];
+          a00 = fmaf(L0[k], xkk, a00);
+          a10 = fmaf(L1[k], xkk, a10);
+          for (int m = k + 1; m < j0; ++m) {
+            const float* Xm = S + pidx(m, k);      // X_mk, X_m,k+1 (k + 1 <= m)
+            const float x0 = Xm[0], x1 = Xm[1], l0 = L0[m], l1 = L1[m];
+            a00 = fmaf(l0, x0, a00);
+            a01 = fmaf(l0, x1, a01);
+            a10 = fmaf(l1, x0, a10);
+            a11 = fmaf(l1, x1, a11);
+          }
         }
-        Tm[e] = acc;
+        Tm[jj * kNB + kk] = a00;
+        Tm[jj * kNB + kk + 1] = a01;
+        Tm[(jj + 1) * kNB + kk] = a10;
+        Tm[(jj + 1) * kNB + kk + 1] = a11;
       }
       __syncthreads();
       // X_JK = -D_J T (D_J lower triangular, rows j, cols i <= j of block J)
-      for (int e = threadIdx.x; e < kNB * kNB; e += kThreads) {
-        const int jj = e / kNB, kk = e % kNB;
-        const int j = j0 + jj, k = k0 + kk;
-        if (j < j1 && k < k1) {
-          const float* Dj = S + pidx(j, j0);
-          float acc = 0.f;
-          for (int ii = 0; ii <= jj; ++ii) acc = fmaf(Dj[ii], Tm[ii * kNB + kk], acc);
-          S[pidx(j, k)] = -acc;
+      if (vj && vk) {
+        const float* D0 = S + pidx(j, j0);
+        const float* D1 = vj1 ? S + pidx(j + 1, j0) : D0;
+        float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
+        for (int ii = 0; ii <= jj; ++ii) {
+          const float t0 = Tm[ii * kNB + kk], t1 = Tm[ii * kNB + kk + 1];
+          const float d0 = D0[ii], d1 = D1[ii];
+          a00 = fmaf(d0, t0, a00);
+          a01 = fmaf(d0, t1, a01);
+          a10 = fmaf(d1, t0, a10);
+          a11 = fmaf(d1, t1, a11);
         }
+        if (vj1) {   // row j+1 has one more term, its diagonal
+          const float d1 = D1[jj + 1];
+          a10 = fmaf(d1, Tm[(jj + 1) * kNB + kk], a10);
+          a11 = fmaf(d1, Tm[(jj + 1) * kNB + kk + 1], a11);
+        }
+        S[pidx(j, k)] = -a00;
+        if (vk1) S[pidx(j, k + 1)] = -a01;
+        if (vj1) S[pidx(j + 1, k)] = -a10;
+        if (vj1 && vk1) S[pidx(j + 1, k + 1)] = -a11;
       }
       __syncthreads();
     }
