@@ -295,15 +295,21 @@ __global__ void __launch_bounds__(256) b_stats_kernel(const BStream* __restrict_
   const BStream& s = S[it.s];
   if (s.d <= kSmallD)
     stats_small_body<float, AccT>(s.x, s.d, s.W, s.d, s.shift, s.S2f);
-  else   // FP64: 32 x 32 blocks, as the single-stream path
-    stats_fp_body<float, AccT, sizeof(AccT) == 8 ? 32 : SB>(s.x, s.d, s.W, s.d, s.shift, s.S2f,
-                                                          it.tile);
+  else if (sizeof(AccT) == 8 || s.d <= 32)   // 32 x 32 blocks, as the single-stream path
+    stats_fp_body<float, AccT, 32>(s.x, s.d, s.W, s.d, s.shift, s.S2f, it.tile);
+  else
+    stats_fp_body<float, AccT, SB>(s.x, s.d, s.W, s.d, s.shift, s.S2f, it.tile);
 }
 
 }  // namespace
 
+// output block edge of the floating scatter: 32 in FP64 (every multiply-add
+// counts) and for d <= 32 (a 64 x 64 block would leave three quarters of the
+// threads idle), 64 otherwise
+int fp_block(int d, bool fp64) { return fp64 || d <= 32 ? 32 : SB; }
+
 int batch_stats_tiles(int d, bool fp64) {
-  return d <= kSmallD ? 1 : n_pairs(d, fp64 ? 32 : SB);
+  return d <= kSmallD ? 1 : n_pairs(d, fp_block(d, fp64));
 }
 
 void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t st) {
@@ -357,19 +363,24 @@ void launch_stats_fp(int in_type, bool fp64, const void* x, int64_t line_stride,
 #undef ERX_SMALL
     return;
   }
-  // FP64: 32 x 32 blocks (less of the triangle wasted); FP32: 64 x 64
-  const dim3 grid(n_pairs(d, fp64 ? 32 : SB), T);
-#define ERX_SFP(IT, AT)                                                                     \
-  stats_fp_kernel<IT, AT, sizeof(AT) == 8 ? 32 : SB><<<grid, 256, 0, st>>>(              \
-      (const IT*)x, line_stride, ps, W, d, shift, S2f)
+  // FP64 and d <= 32: 32 x 32 blocks; FP32 otherwise: 64 x 64
+  const int sbt = fp_block(d, fp64);
+  const dim3 grid(n_pairs(d, sbt), T);
+#define ERX_SFP(IT, AT, SBT)                                                                \
+  stats_fp_kernel<IT, AT, SBT><<<grid, 256, 0, st>>>((const IT*)x, line_stride, ps, W, d, \
+                                                     shift, S2f)
   if (fp64) {
-    if (in_type == 0) ERX_SFP(uint16_t, double);
-    else if (in_type == 1) ERX_SFP(float, double);
-    else ERX_SFP(double, double);
+    if (in_type == 0) ERX_SFP(uint16_t, double, 32);
+    else if (in_type == 1) ERX_SFP(float, double, 32);
+    else ERX_SFP(double, double, 32);
+  } else if (sbt == 32) {
+    if (in_type == 0) ERX_SFP(uint16_t, float, 32);
+    else if (in_type == 1) ERX_SFP(float, float, 32);
+    else ERX_SFP(double, float, 32);
   } else {
-    if (in_type == 0) ERX_SFP(uint16_t, float);
-    else if (in_type == 1) ERX_SFP(float, float);
-    else ERX_SFP(double, float);
+    if (in_type == 0) ERX_SFP(uint16_t, float, SB);
+    else if (in_type == 1) ERX_SFP(float, float, SB);
+    else ERX_SFP(double, float, SB);
   }
 #undef ERX_SFP
 }
