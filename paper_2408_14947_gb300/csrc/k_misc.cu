@@ -86,7 +86,8 @@ __device__ __forceinline__ void ema_element(const EmaSrc& s, int64_t q, int& a, 
     b = -1;
     return;
   }
-  int r = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  // a float square root (FP64 is scarce here) and exact integer correction
+  int r = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
   while ((int64_t)r * (r + 1) / 2 > q) --r;
   while ((int64_t)(r + 1) * (r + 2) / 2 <= q) ++r;
   a = r;
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(128) b_ema_kernel(BStream* __restrict__ S,
   const double alpha = s.alpha, beta = 1.0 - alpha;
   const double Wd = (double)s.W;
   if (q < P) {
-    int a = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+    int a = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);   // corrected below
     while ((int64_t)a * (a + 1) / 2 > q) --a;
     while ((int64_t)(a + 1) * (a + 2) / 2 <= q) ++a;
     const int b = (int)(q - (int64_t)a * (a + 1) / 2);
