@@ -439,6 +439,20 @@ typedef struct {
 erx_status erx_roc_metrics(const void* scores_dev, int32_t score_dtype, const uint8_t* labels_dev,
                            int64_t n, int32_t bins, void* cuda_stream, erx_roc* out);
 
+/* ---- Self-test of the bounded device waits ------------------------------
+ *
+ * Every device-side wait of the library (an mbarrier of an asynchronous copy
+ * or of a tensor-core commit) polls at most a fixed number of times; when the
+ * limit runs out the kernel records ERX_ETIMEOUT, waits once more (bounded)
+ * for its work in flight, releases its tensor memory and returns, so the
+ * context stays usable.  This entry point runs that path on purpose without
+ * any fault: one thread waits on an mbarrier that nothing arrives at, at most
+ * `limit` polls (1 <= limit <= 2^20; each poll returns within the hardware's
+ * suspend window), on cuda_stream.  Returns ERX_ETIMEOUT when the wait ran out
+ * as designed, ERX_OK if it completed (a defect), ERX_EINVAL for a limit out of
+ * range, ERX_ECUDA on a launch error.  Synchronises. */
+erx_status erx_selftest_bounded_wait(uint32_t limit, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

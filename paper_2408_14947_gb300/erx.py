@@ -90,6 +90,7 @@ def load_library() -> C.CDLL:
                                        C.POINTER(I64)]),
         "erx_kernel_name": (C.c_char_p, [I32]),
         "erx_roc_metrics": (C.c_int, [P, I32, P, I64, I32, P, C.POINTER(ErxRoc)]),
+        "erx_selftest_bounded_wait": (C.c_int, [C.c_uint32, P]),
         "erx_train_opts_default": (None, [C.POINTER(ErxTrainOpts)]),
         "erx_encoder_create": (C.c_int, [I32, I32, I32, U64, P, C.POINTER(P)]),
         "erx_encoder_set_norm": (C.c_int, [P, P, P]),
@@ -242,6 +243,14 @@ def roc_metrics(scores, labels, bins: int = 1 << 16, stream=None) -> dict:
 
 def erx_kernel_name(k: int) -> str:
     return load_library().erx_kernel_name(k).decode()
+
+
+def selftest_bounded_wait(limit: int = 1000, stream=None) -> int:
+    """Run the bounded-wait self-test (erx_selftest_bounded_wait) and return its
+    status: ERX_ETIMEOUT when the wait ran out as designed."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return load_library().erx_selftest_bounded_wait(limit, C.c_void_p(st.cuda_stream))
 
 
 def erx_profile_enable(ctx, on: bool) -> None:
