@@ -69,3 +69,23 @@ def test_two_contexts_do_not_interfere():
     assert np.array_equal(torch.cat(ob).cpu().numpy(), rb["delta"])
     da.close()
     db.close()
+
+
+def test_nan_input_propagates_and_is_reported():
+    """A NaN sample in line 3 makes that line's statistics, factor and scores
+    NaN; the bad pivot is reported as ERX_ENOTPD with line 3 (the first one),
+    and the lines before it are untouched."""
+    need_gpu()
+    from paper_2408_14947_gb300 import Detector, ErxError, ERX_ENOTPD
+    cube = synth.gen_lines(synth.dn_c2(width=64, bands=8, seed=6), 0, 6).astype(np.float32)
+    ref = oracle.run_cube(cube[:3].astype(np.float64), warmup=0)
+    cube[3, 10, 2] = np.nan
+    det = Detector(8, 64, in_dtype="f32", warmup=0)
+    out = det.push(to_dev(cube))
+    with pytest.raises(ErxError) as ei:
+        det.sync()
+    assert ei.value.status == ERX_ENOTPD and ei.value.bad_line == 3
+    d = out[0].cpu().numpy()
+    assert rel_err(d[:3], ref["delta"]) < 1e-9
+    assert np.all(np.isnan(d[3]))
+    det.close()
