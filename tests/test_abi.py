@@ -71,3 +71,14 @@ def test_null_handles(lib):
     assert lib.erx_dim(None) == -1
     for s in range(8):
         assert erx.erx_status_str(s).startswith("ERX_")
+
+
+def test_host_side_argument_checks(lib):
+    """Argument checks that return before any CUDA call."""
+    assert lib.erx_selftest_bounded_wait(0, None) == erx.ERX_EINVAL
+    assert lib.erx_selftest_bounded_wait((1 << 20) + 1, None) == erx.ERX_EINVAL
+    assert lib.erx_batch_set_encoder(None, None) == erx.ERX_EINVAL
+    assert lib.erx_batch_push(None, None) == erx.ERX_EINVAL
+    assert lib.erx_batch_destroy(None) == erx.ERX_OK
+    h = ctypes.c_void_p()
+    assert lib.erx_batch_create(0, None, None, ctypes.byref(h)) == erx.ERX_EINVAL
