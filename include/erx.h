@@ -201,10 +201,13 @@ erx_status erx_srp_weights(int32_t bands, int32_t dim, uint64_t seed, double* w_
  * GPU that loads the library until the process exits).  It calls no
  * cudaMalloc, cudaFree or other allocating routine.
  *
- *  cfg           as for erx_create; proj must be ERX_PROJ_NONE and bands <= 224
- *                (the fixed scratch is sized for one line at d = 224), width
- *                <= 2^20; beyond these limits the call returns ERX_EUNSUPPORTED
- *                and does nothing.  cfg->srp_weights and cfg->block_lines are ignored.
+ *  cfg           as for erx_create, within these limits: proj ERX_PROJ_NONE,
+ *                bands <= 224 (the fixed scratch is sized for one line at
+ *                d = 224), width <= 2^20 and averaging ERX_AVG_EMA, else the
+ *                call returns ERX_EUNSUPPORTED; form ERX_FORM_FP64 or
+ *                ERX_FORM_FP32, else ERX_EINVAL.  Either way it does nothing.
+ *                Both orders and all three input types are supported.
+ *                cfg->srp_weights, cfg->block_lines and cfg->flags are ignored.
  *  cuda_stream   cudaStream_t the work runs on (NULL: legacy default stream).
  *  mu_dev        device, d doubles: background mean, read and updated in place.
  *  K_dev         device, d(d+1)/2 doubles: background covariance, packed lower
@@ -215,7 +218,10 @@ erx_status erx_srp_weights(int32_t bands, int32_t dim, uint64_t seed, double* w_
  *
  * Processes the lines one at a time and returns when the GPU work has
  * finished (synchronises cuda_stream), reporting ERX_ENOTPD / ERX_ERANGE
- * directly.  The first call on each device looks up the scratch array's
+ * directly.  Those two come after every line has been processed: the state
+ * in mu_dev / K_dev and *t_host have advanced by n_lines all the same (the
+ * scores of the offending line are NaN or meaningless), so a retry must not
+ * push the same lines again.  The first call on each device looks up the scratch array's
  * device address and raises the shared-memory limit of the large kernels on
  * that device; make that first call before any stream capture.  Every call
  * shares the one scratch array: calls whose GPU work overlaps (from several

@@ -215,12 +215,20 @@ ERX_K_COUNT = 15
 
 def erx_push_lines_static(cfg, stream, mu_ptr, k_ptr, t, lines_ptr, n_lines, stride_bytes,
                           delta_ptr, dn_ptr=0, mask_ptr=0, det_ptr=0) -> int:
-    """Context-free line step on caller-held state; returns the new line count."""
+    """Context-free line step on caller-held state; returns the new line count.
+
+    ERX_ENOTPD and ERX_ERANGE are raised after the lines have been processed
+    (the state has advanced): the raised ErxError carries the new line count
+    as ``t``, so a caller does not apply the same lines twice."""
     tt = C.c_int64(t)
-    _check(load_library().erx_push_lines_static(C.byref(cfg), C.c_void_p(stream), mu_ptr, k_ptr,
-                                                C.byref(tt), lines_ptr, n_lines, stride_bytes,
-                                                delta_ptr, dn_ptr or None, mask_ptr or None,
-                                                det_ptr or None), "erx_push_lines_static")
+    st = load_library().erx_push_lines_static(C.byref(cfg), C.c_void_p(stream), mu_ptr, k_ptr,
+                                              C.byref(tt), lines_ptr, n_lines, stride_bytes,
+                                              delta_ptr, dn_ptr or None, mask_ptr or None,
+                                              det_ptr or None)
+    if st != ERX_OK:
+        err = ErxError(st, "erx_push_lines_static")
+        err.t = tt.value
+        raise err
     return tt.value
 
 

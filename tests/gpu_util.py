@@ -23,12 +23,15 @@ def in_dtype(cube):
             np.dtype(np.float64): "f64"}[cube.dtype]
 
 
-def run_gpu(cube, push_sizes=None, **kw):
-    """Run the CUDA detector over cube; returns numpy outputs and the detector."""
+def run_gpu(cube, push_sizes=None, profile=False, **kw):
+    """Run the CUDA detector over cube; returns numpy outputs and the detector
+    (with per-kernel launch counts and times when profile is set)."""
     from paper_2408_14947_gb300 import Detector
     n, p, b = cube.shape
     kw.setdefault("in_dtype", in_dtype(cube))
     det = Detector(b, p, **kw)
+    if profile:
+        det.profile(True)
     x = to_dev(cube)
     outs = []
     if push_sizes is None:
@@ -61,3 +64,4 @@ def dn_err(got, ref_delta, ref_dn):
     # zero-spread lines have delta_N = 0 exactly on both sides
     e = np.where(np.isfinite(scale), e, np.abs(got - ref_dn))
     return float(np.max(e))
+
