@@ -94,3 +94,86 @@ def test_training_reduces_loss():
         losses.append(np.mean([enc.train_line(params, opt, ema, x, t, shift, scale)
                                for x, t in zip(xs, tg)]))
     assert losses[-1] < 0.9 * losses[0]
+
+
+def test_code_ema_closed_form():
+    """CodeEMA after T lines equals the solved Sec. III-C recursion: weights
+    (1-a)^(T-1) for line 0 and a (1-a)^(T-1-j) for line j >= 1 on each line's
+    code mean and 1/(p-1) covariance (numpy.cov), weights summing to 1."""
+    r = np.random.default_rng(11)
+    a, T, p, k = 0.3, 7, 25, 4
+    codes = [r.standard_normal((p, k)) * (1 + j) + j for j in range(T)]
+    ema = enc.CodeEMA(a)
+    for c in codes:
+        mu, kk = ema.update(c)
+    w = [(1 - a) ** (T - 1)] + [a * (1 - a) ** (T - 1 - j) for j in range(1, T)]
+    assert abs(sum(w) - 1.0) < 1e-15
+    mu_want = sum(wj * c.mean(axis=0) for wj, c in zip(w, codes))
+    k_want = sum(wj * np.cov(c, rowvar=False, ddof=1) for wj, c in zip(w, codes))
+    assert ema.t == T
+    assert np.allclose(mu, mu_want, rtol=1e-12, atol=1e-13)
+    assert np.allclose(kk, k_want, rtol=1e-12, atol=1e-13)
+
+
+def test_code_ema_first_line_initialises():
+    c = np.random.default_rng(2).standard_normal((30, 5))
+    mu, kk = enc.CodeEMA(0.1).update(c)
+    assert np.allclose(mu, c.mean(axis=0), rtol=1e-14)
+    assert np.allclose(kk, np.cov(c, rowvar=False), rtol=1e-12)
+
+
+def _fd_grad(params, x, shift, scale, mu_e, k_e, target, ridge, h=1e-6):
+    """Central differences of one line's loss, statistics held constant."""
+    g = {}
+    for name, v in params.items():
+        g[name] = np.zeros_like(v)
+        for idx in np.ndindex(v.shape):
+            pp = {n: w.copy() for n, w in params.items()}
+            pm = {n: w.copy() for n, w in params.items()}
+            pp[name][idx] += h
+            pm[name][idx] -= h
+            g[name][idx] = (_loss_fixed_stats(pp, x, shift, scale, mu_e, k_e, target, ridge)
+                            - _loss_fixed_stats(pm, x, shift, scale, mu_e, k_e, target, ridge)
+                            ) / (2 * h)
+    return g
+
+
+def _loss_by_inverse(params, x, shift, scale, mu_e, k_e, target, ridge):
+    """The line loss from its definition: explicit inverse, no Cholesky."""
+    c, _ = enc.forward(params, x, shift, scale)
+    inv = np.linalg.inv(k_e + ridge * np.eye(k_e.shape[0]))
+    d = np.sqrt(np.einsum("ij,jk,ik->i", c - mu_e, inv, c - mu_e))
+    return float(np.mean((np.log1p(d) - np.log1p(target)) ** 2))
+
+
+def test_train_line_steps_follow_their_definition():
+    """Two steps of train_line against the training objective written out:
+    step 1 moves every parameter by AdamW's first-step closed form with the
+    finite-difference gradient (statistics of line 1's own codes held
+    constant); step 2's loss is the definition evaluated with the parameters
+    after step 1 and the code EMA updated with line 2's codes (update then
+    score, Sec. III-C/D)."""
+    params, x1, shift, scale, t1 = _setup(p=30, b=5, h=6, k=3, seed=3)
+    r = np.random.default_rng(9)
+    x2 = x1 + 0.05 * r.standard_normal(x1.shape)
+    t2 = t1[::-1].copy()
+    ridge, lr, wd, alpha = 1e-3, 1e-2, 1e-3, 0.25
+    p0 = {n: v.copy() for n, v in params.items()}
+    opt = enc.AdamW(params, lr=lr, wd=wd)
+    ema = enc.CodeEMA(alpha)
+    l1 = enc.train_line(params, opt, ema, x1, t1, shift, scale, ridge)
+    # step 1: statistics of line 1's codes under the initial parameters
+    c1, _ = enc.forward(p0, x1, shift, scale)
+    mu1, k1 = c1.mean(axis=0), np.cov(c1, rowvar=False)
+    assert abs(l1 - _loss_by_inverse(p0, x1, shift, scale, mu1, k1, t1, ridge)) <= 1e-12 * l1
+    g = _fd_grad(p0, x1, shift, scale, mu1, k1, t1, ridge)
+    for n in p0:
+        want = p0[n] - lr * (g[n] / (np.abs(g[n]) + opt.eps) + wd * p0[n])
+        big = np.abs(g[n]) > 1e-6           # the sign of a vanishing gradient is noise
+        assert np.allclose(params[n][big], want[big], rtol=0, atol=1e-9), n
+    p1 = {n: v.copy() for n, v in params.items()}
+    l2 = enc.train_line(params, opt, ema, x2, t2, shift, scale, ridge)
+    c2, _ = enc.forward(p1, x2, shift, scale)
+    mu2 = (1 - alpha) * mu1 + alpha * c2.mean(axis=0)
+    k2 = (1 - alpha) * k1 + alpha * np.cov(c2, rowvar=False)
+    assert abs(l2 - _loss_by_inverse(p1, x2, shift, scale, mu2, k2, t2, ridge)) <= 1e-10 * l2

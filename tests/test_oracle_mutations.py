@@ -125,3 +125,73 @@ def test_pooled_boundary_off_by_one_is_caught(monkeypatch):
     monkeypatch.setattr(eo.ERXOracle, "_update", late)
     errs = {k: fn() for k, (fn, tol) in oc.ALL_CHECKS.items()}
     assert any(errs[k] > oc.ALL_CHECKS[k][1] for k in errs)
+
+
+# ---- the learned encoder's oracle ------------------------------------------
+
+def _encoder_pins():
+    from tests import test_oracle_encoder as te
+    return [getattr(te, n) for n in dir(te) if n.startswith("test_")]
+
+
+def _pins_fail():
+    failed = []
+    for pin in _encoder_pins():
+        try:
+            pin()
+        except (AssertionError, np.linalg.LinAlgError, FloatingPointError, ValueError):
+            failed.append(pin.__name__)
+    return failed
+
+
+def test_encoder_pins_pass_unmutated():
+    assert _pins_fail() == []
+
+
+def _code_ema_swapped(self, c):
+    mu_h, k_h = self_stats = (c.mean(axis=0), np.cov(c, rowvar=False))
+    if self.t == 0:
+        self.mu, self.k = self_stats
+    else:
+        a = self.alpha
+        self.mu = a * self.mu + (1 - a) * mu_h
+        self.k = a * self.k + (1 - a) * k_h
+    self.t += 1
+    return self.mu, self.k
+
+
+def _train_line_score_then_update(params, opt, ema, x, target, shift, scale, ridge=1e-5):
+    from oracle import encoder as enc
+    c, cache = enc.forward(params, x, shift, scale)
+    if ema.t == 0:
+        mu_e, k_e = enc.code_stats(c)
+    else:
+        mu_e, k_e = ema.mu, ema.k
+    ema.update(c)
+    loss, dc, _ = enc.loss_and_dcodes(c, mu_e, k_e, ridge, target)
+    opt.step(params, enc.backward(params, cache, dc))
+    return loss
+
+
+def _backward_no_gate(params, cache, dc):
+    xn, a, h = cache
+    dh = dc @ params["W2"]
+    return {"W2": dc.T @ h, "b2": dc.sum(axis=0), "W1": dh.T @ xn, "b1": dh.sum(axis=0)}
+
+
+ENCODER_MUTATIONS = {
+    "code_ema_weights_swapped": ("CodeEMA.update", _code_ema_swapped),
+    "train_line_scores_before_update": ("train_line", _train_line_score_then_update),
+    "backward_drops_relu_gate": ("backward", _backward_no_gate),
+}
+
+
+@pytest.mark.parametrize("name", sorted(ENCODER_MUTATIONS))
+def test_encoder_mutation_is_caught(name, monkeypatch):
+    from oracle import encoder as enc
+    attr, bad = ENCODER_MUTATIONS[name]
+    if attr == "CodeEMA.update":
+        monkeypatch.setattr(enc.CodeEMA, "update", bad)
+    else:
+        monkeypatch.setattr(enc, attr, bad)
+    assert _pins_fail(), f"mutation {name} passed every encoder pin"
