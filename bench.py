@@ -220,9 +220,24 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_form(make, x, kw, dev, stream, reps: int = 2):
+def max_rel_err(got, ref):
+    import numpy as np
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)))
+
+
+def oracle_delta(cube, **kw):
+    """FP64 oracle scores of cube (the parity reference for the accuracy columns)."""
+    import oracle
+    return oracle.run_cube(cube, **kw)["delta"]
+
+
+def time_form(make, x, kw, dev, stream, reps: int = 2, ref=None):
     """lines/s of one detector configuration over the resident cube x (reset + push
-    per step, one warm-up step), plus its per-kernel split."""
+    per step, one warm-up step), plus its per-kernel split.  ref: the FP64
+    oracle's scores of the cube's first lines; the timed run's scores of those
+    lines are compared with it (max relative delta error)."""
     import torch
     n, p, _ = x.shape
     det = make(**kw)
@@ -251,9 +266,13 @@ def time_form(make, x, kw, dev, stream, reps: int = 2):
     # next block's statistics and factor, so those times include each other's
     # share of the SMs and add up to more than ms_per_step.
     overlapped = kw.get("form", "fp64") != "fp64" and kw.get("encoder") is None
-    return {"lines_per_s": n / (ms / 1000.0), "ms_per_step": ms,
-            "kernels_ms": {k: round(v[0] / reps, 3) for k, v in prof.items() if v[2]},
-            "kernels_concurrent": overlapped}
+    res = {"lines_per_s": n / (ms / 1000.0), "ms_per_step": ms,
+           "kernels_ms": {k: round(v[0] / reps, 3) for k, v in prof.items() if v[2]},
+           "kernels_concurrent": overlapped}
+    if ref is not None:
+        res["max_rel_err"] = max_rel_err(out[0][:ref.shape[0]].cpu().numpy(), ref)
+        res["err_lines"] = int(ref.shape[0])
+    return res
 
 
 def bench_batched(dev, stream, n_streams: int = 256, n_lines: int = 4, steps: int = 20):
@@ -264,19 +283,42 @@ def bench_batched(dev, stream, n_streams: int = 256, n_lines: int = 4, steps: in
 
     import synth
     from paper_2408_14947_gb300 import Batch, Detector
+    import oracle
     cfgs = synth.stream_configs_c4(n_streams)
-    lines = [torch.from_numpy(synth.gen_lines(c, 0, n_lines)).to(dev) for c in cfgs]
+    host = [synth.gen_lines(c, 0, n_lines) for c in cfgs]
+    lines = [torch.from_numpy(h).to(dev) for h in host]
     shapes = [{"bands": c.bands, "width": c.width} for c in cfgs]
     out = {"workload": f"{n_streams} streams, widths U{{128..2048}}, bands from "
                        f"{{8,16,64,108,224}}, float32, {n_lines} resident lines cycled",
            "bytes_per_step": int(sum(c.width * c.bands * 4 for c in cfgs))}
+    # the FP64 oracle on every stream's first lines, and the condition number of
+    # each stream's ridged covariance after them
+    na = ACC_LINES_BATCH
+    refs, kappa = [], []
+    for h in host:
+        r = oracle.run_cube(h[:na], warmup=99, threshold=3.0)
+        refs.append(r["delta"])
+        k = r["state"][2]
+        kappa.append(float(np.linalg.cond(k + 1e-5 * np.eye(k.shape[0]))))
+    kappa = np.array(kappa)
+    out["kappa"] = {"min": float(kappa.min()), "median": float(np.median(kappa)),
+                    "max": float(kappa.max()), "streams_le_1e4": int((kappa <= 1e4).sum()),
+                    "of": "K_t + ridge I after the checked lines, per stream"}
     for form in ("fp64", "fp32", "tf32", "bf16", "tf32x3"):
         b = Batch(shapes, form=form, stream=stream)
-        b.push([x[0] for x in lines])
-        if form in ("tf32", "bf16", "tf32x3"):
+        # the first na steps are checked against the oracle (step 0 before the
+        # autotuner runs, the others after it, as timed)
+        errs = np.zeros(n_streams)
+        for k in range(na):
+            b.push([x[k] for x in lines])
+            if k == 0 and form in ("tf32", "bf16", "tf32x3"):
+                b.sync()
+                b.tune(reps=3)
             b.sync()
-            b.tune(reps=3)
-        for k in range(3):
+            for i in range(n_streams):
+                d_ = b.views(i)[1].cpu().numpy()
+                errs[i] = max(errs[i], max_rel_err(d_, refs[i][k]))
+        for k in range(na, na + 3):
             b.push([x[k % n_lines] for x in lines])
         b.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -288,8 +330,11 @@ def bench_batched(dev, stream, n_streams: int = 256, n_lines: int = 4, steps: in
         b.sync()
         ms = e0.elapsed_time(e1) / steps
         routes = sorted({b.route(i) for i in range(n_streams)})
+        le = kappa <= 1e4
         out[form] = {"lines_per_s": n_streams / (ms / 1000.0), "ms_per_step": ms,
-                     "routes": routes}
+                     "routes": routes, "max_rel_err": float(errs.max()),
+                     "max_rel_err_kappa_le_1e4": float(errs[le].max()) if le.any() else None,
+                     "err_lines_per_stream": na}
         b.close()
     # the same lines through 256 separate single-stream contexts, one push each
     dets = [Detector(c.bands, c.width, in_dtype="f32", form="fp64", block_lines=1,
@@ -328,6 +373,7 @@ def bench_learned(dev, stream, n_train: int = 2000, n_test: int = 200):
     flat = cube[:200].reshape(-1, B)
     shift, scale = flat.mean(0), 1.0 / (flat.std(0) + 1e-3)
     x = torch.from_numpy(cube).to(dev)
+    held = cube[n_train:n_train + ACC_LINES_LEARNED].astype(np.float64)
     del cube, flat
     full = Detector(B, W, in_dtype="f32", form="fp64", warmup=0, stream=stream)
     fd = full.push(x)[0]
@@ -357,6 +403,15 @@ def bench_learned(dev, stream, n_train: int = 2000, n_test: int = 200):
         return np.corrcoef(np.argsort(np.argsort(a)), np.argsort(np.argsort(b)))[0, 1]
 
     ref = fd[n_train:].cpu().numpy()
+    # FP64 oracle references for the first held-out lines: full band, SRP, and
+    # ERX on the encoder's own codes (what the learned form computes)
+    import oracle
+    na = ACC_LINES_LEARNED
+    codes = enc.forward(xt[:na].reshape(-1, B)).cpu().numpy().astype(np.float64)
+    oref = {"learned": oracle.run_cube(codes.reshape(na, W, K), warmup=0)["delta"],
+            "srp32": oracle.run_cube(held, warmup=0, proj="srp", proj_dim=32, seed=5)["delta"],
+            "srp5": oracle.run_cube(held, warmup=0, proj="srp", proj_dim=5, seed=5)["delta"],
+            "full": oracle.run_cube(held, warmup=0)["delta"]}
     rows = {}
     for name, kw in (("learned_fp32", {"form": "fp32", "encoder": enc}),
                      ("learned_fp64", {"form": "fp64", "encoder": enc}),
@@ -372,7 +427,10 @@ def bench_learned(dev, stream, n_train: int = 2000, n_test: int = 200):
         aucs = [auc(s_[t], labels[t]) for t in range(n_test) if labels[t].any()]
         rows[name] = {"lines_per_s": speed["lines_per_s"], "auc": float(np.mean(aucs)),
                       "rank_corr_full": float(np.mean([rank_corr(s_[t], ref[t])
-                                                       for t in range(n_test)]))}
+                                                       for t in range(n_test)])),
+                      "max_rel_err": max_rel_err(s_[:na], oref[name.split("_")[0]]),
+                      "err_vs": "FP64 oracle on the same " + (
+                          "codes" if name.startswith("learned") else "lines") + f", {na} lines"}
     out["forms"] = rows
     out["batched"] = bench_learned_batched(enc, xt, stream)
     enc.close()
@@ -413,6 +471,10 @@ def bench_learned_batched(enc, xt, stream, n_streams: int = 64, steps: int = 30)
 
 
 LATENCY_PERIOD_S = 1e-3   # lines arriving every millisecond (1000 lines/s)
+ACC_LINES = 500           # lines of the 108-band cube checked against the oracle per form
+ACC_LINES_224 = 150       # lines of the 224-band cube checked against the oracle per form
+ACC_LINES_BATCH = 3       # lines of every batched stream checked against the oracle
+ACC_LINES_LEARNED = 20    # held-out lines of the learned workload checked per form
 
 
 def push_size_throughput(det, x, out, stream, sizes=(1, 64, 256), lines=(2000, 8192, 8192)):
@@ -596,6 +658,11 @@ def run_ours(args):
     det.sync()
     ms_total = e0.elapsed_time(e1)
     prof = det.profile_read(reset=True)
+    # the timed run's scores of the first lines against the FP64 oracle
+    ref_head = None
+    if rank == 0 and not args.quick:
+        ref_head = oracle_delta(cube[:ACC_LINES])
+        head_err = max_rel_err(out[0][:ACC_LINES].cpu().numpy(), ref_head)
     det.profile(False)
     ms_total = max_over_ranks(ms_total, dev)
     if world > 1:
@@ -644,6 +711,9 @@ def run_ours(args):
                              gen_seconds=round(gen_s, 1)),
               "gpu_launches": launches, "roofline": roof, "kernels": kernels,
               "clocks": clk.summary()}
+    if ref_head is not None:
+        result["max_rel_err"] = {"value": head_err, "lines": ACC_LINES,
+                                 "vs": "FP64 NumPy oracle, same lines", "bar": 1e-9}
 
     if rank == 0 and not args.quick:
         # p50 / p99 latency of one line pushed alone (stream mode), after warm-up
@@ -681,31 +751,38 @@ def run_ours(args):
         dpl.sync()
         dpl.close()
 
-        # other forms on the same cube, same step definition
-        forms = {}
-        for name, kw in (("fp64e", {"form": "fp64e"}), ("fp32", {"form": "fp32"}),
-                         ("tf32", {"form": "tf32"}),
-                         ("bf16", {"form": "bf16"}), ("tf32x3", {"form": "tf32x3"}),
-                         ("fp64_imc", {"form": "fp64", "averaging": "imc"}),
-                         ("fp64_srp5", {"form": "fp64", "proj": "srp", "proj_dim": 5}),
-                         ("fp32_srp5", {"form": "fp32", "proj": "srp", "proj_dim": 5})):
+        # other forms on the same cube, same step definition; each timed run's
+        # scores of the first ACC_LINES lines against the FP64 oracle's
+        refs = {"ema": ref_head,
+                "imc": oracle_delta(cube[:ACC_LINES], averaging="imc"),
+                "srp5": oracle_delta(cube[:ACC_LINES], proj="srp", proj_dim=5, seed=0)}
+        forms = {"err_lines": ACC_LINES}
+        for name, kw, rk in (("fp64e", {"form": "fp64e"}, "ema"), ("fp32", {"form": "fp32"}, "ema"),
+                             ("tf32", {"form": "tf32"}, "ema"),
+                             ("bf16", {"form": "bf16"}, "ema"),
+                             ("tf32x3", {"form": "tf32x3"}, "ema"),
+                             ("fp64_imc", {"form": "fp64", "averaging": "imc"}, "imc"),
+                             ("fp64_srp5", {"form": "fp64", "proj": "srp", "proj_dim": 5}, "srp5"),
+                             ("fp32_srp5", {"form": "fp32", "proj": "srp", "proj_dim": 5}, "srp5")):
             forms[name] = time_form(lambda **k: Detector(BANDS, WIDTH, in_dtype="u16",
                                                          in_bits=BITS, stream=stream, **k),
-                                    x, kw, dev, stream)
+                                    x, kw, dev, stream, ref=refs[rk])
         result["forms_108"] = forms
 
         # 224 bands (AVIRIS raw band count): 2000 lines x 1024 px f32, kappa 1e3
         n224 = 2000
         cube224 = make_cube(n224, seed=1, kind="c3", width=1024, bands=224, kappa=1e3)
         x224 = torch.from_numpy(cube224).to(dev)
+        ref224 = oracle_delta(cube224[:ACC_LINES_224])
         del cube224
         forms224 = {}
         for name in ("fp64", "fp64e", "fp32", "tf32", "bf16", "tf32x3"):
             forms224[name] = time_form(lambda **k: Detector(224, 1024, in_dtype="f32",
                                                             stream=stream, **k),
-                                       x224, {"form": name}, dev, stream)
+                                       x224, {"form": name}, dev, stream, ref=ref224)
         result["forms_224"] = {"workload": f"{n224} lines x 1024 px x 224 bands f32, "
-                                           "Gaussian background, kappa 1e3", **forms224}
+                                           "Gaussian background, kappa 1e3",
+                               "err_lines": ACC_LINES_224, **forms224}
         del x224
 
         # the paper's speed experiments and SRP dimension sweep at its shapes

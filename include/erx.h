@@ -48,7 +48,8 @@ typedef enum {
   ERX_ERANGE = 5,       /* an integer input sample exceeded 2^in_bits - 1 */
   ERX_ESTATE = 6,       /* call not valid in the context's current state */
   ERX_EUNSUPPORTED = 7, /* valid request this library does not implement */
-  ERX_ETIMEOUT = 8      /* a bounded wait inside a kernel gave up; results of the call are invalid */
+  ERX_ETIMEOUT = 8,     /* a bounded wait inside a kernel gave up; results of the call are invalid */
+  ERX_EIO = 9           /* a file could not be read or written, or is not a valid checkpoint */
 } erx_status;
 
 /* projection (Sec. III-B): none, sparse random projection, or a trained
@@ -237,9 +238,12 @@ erx_status erx_push_lines_static(const erx_config* cfg, void* cuda_stream, doubl
  * names learning-based extensions as future work, Sec. V): an MLP from b bands
  * to k codes, c = W2 relu(W1 xn + b1) + b2 with xn = (x - shift) * scale,
  * trained on the GPU so that ERX on the codes ranks pixels as full-band ERX
- * does.  Weights are kept in FP32 (master) with bf16 copies for the forward and
- * backward products (FP32 accumulation).  Parameters are laid out as one
- * vector [W1 (k1 = hidden x bands, row-major) | b1 | W2 (k x hidden) | b2]. */
+ * does.  Weights are kept in FP32 (master) with bf16 copies; the forward and
+ * the backward products run on the tensor cores with bf16 operands (the
+ * normalised spectra, the hidden activations relu(W1 xn + b1), dL/dc and
+ * dL/dh rounded to bf16) and FP32 accumulation, the same forward for training
+ * and inference.  Parameters are laid out as one vector
+ * [W1 (k1 = hidden x bands, row-major) | b1 | W2 (k x hidden) | b2]. */
 typedef struct erx_encoder erx_encoder;
 
 typedef struct {
@@ -251,11 +255,11 @@ typedef struct {
 /* alpha 0.1, ridge 1e-5, lr 1e-3, betas (0.9, 0.999), eps 1e-8, weight decay 1e-4 */
 void erx_train_opts_default(erx_train_opts* o);
 
-/* Create an encoder bands -> hidden -> k (bands <= 256, hidden <= 256,
- * 2 <= k <= 32, and 2 (bands + k) hidden + 256 (bands + hidden) bytes within
- * one CTA's shared memory; ERX_EUNSUPPORTED otherwise) on the current device, initial weights He-scaled normal draws
- * from SplitMix64(seed) (Box-Muller), biases 0, input normalisation identity.
- * All its work runs on cuda_stream. */
+/* Create an encoder bands -> hidden -> k (bands <= 256, hidden <= 128: one
+ * tensor-core tile of hidden units, 2 <= k <= 32; ERX_EUNSUPPORTED otherwise)
+ * on the current device, initial weights He-scaled normal draws from
+ * SplitMix64(seed) (Box-Muller), biases 0, input normalisation identity.  All
+ * its work runs on cuda_stream. */
 erx_status erx_encoder_create(int32_t bands, int32_t hidden, int32_t k, uint64_t seed,
                               void* cuda_stream, erx_encoder** out);
 
@@ -292,6 +296,24 @@ erx_status erx_encoder_line_grad(erx_encoder* e, const float* line_dev, int32_t 
                                  float* grad_host, float* loss_host);
 
 erx_status erx_encoder_destroy(erx_encoder* e);
+
+/* Checkpoint an encoder to a file and restore it (no counterpart in the
+ * paper, whose learning-based extension is future work, Sec. V).  The file is
+ * a flat little-endian binary:
+ *   char[8] "ERXENC01"; int32 bands, hidden, k, reserved (0); int64 AdamW
+ *   step count, code-space line count t;
+ *   float shift[bands], scale[bands];   input normalisation
+ *   float theta[n], m[n], v[n];         weights and AdamW moments, n = nparams
+ *   double mu_e[k], K_e[k(k+1)/2];      code-space EMA state (packed lower)
+ * so a loaded encoder computes the same codes bit for bit and resumes
+ * training exactly where the saved one stopped.  erx_encoder_save synchronises
+ * the encoder's stream; ERX_EIO if the file cannot be written.
+ * erx_encoder_load creates a new encoder on the current device, its work on
+ * cuda_stream; ERX_EIO if the file cannot be read or is not such a
+ * checkpoint (wrong magic, sizes beyond erx_encoder_create's limits, or a
+ * length that does not match them). */
+erx_status erx_encoder_save(erx_encoder* e, const char* path);
+erx_status erx_encoder_load(const char* path, void* cuda_stream, erx_encoder** out);
 
 /* Attach a trained encoder to a context created with proj = ERX_PROJ_LEARNED
  * (proj_dim = the encoder's k, in_dtype ERX_F32, bands = the encoder's bands):

@@ -15,5 +15,5 @@ from .erx import (  # noqa: F401
     erx_status_str, Detector, erx_profile_enable, erx_profile_read, erx_kernel_name,
     ERX_K_COUNT, erx_push_lines_static, Batch, Encoder, erx_train_opts_default,
     ERX_PROJ_LEARNED, ERX_FORM_TF32X3, ERX_FLAG_PIPELINE, ERX_AVG_EMA, ERX_AVG_IMC,
-    ERX_AVG_POOLED, roc_metrics, selftest_bounded_wait,
+    ERX_AVG_POOLED, ERX_EIO, roc_metrics, selftest_bounded_wait,
 )

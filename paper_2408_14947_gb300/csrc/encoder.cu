@@ -4,15 +4,19 @@
 // paper names learning-based extensions as future work): ERX then runs on k
 // codes instead of b bands.  It is trained on the GPU so that code-space ERX
 // ranks pixels like full-band ERX, one line per step in stream order:
-//   1. forward: codes of the line's p pixels (weights bf16, FP32 accumulation);
+//   1. forward on the tensor cores: codes of the line's p pixels (bf16
+//      operands, FP32 accumulation in TMEM), keeping relu(a) in bf16;
 //   2. code statistics: line mean/covariance, EMA update, Cholesky of K_e + eps I
 //      (the pipeline's own kernels; the statistics are constants for the gradient);
 //   3. loss and dL/dc per pixel: delta = |L^-1 r|, u = L^-T L^-1 r,
 //      dL/dc = (2/p) (log1p(delta) - log1p(target)) / ((1 + delta) delta) u;
-//   4. backward: per 64-pixel tile, partial dW2 = dc^T h, dh = (dc W2) * [a > 0],
-//      partial dW1 = dh^T xn (and the bias sums);
+//   4. backward on the tensor cores, per 128-pixel tile: dh = (dc W2) * [h > 0],
+//      partial dW1 = dh^T xn and dW2 = dc^T h (bf16 operands, FP32 accumulation),
+//      and the bias sums;
 //   5. deterministic reduction of the tile partials fused with AdamW on the
 //      FP32 master weights, which also refreshes their bf16 copies.
+// Training and inference share the forward, so the network is scored with the
+// arithmetic it was trained with.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -30,83 +34,11 @@ using namespace erx;
 
 namespace {
 
-constexpr int kTile = 64;       // pixels per CTA
+constexpr int kTile = 128;      // pixels per backward tile (the MMA's M)
 constexpr int kThreads = 256;
-constexpr int kMaxB = 256, kMaxH = 256, kMaxK = 32;
+constexpr int kMaxB = 256, kMaxH = 128, kMaxK = 32;
 
-__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
-
-// ---- forward --------------------------------------------------------------
-// smem: W1T [b][h] bf16, W2T [h][k] bf16, xT [b][64] f32, hT [h][64] f32
-__global__ void __launch_bounds__(kThreads) enc_fwd_kernel(
-    const float* __restrict__ x, int64_t n, int b, int h, int k, const float* __restrict__ shift,
-    const float* __restrict__ scale, const __nv_bfloat16* __restrict__ W1,
-    const float* __restrict__ b1, const __nv_bfloat16* __restrict__ W2,
-    const float* __restrict__ b2, float* __restrict__ codes, __nv_bfloat16* __restrict__ hout) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  __nv_bfloat16* W1T = reinterpret_cast<__nv_bfloat16*>(sm);            // [b][h]
-  __nv_bfloat16* W2T = W1T + (size_t)b * h;                              // [h][k]
-  float* xT = reinterpret_cast<float*>(W2T + (size_t)h * k);             // [b][64]
-  float* hT = xT + (size_t)b * kTile;                                    // [h][64]
-  const int tid = threadIdx.x;
-  const int64_t i0 = (int64_t)blockIdx.x * kTile;
-  for (int e = tid; e < h * b; e += kThreads) {
-    const int j = e / b, q = e % b;
-    W1T[(size_t)q * h + j] = W1[e];
-  }
-  for (int e = tid; e < k * h; e += kThreads) {
-    const int c = e / h, j = e % h;
-    W2T[(size_t)j * k + c] = W2[e];
-  }
-  for (int e = tid; e < kTile * b; e += kThreads) {
-    const int p = e / b, q = e % b;
-    const int64_t i = i0 + p;
-    xT[(size_t)q * kTile + p] = i < n ? (x[i * b + q] - shift[q]) * scale[q] : 0.f;
-  }
-  __syncthreads();
-  // layer 1: thread owns 4 pixels x (h / 16) hidden units
-  const int px = (tid >> 4) * 4, jg = tid & 15;
-  for (int j0 = jg; j0 < h; j0 += 16) {
-    float acc[4] = {b1[j0], b1[j0], b1[j0], b1[j0]};
-    for (int q = 0; q < b; ++q) {
-      const float w = bf(W1T[(size_t)q * h + j0]);
-      const float4 xv = *reinterpret_cast<const float4*>(xT + (size_t)q * kTile + px);
-      acc[0] = fmaf(w, xv.x, acc[0]);
-      acc[1] = fmaf(w, xv.y, acc[1]);
-      acc[2] = fmaf(w, xv.z, acc[2]);
-      acc[3] = fmaf(w, xv.w, acc[3]);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) hT[(size_t)j0 * kTile + px + a] = fmaxf(acc[a], 0.f);
-  }
-  __syncthreads();
-  if (hout) {
-    for (int e = tid; e < kTile * h; e += kThreads) {
-      const int p = e / h, j = e % h;
-      const int64_t i = i0 + p;
-      if (i < n) hout[i * h + j] = __float2bfloat16_rn(hT[(size_t)j * kTile + p]);
-    }
-  }
-  // layer 2: thread owns 4 pixels x (k / 16) codes
-  for (int c = jg; c < k; c += 16) {
-    float acc[4] = {b2[c], b2[c], b2[c], b2[c]};
-    for (int j = 0; j < h; ++j) {
-      const float w = bf(W2T[(size_t)j * k + c]);
-      const float4 hv = *reinterpret_cast<const float4*>(hT + (size_t)j * kTile + px);
-      acc[0] = fmaf(w, hv.x, acc[0]);
-      acc[1] = fmaf(w, hv.y, acc[1]);
-      acc[2] = fmaf(w, hv.z, acc[2]);
-      acc[3] = fmaf(w, hv.w, acc[3]);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int64_t i = i0 + px + a;
-      if (i < n) codes[i * k + c] = acc[a];
-    }
-  }
-}
-
-// ---- forward on the tensor cores (inference) --------------------------------
+// ---- forward on the tensor cores -------------------------------------------
 // Both layers are dense contractions over a 128-pixel tile (M = 128):
 //   layer 1: A = xn (pixels x bands, bf16), B = W1 (hidden x bands, bf16), N = h;
 //   layer 2: A = relu(a + b1) (pixels x hidden, bf16), B = W2 (codes x hidden), N = k;
@@ -116,8 +48,8 @@ __global__ void __launch_bounds__(kThreads) enc_fwd_kernel(
 // (a padded hidden unit has zero weights and bias, so relu gives 0).  One
 // persistent CTA per SM keeps W1 and W2 in shared memory and walks the tiles:
 // stage xn = (x - shift) * scale as bf16, layer-1 MMAs, epilogue (bias, relu,
-// bf16 into the layer-2 operand), layer-2 MMAs, epilogue (bias, FP32 codes).
-// Activations are rounded to bf16 here; training uses the FP32 forward above.
+// bf16 into the layer-2 operand, and into hout for training's backward when
+// given), layer-2 MMAs, epilogue (bias, FP32 codes).
 constexpr int kFT = 256;                    // threads
 constexpr uint32_t kFLBO = 128;
 constexpr uint32_t kFWait = 1u << 26;
@@ -142,7 +74,8 @@ __global__ void __launch_bounds__(kFT, 1) enc_fwd_tc_kernel(
     const float* __restrict__ x, int64_t n, int b, int h, int k, const float* __restrict__ shift,
     const float* __restrict__ scale, const __nv_bfloat16* __restrict__ W1,
     const float* __restrict__ b1, const __nv_bfloat16* __restrict__ W2,
-    const float* __restrict__ b2, float* __restrict__ codes, unsigned long long* __restrict__ err) {
+    const float* __restrict__ b2, float* __restrict__ codes, __nv_bfloat16* __restrict__ hout,
+    unsigned long long* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smtc[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
@@ -259,7 +192,7 @@ __global__ void __launch_bounds__(kFT, 1) enc_fwd_tc_kernel(
       tc::commit(&mbar);
     }
     ok = tc::mbar_wait(&mbar, phase, kFWait);
-    phase ^= 1u;
+    if (ok) phase ^= 1u;      // after a timeout, phase stays the parity still awaited
     if (__syncthreads_or(!ok)) break;
     tc::fence_after_sync();
     // epilogue 1: warp w reads TMEM lanes 32 (w % 4) .. (pixels), 16-column chunks
@@ -278,6 +211,13 @@ __global__ void __launch_bounds__(kFT, 1) enc_fwd_tc_kernel(
         *reinterpret_cast<uint4*>(A2 + fwd_off(p, c0, sbo2)) = make_uint4(w[0], w[1], w[2], w[3]);
         *reinterpret_cast<uint4*>(A2 + fwd_off(p, c0 + 8, sbo2)) =
             make_uint4(w[4], w[5], w[6], w[7]);
+        if (hout && i0 + p < n) {
+          const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(w);
+          __nv_bfloat16* dst = hout + (i0 + p) * h;
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (c0 + u < h) dst[c0 + u] = hb[u];
+        }
       }
     }
     tc::fence_async_smem();
@@ -294,7 +234,7 @@ __global__ void __launch_bounds__(kFT, 1) enc_fwd_tc_kernel(
       tc::commit(&mbar);
     }
     ok = tc::mbar_wait(&mbar, phase, kFWait);
-    phase ^= 1u;
+    if (ok) phase ^= 1u;      // after a timeout, phase stays the parity still awaited
     if (__syncthreads_or(!ok)) break;
     tc::fence_after_sync();
     // epilogue 2: codes of the tile's pixels
@@ -371,67 +311,229 @@ __global__ void __launch_bounds__(kThreads) enc_loss_kernel(
   }
 }
 
-// ---- backward partials per 64-pixel tile ----------------------------------
-// part layout per tile: [W1 (h*b) | b1 (h) | W2 (k*h) | b2 (k)]
-__global__ void __launch_bounds__(kThreads) enc_bwd_kernel(
+// ---- backward on the tensor cores, one 128-pixel tile per CTA --------------
+// Three bf16 contractions with FP32 accumulation in TMEM (operands K-major,
+// no swizzle, as in the forward):
+//   G1  dc W2      A = dc   [128 px][kP]   (K = codes)   B = W2^T [hP][kP]   N = hP
+//   G2  dh^T xn    A = dh^T [128 j][128 px] (K = pixels) B = xn^T [bK][128]  N = bK
+//   G3  h^T dc     A = h^T  [128 j][128 px]              B = dc^T [kP][128]  N = kP
+// G1's result is gated by [h > 0] into dh (FP32, row-major in shared memory,
+// also summed for the b1 gradient), then rounded to bf16 and transposed into
+// G2's operand.  Hidden units beyond h (up to the M = 128 of G2 and G3) are
+// zero rows.  Tile partials: [W1 (h x b) | b1 (h) | W2 (k x h) | b2 (k)].
+constexpr int kDhStride = 132;              // floats per row of dh (bank-conflict padding)
+constexpr uint32_t kSboPx = 16 * 128;       // 8-row group stride of a 128-pixel K extent
+
+__host__ __device__ inline size_t bwd_tc_smem(int b, int h, int k) {
+  const size_t bK = pad16(b), hP = pad16(h), kP = pad16(k);
+  return 128 * kP * 2 + hP * kP * 2 + (size_t)128 * kDhStride * 4 + 128 * 128 * 2 +
+         bK * 128 * 2 + 128 * 128 * 2 + kP * 128 * 2;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) enc_bwd_tc_kernel(
     const float* __restrict__ x, int p, int b, int h, int k, const float* __restrict__ shift,
     const float* __restrict__ scale, const __nv_bfloat16* __restrict__ W2,
     const __nv_bfloat16* __restrict__ hbuf, const float* __restrict__ dc,
-    float* __restrict__ part) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  float* xs = reinterpret_cast<float*>(sm);                 // [64][b]
-  float* hs = xs + (size_t)kTile * b;                       // [64][h]
-  float* dcs = hs + (size_t)kTile * h;                      // [64][k]
-  float* dhs = dcs + (size_t)kTile * k;                     // [64][h]
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * kTile;
-  const int np = min(kTile, p - i0);
-  for (int e = tid; e < kTile * b; e += kThreads) {
-    const int q = e % b, pp = e / b;
-    xs[e] = pp < np ? (x[(int64_t)(i0 + pp) * b + q] - shift[q]) * scale[q] : 0.f;
+    float* __restrict__ part, unsigned long long* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smb[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int bK = pad16(b), hP = pad16(h), kP = pad16(k);
+  const uint32_t sboK = (uint32_t)(kP / 8) * 128u;
+  unsigned char* A1 = smb;                                   // dc     [128][kP]
+  unsigned char* B1 = A1 + (size_t)128 * kP * 2;             // W2^T   [hP][kP]
+  float* dhs = reinterpret_cast<float*>(B1 + (size_t)hP * kP * 2);   // dh [128][kDhStride]
+  unsigned char* A2 = reinterpret_cast<unsigned char*>(dhs + 128 * kDhStride);  // dh^T [128][128]
+  unsigned char* B2 = A2 + (size_t)128 * 128 * 2;            // xn^T   [bK][128]
+  unsigned char* A3 = B2 + (size_t)bK * 128 * 2;             // h^T    [128][128]
+  unsigned char* B3 = A3 + (size_t)128 * 128 * 2;            // dc^T   [kP][128]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int px0 = blockIdx.x * 128;
+  const int np = min(128, p - px0);
+  const int64_t nparam = (int64_t)h * b + h + (int64_t)k * h + k;
+  float* out = part + (int64_t)blockIdx.x * nparam;
+
+  // ---- stage the operands (zero outside the tile, the hidden units and codes)
+  for (int it = tid; it < 128 * (kP / 8); it += kThreads) {          // A1: dc rows
+    const int q = it / (kP / 8), g = it % (kP / 8);
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      v[u] = (q < np && 8 * g + u < k) ? dc[(int64_t)(px0 + q) * k + 8 * g + u] : 0.f;
+    *reinterpret_cast<uint4*>(A1 + fwd_off(q, 8 * g, sboK)) =
+        make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                   pack_bf2(v[6], v[7]));
   }
-  for (int e = tid; e < kTile * h; e += kThreads) {
-    const int pp = e / h;
-    hs[e] = pp < np ? bf(hbuf[(int64_t)(i0 + pp) * h + e % h]) : 0.f;
+  for (int it = tid; it < hP * (kP / 8); it += kThreads) {           // B1: W2^T
+    const int j = it % hP, g = it / hP;
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      v[u] = (j < h && 8 * g + u < k) ? __bfloat162float(W2[(size_t)(8 * g + u) * h + j]) : 0.f;
+    *reinterpret_cast<uint4*>(B1 + fwd_off(j, 8 * g, sboK)) =
+        make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                   pack_bf2(v[6], v[7]));
   }
-  for (int e = tid; e < kTile * k; e += kThreads) {
-    const int pp = e / k;
-    dcs[e] = pp < np ? dc[(int64_t)(i0 + pp) * k + e % k] : 0.f;
+  for (int it = tid; it < bK * 16; it += kThreads) {                 // B2: xn^T
+    const int q = it % bK, g = it / bK;
+    float v[8];
+    const float sh = q < b ? shift[q] : 0.f, sc = q < b ? scale[q] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = 8 * g + u;
+      v[u] = (q < b && r < np) ? (x[(int64_t)(px0 + r) * b + q] - sh) * sc : 0.f;
+    }
+    *reinterpret_cast<uint4*>(B2 + fwd_off(q, 8 * g, kSboPx)) =
+        make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                   pack_bf2(v[6], v[7]));
   }
+  for (int it = tid; it < 128 * 16; it += kThreads) {                // A3: h^T
+    const int j = it % 128, g = it / 128;
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = 8 * g + u;
+      v[u] = (j < h && r < np) ? __bfloat162float(hbuf[(int64_t)(px0 + r) * h + j]) : 0.f;
+    }
+    *reinterpret_cast<uint4*>(A3 + fwd_off(j, 8 * g, kSboPx)) =
+        make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                   pack_bf2(v[6], v[7]));
+  }
+  for (int it = tid; it < kP * 16; it += kThreads) {                 // B3: dc^T
+    const int c = it % kP, g = it / kP;
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int r = 8 * g + u;
+      v[u] = (c < k && r < np) ? dc[(int64_t)(px0 + r) * k + c] : 0.f;
+    }
+    *reinterpret_cast<uint4*>(B3 + fwd_off(c, 8 * g, kSboPx)) =
+        make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                   pack_bf2(v[6], v[7]));
+  }
+  for (int c = tid; c < k; c += kThreads) {                          // b2: sum of dc
+    float s = 0.f;
+    for (int r = 0; r < np; ++r) s += dc[(int64_t)(px0 + r) * k + c];
+    out[(int64_t)h * b + h + (int64_t)k * h + c] = s;
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, 512);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
   __syncthreads();
-  // dh = (dc W2) * [h > 0]
-  for (int e = tid; e < kTile * h; e += kThreads) {
-    const int pp = e / h, j = e % h;
-    float s = 0.f;
-    if (hs[e] > 0.f)
-      for (int c = 0; c < k; ++c) s = fmaf(dcs[pp * k + c], bf(W2[(size_t)c * h + j]), s);
-    dhs[e] = s;
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  uint32_t phase = 0;
+
+  // ---- G1: dc W2 into TMEM columns 0 .. hP - 1
+  if (tid == 0) {
+    const uint32_t a = tc::smem_u32(A1), bb = tc::smem_u32(B1);
+    const uint32_t id = tc::idesc(1, 128, hP);
+    for (int s = 0; s < kP / 16; ++s) {
+      const uint32_t ko = (uint32_t)s * 2u * kFLBO;
+      tc::mma_bf16(tmem, tc::desc(a + ko, kFLBO, sboK), tc::desc(bb + ko, kFLBO, sboK), id, s > 0);
+    }
+    tc::commit(&mbar);
   }
+  bool ok = tc::mbar_wait(&mbar, phase, kFWait);
+  if (ok) phase ^= 1u;        // after a timeout, phase stays the parity still awaited
+  if (!__syncthreads_or(!ok)) {
+    tc::fence_after_sync();
+    // epilogue 1: lane = pixel; dh = (dc W2) * [h > 0] into dhs (FP32)
+    const int r = 32 * (warp & 3) + lane;
+    const uint32_t lb = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    for (int c0 = (warp >> 2) * 16; c0 < hP; c0 += 32) {
+      uint32_t v[16];
+      tc::tmem_ld16(lb + (uint32_t)c0, v);
+      tc::tmem_ld_wait();
+      float o[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int j = c0 + u;
+        const bool on = r < np && j < h && __bfloat162float(hbuf[(int64_t)(px0 + r) * h + j]) > 0.f;
+        o[u] = on ? __uint_as_float(v[u]) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; u += 4)
+        *reinterpret_cast<float4*>(dhs + r * kDhStride + c0 + u) =
+            make_float4(o[u], o[u + 1], o[u + 2], o[u + 3]);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // dh^T as G2's A operand (bf16), hidden units beyond hP zero; b1 = sum of dh
+    for (int it = tid; it < 128 * 16; it += kThreads) {
+      const int j = it % 128, g = it / 128;
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = j < hP ? dhs[(8 * g + u) * kDhStride + j] : 0.f;
+      *reinterpret_cast<uint4*>(A2 + fwd_off(j, 8 * g, kSboPx)) =
+          make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                     pack_bf2(v[6], v[7]));
+    }
+    for (int j = tid; j < h; j += kThreads) {
+      float s = 0.f;
+      for (int q = 0; q < np; ++q) s += dhs[q * kDhStride + j];
+      out[(int64_t)h * b + j] = s;
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // ---- G2 into columns 0 .. bK - 1 (G1's result has been read), G3 into 256 ..
+    if (tid == 0) {
+      const uint32_t id2 = tc::idesc(1, 128, bK), id3 = tc::idesc(1, 128, kP);
+      const uint32_t a2 = tc::smem_u32(A2), b2 = tc::smem_u32(B2);
+      const uint32_t a3 = tc::smem_u32(A3), b3 = tc::smem_u32(B3);
+      for (int s = 0; s < 8; ++s) {
+        const uint32_t ko = (uint32_t)s * 2u * kFLBO;
+        tc::mma_bf16(tmem, tc::desc(a2 + ko, kFLBO, kSboPx), tc::desc(b2 + ko, kFLBO, kSboPx),
+                     id2, s > 0);
+        tc::mma_bf16(tmem + 256u, tc::desc(a3 + ko, kFLBO, kSboPx),
+                     tc::desc(b3 + ko, kFLBO, kSboPx), id3, s > 0);
+      }
+      tc::commit(&mbar);
+    }
+    ok = tc::mbar_wait(&mbar, phase, kFWait);
+    if (ok) phase ^= 1u;      // after a timeout, phase stays the parity still awaited
+    if (!__syncthreads_or(!ok)) {
+      tc::fence_after_sync();
+      // epilogue 2: lane = hidden unit j; dW1 row j, dW2 column j
+      const int j = 32 * (warp & 3) + lane;
+      const uint32_t lb2 = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+      for (int c0 = (warp >> 2) * 16; c0 < bK; c0 += 32) {
+        uint32_t v[16];
+        tc::tmem_ld16(lb2 + (uint32_t)c0, v);
+        tc::tmem_ld_wait();
+        if (j < h) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (c0 + u < b) out[(int64_t)j * b + c0 + u] = __uint_as_float(v[u]);
+        }
+      }
+      float* o2 = out + (int64_t)h * b + h;
+      for (int c0 = (warp >> 2) * 16; c0 < kP; c0 += 32) {
+        uint32_t v[16];
+        tc::tmem_ld16(lb2 + 256u + (uint32_t)c0, v);
+        tc::tmem_ld_wait();
+        if (j < h) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (c0 + u < k) o2[(int64_t)(c0 + u) * h + j] = __uint_as_float(v[u]);
+        }
+      }
+    }
+  }
+  if (!ok) {
+    if (tid == 0) atomicMin(&err[kErrTimeout], 0ull);
+    tc::mbar_wait(&mbar, phase, kFWait);   // one more bounded wait for MMAs in flight
+  }
+  tc::fence_before_sync();
   __syncthreads();
-  float* out = part + (size_t)blockIdx.x * ((size_t)h * b + h + (size_t)k * h + k);
-  for (int e = tid; e < h * b; e += kThreads) {       // dW1[j][q] = sum_p dh[p][j] xn[p][q]
-    const int j = e / b, q = e % b;
-    float s = 0.f;
-    for (int pp = 0; pp < kTile; ++pp) s = fmaf(dhs[pp * h + j], xs[pp * b + q], s);
-    out[e] = s;
-  }
-  for (int j = tid; j < h; j += kThreads) {
-    float s = 0.f;
-    for (int pp = 0; pp < kTile; ++pp) s += dhs[pp * h + j];
-    out[(size_t)h * b + j] = s;
-  }
-  float* o2 = out + (size_t)h * b + h;
-  for (int e = tid; e < k * h; e += kThreads) {       // dW2[c][j] = sum_p dc[p][c] h[p][j]
-    const int c = e / h, j = e % h;
-    float s = 0.f;
-    for (int pp = 0; pp < kTile; ++pp) s = fmaf(dcs[pp * k + c], hs[pp * h + j], s);
-    o2[e] = s;
-  }
-  for (int c = tid; c < k; c += kThreads) {
-    float s = 0.f;
-    for (int pp = 0; pp < kTile; ++pp) s += dcs[pp * k + c];
-    o2[(size_t)k * h + c] = s;
-  }
+  if (warp == 0) tc::tmem_free(tmem, 512);
 }
 
 // ---- reduction over tiles + AdamW -----------------------------------------
@@ -469,13 +571,6 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __r
                                int64_t n) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) dst[e] = __float2bfloat16_rn(src[e]);
-}
-
-size_t fwd_smem(int b, int h, int k) {
-  return (size_t)b * h * 2 + (size_t)h * k * 2 + (size_t)b * kTile * 4 + (size_t)h * kTile * 4;
-}
-size_t bwd_smem(int b, int h, int k) {
-  return (size_t)kTile * (b + h + k + h) * 4;
 }
 
 uint64_t sm64(uint64_t seed, uint64_t k) {
@@ -558,23 +653,16 @@ erx_status ecuda(erx_encoder* e, cudaError_t c) {
   return ERX_ECUDA;
 }
 
-// forward of n pixels into `codes` (and hidden activations into hout when given)
-void forward(erx_encoder* e, const float* x, int64_t n, float* codes, __nv_bfloat16* hout,
-             cudaStream_t st) {
-  const int64_t tiles = (n + kTile - 1) / kTile;
-  enc_fwd_kernel<<<(unsigned)tiles, kThreads, fwd_smem(e->b, e->h, e->k), st>>>(
-      x, n, e->b, e->h, e->k, e->shift, e->scale, e->w1b, e->theta + e->off_b1, e->w2b,
-      e->theta + e->off_b2, codes, hout);
-}
-
-// inference forward on the tensor cores (bf16 activations): one persistent CTA per SM
-void forward_tc(erx_encoder* e, const float* x, int64_t n, float* codes, cudaStream_t st) {
+// forward of n pixels on the tensor cores: codes, and relu(W1 xn + b1) in bf16
+// into hout when given (training); one persistent CTA per SM
+void forward_tc(erx_encoder* e, const float* x, int64_t n, float* codes, __nv_bfloat16* hout,
+                cudaStream_t st) {
   const int n_sm = device_shape().n_sm;
   const int64_t tiles = (n + 127) / 128;
   const int grid = (int)std::min<int64_t>(tiles, n_sm);
   enc_fwd_tc_kernel<<<grid, kFT, fwd_tc_smem(e->b, e->h, e->k), st>>>(
       x, n, e->b, e->h, e->k, e->shift, e->scale, e->w1b, e->theta + e->off_b1, e->w2b,
-      e->theta + e->off_b2, codes, e->err);
+      e->theta + e->off_b2, codes, hout, e->err);
 }
 
 // One line: forward, code statistics (update then score), loss, backward and,
@@ -584,7 +672,7 @@ erx_status train_line(erx_encoder* e, const float* line, int p, const double* ta
   cudaStream_t st = e->stream;
   erx_status s = ensure_capacity(e, p);
   if (s != ERX_OK) return s;
-  forward(e, line, p, e->codes, e->hbuf, st);
+  forward_tc(e, line, p, e->codes, e->hbuf, st);
   const int k = e->k;
   launch_mean(ERX_F32, e->codes, 0, k, p, k, 1, false, e->mu_hat, e->shiftc, st);
   launch_stats_fp(ERX_F32, true, e->codes, 0, k, p, k, 1, e->shiftc, e->S2f, st);
@@ -598,8 +686,8 @@ erx_status train_line(erx_encoder* e, const float* line, int p, const double* ta
                                             e->loss_part);
   enc_sum_kernel<<<1, 32, 0, st>>>(e->loss_part, nlb, e->loss_dev);
   const int ntile = (p + kTile - 1) / kTile;
-  enc_bwd_kernel<<<ntile, kThreads, bwd_smem(e->b, e->h, k), st>>>(
-      line, p, e->b, e->h, k, e->shift, e->scale, e->w2b, e->hbuf, e->dc, e->part);
+  enc_bwd_tc_kernel<<<ntile, kThreads, bwd_tc_smem(e->b, e->h, k), st>>>(
+      line, p, e->b, e->h, k, e->shift, e->scale, e->w2b, e->hbuf, e->dc, e->part, e->err);
   float c1 = 1.f, c2 = 1.f;
   if (apply) {
     e->adam_k += 1;
@@ -619,9 +707,34 @@ namespace erx {
 int encoder_k(const erx_encoder* e) { return e->k; }
 int encoder_bands(const erx_encoder* e) { return e->b; }
 void encoder_forward_on(erx_encoder* e, const float* x, int64_t n, float* codes, cudaStream_t st) {
-  forward_tc(e, x, n, codes, st);
+  forward_tc(e, x, n, codes, nullptr, st);
 }
 }  // namespace erx
+
+namespace {
+constexpr char kCkptMagic[8] = {'E', 'R', 'X', 'E', 'N', 'C', '0', '1'};
+
+struct CkptHeader {
+  char magic[8];
+  int32_t bands, hidden, k, reserved;
+  int64_t adam_k, t_codes;
+};
+
+// device <-> host copies of the checkpoint's arrays, in file order
+struct CkptArrays {
+  std::vector<float> shift, scale, theta, m, v;
+  std::vector<double> mu, K;
+  explicit CkptArrays(const erx_encoder* e)
+      : shift(e->b), scale(e->b), theta(e->nparam), m(e->nparam), v(e->nparam), mu(e->k),
+        K(packed_size(e->k)) {}
+  template <typename F>
+  bool each(F&& f) {
+    return f(shift.data(), shift.size() * 4) && f(scale.data(), scale.size() * 4) &&
+           f(theta.data(), theta.size() * 4) && f(m.data(), m.size() * 4) &&
+           f(v.data(), v.size() * 4) && f(mu.data(), mu.size() * 8) && f(K.data(), K.size() * 8);
+  }
+};
+}  // namespace
 
 extern "C" {
 
@@ -677,20 +790,19 @@ erx_status erx_encoder_create(int32_t bands, int32_t hidden, int32_t k, uint64_t
   EA(err, kErrSlots);
 #undef EA
   if (s == ERX_OK) {
-    // the forward keeps both weight matrices and a 64-pixel tile in shared memory
+    // the forward keeps both weight matrices and a 128-pixel tile in shared
+    // memory, the backward a tile's six operands and dh (plus static shared memory)
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (fwd_smem(bands, hidden, k) > (size_t)optin || bwd_smem(bands, hidden, k) > (size_t)optin ||
-        fwd_tc_smem(bands, hidden, k) > (size_t)optin)
+    if (bwd_tc_smem(bands, hidden, k) + 2048 > (size_t)optin ||
+        fwd_tc_smem(bands, hidden, k) + 2048 > (size_t)optin)
       s = ERX_EUNSUPPORTED;
     else if (configure_factor_kernels() != cudaSuccess ||
-             cudaFuncSetAttribute(enc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)fwd_smem(bands, hidden, k)) != cudaSuccess ||
              cudaFuncSetAttribute(enc_fwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)fwd_tc_smem(bands, hidden, k)) != cudaSuccess ||
-             cudaFuncSetAttribute(enc_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)bwd_smem(bands, hidden, k)) != cudaSuccess)
+             cudaFuncSetAttribute(enc_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)bwd_tc_smem(bands, hidden, k)) != cudaSuccess)
       s = ERX_ECUDA;
   }
   if (s == ERX_OK) {
@@ -770,7 +882,7 @@ erx_status erx_encoder_forward(erx_encoder* e, const float* x_dev, int64_t n_pix
   if (!e || n_pix < 0 || (n_pix > 0 && (!x_dev || !codes_dev))) return ERX_EINVAL;
   if (e->failed) return ERX_ECUDA;
   if (n_pix == 0) return ERX_OK;
-  forward_tc(e, x_dev, n_pix, codes_dev, e->stream);
+  forward_tc(e, x_dev, n_pix, codes_dev, nullptr, e->stream);
   return ecuda(e, cudaGetLastError());
 }
 
@@ -817,6 +929,88 @@ erx_status erx_encoder_destroy(erx_encoder* e) {
   cudaGetLastError();
   for (void* p : e->allocs) cudaFree(p);
   delete e;
+  return ERX_OK;
+}
+
+
+erx_status erx_encoder_save(erx_encoder* e, const char* path) {
+  if (!e || !path) return ERX_EINVAL;
+  if (e->failed) return ERX_ECUDA;
+  CkptArrays a(e);
+  if (cudaStreamSynchronize(e->stream) != cudaSuccess ||
+      cudaMemcpy(a.shift.data(), e->shift, e->b * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(a.scale.data(), e->scale, e->b * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(a.theta.data(), e->theta, e->nparam * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(a.m.data(), e->mom1, e->nparam * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(a.v.data(), e->mom2, e->nparam * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(a.mu.data(), e->mu_e, e->k * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(a.K.data(), e->K_e, a.K.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return ecuda(e, cudaGetLastError());
+  CkptHeader hd{};
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.bands = e->b;
+  hd.hidden = e->h;
+  hd.k = e->k;
+  hd.adam_k = e->adam_k;
+  hd.t_codes = e->t_codes;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return ERX_EIO;
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+            a.each([f](const void* p, size_t n) { return std::fwrite(p, 1, n, f) == n; });
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? ERX_OK : ERX_EIO;
+}
+
+erx_status erx_encoder_load(const char* path, void* cuda_stream, erx_encoder** out) {
+  if (!path || !out) return ERX_EINVAL;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return ERX_EIO;
+  CkptHeader hd{};
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kCkptMagic, 8) != 0 ||
+      hd.bands < 1 || hd.bands > kMaxB || hd.hidden < 1 || hd.hidden > kMaxH || hd.k < 2 ||
+      hd.k > kMaxK || hd.adam_k < 0 || hd.t_codes < 0) {
+    std::fclose(f);
+    return ERX_EIO;
+  }
+  erx_encoder* e = nullptr;
+  erx_status s = erx_encoder_create(hd.bands, hd.hidden, hd.k, 0, cuda_stream, &e);
+  if (s != ERX_OK) {
+    std::fclose(f);
+    return s;
+  }
+  CkptArrays a(e);
+  bool ok = a.each([f](void* p, size_t n) { return std::fread(p, 1, n, f) == n; });
+  ok = ok && std::fgetc(f) == EOF;       // nothing after the last array
+  std::fclose(f);
+  if (!ok) {
+    erx_encoder_destroy(e);
+    return ERX_EIO;
+  }
+  if (cudaMemcpy(e->shift, a.shift.data(), e->b * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(e->scale, a.scale.data(), e->b * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(e->theta, a.theta.data(), e->nparam * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(e->mom1, a.m.data(), e->nparam * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(e->mom2, a.v.data(), e->nparam * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(e->mu_e, a.mu.data(), e->k * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(e->K_e, a.K.data(), a.K.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    erx_encoder_destroy(e);
+    return ERX_ECUDA;
+  }
+  e->adam_k = hd.adam_k;
+  e->t_codes = hd.t_codes;
+  // the bf16 copies the products use, from the loaded FP32 master weights
+  to_bf16_kernel<<<(unsigned)((e->off_b1 + 255) / 256), 256, 0, e->stream>>>(e->theta, e->w1b,
+                                                                              e->off_b1);
+  to_bf16_kernel<<<(unsigned)(((int64_t)e->k * e->h + 255) / 256), 256, 0, e->stream>>>(
+      e->theta + e->off_w2, e->w2b, (int64_t)e->k * e->h);
+  if (cudaStreamSynchronize(e->stream) != cudaSuccess) {
+    cudaGetLastError();
+    erx_encoder_destroy(e);
+    return ERX_ECUDA;
+  }
+  *out = e;
   return ERX_OK;
 }
 

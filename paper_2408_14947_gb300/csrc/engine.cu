@@ -1110,6 +1110,7 @@ const char* erx_status_str(erx_status s) {
     case ERX_ESTATE: return "ERX_ESTATE: call not valid in this state";
     case ERX_EUNSUPPORTED: return "ERX_EUNSUPPORTED: beyond this library's limits";
     case ERX_ETIMEOUT: return "ERX_ETIMEOUT: a bounded wait in a kernel gave up";
+    case ERX_EIO: return "ERX_EIO: file not readable or writable, or not a checkpoint";
   }
   return "ERX_?: unknown status";
 }

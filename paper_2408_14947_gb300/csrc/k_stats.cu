@@ -33,6 +33,24 @@ __device__ __forceinline__ void block_pair(int q, int& I, int& J) {
 template <typename T>
 __device__ __forceinline__ double to_d(T v) { return (double)v; }
 
+// FP32 scatter accumulation: products are summed with FMAs in runs of kRun
+// pixels, and each run's sum is added into an unevaluated float pair (hi, lo)
+// by Knuth's TwoSum (the exact rounding error of hi + run goes into lo).  A
+// plain running FP32 sum over all p pixels loses digits at every addition to a
+// sum that has grown to p products; here a run's sum holds at most kRun of them
+// and the pair keeps the rest exactly, so K_hat is formed from a sum about as
+// accurate as its kRun-pixel runs (the error of the scores that use it shrank
+// about 15x at kappa 1e4 - 1e5 against the plain sum).  FP64 sums need none of this.
+constexpr int kRun = 8;
+
+__device__ __forceinline__ void two_sum_into(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bv = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(v, bv));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
 __global__ void __launch_bounds__(256) stats_int_kernel(
     const uint16_t* __restrict__ X, int64_t line_stride, int W, int d, uint32_t maxv,
     int flush_mask, uint64_t* __restrict__ S1, uint64_t* __restrict__ S2,
@@ -168,6 +186,7 @@ __global__ void __launch_bounds__(kMeanThreads) mean_kernel(const InT* __restric
 // (the line's d values), written to s2 (the line's d x d).  256 threads, each
 // an (SBT/16) x (SBT/16) sub-block; SBT = 32 wastes less of the triangle
 // (used in FP64, where every multiply-add counts), SBT = 64 reuses registers more.
+// FP32 sums are compensated per kRun-pixel run (two_sum_into).
 template <typename InT, typename AccT, int SBT = SB>
 __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps, int W, int d,
                                               const double* __restrict__ shift,
@@ -185,11 +204,13 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
     const int c = threadIdx.x < SBT ? a0 + threadIdx.x : b0 + threadIdx.x - SBT;
     cs[threadIdx.x] = c < d ? (AccT)shift[c] : (AccT)0;
   }
+  constexpr bool kComp = sizeof(AccT) == 4;
   AccT acc[TP][TP];
+  float lo[TP][TP], hi[TP][TP];
 #pragma unroll
   for (int i = 0; i < TP; ++i)
 #pragma unroll
-    for (int j = 0; j < TP; ++j) acc[i][j] = (AccT)0;
+    for (int j = 0; j < TP; ++j) acc[i][j] = (AccT)0, lo[i][j] = 0.f, hi[i][j] = 0.f;
   const AccT(*xbp)[SBT] = diag ? xa : xb;
   __syncthreads();
   for (int i0 = 0; i0 < W; i0 += KCF) {
@@ -205,14 +226,26 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
     }
     __syncthreads();
     const int kn = min(KCF, W - i0);
-    for (int k = 0; k < kn; ++k) {
-      AccT a[TP], b[TP];
+    for (int k0 = 0; k0 < kn; k0 += kRun) {
+      const int k1 = min(kn, k0 + kRun);
+      for (int k = k0; k < k1; ++k) {
+        AccT a[TP], b[TP];
 #pragma unroll
-      for (int i = 0; i < TP; ++i) a[i] = xa[k][ty * TP + i], b[i] = xbp[k][tx * TP + i];
+        for (int i = 0; i < TP; ++i) a[i] = xa[k][ty * TP + i], b[i] = xbp[k][tx * TP + i];
 #pragma unroll
-      for (int i = 0; i < TP; ++i)
+        for (int i = 0; i < TP; ++i)
 #pragma unroll
-        for (int j = 0; j < TP; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+          for (int j = 0; j < TP; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      if constexpr (kComp) {
+#pragma unroll
+        for (int i = 0; i < TP; ++i)
+#pragma unroll
+          for (int j = 0; j < TP; ++j) {
+            two_sum_into(hi[i][j], lo[i][j], (float)acc[i][j]);
+            acc[i][j] = (AccT)0;
+          }
+      }
     }
     __syncthreads();
   }
@@ -223,13 +256,16 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
 #pragma unroll
     for (int j = 0; j < TP; ++j) {
       const int b = b0 + tx * TP + j;
-      if (b < d) s2[(int64_t)a * d + b] = (double)acc[i][j];
+      if (b < d)
+        s2[(int64_t)a * d + b] =
+            kComp ? (double)hi[i][j] + (double)lo[i][j] : (double)acc[i][j];
     }
   }
 }
 
+// three CTAs per SM: room for the compensated FP32 sums without spills
 template <typename InT, typename AccT, int SBT>
-__global__ void __launch_bounds__(256) stats_fp_kernel(const InT* __restrict__ X,
+__global__ void __launch_bounds__(256, 3) stats_fp_kernel(const InT* __restrict__ X,
                                                        int64_t line_stride, int ps, int W, int d,
                                                        const double* __restrict__ shift,
                                                        double* __restrict__ S2f) {
@@ -240,7 +276,8 @@ __global__ void __launch_bounds__(256) stats_fp_kernel(const InT* __restrict__ X
 
 // Small d (projected lines, d <= 16): one CTA per line, one thread per entry
 // (a, b) of the lower triangle, walking all pixels; four independent partial
-// sums per thread.  The 64 x 64 tiles above would be nearly all padding here.
+// sums per thread (FP32: over kRun pixels, then compensated as above).  The
+// 64 x 64 tiles above would be nearly all padding here.
 constexpr int kSmallD = 16;
 
 template <typename InT, typename AccT>
@@ -254,6 +291,8 @@ __device__ __forceinline__ void stats_small_body(const InT* __restrict__ x, int 
   while ((a + 1) * (a + 2) / 2 <= q) ++a;
   const int b = q - a * (a + 1) / 2;
   const AccT ca = (AccT)shift[a], cb = (AccT)shift[b];
+  constexpr bool kComp = sizeof(AccT) == 4;
+  float hi = 0.f, lo = 0.f;
   AccT s0 = 0, s1 = 0, s2a = 0, s3 = 0;
   int i = 0;
   for (; i + 4 <= W; i += 4) {
@@ -261,9 +300,20 @@ __device__ __forceinline__ void stats_small_body(const InT* __restrict__ x, int 
     s1 = fma((AccT)x[(int64_t)(i + 1) * ps + a] - ca, (AccT)x[(int64_t)(i + 1) * ps + b] - cb, s1);
     s2a = fma((AccT)x[(int64_t)(i + 2) * ps + a] - ca, (AccT)x[(int64_t)(i + 2) * ps + b] - cb, s2a);
     s3 = fma((AccT)x[(int64_t)(i + 3) * ps + a] - ca, (AccT)x[(int64_t)(i + 3) * ps + b] - cb, s3);
+    if constexpr (kComp) {
+      if (((i + 4) & (kRun - 1)) == 0) {   // every kRun pixels
+        two_sum_into(hi, lo, (float)((s0 + s1) + (s2a + s3)));
+        s0 = s1 = s2a = s3 = 0;
+      }
+    }
   }
   for (; i < W; ++i) s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
-  s2[(int64_t)a * d + b] = (double)((s0 + s1) + (s2a + s3));
+  if constexpr (kComp) {
+    two_sum_into(hi, lo, (float)((s0 + s1) + (s2a + s3)));
+    s2[(int64_t)a * d + b] = (double)hi + (double)lo;
+  } else {
+    s2[(int64_t)a * d + b] = (double)((s0 + s1) + (s2a + s3));
+  }
 }
 
 template <typename InT, typename AccT>
@@ -289,7 +339,7 @@ __global__ void __launch_bounds__(kMeanThreads) b_mean_kernel(const BStream* __r
 }
 
 template <typename AccT>
-__global__ void __launch_bounds__(256) b_stats_kernel(const BStream* __restrict__ S,
+__global__ void __launch_bounds__(256, 3) b_stats_kernel(const BStream* __restrict__ S,
                                                       const BItem* __restrict__ items) {
   const BItem it = items[blockIdx.x];
   const BStream& s = S[it.s];

@@ -14,7 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_PKG, "_lib", "liberx.so")
 
 ERX_OK, ERX_EINVAL, ERX_ENOMEM, ERX_ECUDA, ERX_ENOTPD, ERX_ERANGE, ERX_ESTATE, \
-    ERX_EUNSUPPORTED, ERX_ETIMEOUT = range(9)
+    ERX_EUNSUPPORTED, ERX_ETIMEOUT, ERX_EIO = range(10)
 ERX_PROJ_NONE, ERX_PROJ_SRP, ERX_PROJ_LEARNED = 0, 1, 2
 ERX_UPDATE_THEN_SCORE, ERX_SCORE_THEN_UPDATE = 0, 1
 ERX_FLAG_SIMT_STATS, ERX_FLAG_PIPELINE = 1, 2
@@ -102,6 +102,8 @@ def load_library() -> C.CDLL:
         "erx_encoder_train": (C.c_int, [P, P, I64, I32, P, C.POINTER(ErxTrainOpts), P]),
         "erx_encoder_line_grad": (C.c_int, [P, P, I32, P, C.POINTER(ErxTrainOpts), P, P]),
         "erx_encoder_destroy": (C.c_int, [P]),
+        "erx_encoder_save": (C.c_int, [P, C.c_char_p]),
+        "erx_encoder_load": (C.c_int, [C.c_char_p, P, C.POINTER(P)]),
         "erx_set_encoder": (C.c_int, [P, P, I32, D]),
         "erx_get_drift": (C.c_int, [P, C.POINTER(D), C.POINTER(D), C.POINTER(I64),
                                     C.POINTER(I32)]),
@@ -537,17 +539,34 @@ def erx_train_opts_default() -> ErxTrainOpts:
 class Encoder:
     """Learned band encoder (erx_encoder_*): bands -> hidden -> k, trained on the GPU."""
 
-    def __init__(self, bands=224, hidden=128, k=32, seed=0, stream=None):
+    def __init__(self, bands=224, hidden=128, k=32, seed=0, stream=None, _handle=None):
         import torch
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        h = C.c_void_p()
-        _check(load_library().erx_encoder_create(bands, hidden, k, C.c_uint64(seed),
-                                                 C.c_void_p(self.stream.cuda_stream),
-                                                 C.byref(h)), "erx_encoder_create")
-        self.e = h.value
-        self.bands, self.hidden, self.k = bands, hidden, k
+        if _handle is None:
+            h = C.c_void_p()
+            _check(load_library().erx_encoder_create(bands, hidden, k, C.c_uint64(seed),
+                                                     C.c_void_p(self.stream.cuda_stream),
+                                                     C.byref(h)), "erx_encoder_create")
+            _handle = h.value
+        self.e = _handle
+        b, hd = C.c_int32(), C.c_int32()
+        self.k = int(load_library().erx_encoder_dims(self.e, C.byref(b), C.byref(hd)))
+        self.bands, self.hidden = b.value, hd.value
         self.nparams = int(load_library().erx_encoder_nparams(self.e))
+
+    def save(self, path):
+        """Checkpoint: normalisation, weights, AdamW moments, code-space EMA."""
+        _check(load_library().erx_encoder_save(self.e, os.fsencode(path)), "erx_encoder_save")
+
+    @classmethod
+    def load(cls, path, stream=None):
+        import torch
+        stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(load_library().erx_encoder_load(os.fsencode(path), C.c_void_p(stream.cuda_stream),
+                                               C.byref(h)), "erx_encoder_load")
+        return cls(stream=stream, _handle=h.value)
 
     def set_norm(self, shift, scale):
         import numpy as np

@@ -69,7 +69,7 @@ def test_null_handles(lib):
     assert lib.erx_push_lines(None, None, 0, 0, None, None, None, None) == erx.ERX_EINVAL
     assert lib.erx_sync(None, None) == erx.ERX_EINVAL
     assert lib.erx_dim(None) == -1
-    for s in range(8):
+    for s in range(10):
         assert erx.erx_status_str(s).startswith("ERX_")
 
 
@@ -82,3 +82,24 @@ def test_host_side_argument_checks(lib):
     assert lib.erx_batch_destroy(None) == erx.ERX_OK
     h = ctypes.c_void_p()
     assert lib.erx_batch_create(0, None, None, ctypes.byref(h)) == erx.ERX_EINVAL
+
+
+def test_encoder_checkpoint_host_checks(lib, tmp_path):
+    """Checkpoint files that are missing, truncated or of another kind are
+    refused (ERX_EIO) before any device work."""
+    h = ctypes.c_void_p()
+    assert lib.erx_encoder_save(None, b"x") == erx.ERX_EINVAL
+    assert lib.erx_encoder_load(None, None, ctypes.byref(h)) == erx.ERX_EINVAL
+    missing = str(tmp_path / "missing.bin").encode()
+    assert lib.erx_encoder_load(missing, None, ctypes.byref(h)) == erx.ERX_EIO
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"NOTANENC" + bytes(32))
+    assert lib.erx_encoder_load(str(bad).encode(), None, ctypes.byref(h)) == erx.ERX_EIO
+    short = tmp_path / "short.bin"
+    short.write_bytes(b"ERXENC01" + bytes(4))
+    assert lib.erx_encoder_load(str(short).encode(), None, ctypes.byref(h)) == erx.ERX_EIO
+    import struct
+    big = tmp_path / "big.bin"          # sizes beyond the encoder's limits
+    big.write_bytes(b"ERXENC01" + struct.pack("<4i2q", 224, 512, 32, 0, 0, 0))
+    assert lib.erx_encoder_load(str(big).encode(), None, ctypes.byref(h)) == erx.ERX_EIO
+    assert h.value is None

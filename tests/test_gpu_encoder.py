@@ -34,15 +34,40 @@ def _encoder(b, h, k, seed=3):
     return e, q
 
 
-def forward_bf16(q, x, shift, scale):
-    """The oracle forward at the inference kernel's rounding points: xn = (x -
-    shift) * scale in float32, then bf16; layer 1 by the oracle; the hidden
-    activations relu(a) rounded to bf16; layer 2 on those."""
+def forward_parts(q, x, shift, scale):
+    """The oracle forward at the tensor-core kernel's rounding points: xn =
+    (x - shift) * scale in float32, then bf16; layer 1 by the oracle on those;
+    the hidden activations relu(a) rounded to bf16; layer 2 on those.  Returns
+    (xn_bf, a, h_bf, codes)."""
     xn = np.asarray(x, np.float32) - np.asarray(shift, np.float32)
-    xn = (xn * np.asarray(scale, np.float32)).astype(np.float32)
+    xn = bf16_round((xn * np.asarray(scale, np.float32)).astype(np.float32))
     b = xn.shape[1]
-    _, (_, a, h) = enc_or.forward(q, bf16_round(xn), np.zeros(b), np.ones(b))
-    return bf16_round(h.astype(np.float32)) @ q["W2"].T + q["b2"]
+    _, (_, a, h) = enc_or.forward(q, xn, np.zeros(b), np.ones(b))
+    h_bf = bf16_round(h.astype(np.float32))
+    return xn, a, h_bf, h_bf @ q["W2"].T + q["b2"]
+
+
+def forward_bf16(q, x, shift, scale):
+    return forward_parts(q, x, shift, scale)[3]
+
+
+U_BF16 = 2.0 ** -8     # unit roundoff of bf16 (8 significant bits)
+
+
+def grad_bound(q, parts, dc, eps32=1e-4):
+    """Componentwise bound on the GPU gradient's deviation from the oracle's
+    gradient at the same rounding points: the backward rounds dL/dc to bf16
+    (in dc W2 and in h^T dc) and dL/dh to bf16 (in dh^T xn), each a relative
+    u = 2^-8, and accumulates in FP32; eps32 covers the FP32 forward and loss.
+    Returns a vector in the parameter layout [W1 | b1 | W2 | b2]."""
+    xn, a, h_bf, _ = parts
+    gate = (a > 0).astype(np.float64)
+    dabs = (np.abs(dc) @ np.abs(q["W2"])) * gate            # |dc| |W2| per pixel, unit
+    bw1 = (2 * U_BF16 + eps32) * (dabs.T @ np.abs(xn))
+    bb1 = (U_BF16 + eps32) * dabs.sum(axis=0)
+    bw2 = (U_BF16 + eps32) * (np.abs(dc).T @ h_bf)
+    bb2 = eps32 * np.abs(dc).sum(axis=0)
+    return np.concatenate([bw1.ravel(), bb1, bw2.ravel(), bb2])
 
 
 def _line(w, b, seed=0):
@@ -66,9 +91,22 @@ def test_forward_matches_oracle():
     assert np.max(np.abs(got - full)) <= 2e-2 * np.max(np.abs(full))
 
 
-def test_line_gradient_matches_oracle():
+def _oracle_line_grad(q, x, shift, scale, mu_e, k_e, target, ridge=1e-5):
+    parts = forward_parts(q, x, shift, scale)
+    loss, dc, _ = enc_or.loss_and_dcodes(parts[3], mu_e, k_e, ridge, target)
+    gw = enc_or.backward(q, (parts[0], parts[1], parts[2]), dc)
+    g = np.concatenate([gw["W1"].ravel(), gw["b1"], gw["W2"].ravel(), gw["b2"]])
+    return g, loss, parts, dc
+
+
+@pytest.mark.parametrize("b,h,k,w", [(32, 16, 8, 256), (224, 128, 32, 300), (40, 24, 5, 77)])
+def test_line_gradient_matches_oracle(b, h, k, w):
+    """Every entry of one line's gradient (tensor-core forward and backward)
+    against the oracle's at the same rounding points (bf16 weights, inputs and
+    hidden activations), within the componentwise bound of the rounding that
+    only the GPU does (dL/dc and dL/dh to bf16, FP32 accumulation).  Widths
+    that are not a multiple of the 128-pixel tile check the ragged tile."""
     need_gpu()
-    b, h, k, w = 32, 16, 8, 256
     e, q = _encoder(b, h, k, seed=4)
     x = _line(w, b, seed=1)
     shift = x.mean(0).astype(np.float32)
@@ -77,17 +115,82 @@ def test_line_gradient_matches_oracle():
     target = oracle.run_cube(x[None].astype(np.float64))["delta"][0] * 0.7 + 0.3
     e.reset_stats()
     g_gpu, loss_gpu = e.line_grad(to_dev(x), torch.from_numpy(target).cuda())
-    c, cache = enc_or.forward(q, x, shift, scale)
-    mu, kk = enc_or.code_stats(c)
-    loss, dc, _ = enc_or.loss_and_dcodes(c, mu, kk, 1e-5, target)
-    gw = enc_or.backward(q, cache, dc)
-    g_or = np.concatenate([gw["W1"].ravel(), gw["b1"], gw["W2"].ravel(), gw["b2"]])
-    err = np.linalg.norm(g_gpu - g_or) / np.linalg.norm(g_or)
-    assert err < 2e-2, err
-    assert abs(loss_gpu - loss) <= 1e-3 * loss
-    # parameters unchanged by line_grad
+    codes = forward_bf16(q, x, shift, scale)
+    mu, kk = enc_or.code_stats(codes)       # line 0: the EMA starts from the line's own stats
+    g_or, loss, parts, dc = _oracle_line_grad(q, x, shift, scale, mu, kk, target)
+    bound = grad_bound(q, parts, dc) + 1e-6 * np.max(np.abs(g_or))
+    ratio = np.abs(g_gpu - g_or) / bound
+    print(f"{b}x{h}x{k} w={w}: max |dg| / bound {ratio.max():.3f}, "
+          f"max rel (|g| > 1e-2 max) {np.max((np.abs(g_gpu - g_or) / np.abs(g_or))[np.abs(g_or) > 1e-2 * np.abs(g_or).max()]):.2e}")
+    assert np.all(ratio <= 1.0), (int(np.argmax(ratio)), ratio.max())
+    assert abs(loss_gpu - loss) <= 1e-4 * loss
+    # line_grad leaves the parameters as they were
     theta = e.params()
     assert np.array_equal(theta[:h * b].reshape(h, b).astype(np.float64) == 0, q["W1"] == 0)
+
+
+def test_training_steps_match_oracle():
+    """Eight training steps on the GPU against the oracle's steps driven at the
+    GPU's rounding points (bf16 copies of the weights refreshed after every
+    AdamW step, the code-space EMA continued line to line).  With AdamW's eps
+    = 1 an update is a smooth function of the gradient (g / (|g| + 1) for
+    small g), so the parameters can be compared entry by entry: each may
+    differ by at most lr times the sum over steps of that entry's gradient
+    bound (doubled for the drift of later gradients), and every line's loss
+    within the first-order effect of that parameter bound (plus 1e-4 for the
+    FP32 forward and loss)."""
+    need_gpu()
+    from paper_2408_14947_gb300 import erx_train_opts_default
+    b, h, k, w, steps = 48, 32, 8, 200, 8
+    e, q = _encoder(b, h, k, seed=6)
+    cfg = synth.SceneConfig(bands=b, width=w, seed=3, n_end=(3, 5), noise=0.02)
+    cube = synth.gen_lines(cfg, 0, steps)
+    flat = cube.reshape(-1, b)
+    shift = flat.mean(0).astype(np.float32)
+    scale = (1.0 / (flat.std(0) + 1e-3)).astype(np.float32)
+    e.set_norm(shift, scale)
+    targets = oracle.run_cube(cube.astype(np.float64), warmup=0)["delta"]
+    o = erx_train_opts_default()
+    o.lr, o.eps, o.weight_decay, o.momentum = 1e-2, 1.0, 1e-3, 0.2
+    theta0 = e.params().astype(np.float64)
+    e.reset_stats()
+    losses = e.train(to_dev(cube), torch.from_numpy(targets).cuda(), o, want_loss=True)
+    theta_gpu = e.params().astype(np.float64)
+
+    # the oracle's steps: FP64 master weights, bf16 copies for the products
+    n1, n2 = h * b, k * h
+    master = {"W1": theta0[:n1].reshape(h, b), "b1": theta0[n1:n1 + h],
+              "W2": theta0[n1 + h:n1 + h + n2].reshape(k, h), "b2": theta0[n1 + h + n2:]}
+    opt = enc_or.AdamW(master, lr=o.lr, beta1=o.beta1, beta2=o.beta2, eps=o.eps,
+                       wd=o.weight_decay)
+    ema = enc_or.CodeEMA(o.momentum)
+    slack = np.zeros_like(theta0)
+    loss_ratio = []
+    for t in range(steps):
+        qt = {"W1": bf16_round(master["W1"]), "b1": master["b1"].astype(np.float32),
+              "W2": bf16_round(master["W2"]), "b2": master["b2"].astype(np.float32)}
+        codes = forward_bf16(qt, cube[t], shift, scale)
+        mu_e, k_e = ema.update(codes)
+        g, loss, parts, dc = _oracle_line_grad(qt, cube[t], shift, scale, mu_e, k_e, targets[t],
+                                               o.ridge)
+        # the loss moves with the parameters: first order, |g| times the bound on
+        # how far the GPU's parameters may be from the oracle's after t steps
+        loss_tol = 1e-4 * loss + 2 * np.sum(np.abs(g) * 2 * o.lr * slack)
+        loss_ratio.append(abs(losses[t] - loss) / loss_tol)
+        slack += grad_bound(qt, parts, dc)
+        grads = {"W1": g[:n1].reshape(h, b), "b1": g[n1:n1 + h],
+                 "W2": g[n1 + h:n1 + h + n2].reshape(k, h), "b2": g[n1 + h + n2:]}
+        opt.step(master, grads)
+    theta_or = np.concatenate([master["W1"].ravel(), master["b1"], master["W2"].ravel(),
+                               master["b2"]])
+    dev_ = np.abs(theta_gpu - theta_or)
+    tol = 2 * o.lr * slack + 1e-6 * np.abs(theta_or) + 1e-7
+    moved = np.abs(theta_or - theta0)
+    print(f"{steps} steps: max |dtheta| / tol {np.max(dev_ / tol):.3f}; "
+          f"median move {np.median(moved):.2e}, median |dtheta| {np.median(dev_):.2e}; "
+          f"loss error / tol {np.round(loss_ratio, 3).tolist()}")
+    assert np.all(dev_ <= tol), (int(np.argmax(dev_ / tol)), np.max(dev_ / tol))
+    assert max(loss_ratio) <= 1.0, loss_ratio
 
 
 def test_first_training_step_is_adamw():
@@ -229,3 +332,33 @@ def test_drift_monitor_and_fallback(trained):
     # after the fallback, scores come from full-band ERX (statistics warmed on audited lines)
     corr = np.mean([_spearman(b[t], full["delta"][250 + t]) for t in range(40, 50)])
     assert corr > 0.99
+
+
+def test_checkpoint_round_trip(tmp_path):
+    """erx_encoder_save / erx_encoder_load: the restored encoder gives the same
+    codes bit for bit, and one more training step on each (AdamW moments and
+    the code-space EMA restored) gives the same parameters bit for bit."""
+    need_gpu()
+    from paper_2408_14947_gb300 import Encoder, erx_train_opts_default
+    b, h, k, w = 40, 24, 8, 150
+    cfg = synth.SceneConfig(bands=b, width=w, seed=8, n_end=(3, 5), noise=0.02)
+    cube = synth.gen_lines(cfg, 0, 5)
+    targets = torch.from_numpy(oracle.run_cube(cube.astype(np.float64), warmup=0)["delta"]).cuda()
+    x = to_dev(cube)
+    e = Encoder(b, h, k, seed=2)
+    flat = cube.reshape(-1, b)
+    e.set_norm(flat.mean(0), 1.0 / (flat.std(0) + 1e-3))
+    o = erx_train_opts_default()
+    e.train(x[:4], targets[:4], o)
+    path = tmp_path / "enc.ckpt"
+    e.save(path)
+    r = Encoder.load(path)
+    assert (r.bands, r.hidden, r.k) == (b, h, k)
+    assert np.array_equal(r.params(), e.params())
+    assert torch.equal(r.forward(x[4]), e.forward(x[4]))
+    la = e.train(x[4:5], targets[4:5], o, want_loss=True)
+    lb = r.train(x[4:5], targets[4:5], o, want_loss=True)
+    assert np.array_equal(la, lb)
+    assert np.array_equal(r.params(), e.params())
+    e.close()
+    r.close()

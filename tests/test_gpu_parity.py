@@ -332,9 +332,10 @@ def test_long_block_chunked_ema_matches_line_by_line():
         assert rel_err(c["delta"], refc["delta"]) < 1e-9
 
 
-# the cube's pooled covariance has kappa 1.1e4 .. 2e4, just above the range of
-# the FP32 bar (1e-4 up to 1e4); the kappa sweep gives FP32 2.6e-4 at 1e5
-@pytest.mark.parametrize("form,tol", [("fp64", 1e-9), ("fp32", 5e-4)])
+# the cube's pooled covariance has kappa 1.1e4 .. 2e4; with the FP32 scatter
+# compensated per 8-pixel run the FP32 scores sit near 1e-5 here (8e-5 to 1.05e-4
+# with a plain running FP32 sum, which is what once needed a wider tolerance)
+@pytest.mark.parametrize("form,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
 @pytest.mark.parametrize("order", ["update_then_score", "score_then_update"])
 def test_imc_matches_oracle(form, tol, order):
     """IMC averaging (Sec. IV-C ablation): a 70-line block (three chunks of the
