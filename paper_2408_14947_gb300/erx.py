@@ -347,8 +347,14 @@ class Detector:
                    torch.empty((n, p), dtype=torch.uint8, device=dev),
                    torch.empty((n,), dtype=torch.uint8, device=dev))
         delta, dn, mask, det = out
+        cur = torch.cuda.current_stream(dev)
+        other = cur.cuda_stream != self.stream.cuda_stream
+        if other:           # lines (and the outputs' memory) come from the caller's stream
+            self.stream.wait_stream(cur)
         erx_push_lines(self.ctx, lines.data_ptr(), n, 0, delta.data_ptr(), dn.data_ptr(),
                        mask.data_ptr(), det.data_ptr())
+        if other:           # outputs are written on the detector's stream
+            cur.wait_stream(self.stream)
         return delta, dn, mask, det
 
     def push_host(self, lines, out):
@@ -602,8 +608,14 @@ class Encoder:
         xc = x.contiguous()
         n = xc.numel() // self.bands
         out = torch.empty(xc.shape[:-1] + (self.k,), dtype=torch.float32, device=x.device)
+        cur = torch.cuda.current_stream(x.device)
+        other = cur.cuda_stream != self.stream.cuda_stream
+        if other:
+            self.stream.wait_stream(cur)
         _check(load_library().erx_encoder_forward(self.e, xc.data_ptr(), n, out.data_ptr()),
                "erx_encoder_forward")
+        if other:           # codes are written on the encoder's stream
+            cur.wait_stream(self.stream)
         return out
 
     def train(self, lines, targets, opts=None, want_loss=False):
