@@ -830,6 +830,38 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def profile_batched(form, steps):
+    """The C4 batch (256 streams) in one form: tuned, three warm-up steps, then
+    `steps` timed steps (one graph launch each; capture the last steps'
+    kernels)."""
+    import torch
+
+    import synth
+    from paper_2408_14947_gb300 import Batch
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    cfgs = synth.stream_configs_c4(256)
+    lines = [torch.from_numpy(synth.gen_lines(c, 0, 2)).to(dev) for c in cfgs]
+    b = Batch([{"bands": c.bands, "width": c.width} for c in cfgs], form=form, stream=stream)
+    b.push([x[0] for x in lines])
+    b.sync()
+    if form in ("tf32", "bf16", "tf32x3"):
+        b.tune(reps=3)
+    for k in range(3):
+        b.push([x[k % 2] for x in lines])
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        b.push([x[k % 2] for x in lines])
+    e1.record(stream)
+    b.sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": f"c4_{form}", "steps": steps,
+                      "ms_per_step": e0.elapsed_time(e1) / steps}))
+    b.close()
+
+
 def run_profile_case(args):
     """One block of a named workload through one form, for profiler captures:
     a warm-up push, then one push of `--lines` lines (its kernels are the ones
@@ -840,6 +872,8 @@ def run_profile_case(args):
     from paper_2408_14947_gb300 import Detector, _build
     _build.build()
     kind, form = args.profile_case.split("_", 1)
+    if kind == "c4":
+        return profile_batched(form, args.lines)
     avg = "ema"
     if form.endswith("_imc"):
         form, avg = form[: -len("_imc")], "imc"
