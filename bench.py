@@ -926,12 +926,15 @@ def main():
     ap.add_argument("--lines", type=int, default=LINES,
                     help="lines of the workload cube (smaller cubes for profiler captures)")
     ap.add_argument("--profile-case", default=None,
-                    choices=["c2_fp64", "c2_fp64e", "c2_fp32", "c2_tf32", "c2_bf16", "c2_fp64_imc", "c3_fp64",
-                             "c3_fp32", "c3_tf32", "c3_bf16", "c3_tf32x3", "c5_fp32", "c5_fp64"],
+                    choices=["c2_fp64", "c2_fp64e", "c2_fp32", "c2_tf32", "c2_bf16", "c2_fp64_imc",
+                             "c3_fp64", "c3_fp32", "c3_tf32", "c3_bf16", "c3_tf32x3", "c5_fp32",
+                             "c5_fp64", "c4_fp64", "c4_fp32", "c4_tf32", "c4_bf16", "c4_tf32x3"],
                     help="push one block of --lines lines of a workload (c2: 640 px x 108 "
                          "bands u16; c3: 1024 px x 224 bands f32, kappa 1e3; c5: c3 lines "
-                         "through learned 32-dim codes) through one form (_imc: IMC averaging), after one warm-up push, for profiler "
-                         "captures; no bench line")
+                         "through learned 32-dim codes) through one form (_imc: IMC "
+                         "averaging), after one warm-up push; c4: the 256-stream batch, "
+                         "--lines steps after three warm-up steps; for profiler captures, "
+                         "no bench line")
     args = ap.parse_args()
     globals()["LINES"] = args.lines
     if args.profile_case:

@@ -69,6 +69,13 @@ struct erx_batch {
   BItem* solve_items[kRoutes] = {};
   int n_solve[kRoutes] = {};
   int n_hi0 = 0, dmax_lo0 = 1;   // FP64 route: items of streams with d > 128; largest other d
+  // factor and FP32 inverse: every stream, largest d first; the first n_chol_big
+  // have d > 128 and run on the look-ahead schedule (on the batch's stream) while
+  // the others run beside them on a second stream inside the step's graph
+  BItem* chol_items = nullptr;
+  int n_chol_big = 0, dmax_small = 1;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned long long* err = nullptr;
   // learned streams: raw lines [sum W][b_in] and codes [sum W][k], stream order
   int n_learned = 0, learned_b = 0, learned_k = 0;
@@ -103,6 +110,9 @@ erx_status balloc(erx_batch* b, T** p, size_t n) {
 void bfree(erx_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   for (void* p : b->allocs) cudaFree(p);
   for (int i = 0; i < 2; ++i) {
     if (b->ptr_host[i]) cudaFreeHost(b->ptr_host[i]);
@@ -193,8 +203,23 @@ void enqueue_step(erx_batch* b, cudaStream_t st) {
   launch_batch_mean(b->table, b->n, !fp64, st);
   launch_batch_stats(b->table, b->stats_items, b->n_stats, fp64, st);
   launch_batch_ema(b->table, b->ema_items, b->n_ema, st);
-  launch_batch_chol(b->table, b->n, b->dmax, !fp64, b->err, st);
-  if (!fp64) launch_batch_trinv32(b->table, b->n, b->dmax, st);
+  // factor (and the FP32 inverse): the streams above 128 dimensions, one CTA
+  // per SM each, beside the smaller ones on the second stream
+  const int nb = b->n_chol_big, ns = b->n - b->n_chol_big;
+  const bool fork = nb > 0 && ns > 0;
+  cudaStream_t ss = fork ? b->side : st;
+  if (fork) {
+    cudaEventRecord(b->ev_fork, st);
+    cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+  }
+  launch_batch_chol(b->table, b->chol_items, nb, b->dmax, true, !fp64, b->err, st);
+  if (!fp64) launch_batch_trinv32(b->table, b->chol_items, nb, b->dmax, st);
+  launch_batch_chol(b->table, b->chol_items + nb, ns, b->dmax_small, false, !fp64, b->err, ss);
+  if (!fp64) launch_batch_trinv32(b->table, b->chol_items + nb, ns, b->dmax_small, ss);
+  if (fork) {
+    cudaEventRecord(b->ev_join, b->side);
+    cudaStreamWaitEvent(st, b->ev_join, 0);
+  }
   for (int r = 0; r < kRoutes; ++r) {
     if (!b->n_solve[r]) continue;
     if (r == 0)
@@ -370,9 +395,27 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
     std::stable_sort(st_items.begin(), st_items.end(), [&](const BItem& x, const BItem& y) {
       return (int64_t)b->host[x.s].W * b->host[x.s].d > (int64_t)b->host[y.s].W * b->host[y.s].d;
     });
+    std::vector<BItem> ch_items;
+    for (int i = 0; i < n; ++i) ch_items.push_back({i, 0});
+    std::stable_sort(ch_items.begin(), ch_items.end(), [&](const BItem& x, const BItem& y) {
+      return b->host[x.s].d > b->host[y.s].d;
+    });
+    for (const BItem& it : ch_items) {
+      if (b->host[it.s].d > 128) ++b->n_chol_big;
+      else b->dmax_small = std::max(b->dmax_small, b->host[it.s].d);
+    }
+    if (s == ERX_OK) s = balloc(b, &b->chol_items, ch_items.size());
+    if (s == ERX_OK && cudaMemcpy(b->chol_items, ch_items.data(), ch_items.size() * sizeof(BItem),
+                                  cudaMemcpyHostToDevice) != cudaSuccess)
+      s = ERX_ECUDA;
+    if (s == ERX_OK &&
+        (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess))
+      s = ERX_ECUDA;
     b->n_stats = (int)st_items.size();
     b->n_ema = (int)ema_items.size();
-    s = balloc(b, &b->stats_items, st_items.size());
+    if (s == ERX_OK) s = balloc(b, &b->stats_items, st_items.size());
     if (s == ERX_OK) s = balloc(b, &b->ema_items, ema_items.size());
     if (s == ERX_OK &&
         (cudaMemcpy(b->stats_items, st_items.data(), st_items.size() * sizeof(BItem),

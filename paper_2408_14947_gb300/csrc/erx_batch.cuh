@@ -45,9 +45,12 @@ void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t s
 void launch_batch_stats(const BStream* S, const BItem* items, int n_items, bool fp64,
                         cudaStream_t st);
 void launch_batch_ema(const BStream* S, const BItem* items, int n_items, cudaStream_t st);
-void launch_batch_trinv32(const BStream* S, int n, int dmax, cudaStream_t st);
-void launch_batch_chol(const BStream* S, int n, int dmax, bool want32,
-                       unsigned long long* err, cudaStream_t st);
+void launch_batch_trinv32(const BStream* S, const BItem* items, int n, int dmax,
+                          cudaStream_t st);
+// the factor of the streams in items[0 .. n): big = all have d > 128 (look-ahead
+// schedule, one CTA per SM), else all d <= 128; dmax = their largest d
+void launch_batch_chol(const BStream* S, const BItem* items, int n, int dmax, bool big,
+                       bool want32, unsigned long long* err, cudaStream_t st);
 void launch_batch_solve(int route, const BStream* S, const BItem* items, int n_items, int dmax,
                         unsigned long long* err, cudaStream_t st);
 void launch_batch_normalise(const BStream* S, int n, bool fp64, cudaStream_t st);

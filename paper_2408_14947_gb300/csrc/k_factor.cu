@@ -326,13 +326,20 @@ __global__ void __launch_bounds__(NT, MINB) chol_kernel(const double* __restrict
                     t0 + t, inv);
 }
 
-// Batched form: one CTA per stream.
-__global__ void __launch_bounds__(kThreads, 4) b_chol_kernel(const BStream* __restrict__ S,
-                                                         bool want32,
-                                                         unsigned long long* __restrict__ err) {
-  const BStream& s = S[blockIdx.x];
+// Batched form: one CTA per stream, streams taken from a work list (largest d
+// first).  NT / LA as for the single-stream kernel: d > 128 takes the
+// look-ahead schedule with 512 threads (one CTA per SM), the others the column
+// schedule with 256 threads (several CTAs per SM).  A bad pivot records the
+// stream index.
+template <int NT, bool LA>
+__global__ void __launch_bounds__(NT, LA ? 1 : 4) b_chol_kernel(const BStream* __restrict__ S,
+                                                               const BItem* __restrict__ items,
+                                                               bool want32,
+                                                               unsigned long long* __restrict__ err) {
+  const int si = items[blockIdx.x].s;
+  const BStream& s = S[si];
   // the FP32 routes invert the diagonal blocks in trinv32 (FP32)
-  chol_body<2>(s.K_t, s.d, s.ridge, s.Lf, want32 ? s.Lf32 : nullptr, err, blockIdx.x, !want32);
+  chol_body<2, NT, LA>(s.K_t, s.d, s.ridge, s.Lf, want32 ? s.Lf32 : nullptr, err, si, !want32);
 }
 
 // Full inverse X = L^{-1} in FP32 from the float factor (plain diagonal blocks:
@@ -443,8 +450,9 @@ __global__ void __launch_bounds__(kThreads) trinv32_kernel(float* __restrict__ L
   trinv32_body(Lf32 + (int64_t)blockIdx.x * packed_size(d), d);
 }
 
-__global__ void __launch_bounds__(kThreads) b_trinv32_kernel(const BStream* __restrict__ S) {
-  const BStream& s = S[blockIdx.x];
+__global__ void __launch_bounds__(kThreads) b_trinv32_kernel(const BStream* __restrict__ S,
+                                                             const BItem* __restrict__ items) {
+  const BStream& s = S[items[blockIdx.x].s];
   trinv32_body(s.Lf32, s.d);
 }
 
@@ -454,8 +462,10 @@ void launch_trinv32(float* Lf32, int d, int T, cudaStream_t st) {
   trinv32_kernel<<<T, kThreads, (size_t)packed_size(d) * sizeof(float), st>>>(Lf32, d);
 }
 
-void launch_batch_trinv32(const BStream* S, int n, int dmax, cudaStream_t st) {
-  b_trinv32_kernel<<<n, kThreads, (size_t)packed_size(dmax) * sizeof(float), st>>>(S);
+void launch_batch_trinv32(const BStream* S, const BItem* items, int n, int dmax,
+                          cudaStream_t st) {
+  if (n > 0)
+    b_trinv32_kernel<<<n, kThreads, (size_t)packed_size(dmax) * sizeof(float), st>>>(S, items);
 }
 
 cudaError_t configure_factor_kernels() {
@@ -469,7 +479,11 @@ cudaError_t configure_factor_kernels() {
     e = cudaFuncSetAttribute(chol_kernel<2, 1, 512, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(b_chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+    e = cudaFuncSetAttribute(b_chol_kernel<kThreads, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(b_chol_kernel<512, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, m);
   const int m32 = (int)(packed_size(kMaxDim) * sizeof(float));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(trinv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m32);
@@ -478,9 +492,13 @@ cudaError_t configure_factor_kernels() {
   return e;
 }
 
-void launch_batch_chol(const BStream* S, int n, int dmax, bool want32, unsigned long long* err,
-                       cudaStream_t st) {
-  b_chol_kernel<<<n, kThreads, chol_smem(dmax), st>>>(S, want32, err);
+void launch_batch_chol(const BStream* S, const BItem* items, int n, int dmax, bool big,
+                       bool want32, unsigned long long* err, cudaStream_t st) {
+  if (n <= 0) return;
+  if (big)
+    b_chol_kernel<512, true><<<n, 512, chol_smem(dmax), st>>>(S, items, want32, err);
+  else
+    b_chol_kernel<kThreads, false><<<n, kThreads, chol_smem(dmax), st>>>(S, items, want32, err);
 }
 
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, float* Lf32,
