@@ -432,9 +432,52 @@ def bench_learned(dev, stream, n_train: int = 2000, n_test: int = 200):
                       "err_vs": "FP64 oracle on the same " + (
                           "codes" if name.startswith("learned") else "lines") + f", {na} lines"}
     out["forms"] = rows
+    out["rank_corr_linear_code_bound"] = {
+        "value": math.sqrt(K / B),
+        "meaning": "rank agreement of RX on any linear K-dim code with full-band RX on a "
+                   "Gaussian background (tests/test_learned_bound.py)"}
+    out["drift_monitor"] = learned_drift(enc, xt, stream)
     out["batched"] = bench_learned_batched(enc, xt, stream)
     enc.close()
     return out
+
+
+DRIFT_MIN_RANK_CORR = 0.1   # the learned form falls back to full band below this
+DRIFT_AUDIT_EVERY = 10
+
+
+def learned_drift(enc, xt, stream):
+    """The learned form's drift monitor: every DRIFT_AUDIT_EVERY-th line is also
+    scored by full-band ERX; below DRIFT_MIN_RANK_CORR (Spearman of the two score
+    vectors) the context falls back to full band.  Run on the held-out lines as
+    they are, and with a per-band gain change (a sensor calibration drift: gains
+    log-uniform in [1/4, 4], seeded), to which full-band RX is invariant (an
+    invertible linear map of the bands) but the encoder, trained on the old
+    gains, is not."""
+    import numpy as np
+    import torch
+
+    from paper_2408_14947_gb300 import Detector
+    n, W, B = xt.shape
+    g = np.exp(np.random.default_rng(2408).uniform(np.log(0.25), np.log(4.0), B))
+    gain = torch.from_numpy(g.astype(np.float32)).to(xt.device)
+    res = {"min_rank_corr": DRIFT_MIN_RANK_CORR, "audit_every": DRIFT_AUDIT_EVERY}
+    for name, xs in (("held_out", xt), ("band_gain_drift", (xt * gain).contiguous())):
+        d_ = Detector(B, W, in_dtype="f32", warmup=0, stream=stream, form="fp32", encoder=enc,
+                      audit_every=DRIFT_AUDIT_EVERY, min_rank_corr=DRIFT_MIN_RANK_CORR)
+        first_fb = None
+        for t0 in range(0, n, DRIFT_AUDIT_EVERY):
+            d_.push(xs[t0:t0 + DRIFT_AUDIT_EVERY])
+            d_.sync()
+            if first_fb is None and d_.drift()[3]:
+                first_fb = t0 + DRIFT_AUDIT_EVERY
+        last, low, audits, fb = d_.drift()
+        d_.close()
+        res[name] = {"audits": audits, "lowest_rank_corr": low, "last_rank_corr": last,
+                     "fell_back": fb, "fallback_by_line": first_fb,
+                     "lines_on_learned_codes": first_fb if first_fb is not None else n,
+                     "lines": n}
+    return res
 
 
 def bench_learned_batched(enc, xt, stream, n_streams: int = 64, steps: int = 30):

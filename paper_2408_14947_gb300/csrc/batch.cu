@@ -26,7 +26,8 @@
 using namespace erx;
 
 namespace erx {
-int batch_stats_tiles(int d, bool fp64);
+int batch_stats_tiles(int d, int W, bool fp64);
+int batch_scatter_chunks(int d, int W);
 int batch_solve_tiles(int route, int W);
 void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, int n_items,
                              int dmax, cudaStream_t st);
@@ -306,7 +307,7 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
     nx += (size_t)W * d;
     nd += d;
     np += (size_t)packed_size(d);
-    ndd += (size_t)d * d;
+    ndd += (size_t)d * d * batch_scatter_chunks(d, W);
     nw += W;
   }
   const size_t ss = form == ERX_FORM_FP64 ? 8 : 4;
@@ -379,17 +380,18 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
       e.Lf = alf + op;
       e.Lf32 = alf32 + op;
       e.S2f = as2 + odd;
+      e.nch = batch_scatter_chunks(d, W);
       e.delta = adl + ow * ss;
       e.dn = adn + ow * ss;
       e.mask = amk + ow;
       e.det = adt + i;
-      for (int k = 0; k < batch_stats_tiles(d, form == ERX_FORM_FP64); ++k)
+      for (int k = 0; k < batch_stats_tiles(d, W, form == ERX_FORM_FP64); ++k)
         st_items.push_back({i, k});
       const int64_t ne = packed_size(d) + d;
       for (int k = 0; k < (int)((ne + 127) / 128); ++k) ema_items.push_back({i, k});
       od += d;
       op += (size_t)packed_size(d);
-      odd += (size_t)d * d;
+      odd += (size_t)d * d * e.nch;
       ow += W;
     }
     std::stable_sort(st_items.begin(), st_items.end(), [&](const BItem& x, const BItem& y) {

@@ -19,6 +19,15 @@ namespace erx {
 
 constexpr int kMaxDim = 224;   // packed FP64 factor must fit one SM's shared memory
 constexpr int kFactorBlock = 32;  // diagonal blocks of the factor are stored inverted
+// The floating centred scatter of a line (above 16 dimensions) is summed per
+// chunk of kScatterChunk pixels; the chunk sums are then added in FP64 in
+// chunk order.  A single-stream launch adds them as it goes; the batched form
+// gives each chunk its own CTA and adds the chunk sums in the EMA kernel, in the
+// same order, so both give the same bits.
+constexpr int kScatterChunk = 256;
+__host__ __device__ inline int scatter_chunks(int W) {
+  return (W + kScatterChunk - 1) / kScatterChunk;
+}
 
 // error slots (unsigned long long, min-reduced line index; ~0ull = none)
 enum { kErrNotPD = 0, kErrRange = 1, kErrTimeout = 2, kErrSlots = 3 };

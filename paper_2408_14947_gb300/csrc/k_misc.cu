@@ -394,7 +394,11 @@ __global__ void __launch_bounds__(128) b_ema_kernel(BStream* __restrict__ S,
     const int b = (int)(q - (int64_t)a * (a + 1) / 2);
     const double ea = __dsub_rn(s.mu_hat[a], s.shift[a]);
     const double eb = __dsub_rn(s.mu_hat[b], s.shift[b]);
-    const double kh = ema_khat(s.S2f[(int64_t)a * d + b], ea, eb, Wd, __drcp_rn(Wd - 1.0));
+    // the scatter's chunk sums, added in chunk order (as the single-stream scatter does)
+    const double* sp = s.S2f + (int64_t)a * d + b;
+    double S2 = sp[0];
+    for (int c = 1; c < s.nch; ++c) S2 = __dadd_rn(S2, sp[(int64_t)c * d * d]);
+    const double kh = ema_khat(S2, ea, eb, Wd, __drcp_rn(Wd - 1.0));
     const double prev = s.K_state[q];
     const double post = first ? kh : ema_mix(prev, kh, alpha, beta);
     s.K_t[q] = (s.order == 0 || first) ? post : prev;

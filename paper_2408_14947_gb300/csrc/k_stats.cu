@@ -183,14 +183,18 @@ __global__ void __launch_bounds__(kMeanThreads) mean_kernel(const InT* __restric
 }
 
 // One SBT x SBT block pair `pair` of the scatter of one line about `shift`
-// (the line's d values), written to s2 (the line's d x d).  256 threads, each
-// an (SBT/16) x (SBT/16) sub-block; SBT = 32 wastes less of the triangle
-// (used in FP64, where every multiply-add counts), SBT = 64 reuses registers more.
-// FP32 sums are compensated per kRun-pixel run (two_sum_into).
+// (the line's d values), over the pixel chunks c_first .. c_last - 1
+// (kScatterChunk pixels each): chunk c's sum goes to s2 (the line's d x d) when
+// c == c_first, and is added to what s2 holds after that (each entry is only
+// ever touched by its own thread).  256 threads, each an (SBT/16) x (SBT/16)
+// sub-block; SBT = 32 wastes less of the triangle (used in FP64, where every
+// multiply-add counts), SBT = 64 reuses registers more.  FP32 sums are
+// compensated per kRun-pixel run (two_sum_into).
 template <typename InT, typename AccT, int SBT = SB>
 __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps, int W, int d,
                                               const double* __restrict__ shift,
-                                              double* __restrict__ s2, int pair) {
+                                              double* __restrict__ s2, int pair, int c_first,
+                                              int c_last) {
   constexpr int TP = SBT / 16;
   __shared__ __align__(16) AccT xa[KCF][SBT];
   __shared__ __align__(16) AccT xb[KCF][SBT];
@@ -205,19 +209,21 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
     cs[threadIdx.x] = c < d ? (AccT)shift[c] : (AccT)0;
   }
   constexpr bool kComp = sizeof(AccT) == 4;
+  const AccT(*xbp)[SBT] = diag ? xa : xb;
+  __syncthreads();
+  for (int ch = c_first; ch < c_last; ++ch) {
   AccT acc[TP][TP];
   float lo[TP][TP], hi[TP][TP];
 #pragma unroll
   for (int i = 0; i < TP; ++i)
 #pragma unroll
     for (int j = 0; j < TP; ++j) acc[i][j] = (AccT)0, lo[i][j] = 0.f, hi[i][j] = 0.f;
-  const AccT(*xbp)[SBT] = diag ? xa : xb;
-  __syncthreads();
-  for (int i0 = 0; i0 < W; i0 += KCF) {
+  const int p1 = min(W, (ch + 1) * kScatterChunk);
+  for (int i0 = ch * kScatterChunk; i0 < p1; i0 += KCF) {
     for (int e = threadIdx.x; e < KCF * SBT; e += 256) {
       const int p = e / SBT, c = e % SBT, i = i0 + p;
       AccT va = 0, vb = 0;
-      if (i < W) {
+      if (i < p1) {
         if (a0 + c < d) va = (AccT)x[(int64_t)i * ps + a0 + c] - cs[c];
         if (!diag && b0 + c < d) vb = (AccT)x[(int64_t)i * ps + b0 + c] - cs[SBT + c];
       }
@@ -225,7 +231,7 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
       if (!diag) xb[p][c] = vb;
     }
     __syncthreads();
-    const int kn = min(KCF, W - i0);
+    const int kn = min(KCF, p1 - i0);
     for (int k0 = 0; k0 < kn; k0 += kRun) {
       const int k1 = min(kn, k0 + kRun);
       for (int k = k0; k < k1; ++k) {
@@ -256,11 +262,14 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
 #pragma unroll
     for (int j = 0; j < TP; ++j) {
       const int b = b0 + tx * TP + j;
-      if (b < d)
-        s2[(int64_t)a * d + b] =
-            kComp ? (double)hi[i][j] + (double)lo[i][j] : (double)acc[i][j];
+      if (b < d) {
+        const double part = kComp ? (double)hi[i][j] + (double)lo[i][j] : (double)acc[i][j];
+        double* o = s2 + (int64_t)a * d + b;
+        *o = ch == c_first ? part : __dadd_rn(*o, part);
+      }
     }
   }
+  }   // chunk
 }
 
 // three CTAs per SM: room for the compensated FP32 sums without spills
@@ -271,7 +280,7 @@ __global__ void __launch_bounds__(256, 3) stats_fp_kernel(const InT* __restrict_
                                                        double* __restrict__ S2f) {
   const int t = blockIdx.y;
   stats_fp_body<InT, AccT, SBT>(X + (int64_t)t * line_stride, ps, W, d, shift + (int64_t)t * d,
-                                S2f + (int64_t)t * d * d, blockIdx.x);
+                                S2f + (int64_t)t * d * d, blockIdx.x, 0, scatter_chunks(W));
 }
 
 // Small d (projected lines, d <= 16): one CTA per line, one thread per entry
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(256) stats_small_kernel(const InT* __restrict_
                               S2f + (int64_t)t * d * d);
 }
 
-int n_pairs(int d, int sb = SB) {
+__host__ __device__ inline int n_pairs(int d, int sb = SB) {
   const int nb = (d + sb - 1) / sb;
   return nb * (nb + 1) / 2;
 }
@@ -343,12 +352,16 @@ __global__ void __launch_bounds__(256, 3) b_stats_kernel(const BStream* __restri
                                                       const BItem* __restrict__ items) {
   const BItem it = items[blockIdx.x];
   const BStream& s = S[it.s];
-  if (s.d <= kSmallD)
+  const int64_t dd = (int64_t)s.d * s.d;
+  if (s.d <= kSmallD) {
     stats_small_body<float, AccT>(s.x, s.d, s.W, s.d, s.shift, s.S2f);
-  else if (sizeof(AccT) == 8 || s.d <= 32)   // 32 x 32 blocks, as the single-stream path
-    stats_fp_body<float, AccT, 32>(s.x, s.d, s.W, s.d, s.shift, s.S2f, it.tile);
-  else
-    stats_fp_body<float, AccT, SB>(s.x, s.d, s.W, s.d, s.shift, s.S2f, it.tile);
+  } else if (sizeof(AccT) == 8 || s.d <= 32) {   // 32 x 32 blocks, as the single-stream path
+    const int np = n_pairs(s.d, 32), pr = it.tile % np, ch = it.tile / np;
+    stats_fp_body<float, AccT, 32>(s.x, s.d, s.W, s.d, s.shift, s.S2f + ch * dd, pr, ch, ch + 1);
+  } else {
+    const int np = n_pairs(s.d, SB), pr = it.tile % np, ch = it.tile / np;
+    stats_fp_body<float, AccT, SB>(s.x, s.d, s.W, s.d, s.shift, s.S2f + ch * dd, pr, ch, ch + 1);
+  }
 }
 
 }  // namespace
@@ -358,9 +371,11 @@ __global__ void __launch_bounds__(256, 3) b_stats_kernel(const BStream* __restri
 // threads idle), 64 otherwise
 int fp_block(int d, bool fp64) { return fp64 || d <= 32 ? 32 : SB; }
 
-int batch_stats_tiles(int d, bool fp64) {
-  return d <= kSmallD ? 1 : n_pairs(d, fp_block(d, fp64));
+// work items of one stream's scatter: (block pair, pixel chunk); one for d <= 16
+int batch_stats_tiles(int d, int W, bool fp64) {
+  return d <= kSmallD ? 1 : n_pairs(d, fp_block(d, fp64)) * scatter_chunks(W);
 }
+int batch_scatter_chunks(int d, int W) { return d <= kSmallD ? 1 : scatter_chunks(W); }
 
 void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t st) {
   b_mean_kernel<<<n, kMeanThreads, 0, st>>>(S, float_shift);
