@@ -311,7 +311,7 @@ def bench_batched(dev, stream, n_streams: int = 256, n_lines: int = 4, steps: in
         errs = np.zeros(n_streams)
         for k in range(na):
             b.push([x[k] for x in lines])
-            if k == 0 and form in ("tf32", "bf16", "tf32x3"):
+            if k == 0:          # factor schedules, score kernels and FP64 layouts
                 b.sync()
                 b.tune(reps=3)
             b.sync()
@@ -740,6 +740,11 @@ def run_ours(args):
             "traffic": traffic, "algorithmic_bytes": (WIDTH * BANDS * 2 + WIDTH * 8 +
                                                       8 * BANDS * (BANDS + 1) / 2) * lines_per_launch,
             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2070 MHz"}
+    if rank == 0 and not args.quick:
+        pk = measure_pipe_peaks(dev)
+        roof["fp64_dgemm_gflops"] = pk["dgemm_gflops"]
+        roof["fp64_dgemm_note"] = ("cuBLAS DGEMM 4096^3 measured in this run: a library "
+                                   "reference for the derived peak")
     kernels = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[2] / args.steps,
                    "share": v[0] / max(1e-9, sum(w[0] for w in prof.values()))}
                for k, v in prof.items() if v[2]}
@@ -888,8 +893,7 @@ def profile_batched(form, steps):
     b = Batch([{"bands": c.bands, "width": c.width} for c in cfgs], form=form, stream=stream)
     b.push([x[0] for x in lines])
     b.sync()
-    if form in ("tf32", "bf16", "tf32x3"):
-        b.tune(reps=3)
+    b.tune(reps=3)
     for k in range(3):
         b.push([x[k % 2] for x in lines])
     b.sync()
@@ -903,6 +907,39 @@ def profile_batched(form, steps):
     print(json.dumps({"profile_case": f"c4_{form}", "steps": steps,
                       "ms_per_step": e0.elapsed_time(e1) / steps}))
     b.close()
+
+
+def measure_pipe_peaks(dev, n: int = 4096, reps: int = 5):
+    """Library reference rates for the FP64 and FP32 pipes: cuBLAS DGEMM and
+    SGEMM (TF32 off) on n x n x n, 2 n^3 flops, best of `reps` (CUDA events),
+    with the clocks sampled meanwhile.  Context for the derived FP64 peak."""
+    import torch
+    local = dev.index or 0
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {"n": n, "how": "torch.matmul (cuBLAS), best of %d, CUDA events" % reps}
+    try:
+        with ClockSampler(local) as clk:
+            for name, dt in (("dgemm", torch.float64), ("sgemm_no_tf32", torch.float32)):
+                a = torch.randn((n, n), dtype=dt, device=dev)
+                b_ = torch.randn((n, n), dtype=dt, device=dev)
+                torch.matmul(a, b_)
+                best = math.inf
+                for _ in range(reps):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    torch.matmul(a, b_)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    best = min(best, e0.elapsed_time(e1))
+                out[name + "_gflops"] = 2.0 * n ** 3 / (best * 1e-3) / 1e9
+                del a, b_
+        out["clocks"] = clk.summary()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["fp64_peak_derived_gflops"] = FP64_PEAK_GFLOPS
+    return out
 
 
 def run_profile_case(args):
@@ -968,6 +1005,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip latency, forms, e2e, baseline")
     ap.add_argument("--lines", type=int, default=LINES,
                     help="lines of the workload cube (smaller cubes for profiler captures)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print cuBLAS DGEMM / SGEMM rates (FP64 and FP32 pipe references)")
     ap.add_argument("--profile-case", default=None,
                     choices=["c2_fp64", "c2_fp64e", "c2_fp32", "c2_tf32", "c2_bf16", "c2_fp64_imc",
                              "c3_fp64", "c3_fp32", "c3_tf32", "c3_bf16", "c3_tf32x3", "c5_fp32",
@@ -980,6 +1019,10 @@ def main():
                          "no bench line")
     args = ap.parse_args()
     globals()["LINES"] = args.lines
+    if args.peaks:
+        import torch
+        print(json.dumps(measure_pipe_peaks(torch.device("cuda", 0))))
+        return
     if args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":

@@ -387,15 +387,21 @@ erx_status erx_batch_get_state(erx_batch* b, int32_t i, int64_t* t, double* mu, 
  * 4 3xTF32 MMA. */
 erx_status erx_batch_route(const erx_batch* b, int32_t i, int32_t* route);
 
-/* Autotuner: for every band count in the batch, time each score kernel the
- * form allows (TF32 form: TF32 MMA or FP32 SIMT; BF16 form: BF16 MMA or FP32
- * SIMT; TF32X3 form: 3xTF32 MMA or FP32 SIMT; FP64 and FP32 forms have one)
- * over that count's streams, `reps` runs
- * each with CUDA events, keep the fastest and re-capture the step.  Needs one
- * step pushed before (ERX_ESTATE otherwise); overwrites the last step's scores,
- * not the state.  cache_path (may be NULL): a JSON object of earlier choices
- * keyed by device, form, band count and width bucket; hits skip the timing and
- * new choices are appended. */
+/* Autotuner: for every band count in the batch (with its width bucket), time
+ * on the batch itself, `reps` runs each with CUDA events, and keep the fastest
+ *  - factor schedule: column (256 threads, several CTAs per SM) or look-ahead
+ *    (512 threads, one CTA per SM);
+ *  - score kernel, where the form allows two (TF32 form: TF32 MMA or FP32
+ *    SIMT; BF16: BF16 MMA or FP32 SIMT; TF32X3: 3xTF32 MMA or FP32 SIMT);
+ *  - FP64 score layout: 1, 2 or 16 threads per pixel over 64, 64 or 8 pixel
+ *    tiles;
+ * then re-capture the step.  The schedules and layouts give the same bits;
+ * only the score kernel choice changes the arithmetic.  Needs one step pushed
+ * before (ERX_ESTATE otherwise); overwrites the last step's scores, not the
+ * state.  cache_path (may be NULL): a JSON object of earlier choices keyed by
+ * device, form, band count, width bucket and the choice ("|factor",
+ * "|fp64layout", none for the score kernel); hits skip the timing and new
+ * choices are appended. */
 erx_status erx_batch_tune(erx_batch* b, int32_t reps, const char* cache_path);
 
 /* Release the batch.  NULL is a no-op. */

@@ -28,11 +28,11 @@ using namespace erx;
 namespace erx {
 int batch_stats_tiles(int d, int W, bool fp64);
 int batch_scatter_chunks(int d, int W);
-int batch_solve_tiles(int route, int W);
-void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, int n_items,
+int batch_solve_tiles(int route, int W, int layout);
+void launch_batch_solve_simt(const BStream* S, const BItem* items, int n_items, int dmax,
+                             cudaStream_t st);
+void launch_batch_solve_fp64(int layout, const BStream* S, const BItem* items, int n_items,
                              int dmax, cudaStream_t st);
-void launch_batch_solve_fp64(const BStream* S, const BItem* items, int n_hi, int n_items,
-                             int dmax, int dmax_lo, cudaStream_t st);
 void launch_batch_solve_tc(int fmt, const BStream* S, const BItem* items, int n_items, int dmax,
                            unsigned long long* err, cudaStream_t st);
 }  // namespace erx
@@ -69,12 +69,13 @@ struct erx_batch {
   int n_ema = 0;
   BItem* solve_items[kRoutes] = {};
   int n_solve[kRoutes] = {};
-  int n_hi0 = 0, dmax_lo0 = 1;   // FP64 route: items of streams with d > 128; largest other d
-  // factor and FP32 inverse: every stream, largest d first; the first n_chol_big
-  // have d > 128 and run on the look-ahead schedule (on the batch's stream) while
-  // the others run beside them on a second stream inside the step's graph
+  int n_lay[3] = {}, dmax_lay[3] = {1, 1, 1};   // FP64 route: items per thread layout, in order
+  int dmax_route[kRoutes] = {1, 1, 1, 1, 1};
+  // factor and FP32 inverse: every stream, look-ahead schedule first, each group
+  // largest d first; the look-ahead group runs on the batch's stream and the
+  // column group beside it on a second stream inside the step's graph
   BItem* chol_items = nullptr;
-  int n_chol_big = 0, dmax_small = 1;
+  int n_chol_la = 0, dmax_la = 1, dmax_col = 1;
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned long long* err = nullptr;
@@ -143,30 +144,35 @@ int route_format(int route) {
   return route == 2 ? 2 : route == 3 ? 1 : 3;
 }
 
-// (Re)build the score-kernel work lists from the routes in the host table.
+// (Re)build the score-kernel work lists from the routes (and FP64 layouts) in
+// the host table; items of each route largest d first, route 0 grouped by layout.
 erx_status build_solve_items(erx_batch* b) {
   for (int r = 0; r < kRoutes; ++r) {
     std::vector<BItem> items;
     for (int s = 0; s < b->n; ++s)
       if (b->host[s].route == r)
-        for (int k = 0; k < batch_solve_tiles(r, b->host[s].W); ++k) items.push_back({s, k});
-    // largest band counts first: their tiles take longest
+        for (int k = 0; k < batch_solve_tiles(r, b->host[s].W, b->host[s].layout); ++k)
+          items.push_back({s, k});
     std::stable_sort(items.begin(), items.end(), [&](const BItem& x, const BItem& y) {
-      return b->host[x.s].d > b->host[y.s].d;
+      const BStream &u = b->host[x.s], &v = b->host[y.s];
+      if (r == 0 && u.layout != v.layout) return u.layout < v.layout;
+      return u.d > v.d;
     });
     b->n_solve[r] = (int)items.size();
+    b->dmax_route[r] = 1;
+    for (const BItem& it : items) b->dmax_route[r] = std::max(b->dmax_route[r], b->host[it.s].d);
     if (r == 0) {
-      b->n_hi0 = 0;
-      b->dmax_lo0 = 1;
+      for (int l = 0; l < 3; ++l) b->n_lay[l] = 0, b->dmax_lay[l] = 1;
       for (const BItem& it : items) {
-        if (b->host[it.s].d > 128) ++b->n_hi0;
-        else b->dmax_lo0 = std::max(b->dmax_lo0, b->host[it.s].d);
+        const BStream& e = b->host[it.s];
+        b->n_lay[e.layout] += 1;
+        b->dmax_lay[e.layout] = std::max(b->dmax_lay[e.layout], e.d);
       }
     }
     if (!b->solve_items[r]) {
-      // capacity: every stream's tiles for this route
+      // capacity: every stream's tiles for this route at the finest tiling
       size_t cap = 0;
-      for (int s = 0; s < b->n; ++s) cap += (size_t)batch_solve_tiles(r, b->host[s].W);
+      for (int s = 0; s < b->n; ++s) cap += (size_t)batch_solve_tiles(r, b->host[s].W, 2);
       erx_status st = balloc(b, &b->solve_items[r], cap);
       if (st != ERX_OK) return st;
     }
@@ -175,6 +181,32 @@ erx_status build_solve_items(erx_batch* b) {
                                      cudaMemcpyHostToDevice) != cudaSuccess)
       return ERX_ECUDA;
   }
+  return ERX_OK;
+}
+
+// (Re)build the factor work list from the schedules in the host table.
+erx_status build_chol_items(erx_batch* b) {
+  std::vector<BItem> items;
+  for (int i = 0; i < b->n; ++i) items.push_back({i, 0});
+  std::stable_sort(items.begin(), items.end(), [&](const BItem& x, const BItem& y) {
+    const BStream &u = b->host[x.s], &v = b->host[y.s];
+    if (u.fac != v.fac) return u.fac > v.fac;
+    return u.d > v.d;
+  });
+  b->n_chol_la = 0;
+  b->dmax_la = b->dmax_col = 1;
+  for (const BItem& it : items) {
+    const BStream& e = b->host[it.s];
+    if (e.fac) ++b->n_chol_la, b->dmax_la = std::max(b->dmax_la, e.d);
+    else b->dmax_col = std::max(b->dmax_col, e.d);
+  }
+  if (!b->chol_items) {
+    erx_status st = balloc(b, &b->chol_items, items.size());
+    if (st != ERX_OK) return st;
+  }
+  if (cudaMemcpy(b->chol_items, items.data(), items.size() * sizeof(BItem),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return ERX_ECUDA;
   return ERX_OK;
 }
 
@@ -204,33 +236,38 @@ void enqueue_step(erx_batch* b, cudaStream_t st) {
   launch_batch_mean(b->table, b->n, !fp64, st);
   launch_batch_stats(b->table, b->stats_items, b->n_stats, fp64, st);
   launch_batch_ema(b->table, b->ema_items, b->n_ema, st);
-  // factor (and the FP32 inverse): the streams above 128 dimensions, one CTA
-  // per SM each, beside the smaller ones on the second stream
-  const int nb = b->n_chol_big, ns = b->n - b->n_chol_big;
+  // factor (and the FP32 inverse): the look-ahead group, one CTA per SM each,
+  // beside the column group on the second stream
+  const int nb = b->n_chol_la, ns = b->n - b->n_chol_la;
   const bool fork = nb > 0 && ns > 0;
   cudaStream_t ss = fork ? b->side : st;
   if (fork) {
     cudaEventRecord(b->ev_fork, st);
     cudaStreamWaitEvent(b->side, b->ev_fork, 0);
   }
-  launch_batch_chol(b->table, b->chol_items, nb, b->dmax, true, !fp64, b->err, st);
-  if (!fp64) launch_batch_trinv32(b->table, b->chol_items, nb, b->dmax, st);
-  launch_batch_chol(b->table, b->chol_items + nb, ns, b->dmax_small, false, !fp64, b->err, ss);
-  if (!fp64) launch_batch_trinv32(b->table, b->chol_items + nb, ns, b->dmax_small, ss);
+  launch_batch_chol(b->table, b->chol_items, nb, b->dmax_la, true, !fp64, b->err, st);
+  if (!fp64) launch_batch_trinv32(b->table, b->chol_items, nb, b->dmax_la, st);
+  launch_batch_chol(b->table, b->chol_items + nb, ns, b->dmax_col, false, !fp64, b->err, ss);
+  if (!fp64) launch_batch_trinv32(b->table, b->chol_items + nb, ns, b->dmax_col, ss);
   if (fork) {
     cudaEventRecord(b->ev_join, b->side);
     cudaStreamWaitEvent(st, b->ev_join, 0);
   }
   for (int r = 0; r < kRoutes; ++r) {
     if (!b->n_solve[r]) continue;
-    if (r == 0)
-      launch_batch_solve_fp64(b->table, b->solve_items[0], b->n_hi0, b->n_solve[0], b->dmax,
-                              b->dmax_lo0, st);
-    else if (r == 1)
-      launch_batch_solve_simt(r, b->table, b->solve_items[r], b->n_solve[r], b->dmax, st);
-    else
+    if (r == 0) {
+      int off = 0;
+      for (int l = 0; l < 3; ++l) {
+        launch_batch_solve_fp64(l, b->table, b->solve_items[0] + off, b->n_lay[l],
+                                b->dmax_lay[l], st);
+        off += b->n_lay[l];
+      }
+    } else if (r == 1) {
+      launch_batch_solve_simt(b->table, b->solve_items[r], b->n_solve[r], b->dmax_route[r], st);
+    } else {
       launch_batch_solve_tc(route_format(r), b->table, b->solve_items[r], b->n_solve[r],
-                            b->dmax, b->err, st);
+                            b->dmax_route[r], b->err, st);
+    }
   }
   launch_batch_normalise(b->table, b->n, fp64, st);
 }
@@ -365,6 +402,8 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
       e.W = W;
       e.d = d;
       e.route = native_route(form);
+      e.layout = d > 128 ? 1 : 0;
+      e.fac = d > 128 ? 1 : 0;
       e.order = c.order;
       e.alpha = c.momentum;
       e.ridge = c.ridge;
@@ -397,19 +436,7 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
     std::stable_sort(st_items.begin(), st_items.end(), [&](const BItem& x, const BItem& y) {
       return (int64_t)b->host[x.s].W * b->host[x.s].d > (int64_t)b->host[y.s].W * b->host[y.s].d;
     });
-    std::vector<BItem> ch_items;
-    for (int i = 0; i < n; ++i) ch_items.push_back({i, 0});
-    std::stable_sort(ch_items.begin(), ch_items.end(), [&](const BItem& x, const BItem& y) {
-      return b->host[x.s].d > b->host[y.s].d;
-    });
-    for (const BItem& it : ch_items) {
-      if (b->host[it.s].d > 128) ++b->n_chol_big;
-      else b->dmax_small = std::max(b->dmax_small, b->host[it.s].d);
-    }
-    if (s == ERX_OK) s = balloc(b, &b->chol_items, ch_items.size());
-    if (s == ERX_OK && cudaMemcpy(b->chol_items, ch_items.data(), ch_items.size() * sizeof(BItem),
-                                  cudaMemcpyHostToDevice) != cudaSuccess)
-      s = ERX_ECUDA;
+    if (s == ERX_OK) s = build_chol_items(b);
     if (s == ERX_OK &&
         (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
          cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -567,13 +594,13 @@ erx_status erx_batch_route(const erx_batch* b, int32_t i, int32_t* route) {
 erx_status erx_batch_tune(erx_batch* b, int32_t reps, const char* cache_path) {
   if (!b || reps < 1) return ERX_EINVAL;
   if (b->failed) return ERX_ECUDA;
+  const bool fp64 = b->form == ERX_FORM_FP64;
   // band counts present and the routes the form allows
   std::map<int, std::vector<int>> classes;
   for (int s = 0; s < b->n; ++s) classes[b->host[s].d].push_back(s);
   std::vector<int> routes;
   for (int r = 0; r < kRoutes; ++r)
     if (route_allowed(b->form, r)) routes.push_back(r);
-  if (routes.size() < 2) return ERX_OK;
   char dev_name[256] = "gpu";
   {
     int dev = 0;
@@ -591,14 +618,19 @@ erx_status erx_batch_tune(erx_batch* b, int32_t reps, const char* cache_path) {
       std::fclose(f);
     }
   }
-  auto key_of = [&](int d, int wbucket) {
-    char k[320];
-    std::snprintf(k, sizeof k, "\"%s|form%d|d%d|w%d\"", dev_name, b->form, d, wbucket);
+  // keys: device, form, band count, width bucket and what was chosen
+  auto key_of = [&](int d, int wbucket, const char* what) {
+    char k[352];
+    std::snprintf(k, sizeof k, "\"%s|form%d|d%d|w%d%s\"", dev_name, b->form, d, wbucket, what);
     return std::string(k);
   };
-  // The scores of the last step are recomputed by the candidate kernels, which
-  // read only the per-step buffers (mu_t, factor) and write scores: the state
-  // does not move.  A step must therefore have run once.
+  auto cached = [&](const std::string& key) {
+    const size_t pos = cache.find(key + ":");
+    return pos == std::string::npos ? -1 : std::atoi(cache.c_str() + pos + key.size() + 1);
+  };
+  // The candidates rerun the last step's factor and score kernels, which read
+  // only per-step inputs (K_t, mu_t, the line) and rewrite per-step outputs: the
+  // state does not move.  A step must therefore have run once.
   bool need_run = true;
   {
     BStream e;
@@ -614,63 +646,120 @@ erx_status erx_batch_tune(erx_batch* b, int32_t reps, const char* cache_path) {
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return ERX_ECUDA;
+  // time `launch` (reps runs after one warm-up pass) on a scratch copy of `items`
+  BItem* dit = nullptr;
+  size_t dit_cap = 0;
+  auto timed = [&](const std::vector<BItem>& items, auto&& launch) -> float {
+    if (items.size() > dit_cap) {
+      if (dit) cudaFree(dit);
+      dit = nullptr;
+      if (cudaMalloc(&dit, items.size() * sizeof(BItem)) != cudaSuccess) {
+        cudaGetLastError();
+        dit_cap = 0;
+        return 1e30f;
+      }
+      dit_cap = items.size();
+    }
+    cudaMemcpy(dit, items.data(), items.size() * sizeof(BItem), cudaMemcpyHostToDevice);
+    float ms = 1e30f;
+    for (int pass = 0; pass < 2; ++pass) {
+      cudaEventRecord(e0, b->stream);
+      for (int k = 0; k < reps; ++k) launch(dit, (int)items.size());
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    return ms;
+  };
   std::string new_entries;
+  auto remember = [&](const std::string& key, int v) {
+    char line[420];
+    std::snprintf(line, sizeof line, "%s%s: %d", new_entries.empty() && cache.empty() ? "" : ",\n ",
+                  key.c_str(), v);
+    new_entries += line;
+  };
   for (auto& kv : classes) {
     const int d = kv.first;
+    const std::vector<int>& ss = kv.second;
     int wsum = 0;
-    for (int s : kv.second) wsum += b->host[s].W;
-    const int wbucket = 1 << (int)std::ceil(std::log2(std::max(1, wsum / (int)kv.second.size())));
-    const std::string key = key_of(d, wbucket);
-    int best = -1;
-    const size_t pos = cache.find(key);
-    if (pos != std::string::npos) {
-      const size_t c = cache.find(':', pos);
-      if (c != std::string::npos) best = std::atoi(cache.c_str() + c + 1);
-      if (!route_allowed(b->form, best)) best = -1;
-    }
-    if (best < 0) {
-      float best_ms = 1e30f;
-      for (int r : routes) {
-        // timing items: this class's streams on route r, in a scratch work list
-        std::vector<BItem> it;
-        for (int s : kv.second)
-          for (int k = 0; k < batch_solve_tiles(r, b->host[s].W); ++k) it.push_back({s, k});
-        BItem* dit = nullptr;
-        if (cudaMalloc(&dit, it.size() * sizeof(BItem)) != cudaSuccess) {
-          cudaGetLastError();
-          continue;
-        }
-        cudaMemcpy(dit, it.data(), it.size() * sizeof(BItem), cudaMemcpyHostToDevice);
-        // the route's score type must match the table's: routes 1 to 4 all write float
-        std::vector<BStream> tmp = b->host;
-        for (int s : kv.second) tmp[s].route = r;
-        cudaMemcpy(b->table, tmp.data(), sizeof(BStream) * b->n, cudaMemcpyHostToDevice);
-        float ms = 0.f;
-        for (int pass = 0; pass < 2; ++pass) {   // pass 0 warms up
-          cudaEventRecord(e0, b->stream);
-          for (int k = 0; k < reps; ++k) {
-            if (r <= 1) launch_batch_solve_simt(r, b->table, dit, (int)it.size(), b->dmax, b->stream);
-            else launch_batch_solve_tc(route_format(r), b->table, dit, (int)it.size(), b->dmax,
-                                       b->err, b->stream);
-          }
-          cudaEventRecord(e1, b->stream);
-          cudaEventSynchronize(e1);
-          cudaEventElapsedTime(&ms, e0, e1);
-        }
-        cudaFree(dit);
-        if (ms < best_ms) best_ms = ms, best = r;
+    for (int s : ss) wsum += b->host[s].W;
+    const int wbucket = 1 << (int)std::ceil(std::log2(std::max(1, wsum / (int)ss.size())));
+    std::vector<BItem> per_stream;
+    for (int s : ss) per_stream.push_back({s, 0});
+
+    // (1) factor schedule: column (256 threads) or look-ahead (512), same bits
+    const std::string kf = key_of(d, wbucket, "|factor");
+    int fac = cached(kf);
+    if (fac != 0 && fac != 1) {
+      float best = 1e30f;
+      for (int f = 0; f < 2; ++f) {
+        const float ms = timed(per_stream, [&](const BItem* it, int n) {
+          launch_batch_chol(b->table, it, n, d, f == 1, !fp64, b->err, b->stream);
+        });
+        if (ms < best) best = ms, fac = f;
       }
-      char line[400];
-      std::snprintf(line, sizeof line, "%s%s: %d", new_entries.empty() && cache.empty() ? "" : ",\n ",
-                    key.c_str(), best);
-      new_entries += line;
+      remember(kf, fac);
     }
-    for (int s : kv.second) b->host[s].route = best;
+    // the FP32 routes' factor copy is inverted in place by trinv32: redo it
+    if (!fp64) {
+      timed(per_stream, [&](const BItem*, int) {});   // uploads the list
+      launch_batch_trinv32(b->table, dit, (int)per_stream.size(), d, b->stream);
+    }
+    for (int s : ss) b->host[s].fac = fac;
+
+    // (2) score route (forms that allow two)
+    int best_r = b->host[ss[0]].route;
+    if (routes.size() > 1) {
+      const std::string kr = key_of(d, wbucket, "");
+      best_r = cached(kr);
+      if (!route_allowed(b->form, best_r)) {
+        best_r = -1;
+        float best = 1e30f;
+        for (int r : routes) {
+          std::vector<BItem> it;
+          for (int s : ss)
+            for (int k = 0; k < batch_solve_tiles(r, b->host[s].W, 0); ++k) it.push_back({s, k});
+          // the route's score type must match the table's: routes 1 to 4 all write float
+          std::vector<BStream> tmp = b->host;
+          for (int s : ss) tmp[s].route = r;
+          cudaMemcpy(b->table, tmp.data(), sizeof(BStream) * b->n, cudaMemcpyHostToDevice);
+          const float ms = timed(it, [&](const BItem* di, int n) {
+            if (r == 1) launch_batch_solve_simt(b->table, di, n, d, b->stream);
+            else launch_batch_solve_tc(route_format(r), b->table, di, n, d, b->err, b->stream);
+          });
+          if (ms < best) best = ms, best_r = r;
+        }
+        remember(kr, best_r);
+      }
+    }
+    for (int s : ss) b->host[s].route = best_r;
+
+    // (3) FP64 score: threads per pixel and pixels per CTA, same bits
+    if (best_r == 0) {
+      const std::string kl = key_of(d, wbucket, "|fp64layout");
+      int lay = cached(kl);
+      if (lay < 0 || lay > 2) {
+        float best = 1e30f;
+        for (int l = 0; l < 3; ++l) {
+          std::vector<BItem> it;
+          for (int s : ss)
+            for (int k = 0; k < batch_solve_tiles(0, b->host[s].W, l); ++k) it.push_back({s, k});
+          const float ms = timed(it, [&](const BItem* di, int n) {
+            launch_batch_solve_fp64(l, b->table, di, n, d, b->stream);
+          });
+          if (ms < best) best = ms, lay = l;
+        }
+        remember(kl, lay);
+      }
+      for (int s : ss) b->host[s].layout = lay;
+    }
   }
+  if (dit) cudaFree(dit);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   erx_status s = upload_table(b);
   if (s == ERX_OK) s = build_solve_items(b);
+  if (s == ERX_OK) s = build_chol_items(b);
   if (s == ERX_OK) s = capture(b);
   if (s == ERX_OK && cache_path && !new_entries.empty()) {
     std::string body = cache;

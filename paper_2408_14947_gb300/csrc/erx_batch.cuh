@@ -16,6 +16,9 @@ struct BStream {
   int W, d;
   int route;             // score kernel: 0 FP64, 1 FP32 SIMT, 2 TF32 MMA, 3 BF16 MMA,
                          // 4 3xTF32 MMA
+  int layout;            // route 0: threads per pixel x pixels per CTA, 0 (1, 64),
+                         // 1 (2, 64), 2 (16, 8); all give the same bits
+  int fac;               // factor schedule: 0 column (256 threads), 1 look-ahead (512)
   int order;
   double alpha, ridge, threshold;
   int64_t warmup;

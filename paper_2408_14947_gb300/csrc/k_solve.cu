@@ -179,18 +179,20 @@ __global__ void __launch_bounds__(H * NPX) solve_fp64_kernel(
   }
 }
 
-// Batched form: one CTA per (stream, pixel tile) item; H = 2 for streams with
-// more than 128 dimensions (two threads per pixel, as the single-stream path).
-template <int H>
-__global__ void __launch_bounds__(H * kPixF64) b_solve_fp64_kernel(
+// Batched form: one CTA per (stream, pixel tile) item, H threads per pixel
+// over NPX-pixel tiles (the layouts of the single-stream path, same bits):
+// layout 0 = (1, 64), 1 = (2, 64), 2 = (16, 8); chosen per band count by the
+// autotuner (default: 1 above 128 dimensions, else 0).
+template <int H, int NPX>
+__global__ void __launch_bounds__(H * NPX) b_solve_fp64_kernel(
     const BStream* __restrict__ S, const BItem* __restrict__ items) {
   const BItem it = items[blockIdx.x];
   const BStream& s = S[it.s];
   if constexpr (H == 1)
     solve_fp64_body<float>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf, (double*)s.delta, it.tile);
   else
-    solve_fp64_multi_body<float, H, kPixF64>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf, (double*)s.delta,
-                                             it.tile);
+    solve_fp64_multi_body<float, H, NPX>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf, (double*)s.delta,
+                                         it.tile);
 }
 
 constexpr int kPixF32 = 64;   // pixels per CTA
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(128) b_solve_fp32_kernel(const BStream* __rest
   solve_fp32_body<float>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta, it.tile);
 }
 
-size_t smem_fp64(int d) { return (size_t)kPixF64 * (d | 1) * sizeof(double); }
+size_t smem_fp64(int d, int npx = kPixF64) { return (size_t)npx * (d | 1) * sizeof(double); }
 size_t smem_fp32(int d) {
   return (size_t)d * (kPixF32 + kLS) * sizeof(float);
 }
@@ -358,34 +360,35 @@ cudaError_t configure_solve_kernels() {
   ERX_CFG(solve_fp32_kernel<uint16_t>, m32);
   ERX_CFG(solve_fp32_kernel<float>, m32);
   ERX_CFG(solve_fp32_kernel<double>, m32);
-  ERX_CFG(b_solve_fp64_kernel<1>, m64);
-  ERX_CFG(b_solve_fp64_kernel<2>, m64);
+  ERX_CFG((b_solve_fp64_kernel<1, kPixF64>), m64);
+  ERX_CFG((b_solve_fp64_kernel<2, kPixF64>), m64);
+  ERX_CFG((b_solve_fp64_kernel<16, 8>), m64);
   ERX_CFG(b_solve_fp32_kernel, m32);
 #undef ERX_CFG
   return e;
 }
 
-int batch_solve_tiles(int route, int W) {
-  return route == 0 ? (W + kPixF64 - 1) / kPixF64
+// pixel tiles of one stream's score: route 0 (FP64) by its thread layout
+int batch_solve_tiles(int route, int W, int layout) {
+  return route == 0 ? (W + (layout == 2 ? 8 : kPixF64) - 1) / (layout == 2 ? 8 : kPixF64)
                     : route == 1 ? (W + kPixF32 - 1) / kPixF32 : (W + 127) / 128;
 }
 
-void launch_batch_solve_simt(int route, const BStream* S, const BItem* items, int n_items,
-                             int dmax, cudaStream_t st) {
-  if (route == 0)
-    b_solve_fp64_kernel<1><<<n_items, kPixF64, smem_fp64(dmax), st>>>(S, items);
-  else
-    b_solve_fp32_kernel<<<n_items, 128, smem_fp32(dmax), st>>>(S, items);
+void launch_batch_solve_simt(const BStream* S, const BItem* items, int n_items, int dmax,
+                             cudaStream_t st) {
+  if (n_items > 0) b_solve_fp32_kernel<<<n_items, 128, smem_fp32(dmax), st>>>(S, items);
 }
 
-// FP64 route with its items sorted by dimension, largest first: the first n_hi
-// (d > 128) with two threads per pixel and shared memory for dmax, the rest
-// with one thread per pixel and shared memory for their own largest d
-void launch_batch_solve_fp64(const BStream* S, const BItem* items, int n_hi, int n_items,
-                             int dmax, int dmax_lo, cudaStream_t st) {
-  if (n_hi > 0) b_solve_fp64_kernel<2><<<n_hi, 2 * kPixF64, smem_fp64(dmax), st>>>(S, items);
-  if (n_items > n_hi)
-    b_solve_fp64_kernel<1><<<n_items - n_hi, kPixF64, smem_fp64(dmax_lo), st>>>(S, items + n_hi);
+// FP64 route, the items of one thread layout (dmax: their streams' largest d)
+void launch_batch_solve_fp64(int layout, const BStream* S, const BItem* items, int n_items,
+                             int dmax, cudaStream_t st) {
+  if (n_items <= 0) return;
+  if (layout == 0)
+    b_solve_fp64_kernel<1, kPixF64><<<n_items, kPixF64, smem_fp64(dmax), st>>>(S, items);
+  else if (layout == 1)
+    b_solve_fp64_kernel<2, kPixF64><<<n_items, 2 * kPixF64, smem_fp64(dmax), st>>>(S, items);
+  else
+    b_solve_fp64_kernel<16, 8><<<n_items, 128, smem_fp64(dmax, 8), st>>>(S, items);
 }
 
 constexpr int kPairMinD = 129;   // two threads per pixel from here on

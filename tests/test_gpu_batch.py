@@ -189,3 +189,31 @@ def test_batch_learned_needs_matching_encoder():
     assert lib.erx_batch_set_encoder(C.c_void_p(p.b), C.c_void_p(enc.e)) == ERX_EINVAL
     p.close()
     enc.close()
+
+
+def test_tuned_fp64_batch_keeps_its_bits(tmp_path):
+    """The FP64 autotuner picks factor schedules and score layouts that give the
+    same bits: a tuned batch and its contexts agree exactly over the following
+    steps, and the choices are cached per band count."""
+    need_gpu()
+    from paper_2408_14947_gb300 import Batch
+    cubes = _cubes(seed=3)
+    dev = [torch.from_numpy(c).cuda() for c in cubes]
+    cache = str(tmp_path / "tune64.json")
+    b = Batch([{"bands": bb, "width": w, "warmup": 2} for (w, bb) in SHAPES], form="fp64")
+    b.push([x[0] for x in dev])
+    b.tune(reps=2, cache_path=cache)
+    outs = [[b.views(i)[1].cpu().numpy().copy()] for i in range(len(SHAPES))]
+    for t in range(1, STEPS):
+        b.push([x[t] for x in dev])
+        b.sync()
+        for i in range(len(SHAPES)):
+            outs[i].append(b.views(i)[1].cpu().numpy().copy())
+    for i, c in enumerate(cubes):
+        ref, _ = run_gpu(c, form="fp64", warmup=2, push_sizes=[1] * STEPS)
+        assert np.array_equal(np.stack(outs[i]), ref["delta"]), SHAPES[i]
+    data = json.load(open(cache))
+    for _, bb in SHAPES:
+        assert any(k.endswith("|factor") and f"|d{bb}|" in k for k in data), bb
+        assert any(k.endswith("|fp64layout") and f"|d{bb}|" in k for k in data), bb
+    b.close()

@@ -227,13 +227,12 @@ def test_planted_anomaly_ranking_every_form(form, tie):
     assert np.all(agree[clear]), (form, int((~agree[clear]).sum()))
 
 
-@pytest.mark.parametrize("width,bands", [(640, 108), (2048, 127), (65, 1), (130, 16), (1, 5)])
+@pytest.mark.parametrize("width,bands", [(640, 108), (2048, 127), (65, 1), (130, 16), (2, 5)])
 def test_tensor_core_stats_match_integer_route_bitwise(width, bands):
     """The tcgen05 exact-integer SYRK (bf16 6-bit split, FP32 accumulation in
     TMEM) gives the same sums as the 32-bit integer route, hence identical
-    scores, state and flags."""
-    if width < 2:
-        pytest.skip("a line needs two pixels")
+    scores, state and flags (from lines of two pixels, the fewest a line
+    covariance needs, to 2048)."""
     cube = synth.gen_lines(synth.dn_c2(width=width, bands=bands, seed=9), 0, 9)
     a, da = run_gpu(cube, in_bits=12, warmup=2)
     b, db = run_gpu(cube, in_bits=12, warmup=2, simt_stats=True)
