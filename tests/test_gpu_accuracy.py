@@ -5,8 +5,9 @@ Prints the table; asserts each form's stated bar over the range of kappa on
 which it is claimed: FP64 and FP64E (double-float score) 1e-9 up to 1e6; FP32
 and 3xTF32 1e-4 up to 1e4;
 TF32 5e-3 up to 1e4; BF16 4e-2 up to 1e3 (max relative delta error over all
-pixels).  The tensor-core forms take S2 on the tensor cores here (float lines,
-512 x 224 samples: the TC scatter route)."""
+pixels).  The cubes have the 224-band workload's width, 1024 px.  The
+tensor-core forms take S2 on the tensor cores here (float lines: the TC
+scatter route)."""
 import numpy as np
 import pytest
 
@@ -26,12 +27,12 @@ def table():
     need_gpu()
     out = {}
     for kappa in KAPPAS:
-        cube = synth.gen_lines(synth.cov_c3(kappa, width=512, bands=224, seed=2), 0, 4)
+        cube = synth.gen_lines(synth.cov_c3(kappa, width=1024, bands=224, seed=2), 0, 4)
         ref = oracle.run_cube(cube, warmup=0)
         for form in BARS:
             got, _ = run_gpu(cube, form=form, warmup=0)
             out[(form, kappa)] = rel_err(got["delta"], ref["delta"])
-    print("\nmax relative delta error, 4 lines x 512 px x 224 bands")
+    print("\nmax relative delta error, 4 lines x 1024 px x 224 bands")
     print("kappa   " + "".join(f"{f:>11s}" for f in BARS))
     for kappa in KAPPAS:
         print(f"{kappa:7.0e} " + "".join(f"{out[(f, kappa)]:11.2e}" for f in BARS))
