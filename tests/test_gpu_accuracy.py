@@ -3,9 +3,9 @@ covariance's condition number grows (224-band Gaussian cubes, GPU).
 
 Prints the table; asserts each form's stated bar over the range of kappa on
 which it is claimed: FP64 and FP64E (double-float score) 1e-9 up to 1e6; FP32
-and 3xTF32 1e-4 up to 1e4;
-TF32 5e-3 up to 1e4; BF16 4e-2 up to 1e3 (max relative delta error over all
-pixels).  The cubes have the 224-band workload's width, 1024 px.  The
+and 3xTF32 1e-4 up to 1e6 (the scatter's compensated FP32 sums keep them near
+5e-5 there); TF32 5e-3 up to 1e4; BF16 4e-2 up to 1e4 (max relative delta error
+over all pixels).  The cubes have the 224-band workload's width, 1024 px.  The
 tensor-core forms take S2 on the tensor cores here (float lines: the TC
 scatter route)."""
 import numpy as np
@@ -18,8 +18,8 @@ from tests.gpu_util import need_gpu, rel_err, run_gpu
 pytestmark = pytest.mark.gpu
 
 KAPPAS = [1e2, 1e3, 1e4, 1e5, 1e6]
-BARS = {"fp64": (1e-9, 1e6), "fp64e": (1e-9, 1e6), "fp32": (1e-4, 1e4), "tf32x3": (1e-4, 1e4),
-        "tf32": (5e-3, 1e4), "bf16": (4e-2, 1e3)}
+BARS = {"fp64": (1e-9, 1e6), "fp64e": (1e-9, 1e6), "fp32": (1e-4, 1e6), "tf32x3": (1e-4, 1e6),
+        "tf32": (5e-3, 1e4), "bf16": (4e-2, 1e4)}
 
 
 @pytest.fixture(scope="module")

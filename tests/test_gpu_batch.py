@@ -65,21 +65,33 @@ def test_batch_matches_single_stream_contexts(form):
 
 # These streams switch scene every 3 lines; K_t + ridge I reaches condition
 # numbers of 1e5 .. 1e6 (few materials against 0.01 noise, and 224 bands over
-# only 260 px).  The bars of the mixed forms are stated up to kappa 1e4 (FP32,
-# TF32) and 1e3 (BF16) in tests/test_gpu_accuracy.py; at kappa 1e6 that sweep
-# measures 2.2e-3 (FP32), 6.6e-3 (TF32) and 9.4e-2 (BF16), so the tolerances
-# here are about twice those.  The bit-for-bit check against single-stream
-# contexts above is the exact test of the batched path.
-@pytest.mark.parametrize("form,tol", [("fp64", 1e-9), ("fp32", 5e-3), ("tf32", 2e-2),
-                                      ("bf16", 0.2), ("tf32x3", 5e-3)])
+# only 260 px).  FP32 and 3xTF32 hold the 1e-4 bar there (the kappa sweep gives
+# 5e-5 at 1e6 with the compensated scatter).  TF32 and BF16 round the score's
+# operands: each pixel is held to the first-order bound of that rounding, 2 u c
+# with c the componentwise condition of L^{-1} r from the oracle's factor
+# (tests/rounding.py), plus 10 % and 1e-4 for the FP32 scatter and inverse.  The
+# bit-for-bit check against single-stream contexts above is the exact test of
+# the batched path.
+U_SCORE = {"tf32": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+@pytest.mark.parametrize("form,tol", [("fp64", 1e-9), ("fp32", 1e-4), ("tf32", None),
+                                      ("bf16", None), ("tf32x3", 1e-4)])
 def test_batch_matches_oracle(form, tol):
     need_gpu()
+    from tests.rounding import score_condition
     cubes = _cubes(seed=1)
     b, outs = _run_batch(form, cubes)
     for i, c in enumerate(cubes):
         ref = oracle.run_cube(c.astype(np.float64), warmup=2)
-        got = np.stack([o[0] for o in outs[i]])
-        assert rel_err(got, ref["delta"]) <= tol, (form, SHAPES[i])
+        got = np.stack([o[0] for o in outs[i]]).astype(np.float64)
+        if tol is not None:
+            assert rel_err(got, ref["delta"]) <= tol, (form, SHAPES[i])
+        else:
+            cond = score_condition(c.astype(np.float64), warmup=2)
+            err = np.abs(got - ref["delta"]) / ref["delta"]
+            bound = 2.2 * U_SCORE[form] * cond + 1e-4
+            assert np.all(err <= bound), (form, SHAPES[i], float(np.max(err / bound)))
     b.close()
 
 
