@@ -27,7 +27,7 @@ struct BStream {
   double* K_state;       // d(d+1)/2 packed
   double* mu_hat;        // d
   double* shift;         // d
-  double* S2f;           // nch x d x d: the scatter's chunk sums (one for d <= 16)
+  double* S2f;           // nch x d x d: the scatter's 256-pixel chunk sums
   int nch;               // chunk sums in S2f
   double* mu_t;          // d
   double* K_t;           // d(d+1)/2

@@ -19,7 +19,7 @@ namespace erx {
 
 constexpr int kMaxDim = 224;   // packed FP64 factor must fit one SM's shared memory
 constexpr int kFactorBlock = 32;  // diagonal blocks of the factor are stored inverted
-// The floating centred scatter of a line (above 16 dimensions) is summed per
+// The floating centred scatter of a line is summed per
 // chunk of kScatterChunk pixels; the chunk sums are then added in FP64 in
 // chunk order.  A single-stream launch adds them as it goes; the batched form
 // gives each chunk its own CTA and adds the chunk sums in the EMA kernel, in the

@@ -292,7 +292,8 @@ constexpr int kSmallD = 16;
 template <typename InT, typename AccT>
 __device__ __forceinline__ void stats_small_body(const InT* __restrict__ x, int ps, int W, int d,
                                                  const double* __restrict__ shift,
-                                                 double* __restrict__ s2) {
+                                                 double* __restrict__ s2, int c_first,
+                                                 int c_last) {
   const int P = d * (d + 1) / 2;
   const int q = threadIdx.x;
   if (q >= P) return;
@@ -301,27 +302,37 @@ __device__ __forceinline__ void stats_small_body(const InT* __restrict__ x, int 
   const int b = q - a * (a + 1) / 2;
   const AccT ca = (AccT)shift[a], cb = (AccT)shift[b];
   constexpr bool kComp = sizeof(AccT) == 4;
-  float hi = 0.f, lo = 0.f;
-  AccT s0 = 0, s1 = 0, s2a = 0, s3 = 0;
-  int i = 0;
-  for (; i + 4 <= W; i += 4) {
-    s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
-    s1 = fma((AccT)x[(int64_t)(i + 1) * ps + a] - ca, (AccT)x[(int64_t)(i + 1) * ps + b] - cb, s1);
-    s2a = fma((AccT)x[(int64_t)(i + 2) * ps + a] - ca, (AccT)x[(int64_t)(i + 2) * ps + b] - cb, s2a);
-    s3 = fma((AccT)x[(int64_t)(i + 3) * ps + a] - ca, (AccT)x[(int64_t)(i + 3) * ps + b] - cb, s3);
-    if constexpr (kComp) {
-      if (((i + 4) & (kRun - 1)) == 0) {   // every kRun pixels
-        two_sum_into(hi, lo, (float)((s0 + s1) + (s2a + s3)));
-        s0 = s1 = s2a = s3 = 0;
+  double* o = s2 + (int64_t)a * d + b;
+  for (int ch = c_first; ch < c_last; ++ch) {   // chunk sums added in order, as stats_fp_body
+    const int p0 = ch * kScatterChunk, p1 = min(W, p0 + kScatterChunk);
+    float hi = 0.f, lo = 0.f;
+    AccT s0 = 0, s1 = 0, s2a = 0, s3 = 0;
+    int i = p0;
+    for (; i + 4 <= p1; i += 4) {
+      s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
+      s1 = fma((AccT)x[(int64_t)(i + 1) * ps + a] - ca, (AccT)x[(int64_t)(i + 1) * ps + b] - cb,
+               s1);
+      s2a = fma((AccT)x[(int64_t)(i + 2) * ps + a] - ca, (AccT)x[(int64_t)(i + 2) * ps + b] - cb,
+                s2a);
+      s3 = fma((AccT)x[(int64_t)(i + 3) * ps + a] - ca, (AccT)x[(int64_t)(i + 3) * ps + b] - cb,
+               s3);
+      if constexpr (kComp) {
+        if (((i + 4 - p0) & (kRun - 1)) == 0) {   // every kRun pixels of the chunk
+          two_sum_into(hi, lo, (float)((s0 + s1) + (s2a + s3)));
+          s0 = s1 = s2a = s3 = 0;
+        }
       }
     }
-  }
-  for (; i < W; ++i) s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
-  if constexpr (kComp) {
-    two_sum_into(hi, lo, (float)((s0 + s1) + (s2a + s3)));
-    s2[(int64_t)a * d + b] = (double)hi + (double)lo;
-  } else {
-    s2[(int64_t)a * d + b] = (double)((s0 + s1) + (s2a + s3));
+    for (; i < p1; ++i)
+      s0 = fma((AccT)x[(int64_t)i * ps + a] - ca, (AccT)x[(int64_t)i * ps + b] - cb, s0);
+    double part;
+    if constexpr (kComp) {
+      two_sum_into(hi, lo, (float)((s0 + s1) + (s2a + s3)));
+      part = (double)hi + (double)lo;
+    } else {
+      part = (double)((s0 + s1) + (s2a + s3));
+    }
+    *o = ch == c_first ? part : __dadd_rn(*o, part);
   }
 }
 
@@ -332,7 +343,7 @@ __global__ void __launch_bounds__(256) stats_small_kernel(const InT* __restrict_
                                                           double* __restrict__ S2f) {
   const int t = blockIdx.x;
   stats_small_body<InT, AccT>(X + (int64_t)t * line_stride, ps, W, d, shift + (int64_t)t * d,
-                              S2f + (int64_t)t * d * d);
+                              S2f + (int64_t)t * d * d, 0, scatter_chunks(W));
 }
 
 __host__ __device__ inline int n_pairs(int d, int sb = SB) {
@@ -354,7 +365,8 @@ __global__ void __launch_bounds__(256, 3) b_stats_kernel(const BStream* __restri
   const BStream& s = S[it.s];
   const int64_t dd = (int64_t)s.d * s.d;
   if (s.d <= kSmallD) {
-    stats_small_body<float, AccT>(s.x, s.d, s.W, s.d, s.shift, s.S2f);
+    const int ch = it.tile;
+    stats_small_body<float, AccT>(s.x, s.d, s.W, s.d, s.shift, s.S2f + ch * dd, ch, ch + 1);
   } else if (sizeof(AccT) == 8 || s.d <= 32) {   // 32 x 32 blocks, as the single-stream path
     const int np = n_pairs(s.d, 32), pr = it.tile % np, ch = it.tile / np;
     stats_fp_body<float, AccT, 32>(s.x, s.d, s.W, s.d, s.shift, s.S2f + ch * dd, pr, ch, ch + 1);
@@ -371,11 +383,11 @@ __global__ void __launch_bounds__(256, 3) b_stats_kernel(const BStream* __restri
 // threads idle), 64 otherwise
 int fp_block(int d, bool fp64) { return fp64 || d <= 32 ? 32 : SB; }
 
-// work items of one stream's scatter: (block pair, pixel chunk); one for d <= 16
+// work items of one stream's scatter: (block pair, pixel chunk); d <= 16: (chunk)
 int batch_stats_tiles(int d, int W, bool fp64) {
-  return d <= kSmallD ? 1 : n_pairs(d, fp_block(d, fp64)) * scatter_chunks(W);
+  return (d <= kSmallD ? 1 : n_pairs(d, fp_block(d, fp64))) * scatter_chunks(W);
 }
-int batch_scatter_chunks(int d, int W) { return d <= kSmallD ? 1 : scatter_chunks(W); }
+int batch_scatter_chunks(int, int W) { return scatter_chunks(W); }
 
 void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t st) {
   b_mean_kernel<<<n, kMeanThreads, 0, st>>>(S, float_shift);
