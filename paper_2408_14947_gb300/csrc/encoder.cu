@@ -6,8 +6,9 @@
 // ranks pixels like full-band ERX, one line per step in stream order:
 //   1. forward on the tensor cores: codes of the line's p pixels (bf16
 //      operands, FP32 accumulation in TMEM), keeping relu(a) in bf16;
-//   2. code statistics: line mean/covariance, EMA update, Cholesky of K_e + eps I
-//      (the pipeline's own kernels; the statistics are constants for the gradient);
+//   2. code statistics: line mean/covariance (the FP32 forms' compensated
+//      scatter), EMA update and Cholesky of K_e + eps I in FP64 (the pipeline's
+//      own kernels; the statistics are constants for the gradient);
 //   3. loss and dL/dc per pixel: delta = |L^-1 r|, u = L^-T L^-1 r,
 //      dL/dc = (2/p) (log1p(delta) - log1p(target)) / ((1 + delta) delta) u;
 //   4. backward on the tensor cores, per 128-pixel tile: dh = (dc W2) * [h > 0],
@@ -674,8 +675,12 @@ erx_status train_line(erx_encoder* e, const float* line, int p, const double* ta
   if (s != ERX_OK) return s;
   forward_tc(e, line, p, e->codes, e->hbuf, st);
   const int k = e->k;
-  launch_mean(ERX_F32, e->codes, 0, k, p, k, 1, false, e->mu_hat, e->shiftc, st);
-  launch_stats_fp(ERX_F32, true, e->codes, 0, k, p, k, 1, e->shiftc, e->S2f, st);
+  // code statistics with the FP32 forms' scatter (products in 8-pixel FMA runs
+  // added into TwoSum-compensated float pairs, about a float rounding of the
+  // exact sums): a line's k x k scatter is one block pair, and in FP64 that one
+  // CTA would spend ~1M DFMA on a single SM; the mean, EMA and factor stay FP64
+  launch_mean(ERX_F32, e->codes, 0, k, p, k, 1, true, e->mu_hat, e->shiftc, st);
+  launch_stats_fp(ERX_F32, false, e->codes, 0, k, p, k, 1, e->shiftc, e->S2f, st);
   launch_ema_scan(false, nullptr, nullptr, e->mu_hat, e->shiftc, e->S2f, 1, k, p, o->momentum,
                   e->t_codes, ERX_UPDATE_THEN_SCORE, e->mu_e, e->K_e, e->mu_t, e->K_t, nullptr,
                   st);
