@@ -942,6 +942,37 @@ def measure_pipe_peaks(dev, n: int = 4096, reps: int = 5):
     return out
 
 
+def profile_training(n_lines):
+    """Encoder training (224 -> 128 -> 32) on C5 lines of 1024 px: one warm-up
+    line, then `n_lines` timed lines (one AdamW step each)."""
+    import torch
+
+    from paper_2408_14947_gb300 import Detector, Encoder, erx_train_opts_default
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    W, B = 1024, 224
+    cube = make_cube(n_lines + 1, seed=11, kind="c5", width=W, bands=B)
+    x = torch.from_numpy(cube).to(dev)
+    flat = cube.reshape(-1, B)
+    full = Detector(B, W, in_dtype="f32", form="fp64", warmup=0, stream=stream)
+    fd = full.push(x)[0]
+    full.sync()
+    full.close()
+    enc = Encoder(B, 128, 32, seed=0, stream=stream)
+    enc.set_norm(flat.mean(0), 1.0 / (flat.std(0) + 1e-3))
+    o = erx_train_opts_default()
+    enc.train(x[:1], fd[:1], o)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    enc.train(x[1:], fd[1:], o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "c5_train", "lines": n_lines,
+                      "ms_per_line": e0.elapsed_time(e1) / n_lines}))
+    enc.close()
+
+
 def run_profile_case(args):
     """One block of a named workload through one form, for profiler captures:
     a warm-up push, then one push of `--lines` lines (its kernels are the ones
@@ -954,6 +985,8 @@ def run_profile_case(args):
     kind, form = args.profile_case.split("_", 1)
     if kind == "c4":
         return profile_batched(form, args.lines)
+    if args.profile_case == "c5_train":
+        return profile_training(args.lines)
     avg = "ema"
     if form.endswith("_imc"):
         form, avg = form[: -len("_imc")], "imc"
@@ -1010,13 +1043,14 @@ def main():
     ap.add_argument("--profile-case", default=None,
                     choices=["c2_fp64", "c2_fp64e", "c2_fp32", "c2_tf32", "c2_bf16", "c2_fp64_imc",
                              "c3_fp64", "c3_fp32", "c3_tf32", "c3_bf16", "c3_tf32x3", "c5_fp32",
-                             "c5_fp64", "c4_fp64", "c4_fp32", "c4_tf32", "c4_bf16", "c4_tf32x3"],
+                             "c5_fp64", "c4_fp64", "c4_fp32", "c4_tf32", "c4_bf16", "c4_tf32x3",
+                             "c5_train"],
                     help="push one block of --lines lines of a workload (c2: 640 px x 108 "
                          "bands u16; c3: 1024 px x 224 bands f32, kappa 1e3; c5: c3 lines "
                          "through learned 32-dim codes) through one form (_imc: IMC "
                          "averaging), after one warm-up push; c4: the 256-stream batch, "
-                         "--lines steps after three warm-up steps; for profiler captures, "
-                         "no bench line")
+                         "--lines steps after three warm-up steps; c5_train: --lines encoder "
+                         "training steps; for profiler captures, no bench line")
     args = ap.parse_args()
     globals()["LINES"] = args.lines
     if args.peaks:
