@@ -17,6 +17,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/erx.h"
@@ -52,6 +53,12 @@ __global__ void gather_kernel(const float* const* __restrict__ src, const BStrea
 
 }  // namespace
 
+// a run of work items for one launch: items [off, off + n) of a list, dmax the
+// largest d among their streams
+struct Seg {
+  int off = 0, n = 0, dmax = 1;
+};
+
 struct erx_batch {
   int n = 0;
   int form = ERX_FORM_FP64;
@@ -62,20 +69,23 @@ struct erx_batch {
   std::vector<BStream> host;      // host mirror of the table (pointers, shapes, routes)
   BStream* table = nullptr;       // device table
   std::vector<void*> allocs;
-  // work lists
+  // Work lists.  The step runs as two chains side by side inside its graph:
+  // chain 0, the streams above 128 dimensions (their single-SM factors are the
+  // step's long pole), on the batch's stream; chain 1, all others, on a second
+  // stream.  Every list is ordered by chain, and each chain's part is a run of
+  // segments (one per launch) recorded below.
+  BItem* stream_items = nullptr;  // mean and normalise: one item per stream
+  Seg seg_stream[2];
   BItem* stats_items = nullptr;
-  int n_stats = 0;
+  Seg seg_stats[2];
   BItem* ema_items = nullptr;
-  int n_ema = 0;
+  Seg seg_ema[2];
   BItem* solve_items[kRoutes] = {};
-  int n_solve[kRoutes] = {};
-  int n_lay[3] = {}, dmax_lay[3] = {1, 1, 1};   // FP64 route: items per thread layout, in order
-  int dmax_route[kRoutes] = {1, 1, 1, 1, 1};
-  // factor and FP32 inverse: every stream, look-ahead schedule first, each group
-  // largest d first; the look-ahead group runs on the batch's stream and the
-  // column group beside it on a second stream inside the step's graph
+  Seg seg_solve[kRoutes][2][3];   // route, chain, FP64 layout (layout 0 for routes 1..4)
+  // factor and FP32 inverse: per chain, the look-ahead schedule group, then the
+  // column group, each largest d first
   BItem* chol_items = nullptr;
-  int n_chol_la = 0, dmax_la = 1, dmax_col = 1;
+  Seg seg_chol[2][2];             // chain, schedule (0 look-ahead, 1 column)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   unsigned long long* err = nullptr;
@@ -144,8 +154,48 @@ int route_format(int route) {
   return route == 2 ? 2 : route == 3 ? 1 : 3;
 }
 
+// chain of a stream in the step's graph: 0 above 128 dimensions, else 1
+int chain_of(const BStream& e) { return e.d > 128 ? 0 : 1; }
+
+// Sort `items` by (chain, sub(stream)) and record the runs in segs[chain][sub]:
+// offsets in that order, counts and each run's largest d.  `then` orders items
+// within a run.
+template <int NS, typename Sub, typename Then>
+void order_segments(const erx_batch* b, std::vector<BItem>& items, Seg (&segs)[2][NS], Sub sub,
+                    Then then) {
+  std::stable_sort(items.begin(), items.end(), [&](const BItem& x, const BItem& y) {
+    const BStream &u = b->host[x.s], &v = b->host[y.s];
+    if (chain_of(u) != chain_of(v)) return chain_of(u) < chain_of(v);
+    if (sub(u) != sub(v)) return sub(u) < sub(v);
+    return then(x, y);
+  });
+  for (int c = 0; c < 2; ++c)
+    for (int k = 0; k < NS; ++k) segs[c][k] = Seg{};
+  for (const BItem& it : items) {
+    const BStream& e = b->host[it.s];
+    Seg& g = segs[chain_of(e)][sub(e)];
+    g.n += 1;
+    g.dmax = std::max(g.dmax, e.d);
+  }
+  int off = 0;
+  for (int c = 0; c < 2; ++c)
+    for (int k = 0; k < NS; ++k) segs[c][k].off = off, off += segs[c][k].n;
+}
+
+// copy a work list to the device, allocating it on first use with `cap` items
+erx_status upload_items(erx_batch* b, BItem** dev, const std::vector<BItem>& items, size_t cap) {
+  if (!*dev) {
+    erx_status st = balloc(b, dev, std::max(cap, items.size()));
+    if (st != ERX_OK) return st;
+  }
+  if (!items.empty() && cudaMemcpy(*dev, items.data(), items.size() * sizeof(BItem),
+                                   cudaMemcpyHostToDevice) != cudaSuccess)
+    return ERX_ECUDA;
+  return ERX_OK;
+}
+
 // (Re)build the score-kernel work lists from the routes (and FP64 layouts) in
-// the host table; items of each route largest d first, route 0 grouped by layout.
+// the host table: per route, by chain, then FP64 layout, largest d first.
 erx_status build_solve_items(erx_batch* b) {
   for (int r = 0; r < kRoutes; ++r) {
     std::vector<BItem> items;
@@ -153,33 +203,14 @@ erx_status build_solve_items(erx_batch* b) {
       if (b->host[s].route == r)
         for (int k = 0; k < batch_solve_tiles(r, b->host[s].W, b->host[s].layout); ++k)
           items.push_back({s, k});
-    std::stable_sort(items.begin(), items.end(), [&](const BItem& x, const BItem& y) {
-      const BStream &u = b->host[x.s], &v = b->host[y.s];
-      if (r == 0 && u.layout != v.layout) return u.layout < v.layout;
-      return u.d > v.d;
-    });
-    b->n_solve[r] = (int)items.size();
-    b->dmax_route[r] = 1;
-    for (const BItem& it : items) b->dmax_route[r] = std::max(b->dmax_route[r], b->host[it.s].d);
-    if (r == 0) {
-      for (int l = 0; l < 3; ++l) b->n_lay[l] = 0, b->dmax_lay[l] = 1;
-      for (const BItem& it : items) {
-        const BStream& e = b->host[it.s];
-        b->n_lay[e.layout] += 1;
-        b->dmax_lay[e.layout] = std::max(b->dmax_lay[e.layout], e.d);
-      }
-    }
-    if (!b->solve_items[r]) {
-      // capacity: every stream's tiles for this route at the finest tiling
-      size_t cap = 0;
-      for (int s = 0; s < b->n; ++s) cap += (size_t)batch_solve_tiles(r, b->host[s].W, 2);
-      erx_status st = balloc(b, &b->solve_items[r], cap);
-      if (st != ERX_OK) return st;
-    }
-    if (!items.empty() && cudaMemcpy(b->solve_items[r], items.data(),
-                                     items.size() * sizeof(BItem),
-                                     cudaMemcpyHostToDevice) != cudaSuccess)
-      return ERX_ECUDA;
+    order_segments(
+        b, items, b->seg_solve[r], [&](const BStream& e) { return r == 0 ? e.layout : 0; },
+        [&](const BItem& x, const BItem& y) { return b->host[x.s].d > b->host[y.s].d; });
+    // capacity: every stream's tiles for this route at the finest tiling
+    size_t cap = 0;
+    for (int s = 0; s < b->n; ++s) cap += (size_t)batch_solve_tiles(r, b->host[s].W, 2);
+    erx_status st = upload_items(b, &b->solve_items[r], items, cap);
+    if (st != ERX_OK) return st;
   }
   return ERX_OK;
 }
@@ -188,26 +219,33 @@ erx_status build_solve_items(erx_batch* b) {
 erx_status build_chol_items(erx_batch* b) {
   std::vector<BItem> items;
   for (int i = 0; i < b->n; ++i) items.push_back({i, 0});
-  std::stable_sort(items.begin(), items.end(), [&](const BItem& x, const BItem& y) {
-    const BStream &u = b->host[x.s], &v = b->host[y.s];
-    if (u.fac != v.fac) return u.fac > v.fac;
-    return u.d > v.d;
+  order_segments(
+      b, items, b->seg_chol, [](const BStream& e) { return e.fac ? 0 : 1; },
+      [&](const BItem& x, const BItem& y) { return b->host[x.s].d > b->host[y.s].d; });
+  return upload_items(b, &b->chol_items, items, items.size());
+}
+
+// The per-stream, scatter and EMA work lists (fixed for the batch's life).
+erx_status build_step_items(erx_batch* b, std::vector<BItem> st_items,
+                            std::vector<BItem> ema_items) {
+  std::vector<BItem> str;
+  for (int i = 0; i < b->n; ++i) str.push_back({i, 0});
+  Seg sg[2][1], ss[2][1], se[2][1];
+  auto none = [](const BStream&) { return 0; };
+  order_segments(b, str, sg, none, [&](const BItem& x, const BItem& y) {
+    return b->host[x.s].d > b->host[y.s].d;
   });
-  b->n_chol_la = 0;
-  b->dmax_la = b->dmax_col = 1;
-  for (const BItem& it : items) {
-    const BStream& e = b->host[it.s];
-    if (e.fac) ++b->n_chol_la, b->dmax_la = std::max(b->dmax_la, e.d);
-    else b->dmax_col = std::max(b->dmax_col, e.d);
-  }
-  if (!b->chol_items) {
-    erx_status st = balloc(b, &b->chol_items, items.size());
-    if (st != ERX_OK) return st;
-  }
-  if (cudaMemcpy(b->chol_items, items.data(), items.size() * sizeof(BItem),
-                 cudaMemcpyHostToDevice) != cudaSuccess)
-    return ERX_ECUDA;
-  return ERX_OK;
+  order_segments(b, st_items, ss, none, [&](const BItem& x, const BItem& y) {
+    const BStream &u = b->host[x.s], &v = b->host[y.s];
+    return (int64_t)u.W * u.d > (int64_t)v.W * v.d;
+  });
+  order_segments(b, ema_items, se, none, [](const BItem&, const BItem&) { return false; });
+  for (int c = 0; c < 2; ++c)
+    b->seg_stream[c] = sg[c][0], b->seg_stats[c] = ss[c][0], b->seg_ema[c] = se[c][0];
+  erx_status s = upload_items(b, &b->stream_items, str, str.size());
+  if (s == ERX_OK) s = upload_items(b, &b->stats_items, st_items, st_items.size());
+  if (s == ERX_OK) s = upload_items(b, &b->ema_items, ema_items, ema_items.size());
+  return s;
 }
 
 // The device table's line counts advance on the device; pull them into the
@@ -229,47 +267,46 @@ erx_status upload_table(erx_batch* b) {
   return ERX_OK;
 }
 
-void enqueue_step(erx_batch* b, cudaStream_t st) {
+// One chain's share of a step: every phase for the chain's streams, in order.
+void enqueue_chain(erx_batch* b, int c, cudaStream_t st) {
   const bool fp64 = b->form == ERX_FORM_FP64;
+  const Seg& sg = b->seg_stream[c];
+  launch_batch_mean(b->table, b->stream_items + sg.off, sg.n, !fp64, st);
+  launch_batch_stats(b->table, b->stats_items + b->seg_stats[c].off, b->seg_stats[c].n, fp64, st);
+  launch_batch_ema(b->table, b->ema_items + b->seg_ema[c].off, b->seg_ema[c].n, st);
+  for (int f = 0; f < 2; ++f) {   // look-ahead group, then column group
+    const Seg& g = b->seg_chol[c][f];
+    launch_batch_chol(b->table, b->chol_items + g.off, g.n, g.dmax, f == 0, !fp64, b->err, st);
+    if (!fp64) launch_batch_trinv32(b->table, b->chol_items + g.off, g.n, g.dmax, st);
+  }
+  for (int r = 0; r < kRoutes; ++r) {
+    for (int l = 0; l < (r == 0 ? 3 : 1); ++l) {
+      const Seg& g = b->seg_solve[r][c][l];
+      if (!g.n) continue;
+      const BItem* it = b->solve_items[r] + g.off;
+      if (r == 0) launch_batch_solve_fp64(l, b->table, it, g.n, g.dmax, st);
+      else if (r == 1) launch_batch_solve_simt(b->table, it, g.n, g.dmax, st);
+      else launch_batch_solve_tc(route_format(r), b->table, it, g.n, g.dmax, b->err, st);
+    }
+  }
+  launch_batch_normalise(b->table, b->stream_items + sg.off, sg.n, fp64, st);
+}
+
+void enqueue_step(erx_batch* b, cudaStream_t st) {
   if (b->enc && b->learned_pix > 0)
     encoder_forward_on(b->enc, b->xin, b->learned_pix, b->codes, st);
-  launch_batch_mean(b->table, b->n, !fp64, st);
-  launch_batch_stats(b->table, b->stats_items, b->n_stats, fp64, st);
-  launch_batch_ema(b->table, b->ema_items, b->n_ema, st);
-  // factor (and the FP32 inverse): the look-ahead group, one CTA per SM each,
-  // beside the column group on the second stream
-  const int nb = b->n_chol_la, ns = b->n - b->n_chol_la;
-  const bool fork = nb > 0 && ns > 0;
-  cudaStream_t ss = fork ? b->side : st;
+  // chain 0 (streams above 128 dimensions) on st, chain 1 beside it
+  const bool fork = b->seg_stream[0].n > 0 && b->seg_stream[1].n > 0;
   if (fork) {
     cudaEventRecord(b->ev_fork, st);
     cudaStreamWaitEvent(b->side, b->ev_fork, 0);
   }
-  launch_batch_chol(b->table, b->chol_items, nb, b->dmax_la, true, !fp64, b->err, st);
-  if (!fp64) launch_batch_trinv32(b->table, b->chol_items, nb, b->dmax_la, st);
-  launch_batch_chol(b->table, b->chol_items + nb, ns, b->dmax_col, false, !fp64, b->err, ss);
-  if (!fp64) launch_batch_trinv32(b->table, b->chol_items + nb, ns, b->dmax_col, ss);
+  enqueue_chain(b, 0, st);
+  enqueue_chain(b, 1, fork ? b->side : st);
   if (fork) {
     cudaEventRecord(b->ev_join, b->side);
     cudaStreamWaitEvent(st, b->ev_join, 0);
   }
-  for (int r = 0; r < kRoutes; ++r) {
-    if (!b->n_solve[r]) continue;
-    if (r == 0) {
-      int off = 0;
-      for (int l = 0; l < 3; ++l) {
-        launch_batch_solve_fp64(l, b->table, b->solve_items[0] + off, b->n_lay[l],
-                                b->dmax_lay[l], st);
-        off += b->n_lay[l];
-      }
-    } else if (r == 1) {
-      launch_batch_solve_simt(b->table, b->solve_items[r], b->n_solve[r], b->dmax_route[r], st);
-    } else {
-      launch_batch_solve_tc(route_format(r), b->table, b->solve_items[r], b->n_solve[r],
-                            b->dmax_route[r], b->err, st);
-    }
-  }
-  launch_batch_normalise(b->table, b->n, fp64, st);
 }
 
 erx_status capture(erx_batch* b) {
@@ -433,24 +470,12 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
       odd += (size_t)d * d * e.nch;
       ow += W;
     }
-    std::stable_sort(st_items.begin(), st_items.end(), [&](const BItem& x, const BItem& y) {
-      return (int64_t)b->host[x.s].W * b->host[x.s].d > (int64_t)b->host[y.s].W * b->host[y.s].d;
-    });
+    if (s == ERX_OK) s = build_step_items(b, std::move(st_items), std::move(ema_items));
     if (s == ERX_OK) s = build_chol_items(b);
     if (s == ERX_OK &&
         (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
          cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
          cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess))
-      s = ERX_ECUDA;
-    b->n_stats = (int)st_items.size();
-    b->n_ema = (int)ema_items.size();
-    if (s == ERX_OK) s = balloc(b, &b->stats_items, st_items.size());
-    if (s == ERX_OK) s = balloc(b, &b->ema_items, ema_items.size());
-    if (s == ERX_OK &&
-        (cudaMemcpy(b->stats_items, st_items.data(), st_items.size() * sizeof(BItem),
-                    cudaMemcpyHostToDevice) != cudaSuccess ||
-         cudaMemcpy(b->ema_items, ema_items.data(), ema_items.size() * sizeof(BItem),
-                    cudaMemcpyHostToDevice) != cudaSuccess))
       s = ERX_ECUDA;
   }
   if (s == ERX_OK) s = build_solve_items(b);

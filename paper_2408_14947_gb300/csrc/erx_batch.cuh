@@ -45,7 +45,8 @@ struct BItem {
 };
 
 // Batched phase launchers: each CTA takes items[blockIdx.x].
-void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t st);
+void launch_batch_mean(const BStream* S, const BItem* items, int n, bool float_shift,
+                       cudaStream_t st);
 void launch_batch_stats(const BStream* S, const BItem* items, int n_items, bool fp64,
                         cudaStream_t st);
 void launch_batch_ema(const BStream* S, const BItem* items, int n_items, cudaStream_t st);
@@ -57,7 +58,8 @@ void launch_batch_chol(const BStream* S, const BItem* items, int n, int dmax, bo
                        bool want32, unsigned long long* err, cudaStream_t st);
 void launch_batch_solve(int route, const BStream* S, const BItem* items, int n_items, int dmax,
                         unsigned long long* err, cudaStream_t st);
-void launch_batch_normalise(const BStream* S, int n, bool fp64, cudaStream_t st);
+void launch_batch_normalise(const BStream* S, const BItem* items, int n, bool fp64,
+                            cudaStream_t st);
 cudaError_t configure_batch_kernels();
 
 }  // namespace erx

@@ -415,8 +415,9 @@ __global__ void __launch_bounds__(128) b_ema_kernel(BStream* __restrict__ S,
 
 // Normalisation per stream; thread 0 then advances the stream's line count.
 template <typename ST>
-__global__ void __launch_bounds__(256) b_normalise_kernel(BStream* __restrict__ S) {
-  BStream& s = S[blockIdx.x];
+__global__ void __launch_bounds__(256) b_normalise_kernel(BStream* __restrict__ S,
+                                                          const BItem* __restrict__ items) {
+  BStream& s = S[items[blockIdx.x].s];
   const bool st64 = (s.route == 0);
   if ((sizeof(ST) == 8) == st64)
     normalise_body<ST>((const ST*)s.delta, s.W, s.threshold, s.t, s.warmup, (ST*)s.dn, s.mask,
@@ -513,12 +514,14 @@ size_t ema_scratch_doubles(int d, int T) {
 }
 
 void launch_batch_ema(const BStream* S, const BItem* items, int n_items, cudaStream_t st) {
-  b_ema_kernel<<<n_items, 128, 0, st>>>(const_cast<BStream*>(S), items);
+  if (n_items > 0) b_ema_kernel<<<n_items, 128, 0, st>>>(const_cast<BStream*>(S), items);
 }
 
-void launch_batch_normalise(const BStream* S, int n, bool fp64, cudaStream_t st) {
-  if (fp64) b_normalise_kernel<double><<<n, 256, 0, st>>>(const_cast<BStream*>(S));
-  else b_normalise_kernel<float><<<n, 256, 0, st>>>(const_cast<BStream*>(S));
+void launch_batch_normalise(const BStream* S, const BItem* items, int n, bool fp64,
+                            cudaStream_t st) {
+  if (n <= 0) return;
+  if (fp64) b_normalise_kernel<double><<<n, 256, 0, st>>>(const_cast<BStream*>(S), items);
+  else b_normalise_kernel<float><<<n, 256, 0, st>>>(const_cast<BStream*>(S), items);
 }
 
 void launch_normalise(bool fp64, const void* delta, int W, int T, double threshold, int64_t t0,

@@ -353,8 +353,9 @@ __host__ __device__ inline int n_pairs(int d, int sb = SB) {
 
 // Batched form: one CTA per stream (mean) / per (stream, block pair) item.
 __global__ void __launch_bounds__(kMeanThreads) b_mean_kernel(const BStream* __restrict__ S,
-                                                     bool float_shift) {
-  const BStream& s = S[blockIdx.x];
+                                                              const BItem* __restrict__ items,
+                                                              bool float_shift) {
+  const BStream& s = S[items[blockIdx.x].s];
   mean_body<float>(s.x, s.d, s.W, s.d, float_shift, s.mu_hat, s.shift);
 }
 
@@ -389,12 +390,14 @@ int batch_stats_tiles(int d, int W, bool fp64) {
 }
 int batch_scatter_chunks(int, int W) { return scatter_chunks(W); }
 
-void launch_batch_mean(const BStream* S, int n, bool float_shift, cudaStream_t st) {
-  b_mean_kernel<<<n, kMeanThreads, 0, st>>>(S, float_shift);
+void launch_batch_mean(const BStream* S, const BItem* items, int n, bool float_shift,
+                       cudaStream_t st) {
+  if (n > 0) b_mean_kernel<<<n, kMeanThreads, 0, st>>>(S, items, float_shift);
 }
 
 void launch_batch_stats(const BStream* S, const BItem* items, int n_items, bool fp64,
                         cudaStream_t st) {
+  if (n_items <= 0) return;
   if (fp64) b_stats_kernel<double><<<n_items, 256, 0, st>>>(S, items);
   else b_stats_kernel<float><<<n_items, 256, 0, st>>>(S, items);
 }
