@@ -47,6 +47,76 @@ __device__ __forceinline__ double ema_khat(double S, double ea, double eb, doubl
 __device__ __forceinline__ double ema_mix(double s, double x, double alpha, double beta) {
   return __dadd_rn(__dmul_rn(beta, s), __dmul_rn(alpha, x));
 }
+
+// S4's diagonal blocks D_J = L_JJ^{-1}, shared by every factor kernel so that
+// all of them give the same bits.  The nb x nb block at (j0, j0) of the packed
+// lower matrix A (row i at i(i+1)/2) is inverted in place, lane i of each warp
+// taking row i; ri[k] = 1 / l_kk.  From X L = I: X_kk = ri_k and, for i > j,
+//   X_ij = -ri_j * sum_{k = j+1 .. i} X_ik l_kj,
+// the sum taken from k = i down to k = j + 1.  Columns are finished right to
+// left.  When column k is final, every row i > k adds its term X_ik l_kj to
+// its partial sums S_ij (j < k), kept in place of l_ij (row i of L is read only
+// while column i is finished, which is earlier), and row k then starts its own
+// sums with the first term ri_k l_kj, one lane per j.  From one column to the
+// next the chain is a multiplication and one multiply-add (not a whole sum as
+// in a column-by-column evaluation), with the same d^3/6 multiply-adds.
+//
+// NW warps share a block (warp w of the group: w = 0 .. NW-1): warp w adds the
+// terms of the columns j = k-1-w, k-1-w-NW, ... (each warp's multiply-adds run
+// on its own SM sub-partition's FP64 unit); with NW > 1 warp 0 finishes X_ik
+// into shared memory for all (one multiplication instead of one per warp) and
+// warp 1 starts row k's sums.  Every S_ij still receives one multiply-add per
+// step, in the same order, whatever NW.  NW > 1 synchronises the group with
+// named barrier `bar` (NW * 32 threads).
+template <int NW>
+__device__ __forceinline__ void invert_diag_block(double* __restrict__ A, int j0, int nb,
+                                                  const double* __restrict__ ri, int w, int lane,
+                                                  int bar = 1) {
+  auto row = [&](int i) { return A + (j0 + i) * (j0 + i + 1) / 2 + j0; };
+  auto sync = [&]() {
+    if constexpr (NW == 1)
+      __syncwarp();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NW * 32) : "memory");
+  };
+  double* Si = row(lane);            // dereferenced for lane < nb only
+  for (int k = nb - 1; k >= 0; --k) {
+    const double rk = ri[k];
+    const double* Lk = row(k);
+    double x = 0.0;
+    if constexpr (NW == 1) {
+      if (lane > k && lane < nb) {
+        x = -rk * Si[k];             // X_ik: S_ik has all its terms
+        Si[k] = x;
+      }
+    } else {
+      if (w == 0 && lane > k && lane < nb) Si[k] = -rk * Si[k];
+      sync();
+      if (lane > k && lane < nb) x = Si[k];
+    }
+    if (lane > k && lane < nb) {
+      // this warp's columns, four at a time (loads, multiply-adds, stores) so
+      // that the multiply-adds do not wait on each other's stores
+      int j = k - 1 - w;
+      for (; j >= 3 * NW; j -= 4 * NW) {
+        double l[4], s[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) l[u] = Lk[j - u * NW], s[u] = Si[j - u * NW];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = fma(x, l[u], s[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) Si[j - u * NW] = s[u];
+      }
+      for (; j >= 0; j -= NW) Si[j] = fma(x, Lk[j], Si[j]);
+    }
+    sync();
+    // row k starts its sums (row k of L is no longer read)
+    if (w == (NW > 1 ? 1 : 0) && lane < k) row(k)[lane] = fma(rk, row(k)[lane], 0.0);
+    sync();
+  }
+  if (w == 0 && lane < nb) Si[lane] = ri[lane];
+  sync();
+}
 #endif
 
 // Opt the kernels that need it into large dynamic shared memory on the
@@ -113,6 +183,15 @@ void launch_imc_scan(bool int_stats, const uint64_t* S1i, const uint64_t* S2i,
 void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Linv, float* Linv32,
                      unsigned long long* err, int64_t t0, cudaStream_t st, bool invert = true,
                      bool leave_room = false);
+// The same factor for a few lines, each over a cluster of chol_cluster_ctas()
+// CTAs on as many SMs (k_factor_cluster.cu); bit-equal to launch_chol_inv's
+// one-CTA kernels.  configure_cluster_factor returns the clusters that fit on
+// the device at once (0: the cluster form is not used).
+int chol_cluster_ctas();
+int configure_cluster_factor(int smem_per_sm);
+void launch_chol_cluster(const double* K_t, int d, int T, double ridge, double* Lf, float* Lf32,
+                         unsigned long long* err, int64_t t0, bool invert, int smem_per_sm,
+                         cudaStream_t st);
 
 // In place: the float blocked factor of T lines becomes the full L^{-1} (FP32).
 void launch_trinv32(float* Lf32, int d, int T, cudaStream_t st);

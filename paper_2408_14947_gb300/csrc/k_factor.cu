@@ -34,10 +34,10 @@
 // In both, every element receives the same multiply-adds in the same order as
 // in the column-by-column algorithm (a_ik = fma(-l_ij, l_kj, a_ik), j
 // ascending), so all variants give the same bits.
-// Each diagonal block is then inverted by one warp, one column per lane (the
-// FP64 forms; the FP32 routes invert them in FP32 in trinv32).  A pivot that is
-// not positive and finite records the line in the error slot and poisons its
-// scores (NaN).
+// Each diagonal block is then inverted by one warp, one row per lane
+// (invert_diag_block, erx_internal.cuh; the FP64 forms: the FP32 routes invert
+// them in FP32 in trinv32).  A pivot that is not positive and finite records
+// the line in the error slot and poisons its scores (NaN).
 #include <cmath>
 
 #include "erx_batch.cuh"
@@ -49,6 +49,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kNB = kFactorBlock;
 constexpr int kPB = 8;             // panel width
+// smallest d whose lone lines take the cluster factor (below it a line's
+// factor is a few microseconds on one SM)
+constexpr int kClusterMinD = 48;
 
 __device__ __forceinline__ int pidx(int i, int k) { return i * (i + 1) / 2 + k; }
 
@@ -285,28 +288,10 @@ __device__ __forceinline__ void chol_body(const double* __restrict__ src, int d,
   }
 
   __syncthreads();
-  // invert each 32 x 32 diagonal block in place, warp w taking blocks w, w + 8, ...:
-  // columns right to left; with T = the already inverted trailing part of the
-  // block, column j becomes -(1/l_jj) T l_col (lane i computes row i), so no
-  // per-lane arrays are needed and the kernel keeps few registers.
+  // invert each 32 x 32 diagonal block in place, warp w taking blocks w, w + 8, ...
   const int nblk = inv ? (d + kNB - 1) / kNB : 0;
-  for (int bk = warp; bk < nblk; bk += NT / 32) {
-    const int j0 = bk * kNB;
-    const int nb = min(kNB, d - j0);
-    for (int j = nb - 1; j >= 0; --j) {
-      const double djj = rdiag[j0 + j];               // 1 / l_jj
-      const int i = lane;
-      double s = 0.0;
-      if (i > j && i < nb) {
-        const double* Ti = A + pidx(j0 + i, j0);
-        for (int k = j + 1; k <= i; ++k) s = fma(Ti[k], A[pidx(j0 + k, j0 + j)], s);
-      }
-      __syncwarp();
-      if (i > j && i < nb) A[pidx(j0 + i, j0 + j)] = -djj * s;
-      if (i == j) A[pidx(j0 + j, j0 + j)] = djj;
-      __syncwarp();
-    }
-  }
+  for (int bk = warp; bk < nblk; bk += NT / 32)
+    invert_diag_block<1>(A, bk * kNB, min(kNB, d - bk * kNB), rdiag + bk * kNB, 0, lane);
   __syncthreads();
   for (int q = threadIdx.x; q < P; q += NT) dst[q] = A[q];
   if (d32) {
@@ -468,6 +453,12 @@ void launch_batch_trinv32(const BStream* S, const BItem* items, int n, int dmax,
     b_trinv32_kernel<<<n, kThreads, (size_t)packed_size(dmax) * sizeof(float), st>>>(S, items);
 }
 
+// clusters of the cluster factor that fit on the device at once (0: not used)
+int& cluster_slots() {
+  static int n = 0;
+  return n;
+}
+
 cudaError_t configure_factor_kernels() {
   const int m = (int)chol_smem(kMaxDim);
   cudaError_t e =
@@ -484,6 +475,7 @@ cudaError_t configure_factor_kernels() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(b_chol_kernel<512, true>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, m);
+  if (e == cudaSuccess) cluster_slots() = configure_cluster_factor(device_shape().smem_per_sm);
   const int m32 = (int)(packed_size(kMaxDim) * sizeof(float));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(trinv32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, m32);
@@ -514,7 +506,11 @@ void launch_chol_inv(const double* K_t, int d, int T, double ridge, double* Lf, 
   // d <= 128 (a line pushed alone): the column schedule with 1024 threads, whose
   // pivot chain is shorter than the look-ahead's one-warp block chain there
   // (measured: 27 us more per line with the look-ahead at d = 108).
-  if (d > 128)
+  // A line or a few pushed alone at d >= kClusterMinD: each over a cluster of
+  // SMs (k_factor_cluster.cu), as long as all clusters are resident at once.
+  if (d >= kClusterMinD && T <= cluster_slots() && T * chol_cluster_ctas() <= n_sm)
+    launch_chol_cluster(K_t, d, T, ridge, Lf, Lf32, err, t0, invert, smem_sm, st);
+  else if (d > 128)
     chol_kernel<2, 1, 512, true><<<T, 512, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);
   else if (T < n_sm)
     chol_kernel<2, 1, 1024><<<T, 1024, sm, st>>>(K_t, d, ridge, Lf, Lf32, err, t0, invert);

@@ -179,6 +179,122 @@ __global__ void __launch_bounds__(H * NPX) solve_fp64_kernel(
   }
 }
 
+// Lines scored alone (fewer 64-pixel tiles than SMs): NPX pixels per CTA, H
+// threads per pixel, over a persistent grid.  The CTA stages the line's
+// blocked factor in shared memory once (coalesced; the other layouts read it
+// from L2 row by row, a dependent load per multiply-add), and the solve is
+// reorganised right-looking: once m_J of block J is final, every row of the
+// later blocks takes block J's 32 terms, four rows per thread at a time, so a
+// thread runs several independent chains instead of one long one.  Every y_j
+// still receives its multiply-adds in ascending k, m_J = D_J y_J its terms in
+// ascending order, and the squares are summed in row order: the bits of the
+// other layouts.
+template <typename InT, int H, int NPX>
+__global__ void __launch_bounds__(H * NPX, 1) solve_fp64_line_kernel(
+    const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
+    const double* __restrict__ mu_t, const double* __restrict__ Lf, double* __restrict__ delta,
+    int T) {
+  constexpr int NT = H * NPX;
+  extern __shared__ __align__(16) double sm[];
+  const int P = d * (d + 1) / 2;
+  const int dp = d | 1;
+  double* Ls = sm;                          // the packed blocked factor
+  double* r = sm + ((P + 1) & ~1);          // [NPX][dp] residuals, overwritten by m
+  const int tid = threadIdx.x;
+  const int p = tid % NPX, h = tid / NPX;
+  double* rr = r + p * dp;
+  const int ntiles = (W + NPX - 1) / NPX;
+  const int64_t total = (int64_t)T * ntiles;
+  int staged = -1;
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const int t = (int)(w / ntiles), tile = (int)(w % ntiles);
+    __syncthreads();                        // the previous tile is done with shared memory
+    // staging: eight loads in flight per thread before their stores
+    if (t != staged) {
+      const double* L = Lf + (int64_t)t * P;
+      for (int q0 = tid; q0 < P; q0 += 8 * NT) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (q0 + u * NT < P) v[u] = __ldg(L + q0 + u * NT);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (q0 + u * NT < P) Ls[q0 + u * NT] = v[u];
+      }
+      staged = t;
+    }
+    const InT* x = X + (int64_t)t * line_stride;
+    const double* mu = mu_t + (int64_t)t * d;
+    const int i0 = tile * NPX;
+    for (int e0 = tid; e0 < NPX * d; e0 += 8 * NT) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * NT, pp = e / d, k = e - pp * d, i = i0 + pp;
+        v[u] = (e < NPX * d && i < W) ? to_d(__ldg(x + (int64_t)i * ps + k)) - __ldg(mu + k) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * NT, pp = e / d, k = e - pp * d;
+        if (e < NPX * d) r[pp * dp + k] = v[u];
+      }
+    }
+    __syncthreads();
+    static_assert(H > kNB / 2, "rows jj and 31 - jj of a block pair up on threads h < 16");
+    double d2 = 0.0;                       // the squares, in row order (thread h = H - 1)
+    for (int j0 = 0; j0 < d; j0 += kNB) {
+      const int nb = min(kNB, d - j0);
+      // m_J = D_J y_J: thread h < 16 takes rows h and 31 - h, 33 multiply-adds in
+      // all, one chain after the other with one multiply-add per step
+      double s1 = 0.0, s2 = 0.0;
+      if (h < kNB / 2) {
+        const int h2 = kNB - 1 - h;
+        const double* D1 = Ls + (j0 + h) * (j0 + h + 1) / 2 + j0;
+        const double* D2 = Ls + (j0 + h2) * (j0 + h2 + 1) / 2 + j0;
+        const bool v1 = h < nb, v2 = h2 < nb;
+        for (int st = 0; st <= kNB; ++st) {
+          const bool first = st <= h;
+          const int kk = first ? st : st - h - 1;
+          const double* D = first ? D1 : D2;
+          double acc = first ? s1 : s2;
+          if (first ? v1 : v2) acc = fma(D[kk], rr[j0 + kk], acc);
+          if (first) s1 = acc; else s2 = acc;
+        }
+      } else if (h == H - 1 && j0 > 0) {
+        // meanwhile the previous block's squares (its m are final)
+        for (int jj = 0; jj < kNB; ++jj) d2 = fma(rr[j0 - kNB + jj], rr[j0 - kNB + jj], d2);
+      }
+      __syncthreads();
+      if (h < kNB / 2) {
+        if (h < nb) rr[j0 + h] = s1;
+        if (kNB - 1 - h < nb) rr[j0 + kNB - 1 - h] = s2;
+      }
+      __syncthreads();
+      if (j0 + kNB >= d && h == H - 1)   // the last block's squares
+        for (int jj = 0; jj < nb; ++jj) d2 = fma(rr[j0 + jj], rr[j0 + jj], d2);
+      // rows of the later blocks take this block's terms, k ascending: rows dealt
+      // out one per thread per pass (every thread busy while rows remain), two
+      // passes at a time so that each thread runs two independent chains
+      const double* mJ = rr + j0;
+      for (int j = j0 + nb + h; j < d; j += 2 * H) {
+        const int j2 = j + H < d ? j + H : j;
+        const double* L1 = Ls + j * (j + 1) / 2 + j0;
+        const double* L2 = Ls + j2 * (j2 + 1) / 2 + j0;
+        double a1 = rr[j], a2 = rr[j2];
+        for (int kk = 0; kk < nb; ++kk) {
+          const double mk = mJ[kk];
+          a1 = fma(-L1[kk], mk, a1);
+          a2 = fma(-L2[kk], mk, a2);
+        }
+        rr[j] = a1;
+        if (j2 != j) rr[j2] = a2;
+      }
+      __syncthreads();
+    }
+    if (h == H - 1 && i0 + p < W) delta[(int64_t)t * W + i0 + p] = sqrt(d2);
+  }
+}
+
 // Batched form: one CTA per (stream, pixel tile) item, H threads per pixel
 // over NPX-pixel tiles (the layouts of the single-stream path, same bits):
 // layout 0 = (1, 64), 1 = (2, 64), 2 = (16, 8); chosen per band count by the
@@ -332,6 +448,13 @@ size_t smem_fp32(int d) {
 
 }  // namespace
 
+// single lines: 24 threads per pixel over 5-pixel tiles (4 warps; 128 CTAs, one
+// per SM, for a 640-pixel line)
+constexpr int kLineH = 24, kLinePix = 5;
+size_t line_smem(int d) {
+  return (size_t)(((packed_size(d) + 1) & ~1) + kLinePix * (d | 1)) * sizeof(double);
+}
+
 cudaError_t configure_solve_kernels() {
   cudaError_t e = cudaSuccess;
   const int m64 = (int)smem_fp64(kMaxDim), m32 = (int)smem_fp32(kMaxDim);
@@ -340,7 +463,8 @@ cudaError_t configure_solve_kernels() {
 #define ERX_CFG3(IT)                                 \
   ERX_CFG((solve_fp64_kernel<IT, 1, kPixF64>), m64); \
   ERX_CFG((solve_fp64_kernel<IT, 2, kPixF64>), m64); \
-  ERX_CFG((solve_fp64_kernel<IT, 16, 8>), m64);
+  ERX_CFG((solve_fp64_kernel<IT, 16, 8>), m64);     \
+  ERX_CFG((solve_fp64_line_kernel<IT, kLineH, kLinePix>), (int)line_smem(kMaxDim));
   ERX_CFG3(uint16_t)
   ERX_CFG3(float)
   ERX_CFG3(double)
@@ -411,12 +535,27 @@ void launch_fp64_t(const InT* x, int64_t line_stride, int ps, int W, int d, int 
 }
 
 template <typename InT>
+void launch_fp64_line(const InT* x, int64_t line_stride, int ps, int W, int d, int T,
+                      const double* mu_t, const double* Linv, double* delta, int n_sm,
+                      cudaStream_t st) {
+  const size_t sm = line_smem(d);
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, solve_fp64_line_kernel<InT, kLineH, kLinePix>, kLineH * kLinePix, sm);
+  per_sm = std::max(1, per_sm);
+  const int64_t total = (int64_t)T * ((W + kLinePix - 1) / kLinePix);
+  const int grid = (int)std::min<int64_t>(total, (int64_t)n_sm * per_sm);
+  solve_fp64_line_kernel<InT, kLineH, kLinePix><<<grid, kLineH * kLinePix, sm, st>>>(
+      x, line_stride, ps, W, d, mu_t, Linv, delta, T);
+}
+
+template <typename InT>
 void launch_fp64_in(const InT* x, int64_t line_stride, int ps, int W, int d, int T,
                     const double* mu_t, const double* Linv, double* delta, cudaStream_t st) {
   const int n_sm = device_shape().n_sm;
   const int64_t tiles64 = (int64_t)T * ((W + kPixF64 - 1) / kPixF64);
   if (tiles64 < n_sm)
-    launch_fp64_t<InT, 16, 8>(x, line_stride, ps, W, d, T, mu_t, Linv, delta, n_sm, st);
+    launch_fp64_line<InT>(x, line_stride, ps, W, d, T, mu_t, Linv, delta, n_sm, st);
   else if (d >= kPairMinD)
     launch_fp64_t<InT, 2, kPixF64>(x, line_stride, ps, W, d, T, mu_t, Linv, delta, n_sm, st);
   else

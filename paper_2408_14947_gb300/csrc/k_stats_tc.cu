@@ -17,6 +17,8 @@
 // rounded to 16, K = 16 pixels) per chunk into three accumulators
 // (HH | HL+LH | LL, 512 TMEM columns) and commits them to the buffer's
 // mbarrier.  The drain converts the three FP32 accumulators to int64 sums.
+#include <algorithm>
+
 #include "erx_internal.cuh"
 #include "tc_util.cuh"
 
@@ -195,6 +197,10 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_kernel(
 // mbarrier with a transaction count) that thread 0 issues kRawStages chunks
 // ahead, so the global-memory latency overlaps the conversion and the MMAs.
 // Needs 16-byte aligned lines and p * d * 2 a multiple of 16.
+// split > 1 (a line or a few pushed alone): CTA b takes only the chunks
+// b % split, b % split + split, ... of line b / split and adds its sums into
+// S1 and S2 (zeroed by the launcher) with 64-bit integer atomics; integer
+// sums do not depend on their order, so the result is the same bits.
 constexpr int kRawStages = 4;
 constexpr int kRawBytes = 16384;                  // >= 64 px * 127 bands * 2 B
 constexpr int kBulkSmem = 4 * kTileBytes + kRawStages * kRawBytes;
@@ -202,7 +208,7 @@ constexpr int kBulkSmem = 4 * kTileBytes + kRawStages * kRawBytes;
 __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
     const uint16_t* __restrict__ X, int64_t line_stride, int W, int d, uint32_t maxv, int T,
     uint64_t* __restrict__ S1, uint64_t* __restrict__ S2, unsigned long long* __restrict__ err,
-    int64_t t0) {
+    int64_t t0, int split) {
   extern __shared__ __align__(1024) unsigned char sm[];   // [2][H|L] tiles, then raw ring
   unsigned char* raw = sm + 4 * kTileBytes;
   __shared__ __align__(8) uint64_t mbar[2];
@@ -226,14 +232,22 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
   const uint32_t tmem = tslot;
   const uint32_t id = tc::idesc(1, kRows, np);
   const int nchunk = (W + kKC - 1) / kKC;
-  const int nlines = blockIdx.x < T ? (T - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int Q = nlines * nchunk;
+  // this CTA's lines and chunks: whole lines blockIdx.x, blockIdx.x + gridDim.x,
+  // ... (split 1), or the chunks c0, c0 + split, ... of line blockIdx.x / split
+  const int c0 = split > 1 ? (int)blockIdx.x % split : 0, cs = split > 1 ? split : 1;
+  const int nch = c0 < nchunk ? (nchunk - c0 + cs - 1) / cs : 0;
+  const int nlines = split > 1 ? ((int)blockIdx.x / split < T ? 1 : 0)
+                   : (blockIdx.x < T ? (T - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
+  const int Q = nlines * nch;
   const int items = (d + 1) * (kKC / 8);
-  // chunk q of this CTA: line blockIdx.x + (q / nchunk) * gridDim.x, chunk q % nchunk
+  auto line_of = [&](int q) {
+    return split > 1 ? (int)blockIdx.x / split : (int)blockIdx.x + (q / nch) * (int)gridDim.x;
+  };
+  // chunk q of this CTA: the (q % nch)-th of its chunks of line line_of(q)
   auto issue = [&](int q) {
     if (q >= Q) return;
     const int slot = q % kRawStages;
-    const int t = blockIdx.x + (q / nchunk) * gridDim.x, ci = q % nchunk;
+    const int t = line_of(q), ci = c0 + (q % nch) * cs;
     const int npx = min(kKC, W - ci * kKC);
     const uint32_t bytes = (uint32_t)npx * (uint32_t)d * 2u;
     tc::mbar_expect_tx(&rbar[slot], bytes);
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
   bool timed_out = false, bad = false;
   int q = 0;
   for (; q < Q && !timed_out; ++q) {
-    const int t = blockIdx.x + (q / nchunk) * gridDim.x, ci = q % nchunk;
+    const int t = line_of(q), k = q % nch, ci = c0 + k * cs;
     const int b = q & 1;
     if (issued[b] != done[b]) {
       const bool ok = tc::mbar_wait(&mbar[b], done[b] & 1u, kWaitLimit);
@@ -301,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
         const uint32_t ko = (uint32_t)s2 * 2u * kLBO;
         const uint64_t dH = tc::desc(aH + ko, kLBO, kSBO);
         const uint64_t dL = tc::desc(aL + ko, kLBO, kSBO);
-        const uint32_t acc = (ci > 0 || s2 > 0) ? 1u : 0u;
+        const uint32_t acc = (k > 0 || s2 > 0) ? 1u : 0u;
         tc::mma_bf16(tmem + kColHH, dH, dH, id, acc);
         tc::mma_bf16(tmem + kColMid, dH, dL, id, acc);
         tc::mma_bf16(tmem + kColMid, dL, dH, id, 1u);
@@ -312,7 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
     }
     issued_raw = min(Q, q + 1 + kRawStages);
     ++issued[b];
-    if (ci != nchunk - 1) continue;
+    if (k != nch - 1) continue;
     // end of line t: range flag, wait for its MMAs, drain
     if (__syncthreads_or(bad)) {
       if (tid == 0) atomicMin(&err[kErrRange], (unsigned long long)(t0 + t));
@@ -348,10 +362,17 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
           const uint64_t v = ((uint64_t)__float2uint_rz(__uint_as_float(hh[j])) << 12) +
                              ((uint64_t)__float2uint_rz(__uint_as_float(md[j])) << 6) +
                              (uint64_t)__float2uint_rz(__uint_as_float(ll[j]));
+          uint64_t* o = nullptr;
           if (n < d) {
-            if (n <= m) s2p[(int64_t)m * d + n] = v;
+            if (n <= m) o = s2p + (int64_t)m * d + n;
           } else if (n == d) {
-            S1[(int64_t)t * d + m] = v;
+            o = S1 + (int64_t)t * d + m;
+          }
+          if (o) {
+            if (split > 1)
+              atomicAdd(reinterpret_cast<unsigned long long*>(o), (unsigned long long)v);
+            else
+              *o = v;
           }
         }
       }
@@ -394,9 +415,17 @@ void launch_stats_tc(const uint16_t* x, int64_t line_stride, int W, int d, uint3
   const int grid = T < n_sm ? T : n_sm;
   const bool aligned = ((uintptr_t)x % 16 == 0) && ((line_stride * 2) % 16 == 0) &&
                        (((int64_t)W * d * 2) % 16 == 0);
-  if (aligned)
+  // fewer lines than half the SMs: split each line's chunks over the idle SMs
+  const int nchunk = (W + kKC - 1) / kKC;
+  const int split = aligned && 2 * T <= n_sm ? std::min(nchunk, n_sm / T) : 1;
+  if (split > 1) {
+    cudaMemsetAsync(S2, 0, (size_t)T * d * d * sizeof(uint64_t), st);
+    cudaMemsetAsync(S1, 0, (size_t)T * d * sizeof(uint64_t), st);
+    stats_tc_bulk_kernel<<<T * split, kThreads, kBulkSmem, st>>>(x, line_stride, W, d, maxv, T,
+                                                                 S1, S2, err, t0, split);
+  } else if (aligned)
     stats_tc_bulk_kernel<<<grid, kThreads, kBulkSmem, st>>>(x, line_stride, W, d, maxv, T, S1,
-                                                            S2, err, t0);
+                                                            S2, err, t0, 1);
   else
     stats_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, line_stride, W, d, maxv, T, S1, S2,
                                                         err, t0);

@@ -474,3 +474,38 @@ def test_overlapped_blocks_are_bitwise_block_pushes(form, kw):
         assert np.array_equal(one[k], sep[k]), k
     s1, s2 = d1.state(), d2.state()
     assert np.array_equal(s1[1], s2[1]) and np.array_equal(s1[2], s2[2])
+
+
+@pytest.mark.parametrize("bands", [57, 108, 224])
+@pytest.mark.parametrize("form", ["fp64", "fp32"])
+def test_cluster_factor_is_bitwise_one_cta(bands, form):
+    """Lines pushed one or three at a time at d >= 48 take the factor over a
+    cluster of SMs (a master CTA for the pivot chain, helper CTAs for the
+    trailing panels and the inverted diagonal blocks); the same 23 lines in
+    one push take the one-CTA kernels.  Same K_t (momentum 1: each line's
+    statistics alone), same factor bits, hence the same scores bit for bit.
+    d = 57 ends on a one-column panel and a 25-row diagonal block; d = 224 is
+    the largest d and the look-ahead kernel's range; FP32 takes the float copy
+    of the factor without the FP64 block inversion."""
+    cube = synth.gen_lines(synth.cov_c3(1e4, width=320, bands=bands), 0, 23)
+    kw = dict(form=form, warmup=0, momentum=1.0)
+    one, d1 = run_gpu(cube, profile=True, **kw)
+    sep, d2 = run_gpu(cube, push_sizes=[1] * 14 + [3] * 3, profile=True, **kw)
+    assert d1.profile_read()["chol"][2] == 1 and d2.profile_read()["chol"][2] == 17
+    for k in ("delta", "delta_n", "mask", "detecting"):
+        assert np.array_equal(one[k], sep[k]), k
+    ref = oracle.run_cube(cube, warmup=0, threshold=3.0, momentum=1.0)
+    assert rel_err(sep["delta"], ref["delta"]) <= TOL[form]
+
+
+def test_cluster_factor_not_positive_definite_reports_line():
+    """ridge 0 and constant lines at d = 64 (the cluster factor): the first
+    pivot is 0, the line is reported and its scores poisoned, and the next
+    push still runs."""
+    from paper_2408_14947_gb300 import Detector, ErxError, ERX_ENOTPD
+    det = Detector(64, 80, ridge=0.0)
+    det.push(torch.ones((1, 80, 64), dtype=torch.float32, device="cuda"))
+    with pytest.raises(ErxError) as ei:
+        det.sync()
+    assert ei.value.status == ERX_ENOTPD and ei.value.bad_line == 0
+    det.sync()  # cleared
