@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(H * NPX) solve_fp64_kernel(
 // blocked factor in shared memory once (coalesced; the other layouts read it
 // from L2 row by row, a dependent load per multiply-add), and the solve is
 // reorganised right-looking: once m_J of block J is final, every row of the
-// later blocks takes block J's 32 terms, four rows per thread at a time, so a
-// thread runs several independent chains instead of one long one.  Every y_j
+// later blocks takes block J's 32 terms, two rows per thread at a time, so a
+// thread runs independent chains instead of one long one.  Every y_j
 // still receives its multiply-adds in ascending k, m_J = D_J y_J its terms in
 // ascending order, and the squares are summed in row order: the bits of the
 // other layouts.
@@ -226,62 +226,45 @@ __global__ void __launch_bounds__(H * NPX, 1) solve_fp64_line_kernel(
     const InT* x = X + (int64_t)t * line_stride;
     const double* mu = mu_t + (int64_t)t * d;
     const int i0 = tile * NPX;
-    for (int e0 = tid; e0 < NPX * d; e0 += 8 * NT) {
-      double v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * NT, pp = e / d, k = e - pp * d, i = i0 + pp;
-        v[u] = (e < NPX * d && i < W) ? to_d(__ldg(x + (int64_t)i * ps + k)) - __ldg(mu + k) : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * NT, pp = e / d, k = e - pp * d;
-        if (e < NPX * d) r[pp * dp + k] = v[u];
-      }
+    for (int pp = 0; pp < NPX; ++pp) {
+      const int i = i0 + pp;
+      for (int k = tid; k < d; k += NT)
+        r[pp * dp + k] = i < W ? to_d(__ldg(x + (int64_t)i * ps + k)) - __ldg(mu + k) : 0.0;
     }
     __syncthreads();
-    static_assert(H > kNB / 2, "rows jj and 31 - jj of a block pair up on threads h < 16");
+    static_assert(H >= kNB + 1, "rows of a block on threads h < 32, the squares on h = H - 1");
     double d2 = 0.0;                       // the squares, in row order (thread h = H - 1)
     for (int j0 = 0; j0 < d; j0 += kNB) {
       const int nb = min(kNB, d - j0);
-      // m_J = D_J y_J: thread h < 16 takes rows h and 31 - h, 33 multiply-adds in
-      // all, one chain after the other with one multiply-add per step
-      double s1 = 0.0, s2 = 0.0;
-      if (h < kNB / 2) {
-        const int h2 = kNB - 1 - h;
+      // m_J = D_J y_J: thread h < nb takes row h (h + 1 multiply-adds, ascending)
+      double s1 = 0.0;
+      if (h < nb) {
         const double* D1 = Ls + (j0 + h) * (j0 + h + 1) / 2 + j0;
-        const double* D2 = Ls + (j0 + h2) * (j0 + h2 + 1) / 2 + j0;
-        const bool v1 = h < nb, v2 = h2 < nb;
-        for (int st = 0; st <= kNB; ++st) {
-          const bool first = st <= h;
-          const int kk = first ? st : st - h - 1;
-          const double* D = first ? D1 : D2;
-          double acc = first ? s1 : s2;
-          if (first ? v1 : v2) acc = fma(D[kk], rr[j0 + kk], acc);
-          if (first) s1 = acc; else s2 = acc;
-        }
+        const double* y = rr + j0;
+#pragma unroll 4
+        for (int kk = 0; kk <= h; ++kk) s1 = fma(D1[kk], y[kk], s1);
       } else if (h == H - 1 && j0 > 0) {
         // meanwhile the previous block's squares (its m are final)
+#pragma unroll 8
         for (int jj = 0; jj < kNB; ++jj) d2 = fma(rr[j0 - kNB + jj], rr[j0 - kNB + jj], d2);
       }
       __syncthreads();
-      if (h < kNB / 2) {
-        if (h < nb) rr[j0 + h] = s1;
-        if (kNB - 1 - h < nb) rr[j0 + kNB - 1 - h] = s2;
-      }
+      if (h < nb) rr[j0 + h] = s1;
       __syncthreads();
       if (j0 + kNB >= d && h == H - 1)   // the last block's squares
         for (int jj = 0; jj < nb; ++jj) d2 = fma(rr[j0 + jj], rr[j0 + jj], d2);
-      // rows of the later blocks take this block's terms, k ascending: rows dealt
-      // out one per thread per pass (every thread busy while rows remain), two
-      // passes at a time so that each thread runs two independent chains
+      // rows of the later blocks take this block's terms, k ascending (a block
+      // with rows after it is a whole one): rows dealt out one per thread per
+      // pass, two passes at a time so that each thread runs two chains
       const double* mJ = rr + j0;
-      for (int j = j0 + nb + h; j < d; j += 2 * H) {
+      for (int j = j0 + kNB + h; j < d; j += 2 * H) {
         const int j2 = j + H < d ? j + H : j;
         const double* L1 = Ls + j * (j + 1) / 2 + j0;
         const double* L2 = Ls + j2 * (j2 + 1) / 2 + j0;
         double a1 = rr[j], a2 = rr[j2];
-        for (int kk = 0; kk < nb; ++kk) {
+#pragma unroll
+        for (int kk = 0; kk < kNB; ++kk) {
           const double mk = mJ[kk];
           a1 = fma(-L1[kk], mk, a1);
           a2 = fma(-L2[kk], mk, a2);
@@ -448,9 +431,9 @@ size_t smem_fp32(int d) {
 
 }  // namespace
 
-// single lines: 24 threads per pixel over 5-pixel tiles (4 warps; 128 CTAs, one
+// single lines: 48 threads per pixel over 5-pixel tiles (8 warps; 128 CTAs, one
 // per SM, for a 640-pixel line)
-constexpr int kLineH = 24, kLinePix = 5;
+constexpr int kLineH = 48, kLinePix = 5;
 size_t line_smem(int d) {
   return (size_t)(((packed_size(d) + 1) & ~1) + kLinePix * (d | 1)) * sizeof(double);
 }
