@@ -909,6 +909,21 @@ def profile_batched(form, steps):
     b.close()
 
 
+def run_pipe_probe():
+    """Compile pipe_probe.cu (beside this file) for sm_103a into _build/ and run
+    it; it prints its own JSON object."""
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.abspath(__file__))
+    out_dir = os.path.join(root, "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    exe = os.path.join(out_dir, "pipe_probe")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe,
+                    os.path.join(root, "pipe_probe.cu")], check=True)
+    subprocess.run([exe], check=True)
+
+
 def measure_pipe_peaks(dev, n: int = 4096, reps: int = 5):
     """Library reference rates for the FP64 and FP32 pipes: cuBLAS DGEMM and
     SGEMM (TF32 off) on n x n x n, 2 n^3 flops, best of `reps` (CUDA events),
@@ -1040,6 +1055,9 @@ def main():
                     help="lines of the workload cube (smaller cubes for profiler captures)")
     ap.add_argument("--peaks", action="store_true",
                     help="print cuBLAS DGEMM / SGEMM rates (FP64 and FP32 pipe references)")
+    ap.add_argument("--pipe-probe", action="store_true",
+                    help="build and run pipe_probe.cu: FP64 / FP32 / integer pipe rates per SM, "
+                         "DFMA and double rsqrt latency, barrier and cluster costs (JSON)")
     ap.add_argument("--profile-case", default=None,
                     choices=["c2_fp64", "c2_fp64e", "c2_fp32", "c2_tf32", "c2_bf16", "c2_fp64_imc",
                              "c3_fp64", "c3_fp32", "c3_tf32", "c3_bf16", "c3_tf32x3", "c5_fp32",
@@ -1056,6 +1074,9 @@ def main():
     if args.peaks:
         import torch
         print(json.dumps(measure_pipe_peaks(torch.device("cuda", 0))))
+        return
+    if args.pipe_probe:
+        run_pipe_probe()
         return
     if args.profile_case:
         run_profile_case(args)
