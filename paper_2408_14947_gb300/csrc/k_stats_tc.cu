@@ -197,6 +197,12 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_kernel(
 // mbarrier with a transaction count) that thread 0 issues kRawStages chunks
 // ahead, so the global-memory latency overlaps the conversion and the MMAs.
 // Needs 16-byte aligned lines and p * d * 2 a multiple of 16.
+// Roles: warps 0-7 convert the chunks into the bf16 tiles and drain the
+// accumulators; warp 8's lane 0 issues each chunk's MMAs and the bulk copies,
+// so that the converters go on with the next chunk while the MMAs are issued
+// (with one thread of warp 0 issuing them, its warp and then the whole CTA at
+// the next barrier waited for it).  Each converter's (band, 8-pixel group)
+// items are the same in every chunk and are worked out once.
 // split > 1 (a line or a few pushed alone): CTA b takes only the chunks
 // b % split, b % split + split, ... of line b / split and adds its sums into
 // S1 and S2 (zeroed by the launcher) with 64-bit integer atomics; integer
@@ -205,7 +211,11 @@ constexpr int kRawStages = 4;
 constexpr int kRawBytes = 16384;                  // >= 64 px * 127 bands * 2 B
 constexpr int kBulkSmem = 4 * kTileBytes + kRawStages * kRawBytes;
 
-__global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
+constexpr int kConv = 256;                      // converter threads (warps 0-7)
+constexpr int kBulkThreads = kConv + 32;        // + the issuing warp
+constexpr int kMaxItems = (kRows * (kKC / 8) + kConv - 1) / kConv;   // items per converter
+
+__global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
     const uint16_t* __restrict__ X, int64_t line_stride, int W, int d, uint32_t maxv, int T,
     uint64_t* __restrict__ S1, uint64_t* __restrict__ S2, unsigned long long* __restrict__ err,
     int64_t t0, int split) {
@@ -216,8 +226,9 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int np = ((d + 1) + 15) & ~15;
-  for (int i = tid; i < 4 * kTileBytes / 16; i += kThreads)
+  for (int i = tid; i < 4 * kTileBytes / 16; i += kBulkThreads)
     reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+  const bool conv = tid < kConv;              // converter; tid == kConv issues
   if (tid == 0) {
     tc::mbar_init(&mbar[0], 1);
     tc::mbar_init(&mbar[1], 1);
@@ -254,8 +265,17 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
     tc::bulk_g2s(raw + slot * kRawBytes, X + (int64_t)t * line_stride + (int64_t)ci * kKC * d,
                  bytes, &rbar[slot]);
   };
-  if (tid == 0)
+  if (tid == kConv)
     for (int q = 0; q < kRawStages; ++q) issue(q);
+  // this converter's items: band m, pixel group g
+  int im[kMaxItems], ig[kMaxItems], nit = 0;
+#pragma unroll
+  for (int u = 0; u < kMaxItems; ++u) {
+    const int it = tid + u * kConv;
+    im[u] = conv ? it % (d + 1) : 0;
+    ig[u] = conv ? it / (d + 1) : 0;
+    if (conv && it < items) nit = u + 1;
+  }
   int issued_raw = min(Q, kRawStages);
   uint32_t issued[2] = {0u, 0u}, done[2] = {0u, 0u};
   bool timed_out = false, bad = false;
@@ -283,8 +303,10 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
     unsigned char* tH = sm + b * 2 * kTileBytes;
     unsigned char* tL = tH + kTileBytes;
     const int npx = min(kKC, W - ci * kKC);
-    for (int it = tid; it < items; it += kThreads) {
-      const int m = it % (d + 1), g = it / (d + 1);
+#pragma unroll
+    for (int u = 0; u < kMaxItems; ++u) {
+      if (u >= nit) break;
+      const int m = im[u], g = ig[u];
       uint32_t hv[4], lv[4];
 #pragma unroll
       for (int qq = 0; qq < 8; qq += 2) {
@@ -308,7 +330,7 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (tid == 0) {
+    if (tid == kConv) {
       const uint32_t aH = tc::smem_u32(tH), aL = tc::smem_u32(tL);
 #pragma unroll
       for (int s2 = 0; s2 < kKC / 16; ++s2) {
@@ -346,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_bulk_kernel(
     tc::fence_after_sync();
     const int m = 32 * (warp & 3) + lane;
     uint64_t* s2p = S2 + (int64_t)t * d * d;
-    for (int c0 = (warp >> 2) * 16; c0 < np; c0 += 32) {
+    for (int c0 = (warp >> 2) * 16; conv && c0 < np; c0 += 32) {
       uint32_t hh[16], md[16], ll[16];
       const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
       tc::tmem_ld16(lane_base + kColHH, hh);
@@ -421,11 +443,11 @@ void launch_stats_tc(const uint16_t* x, int64_t line_stride, int W, int d, uint3
   if (split > 1) {
     cudaMemsetAsync(S2, 0, (size_t)T * d * d * sizeof(uint64_t), st);
     cudaMemsetAsync(S1, 0, (size_t)T * d * sizeof(uint64_t), st);
-    stats_tc_bulk_kernel<<<T * split, kThreads, kBulkSmem, st>>>(x, line_stride, W, d, maxv, T,
-                                                                 S1, S2, err, t0, split);
+    stats_tc_bulk_kernel<<<T * split, kBulkThreads, kBulkSmem, st>>>(x, line_stride, W, d, maxv,
+                                                                     T, S1, S2, err, t0, split);
   } else if (aligned)
-    stats_tc_bulk_kernel<<<grid, kThreads, kBulkSmem, st>>>(x, line_stride, W, d, maxv, T, S1,
-                                                            S2, err, t0, 1);
+    stats_tc_bulk_kernel<<<grid, kBulkThreads, kBulkSmem, st>>>(x, line_stride, W, d, maxv, T, S1,
+                                                                S2, err, t0, 1);
   else
     stats_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(x, line_stride, W, d, maxv, T, S1, S2,
                                                         err, t0);

@@ -11,9 +11,11 @@
 //
 // One persistent CTA per SM walks lines.  The line's 32-pixel chunks (32 x d
 // floats, contiguous) arrive in a 3-stage ring of bulk asynchronous copies
-// issued ahead by one thread; all threads convert a chunk into the operand
-// tile of one of two buffers while the MMAs of the previous chunk run.  At
-// the end of a line the accumulators are drained to the FP64 scatter array.
+// issued ahead; warps 0-7 convert a chunk into the operand tile of one of two
+// buffers while the MMAs of the previous chunk run, and warp 8's lane 0
+// issues the MMAs and the copies (so the converters do not wait for the
+// issue; each converter's items are worked out once).  At the end of a line
+// the accumulators are drained to the FP64 scatter array.
 #include <cuda_bf16.h>
 
 #include "erx_internal.cuh"
@@ -22,8 +24,10 @@
 namespace erx {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kConv = 256;              // converter threads (warps 0-7)
+constexpr int kThreads = kConv + 32;    // + the issuing warp
 constexpr int kKC = 32;                 // pixels per chunk
+constexpr int kMaxItems = (kMaxDim * (kKC / 4) + kConv - 1) / kConv;   // items per converter
 constexpr int kStages = 3;              // raw ring depth
 constexpr uint32_t kLBO = 128;          // next core matrix along K
 constexpr uint32_t kWaitLimit = 1u << 26;
@@ -90,8 +94,18 @@ __global__ void __launch_bounds__(kThreads, 1) syrk_tc_kernel(
     tc::bulk_g2s(raw + slot * raw_bytes, X + (int64_t)t * line_stride + (int64_t)ci * kKC * d,
                  bytes, &rbar[slot]);
   };
-  if (tid == 0)
+  const bool conv = tid < kConv;        // converter; tid == kConv issues
+  if (tid == kConv)
     for (int q = 0; q < kStages; ++q) issue(q);
+  // this converter's items: band m, pixel group g
+  int im[kMaxItems], ig[kMaxItems], nit = 0;
+#pragma unroll
+  for (int u = 0; u < kMaxItems; ++u) {
+    const int it = tid + u * kConv;
+    im[u] = conv ? it % d : 0;
+    ig[u] = conv ? it / d : 0;
+    if (conv && it < items) nit = u + 1;
+  }
   int issued_raw = min(Q, kStages);
   uint32_t issued[2] = {0u, 0u}, done[2] = {0u, 0u};
   bool timed_out = false;
@@ -119,8 +133,10 @@ __global__ void __launch_bounds__(kThreads, 1) syrk_tc_kernel(
     const float* rw = reinterpret_cast<const float*>(raw + (q % kStages) * raw_bytes);
     unsigned char* tH = sm + b * tile_bytes;
     const int npx = min(kKC, W - ci * kKC);
-    for (int it = tid; it < items; it += kThreads) {
-      const int m = it % d, g = it / d;
+#pragma unroll
+    for (int u = 0; u < kMaxItems; ++u) {
+      if (u >= nit) break;
+      const int m = im[u], g = ig[u];
       const float c = sh[m];
       float v[CK];
 #pragma unroll
@@ -148,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1) syrk_tc_kernel(
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (tid == 0) {
+    if (tid == kConv) {
       const uint32_t aH = tc::smem_u32(tH);
 #pragma unroll
       for (int s = 0; s < kKC / KS; ++s) {
@@ -189,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 1) syrk_tc_kernel(
     for (int mt = 0; mt < (N1 ? 2 : 1); ++mt) {
       const int m = mt * 128 + 32 * quarter + lane;
       const int N = mt ? N1 : N0;
-      for (int c0 = (warp >> 2) * 16; c0 < N; c0 += 32) {
+      for (int c0 = (warp >> 2) * 16; conv && c0 < N; c0 += 32) {
         uint32_t v[16];
         tc::tmem_ld16(lane_base + (uint32_t)(mt * 128 + c0), v);
         tc::tmem_ld_wait();

@@ -15,7 +15,7 @@
 
 namespace {
 
-constexpr int kChains = 8;
+constexpr int kChains = 16;
 constexpr unsigned kPollLimit = 1u << 22;
 
 __device__ unsigned long long g_cycles[64];
@@ -182,10 +182,10 @@ int main() {
   cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
   const int n = 1024, nr = 256;
   for (int rep = 0; rep < 2; ++rep) {   // the first pass warms up, the second is kept
-    dfma_rate<<<n_sm, 512>>>(nr, 0.999, 32, 0);
-    dfma_rate<<<n_sm, 512>>>(nr, 0.999, 1, 1);
-    ffma_rate<<<n_sm, 512>>>(nr, 0.999f, 2);
-    imad_rate<<<n_sm, 512>>>(nr, 3u, 3);
+    dfma_rate<<<n_sm, 1024>>>(nr, 0.999, 32, 0);
+    dfma_rate<<<n_sm, 1024>>>(nr, 0.999, 1, 1);
+    ffma_rate<<<n_sm, 1024>>>(nr, 0.999f, 2);
+    imad_rate<<<n_sm, 1024>>>(nr, 3u, 3);
     dfma_latency<<<1, 32>>>(n, 0.999, 4);
     rsqrt_latency<<<1, 32>>>(n, 0.999, 5);
     barrier_cost<<<1, 1024>>>(n, 6);
@@ -201,8 +201,8 @@ int main() {
   int err = 0;
   cudaMemcpyFromSymbol(c, g_cycles, sizeof(c));
   cudaMemcpyFromSymbol(&err, g_err, sizeof(int));
-  // warp instructions per SM in the rate kernels: 16 warps x nr x kChains
-  const double winst = 16.0 * nr * kChains;
+  // warp instructions per SM in the rate kernels: 32 warps x nr x kChains
+  const double winst = 32.0 * nr * kChains;
   const double ghz = clk_khz * 1e-6;
   auto lanes_per_clk = [&](unsigned long long cyc) { return winst * 32.0 / (double)cyc; };
   printf("{\"sm_count\": %d, \"sm_clock_ghz_nominal\": %.3f,\n", n_sm, ghz);
