@@ -30,6 +30,9 @@ UNIT = "lines/s"
 # FP64 pipe of GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2070 MHz (the
 # nominal 1.25 TFLOP/s FP64 rate over 152 SMs at the maximum SM clock).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
+# What the scalar DFMA pipe issues: 1.671 lanes per clock per SM, measured by
+# pipe_probe.cu (python bench.py --pipe-probe), at the same clock.
+DFMA_PIPE_GFLOPS = 152 * 1.671 * 2 * 2.070
 IMAD_PEAK_GOPS = 152 * 64 * 2.070        # 32-bit integer multiply-add, per second (G)
 
 
@@ -740,6 +743,12 @@ def run_ours(args):
             "traffic": traffic, "algorithmic_bytes": (WIDTH * BANDS * 2 + WIDTH * 8 +
                                                       8 * BANDS * (BANDS + 1) / 2) * lines_per_launch,
             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2070 MHz"}
+    if roof["pipe"] == "fp64":
+        roof["dfma_pipe_gflops"] = DFMA_PIPE_GFLOPS
+        roof["frac_of_dfma_pipe"] = achieved / DFMA_PIPE_GFLOPS
+        roof["dfma_pipe_note"] = ("scalar DFMA issue rate, 1.671 lanes/clk/SM at 2070 MHz "
+                                  "(python bench.py --pipe-probe); the derived peak above is "
+                                  "the nominal FP64 rate")
     if rank == 0 and not args.quick:
         pk = measure_pipe_peaks(dev)
         roof["fp64_dgemm_gflops"] = pk["dgemm_gflops"]

@@ -197,6 +197,20 @@ int main() {
       return 1;
     }
   }
+  // the same FP64 rate kernel timed by the wall clock (CUDA events), all SMs:
+  // DFMA lanes per second, independent of what clock64() counts
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int nr_long = 4096;
+  dfma_rate<<<n_sm, 1024>>>(nr_long, 0.999, 32, 10);
+  cudaEventRecord(e0);
+  dfma_rate<<<n_sm, 1024>>>(nr_long, 0.999, 32, 10);
+  cudaEventRecord(e1);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  const double dfma_per_s = (double)n_sm * 1024.0 * nr_long * kChains / (ms * 1e-3);
   unsigned long long c[64];
   int err = 0;
   cudaMemcpyFromSymbol(c, g_cycles, sizeof(c));
@@ -219,6 +233,10 @@ int main() {
          c[7] / (double)n);
   printf(" \"cluster8_barrier_cycles\": %.1f, \"dsmem_flag_round_trip_cycles\": %.1f,\n",
          c[8] / (double)n, c[9] / (double)n);
+  printf(" \"dfma_per_s_events\": %.4g, \"dfma_lanes_per_clk_per_sm_events_at_nominal\": %.3f,\n",
+         dfma_per_s, dfma_per_s / (n_sm * ghz * 1e9));
+  printf(" \"dfma_cycles_long_run_per_warp_instr_per_sm\": %.2f,\n",
+         c[10] / (32.0 * nr_long * kChains));
   printf(" \"poll_limit_hit\": %d}\n", err);
   return err ? 2 : 0;
 }
