@@ -210,7 +210,25 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
   }
   constexpr bool kComp = sizeof(AccT) == 4;
   const AccT(*xbp)[SBT] = diag ? xa : xb;
+  // staging: thread (sp, sc) holds column sc of the pixels sp, sp + kPStep, ...
+  // of a KCF-pixel stage in registers; the next stage's loads are issued before
+  // the current stage's multiply-adds, so their latency is hidden behind them
+  constexpr int kPStep = 256 / SBT, kPer = KCF / kPStep;
+  static_assert(kPer * kPStep == KCF, "whole stages per thread");
+  const int sc = threadIdx.x % SBT, sp = threadIdx.x / SBT;
+  AccT pa[kPer], pb[kPer];
+  auto fetch = [&](int i0, int p1) {
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int i = i0 + sp + u * kPStep;
+      pa[u] = (i < p1 && a0 + sc < d) ? (AccT)x[(int64_t)i * ps + a0 + sc] - cs[sc] : (AccT)0;
+      pb[u] = (!diag && i < p1 && b0 + sc < d) ? (AccT)x[(int64_t)i * ps + b0 + sc] - cs[SBT + sc]
+                                               : (AccT)0;
+    }
+  };
+  const int pend = min(W, c_last * kScatterChunk);
   __syncthreads();
+  if (c_first * kScatterChunk < pend) fetch(c_first * kScatterChunk, min(W, (c_first + 1) * kScatterChunk));
   for (int ch = c_first; ch < c_last; ++ch) {
   AccT acc[TP][TP];
   float lo[TP][TP], hi[TP][TP];
@@ -220,17 +238,17 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
     for (int j = 0; j < TP; ++j) acc[i][j] = (AccT)0, lo[i][j] = 0.f, hi[i][j] = 0.f;
   const int p1 = min(W, (ch + 1) * kScatterChunk);
   for (int i0 = ch * kScatterChunk; i0 < p1; i0 += KCF) {
-    for (int e = threadIdx.x; e < KCF * SBT; e += 256) {
-      const int p = e / SBT, c = e % SBT, i = i0 + p;
-      AccT va = 0, vb = 0;
-      if (i < p1) {
-        if (a0 + c < d) va = (AccT)x[(int64_t)i * ps + a0 + c] - cs[c];
-        if (!diag && b0 + c < d) vb = (AccT)x[(int64_t)i * ps + b0 + c] - cs[SBT + c];
-      }
-      xa[p][c] = va;
-      if (!diag) xb[p][c] = vb;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      xa[sp + u * kPStep][sc] = pa[u];
+      if (!diag) xb[sp + u * kPStep][sc] = pb[u];
     }
     __syncthreads();
+    {
+      // the next stage: the rest of this chunk, else the next chunk's first
+      const int nx = i0 + KCF < p1 ? i0 + KCF : (ch + 1) * kScatterChunk;
+      if (nx < pend) fetch(nx, min(W, (nx / kScatterChunk + 1) * kScatterChunk));
+    }
     const int kn = min(KCF, p1 - i0);
     for (int k0 = 0; k0 < kn; k0 += kRun) {
       const int k1 = min(kn, k0 + kRun);
@@ -272,9 +290,10 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
   }   // chunk
 }
 
-// three CTAs per SM: room for the compensated FP32 sums without spills
+// three CTAs per SM (two for the 64 x 64 blocks: room for the compensated FP32
+// sums and the next stage's prefetched samples without spills)
 template <typename InT, typename AccT, int SBT>
-__global__ void __launch_bounds__(256, 3) stats_fp_kernel(const InT* __restrict__ X,
+__global__ void __launch_bounds__(256, SBT == 64 ? 2 : 3) stats_fp_kernel(const InT* __restrict__ X,
                                                        int64_t line_stride, int ps, int W, int d,
                                                        const double* __restrict__ shift,
                                                        double* __restrict__ S2f) {
@@ -360,7 +379,7 @@ __global__ void __launch_bounds__(kMeanThreads) b_mean_kernel(const BStream* __r
 }
 
 template <typename AccT>
-__global__ void __launch_bounds__(256, 3) b_stats_kernel(const BStream* __restrict__ S,
+__global__ void __launch_bounds__(256, sizeof(AccT) == 4 ? 2 : 3) b_stats_kernel(const BStream* __restrict__ S,
                                                       const BItem* __restrict__ items) {
   const BItem it = items[blockIdx.x];
   const BStream& s = S[it.s];
