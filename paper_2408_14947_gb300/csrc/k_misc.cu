@@ -20,14 +20,16 @@ __device__ __forceinline__ double to_d(T v) { return (double)v; }
 // go to mu_t / K_t.
 //
 // The recursion is linear, so a block is cut into chunks of kEmaChunk lines:
-//   pass A  each (element, chunk) runs the recursion from 0 over its chunk;
+//   pass A  each (element, chunk) forms the value the recursion reaches from 0
+//           over its chunk, as the sum of the chunk's statistics with their
+//           weights a (1-a)^k (a weighted sum, not the recursion step by step);
 //   pass B  each element chains the chunk results sequentially:
 //           s_end = (1-a)^len s_start + u_chunk  (or u_chunk if the chunk holds line 0);
 //   pass C  each (element, chunk) reruns its chunk from the carried-in state
 //           and writes the per-line values.
 // Within a chunk the arithmetic is the sequential recursion; across chunk
-// boundaries the carried value is formed in closed form, which differs from
-// the sequential recursion only by rounding.  Blocks of at most kEmaChunk lines
+// boundaries the carried value is formed in closed form (passes A and B), which
+// differs from the sequential recursion only by rounding.  Blocks of at most kEmaChunk lines
 // run pass C alone on the state (purely sequential).
 constexpr int kEmaChunk = 32;
 constexpr int kEmaPre = 8;     // line statistics in flight per thread
@@ -94,27 +96,62 @@ __device__ __forceinline__ void ema_element(const EmaSrc& s, int64_t q, int& a, 
   b = (int)(q - (int64_t)r * (r + 1) / 2);
 }
 
-// pass A: chunk-local recursion from zero; E[g][q] = its final value
+// pass A: chunk g's aggregate from zero, E[g][q] = sum_t w_t Khat_t with
+// w_t = alpha (1 - alpha)^(te - 1 - t), the line that starts the EMA (t0 + t = 0)
+// taking (1 - alpha)^(te - 1 - t): the value the recursion of Sec. III-C reaches
+// over the chunk from a zero state.  It only feeds the carry into the next
+// chunks (pass B); pass C then runs the recursion itself line by line.  The
+// weights are a per-chunk table, so an element of the integer sums takes one
+// exact conversion and one multiply-add per line (Khat = v / (W (W - 1)) with
+// the integer v, the division applied once per chunk), instead of the five FP64
+// operations of the recursion.
 __global__ void __launch_bounds__(128) ema_pass_a(EmaSrc s, int T, double alpha, int64_t t0,
                                                   double* __restrict__ E) {
+  __shared__ double wt[kEmaChunk];
+  const int g = blockIdx.y;
+  const int tb = g * kEmaChunk, te = min(T, tb + kEmaChunk);
+  const double beta = 1.0 - alpha;
+  if (threadIdx.x == 0) {
+    double w = 1.0;
+    for (int t = te - 1; t >= tb; --t) {
+      wt[t - tb] = (t0 + t == 0) ? w : w * alpha;
+      w *= beta;
+    }
+  }
+  __syncthreads();
   const int64_t n = s.P + s.d;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
-  const int g = blockIdx.y;
   int a, b;
   ema_element(s, q, a, b);
-  const double beta = 1.0 - alpha;
-  const int tb = g * kEmaChunk, te = min(T, tb + kEmaChunk);
   double u = 0.0;
-  // the line statistics are loaded kEmaPre lines ahead of the recursion, so
-  // their loads overlap instead of each waiting on the last
-  for (int t8 = tb; t8 < te; t8 += kEmaPre) {
-    double kh[kEmaPre];
+  if (s.int_stats && b >= 0) {
+    const int64_t dd = (int64_t)s.d * s.d, ab = (int64_t)a * s.d + b;
+    for (int t8 = tb; t8 < te; t8 += kEmaPre) {
+      double v[kEmaPre];
 #pragma unroll
-    for (int j = 0; j < kEmaPre; ++j) kh[j] = t8 + j < te ? ema_stat(s, t8 + j, a, b) : 0.0;
+      for (int j = 0; j < kEmaPre; ++j) {
+        const int t = t8 + j < te ? t8 + j : te - 1;
+        const int64_t s1a = (int64_t)__ldg(s.S1i + t * s.d + a);
+        const int64_t s1b = (int64_t)__ldg(s.S1i + t * s.d + b);
+        const int64_t s2 = (int64_t)__ldg(s.S2i + t * dd + ab);
+        const int64_t iv = (int64_t)s.W * s2 - s1a * s1b;
+        v[j] = s.small_ints ? i2d_exact(iv) : (double)iv;
+      }
 #pragma unroll
-    for (int j = 0; j < kEmaPre; ++j)
-      if (t8 + j < te) u = (t0 + t8 + j == 0) ? kh[j] : ema_mix(u, kh[j], alpha, beta);
+      for (int j = 0; j < kEmaPre; ++j)
+        if (t8 + j < te) u = fma(wt[t8 + j - tb], v[j], u);
+    }
+    u *= s.rw12;
+  } else {
+    for (int t8 = tb; t8 < te; t8 += kEmaPre) {
+      double kh[kEmaPre];
+#pragma unroll
+      for (int j = 0; j < kEmaPre; ++j) kh[j] = t8 + j < te ? ema_stat(s, t8 + j, a, b) : 0.0;
+#pragma unroll
+      for (int j = 0; j < kEmaPre; ++j)
+        if (t8 + j < te) u = fma(wt[t8 + j - tb], kh[j], u);
+    }
   }
   E[(int64_t)g * n + q] = u;
 }
