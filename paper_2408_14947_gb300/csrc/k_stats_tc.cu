@@ -19,6 +19,8 @@
 // mbarrier.  The drain converts the three FP32 accumulators to int64 sums.
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "erx_internal.cuh"
 #include "tc_util.cuh"
 
@@ -39,6 +41,16 @@ constexpr int kSmemBytes = 118 * 1024;
 
 __device__ __forceinline__ uint32_t tile_off(int m, int g) {
   return (uint32_t)(m >> 3) * kSBO + (uint32_t)g * kLBO + (uint32_t)(m & 7) * 16;
+}
+
+// Two integers below 128 in the halves of x -> the bf16 pair of their values,
+// exactly: bf16 bits 0x4300 | n encode 128 + n (eight significant bits), and
+// one bf16x2 subtraction of 128 leaves n.
+__device__ __forceinline__ uint32_t bf16x2_small(uint32_t x) {
+  const uint32_t biased = x | 0x43004300u;
+  const __nv_bfloat162 r = __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&biased),
+                                   __floats2bfloat162_rn(128.0f, 128.0f));
+  return *reinterpret_cast<const uint32_t*>(&r);
 }
 
 __device__ __forceinline__ uint32_t bf16_pair(uint32_t a, uint32_t b) {
@@ -207,9 +219,12 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_kernel(
 // b % split, b % split + split, ... of line b / split and adds its sums into
 // S1 and S2 (zeroed by the launcher) with 64-bit integer atomics; integer
 // sums do not depend on their order, so the result is the same bits.
-constexpr int kRawStages = 4;
+constexpr int kRawStages = 8;
 constexpr int kRawBytes = 16384;                  // >= 64 px * 127 bands * 2 B
-constexpr int kBulkSmem = 4 * kTileBytes + kRawStages * kRawBytes;
+// tile buffers (H | L pairs) and raw stages: two and eight (four tile buffers
+// with four raw stages measured the same)
+constexpr int kTileBufs = 2;
+constexpr int kBulkSmem = 2 * kTileBufs * kTileBytes + kRawStages * kRawBytes;
 
 constexpr int kConv = 256;                      // converter threads (warps 0-7)
 constexpr int kBulkThreads = kConv + 32;        // + the issuing warp
@@ -220,18 +235,17 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
     uint64_t* __restrict__ S1, uint64_t* __restrict__ S2, unsigned long long* __restrict__ err,
     int64_t t0, int split) {
   extern __shared__ __align__(1024) unsigned char sm[];   // [2][H|L] tiles, then raw ring
-  unsigned char* raw = sm + 4 * kTileBytes;
-  __shared__ __align__(8) uint64_t mbar[2];
+  unsigned char* raw = sm + 2 * kTileBufs * kTileBytes;
+  __shared__ __align__(8) uint64_t mbar[kTileBufs];
   __shared__ __align__(8) uint64_t rbar[kRawStages];
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int np = ((d + 1) + 15) & ~15;
-  for (int i = tid; i < 4 * kTileBytes / 16; i += kBulkThreads)
+  for (int i = tid; i < 2 * kTileBufs * kTileBytes / 16; i += kBulkThreads)
     reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
   const bool conv = tid < kConv;              // converter; tid == kConv issues
   if (tid == 0) {
-    tc::mbar_init(&mbar[0], 1);
-    tc::mbar_init(&mbar[1], 1);
+    for (int bb = 0; bb < kTileBufs; ++bb) tc::mbar_init(&mbar[bb], 1);
     for (int r = 0; r < kRawStages; ++r) tc::mbar_init(&rbar[r], 1);
     tc::fence_mbar_init();
   }
@@ -241,7 +255,11 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tslot;
-  const uint32_t id = tc::idesc(1, kRows, np);
+  // one MMA per operand half and 16 pixels: A = H (or L), 128 bands; B = the H
+  // and L tiles together (they are adjacent with the same 8-row stride), N =
+  // 256, so that columns 0-127 hold H.H^T (or L.H^T) and 128-255 H.L^T (or
+  // L.L^T): two MMAs of N = 256 instead of four of N = 112
+  const uint32_t id = tc::idesc(1, kRows, 2 * kRows);
   const int nchunk = (W + kKC - 1) / kKC;
   // this CTA's lines and chunks: whole lines blockIdx.x, blockIdx.x + gridDim.x,
   // ... (split 1), or the chunks c0, c0 + split, ... of line blockIdx.x / split
@@ -250,7 +268,12 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
   const int nlines = split > 1 ? ((int)blockIdx.x / split < T ? 1 : 0)
                    : (blockIdx.x < T ? (T - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
   const int Q = nlines * nch;
-  const int items = (d + 1) * (kKC / 8);
+  // even d: an item is a pair of bands (2 m2, 2 m2 + 1) over an 8-pixel group,
+  // read as one 32-bit word per pixel, and the row of ones is written apart;
+  // odd d: an item is one band (the row of ones, m = d, among them)
+  const bool pairs = (d & 1) == 0;
+  const int dh = d >> 1;
+  const int items = pairs ? dh * (kKC / 8) : (d + 1) * (kKC / 8);
   auto line_of = [&](int q) {
     return split > 1 ? (int)blockIdx.x / split : (int)blockIdx.x + (q / nch) * (int)gridDim.x;
   };
@@ -272,17 +295,18 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
 #pragma unroll
   for (int u = 0; u < kMaxItems; ++u) {
     const int it = tid + u * kConv;
-    im[u] = conv ? it % (d + 1) : 0;
-    ig[u] = conv ? it / (d + 1) : 0;
+    const int per = pairs ? dh : d + 1;
+    im[u] = conv ? it % per : 0;
+    ig[u] = conv ? it / per : 0;
     if (conv && it < items) nit = u + 1;
   }
   int issued_raw = min(Q, kRawStages);
-  uint32_t issued[2] = {0u, 0u}, done[2] = {0u, 0u};
+  uint32_t issued[kTileBufs] = {}, done[kTileBufs] = {};
   bool timed_out = false, bad = false;
   int q = 0;
   for (; q < Q && !timed_out; ++q) {
     const int t = line_of(q), k = q % nch, ci = c0 + k * cs;
-    const int b = q & 1;
+    const int b = q % kTileBufs;
     if (issued[b] != done[b]) {
       const bool ok = tc::mbar_wait(&mbar[b], done[b] & 1u, kWaitLimit);
       if (ok) ++done[b];
@@ -303,6 +327,51 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
     unsigned char* tH = sm + b * 2 * kTileBytes;
     unsigned char* tL = tH + kTileBytes;
     const int npx = min(kKC, W - ci * kKC);
+    if (pairs) {
+      const uint32_t* rw32 = reinterpret_cast<const uint32_t*>(rw);
+      const uint32_t rmask = ~(maxv | (maxv << 16));
+      const bool full = npx == kKC;
+#pragma unroll
+      for (int u = 0; u < kMaxItems; ++u) {
+        if (u >= nit) break;
+        const int m2 = im[u], g = ig[u];
+        uint32_t w[8], orv = 0u;
+#pragma unroll
+        for (int k8 = 0; k8 < 8; ++k8) {
+          const int px = g * 8 + k8;
+          w[k8] = (full || px < npx) ? rw32[px * dh + m2] : 0u;
+          orv |= w[k8];
+        }
+        bad |= (orv & rmask) != 0u;
+        uint32_t hA[4], lA[4], hB[4], lB[4];   // bands 2 m2 (A) and 2 m2 + 1 (B)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+          const uint32_t ta = __byte_perm(w[2 * k2], w[2 * k2 + 1], 0x5410);   // pixels 2k2, 2k2+1
+          const uint32_t tb = __byte_perm(w[2 * k2], w[2 * k2 + 1], 0x7632);
+          hA[k2] = bf16x2_small((ta >> 6) & 0x003F003Fu);
+          lA[k2] = bf16x2_small(ta & 0x003F003Fu);
+          hB[k2] = bf16x2_small((tb >> 6) & 0x003F003Fu);
+          lB[k2] = bf16x2_small(tb & 0x003F003Fu);
+        }
+        const uint32_t oA = tile_off(2 * m2, g), oB = tile_off(2 * m2 + 1, g);
+        *reinterpret_cast<uint4*>(tH + oA) = make_uint4(hA[0], hA[1], hA[2], hA[3]);
+        *reinterpret_cast<uint4*>(tL + oA) = make_uint4(lA[0], lA[1], lA[2], lA[3]);
+        *reinterpret_cast<uint4*>(tH + oB) = make_uint4(hB[0], hB[1], hB[2], hB[3]);
+        *reinterpret_cast<uint4*>(tL + oB) = make_uint4(lB[0], lB[1], lB[2], lB[3]);
+      }
+      if (tid < kKC / 8) {   // the row of ones (band d): 1 = 64 * 0 + 1
+        const int g = tid;
+        uint32_t lv[4];
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+          const int px = g * 8 + 2 * k2;
+          lv[k2] = (px < npx ? 0x3F80u : 0u) | (px + 1 < npx ? 0x3F800000u : 0u);
+        }
+        const uint32_t off = tile_off(d, g);
+        *reinterpret_cast<uint4*>(tH + off) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(tL + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+      }
+    } else {
 #pragma unroll
     for (int u = 0; u < kMaxItems; ++u) {
       if (u >= nit) break;
@@ -312,12 +381,12 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
       for (int qq = 0; qq < 8; qq += 2) {
         uint32_t v[2];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int px = g * 8 + qq + u;
+        for (int u2 = 0; u2 < 2; ++u2) {
+          const int px = g * 8 + qq + u2;
           uint32_t sv = 0u;
           if (px < npx) sv = (m < d) ? (uint32_t)rw[px * d + m] : 1u;
           bad |= (m < d) && (sv > maxv);
-          v[u] = sv;
+          v[u2] = sv;
         }
         hv[qq / 2] = bf16_pair(v[0] >> 6, v[1] >> 6);
         lv[qq / 2] = bf16_pair(v[0] & 63u, v[1] & 63u);
@@ -325,6 +394,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
       const uint32_t off = tile_off(m, g);
       *reinterpret_cast<uint4*>(tH + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
       *reinterpret_cast<uint4*>(tL + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+    }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -338,10 +408,8 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
         const uint64_t dH = tc::desc(aH + ko, kLBO, kSBO);
         const uint64_t dL = tc::desc(aL + ko, kLBO, kSBO);
         const uint32_t acc = (k > 0 || s2 > 0) ? 1u : 0u;
-        tc::mma_bf16(tmem + kColHH, dH, dH, id, acc);
-        tc::mma_bf16(tmem + kColMid, dH, dL, id, acc);
-        tc::mma_bf16(tmem + kColMid, dL, dH, id, 1u);
-        tc::mma_bf16(tmem + kColLL, dL, dL, id, acc);
+        tc::mma_bf16(tmem, dH, dH, id, acc);                  // HH | HL
+        tc::mma_bf16(tmem + 2 * kRows, dL, dH, id, acc);      // LH | LL
       }
       tc::commit(&mbar[b]);
       issue(q + kRawStages);      // this chunk's raw slot is free: every thread converted it
@@ -354,7 +422,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
       if (tid == 0) atomicMin(&err[kErrRange], (unsigned long long)(t0 + t));
     }
     bad = false;
-    for (int bb = 0; bb < 2; ++bb) {
+    for (int bb = 0; bb < kTileBufs; ++bb) {
       if (issued[bb] != done[bb]) {
         const bool ok = tc::mbar_wait(&mbar[bb], done[bb] & 1u, kWaitLimit);
         if (ok) ++done[bb];
@@ -369,11 +437,12 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
     const int m = 32 * (warp & 3) + lane;
     uint64_t* s2p = S2 + (int64_t)t * d * d;
     for (int c0 = (warp >> 2) * 16; conv && c0 < np; c0 += 32) {
-      uint32_t hh[16], md[16], ll[16];
+      uint32_t hh[16], hl[16], lh[16], ll[16];
       const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0;
-      tc::tmem_ld16(lane_base + kColHH, hh);
-      tc::tmem_ld16(lane_base + kColMid, md);
-      tc::tmem_ld16(lane_base + kColLL, ll);
+      tc::tmem_ld16(lane_base, hh);
+      tc::tmem_ld16(lane_base + kRows, hl);
+      tc::tmem_ld16(lane_base + 2 * kRows, lh);
+      tc::tmem_ld16(lane_base + 3 * kRows, ll);
       tc::tmem_ld_wait();
       if (m < d) {
 #pragma unroll
@@ -382,7 +451,8 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
           if (n > m && n != d) continue;        // upper triangle: not needed
           // each accumulator holds an exact integer below 2^24: convert through u32
           const uint64_t v = ((uint64_t)__float2uint_rz(__uint_as_float(hh[j])) << 12) +
-                             ((uint64_t)__float2uint_rz(__uint_as_float(md[j])) << 6) +
+                             (((uint64_t)__float2uint_rz(__uint_as_float(hl[j])) +
+                               (uint64_t)__float2uint_rz(__uint_as_float(lh[j]))) << 6) +
                              (uint64_t)__float2uint_rz(__uint_as_float(ll[j]));
           uint64_t* o = nullptr;
           if (n < d) {
@@ -408,7 +478,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1) stats_tc_bulk_kernel(
     // copies and MMAs still in flight get one more bounded wait before the CTA leaves
     for (int r = q; r < issued_raw; ++r)
       tc::mbar_wait(&rbar[r % kRawStages], (uint32_t)(r / kRawStages) & 1u, kWaitLimit);
-    for (int bb = 0; bb < 2; ++bb)
+    for (int bb = 0; bb < kTileBufs; ++bb)
       if (issued[bb] != done[bb]) tc::mbar_wait(&mbar[bb], done[bb] & 1u, kWaitLimit);
   }
   tc::fence_before_sync();
