@@ -216,19 +216,30 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
   constexpr int kPStep = 256 / SBT, kPer = KCF / kPStep;
   static_assert(kPer * kPStep == KCF, "whole stages per thread");
   const int sc = threadIdx.x % SBT, sp = threadIdx.x / SBT;
-  AccT pa[kPer], pb[kPer];
+  // the raw samples are held (the centring happens at the store, so that no
+  // instruction waits on these loads before the multiply-adds)
+  InT pa[kPer], pb[kPer];
+  uint32_t oka = 0u, okb = 0u;   // bit u: sample u is inside the line and the bands
   auto fetch = [&](int i0, int p1) {
+    oka = okb = 0u;
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int i = i0 + sp + u * kPStep;
-      pa[u] = (i < p1 && a0 + sc < d) ? (AccT)x[(int64_t)i * ps + a0 + sc] - cs[sc] : (AccT)0;
-      pb[u] = (!diag && i < p1 && b0 + sc < d) ? (AccT)x[(int64_t)i * ps + b0 + sc] - cs[SBT + sc]
-                                               : (AccT)0;
+      const bool va = i < p1 && a0 + sc < d, vb = !diag && i < p1 && b0 + sc < d;
+      pa[u] = va ? x[(int64_t)i * ps + a0 + sc] : InT(0);
+      pb[u] = vb ? x[(int64_t)i * ps + b0 + sc] : InT(0);
+      oka |= (uint32_t)va << u;
+      okb |= (uint32_t)vb << u;
     }
   };
+  // FP64 accumulation (DFMA-bound) keeps the plain staging: each stage loaded
+  // and centred just before its multiply-adds, element by element (measured
+  // 11 % faster there than the batched and prefetched staging)
+  constexpr bool kPrefetch = sizeof(AccT) == 4;
   const int pend = min(W, c_last * kScatterChunk);
   __syncthreads();
-  if (c_first * kScatterChunk < pend) fetch(c_first * kScatterChunk, min(W, (c_first + 1) * kScatterChunk));
+  if (kPrefetch && c_first * kScatterChunk < pend)
+    fetch(c_first * kScatterChunk, min(W, (c_first + 1) * kScatterChunk));
   for (int ch = c_first; ch < c_last; ++ch) {
   AccT acc[TP][TP];
   float lo[TP][TP], hi[TP][TP];
@@ -238,16 +249,30 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
     for (int j = 0; j < TP; ++j) acc[i][j] = (AccT)0, lo[i][j] = 0.f, hi[i][j] = 0.f;
   const int p1 = min(W, (ch + 1) * kScatterChunk);
   for (int i0 = ch * kScatterChunk; i0 < p1; i0 += KCF) {
+    if constexpr (kPrefetch) {
 #pragma unroll
-    for (int u = 0; u < kPer; ++u) {
-      xa[sp + u * kPStep][sc] = pa[u];
-      if (!diag) xb[sp + u * kPStep][sc] = pb[u];
+      for (int u = 0; u < kPer; ++u) {
+        xa[sp + u * kPStep][sc] = ((oka >> u) & 1u) ? (AccT)pa[u] - cs[sc] : (AccT)0;
+        if (!diag)
+          xb[sp + u * kPStep][sc] = ((okb >> u) & 1u) ? (AccT)pb[u] - cs[SBT + sc] : (AccT)0;
+      }
+    } else {
+      for (int e = threadIdx.x; e < KCF * SBT; e += 256) {
+        const int p = e / SBT, c = e % SBT, i = i0 + p;
+        AccT va = 0, vb = 0;
+        if (i < p1) {
+          if (a0 + c < d) va = (AccT)x[(int64_t)i * ps + a0 + c] - cs[c];
+          if (!diag && b0 + c < d) vb = (AccT)x[(int64_t)i * ps + b0 + c] - cs[SBT + c];
+        }
+        xa[p][c] = va;
+        if (!diag) xb[p][c] = vb;
+      }
     }
     __syncthreads();
     {
       // the next stage: the rest of this chunk, else the next chunk's first
       const int nx = i0 + KCF < p1 ? i0 + KCF : (ch + 1) * kScatterChunk;
-      if (nx < pend) fetch(nx, min(W, (nx / kScatterChunk + 1) * kScatterChunk));
+      if (kPrefetch && nx < pend) fetch(nx, min(W, (nx / kScatterChunk + 1) * kScatterChunk));
     }
     const int kn = min(KCF, p1 - i0);
     for (int k0 = 0; k0 < kn; k0 += kRun) {
