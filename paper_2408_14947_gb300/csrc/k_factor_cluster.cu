@@ -207,6 +207,16 @@ __device__ void apply_panel(double* __restrict__ C, int q0, int jbq, int d,
   }
 }
 
+// the master's rows: row blocks 0-5 (32 rows each) on warps 1, 2, 3, 5, 6, 7 and
+// block 6 on warp 4, so that warp 0 and its SM sub-partition stay free for the
+// pivots (warp 4, on the same sub-partition, takes rows only beyond 192)
+static_assert(7 * 32 >= kMaxDim, "seven row warps cover the largest panel");
+__device__ __forceinline__ int row_of_thread(int tid) {
+  const int w = tid >> 5, lane = tid & 31;
+  const int k = w == 0 ? -1 : w < 4 ? w - 1 : w == 4 ? 6 : w - 2;
+  return k < 0 ? -1 : 32 * k + lane;
+}
+
 // the helper that owns panel q >= 2
 __device__ __forceinline__ int owner_of(int q) { return 1 + (q - 2) % kH; }
 // the last panel of diagonal block b, and the helper that inverts it: the one
@@ -221,6 +231,7 @@ __device__ void master(Flags& f, double* __restrict__ sm, const double* __restri
                        unsigned long long* __restrict__ err, int64_t line) {
   __shared__ double Pl[kPB][kPB];   // Pl[r][c] = l_{j0+r, j0+c}: the panel rows' scaled entries
   __shared__ double s_ri[kPB];      // 1 / l_jj of the panel's columns
+  __shared__ double s_piv[2];       // the next pivot's updated diagonal, and its l_jj
   double* CP = sm + kOffCP;
   double* LB = sm + kOffLB;
   double* RD = sm + kOffRD;
@@ -242,31 +253,55 @@ __device__ void master(Flags& f, double* __restrict__ sm, const double* __restri
   for (int p = 0; p < np; ++p) {
     const int j0 = p * kPB, jb = min(kPB, d - j0), m = d - j0;
     const double* C = CP + (p & 1) * kPanel;
-    // (1) the column schedule of k_factor.cu on this panel: thread rl owns row j0 + rl
-    const int rl = tid, i = j0 + rl;
-    const bool own = rl < m;
+    // (1) the column schedule of k_factor.cu on this panel.  Row rl of the panel
+    //     is on the thread row_of_thread maps to it; thread 0 (warp 0) takes the
+    //     pivots, alone on its SM sub-partition's FP64 unit while the panel has at
+    //     most 192 rows.  Per column the next pivot's row scales its entry and
+    //     updates its diagonal first and hands it over; the pivot then runs while
+    //     the other rows update their entries on the other sub-partitions.
+    //     Every entry gets the same operations as in the one-CTA kernels.
+    const int rl = row_of_thread(tid), i = j0 + rl;
+    const bool own = rl >= 0 && rl < m;
     double a[kPB];
 #pragma unroll
     for (int c = 0; c < kPB; ++c) a[c] = (own && c < jb && c <= rl) ? C[rl * kPB + c] : 0.0;
-    if (own && rl == 0) pivot(a[0], 0, j0);
+    if (own && rl == 0) s_piv[0] = a[0];
     __syncthreads();
+    if (tid == 0) {
+      double v = s_piv[0];
+      pivot(v, 0, j0);
+      s_piv[1] = v;
+    }
+    __syncthreads();
+    if (own && rl == 0) a[0] = s_piv[1];
 #pragma unroll
     for (int jj = 0; jj < kPB; ++jj) {
       if (jj >= jb) break;
+      const int jn = min(jj + 1, kPB - 1);
+      const bool nxt = own && rl == jj + 1 && rl < jb;   // the next pivot's row
       double lij = 0.0;
       if (own && rl > jj) {
         lij = a[jj] * s_ri[jj];
         a[jj] = lij;
         if (rl < jb) Pl[rl][jj] = lij;
+        if (nxt) {
+          a[jn] = fma(-lij, lij, a[jn]);   // its own entry of column jj: Pl[jj + 1][jj] = lij
+          s_piv[0] = a[jn];
+        }
       }
       __syncthreads();
+      if (tid == 0 && jj + 1 < jb) {
+        double v = s_piv[0];
+        pivot(v, jj + 1, j0 + jj + 1);
+        s_piv[1] = v;
+      }
       if (own && rl > jj) {
 #pragma unroll
         for (int c = jj + 1; c < kPB; ++c)
-          if (c < jb && c <= rl) a[c] = fma(-lij, Pl[c][jj], a[c]);
-        if (rl == jj + 1 && rl < jb) pivot(a[min(jj + 1, kPB - 1)], jj + 1, i);
+          if (c < jb && c <= rl && !(nxt && c == jj + 1)) a[c] = fma(-lij, Pl[c][jj], a[c]);
       }
       __syncthreads();
+      if (nxt) a[jn] = s_piv[1];
     }
     // (2) the panel's L below it into ring slot p % kRing, once the helpers have
     //     all copied the panel that used the slot before; then its final entries
