@@ -277,7 +277,7 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
     const int kn = min(KCF, p1 - i0);
     for (int k0 = 0; k0 < kn; k0 += kRun) {
       const int k1 = min(kn, k0 + kRun);
-      for (int k = k0; k < k1; ++k) {
+      auto step = [&](int k) {
         AccT a[TP], b[TP];
 #pragma unroll
         for (int i = 0; i < TP; ++i) a[i] = xa[k][ty * TP + i], b[i] = xbp[k][tx * TP + i];
@@ -285,6 +285,12 @@ __device__ __forceinline__ void stats_fp_body(const InT* __restrict__ x, int ps,
         for (int i = 0; i < TP; ++i)
 #pragma unroll
           for (int j = 0; j < TP; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      };
+      if (k1 - k0 == kRun) {   // a whole run (all but a chunk's ragged tail): unrolled
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) step(k0 + k);
+      } else {
+        for (int k = k0; k < k1; ++k) step(k);
       }
       if constexpr (kComp) {
 #pragma unroll
