@@ -136,31 +136,54 @@ __global__ void __launch_bounds__(kFT, 1) enc_fwd_tc_kernel(
   const bool vec8 = (b % 8) == 0 && ((uintptr_t)x % 16) == 0;   // pixel rows start on 32 bytes
   uint32_t phase = 0;
   bool ok = true;
+  // vec8: a thread's items (8 bands of a pixel each) of the next tile are loaded
+  // into registers right after the current tile's layer-1 MMAs are issued, so
+  // the loads run under the MMAs and both epilogues instead of before them
+  constexpr int kFItems = 128 * (kMaxB / 8) / kFT;   // items per thread at most
+  const int nit = 128 * (bK / 8);
+  float4 pf0[kFItems], pf1[kFItems];
+  auto load_tile = [&](int64_t i0n) {
+#pragma unroll
+    for (int u = 0; u < kFItems; ++u) {
+      const int it = tid + u * kFT;
+      const int p = it / (bK / 8), g = it % (bK / 8);
+      const int64_t i = i0n + p;
+      if (it < nit && i < n && 8 * g < b) {
+        pf0[u] = __ldg(reinterpret_cast<const float4*>(x + i * b + 8 * g));
+        pf1[u] = __ldg(reinterpret_cast<const float4*>(x + i * b + 8 * g + 4));
+      }
+    }
+  };
+  auto store_tile = [&](int64_t i0c) {
+#pragma unroll
+    for (int u = 0; u < kFItems; ++u) {
+      const int it = tid + u * kFT;
+      if (it >= nit) break;
+      const int p = it / (bK / 8), g = it % (bK / 8);
+      const int64_t i = i0c + p;
+      float v[8];
+      if (i < n && 8 * g < b) {
+        v[0] = pf0[u].x, v[1] = pf0[u].y, v[2] = pf0[u].z, v[3] = pf0[u].w;
+        v[4] = pf1[u].x, v[5] = pf1[u].y, v[6] = pf1[u].z, v[7] = pf1[u].w;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = (v[q] - s_shift[8 * g + q]) * s_scale[8 * g + q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = 0.f;
+      }
+      *reinterpret_cast<uint4*>(A1 + fwd_off(p, 8 * g, sbo1)) =
+          make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                     pack_bf2(v[6], v[7]));
+    }
+  };
+  if (vec8 && (int64_t)blockIdx.x < ntile) load_tile((int64_t)blockIdx.x * 128);
   for (int64_t tile = blockIdx.x; tile < ntile && ok; tile += gridDim.x) {
     const int64_t i0 = tile * 128;
     // xn of the tile's pixels as bf16 (rows beyond n and bands beyond b: 0)
     if (vec8) {
-      // eight bands per item in two 16-byte loads, two items in flight per thread
-#pragma unroll 2
-      for (int it = tid; it < 128 * (bK / 8); it += kFT) {
-        const int p = it / (bK / 8), g = it % (bK / 8);
-        const int64_t i = i0 + p;
-        float v[8];
-        if (i < n && 8 * g < b) {
-          const float4 f0 = __ldg(reinterpret_cast<const float4*>(x + i * b + 8 * g));
-          const float4 f1 = __ldg(reinterpret_cast<const float4*>(x + i * b + 8 * g + 4));
-          v[0] = f0.x, v[1] = f0.y, v[2] = f0.z, v[3] = f0.w;
-          v[4] = f1.x, v[5] = f1.y, v[6] = f1.z, v[7] = f1.w;
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = (v[u] - s_shift[8 * g + u]) * s_scale[8 * g + u];
-        } else {
-#pragma unroll
-          for (int u = 0; u < 8; ++u) v[u] = 0.f;
-        }
-        *reinterpret_cast<uint4*>(A1 + fwd_off(p, 8 * g, sbo1)) =
-            make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
-                       pack_bf2(v[6], v[7]));
-      }
+      // eight bands per item from the two 16-byte loads made while the previous
+      // tile was multiplied (prefetch below)
+      store_tile(i0);
     } else {
       for (int it = tid; it < 128 * (bK / 8); it += kFT) {
         const int p = it / (bK / 8), g = it % (bK / 8);
@@ -192,6 +215,8 @@ __global__ void __launch_bounds__(kFT, 1) enc_fwd_tc_kernel(
       }
       tc::commit(&mbar);
     }
+    // A1 is read by the MMAs only; the registers are free: the next tile's loads
+    if (vec8 && tile + gridDim.x < ntile) load_tile((tile + gridDim.x) * 128);
     ok = tc::mbar_wait(&mbar, phase, kFWait);
     if (ok) phase ^= 1u;      // after a timeout, phase stays the parity still awaited
     if (__syncthreads_or(!ok)) break;
