@@ -204,17 +204,21 @@ __global__ void __launch_bounds__(kThreads, 1) stats_tc_kernel(
   if (warp == 0) tc::tmem_free(tmem, kTmemCols);
 }
 
-// Same sums, with the line's 64-pixel chunks brought into a 4-stage ring in
-// shared memory by bulk asynchronous copies (cp.async.bulk, completing on an
-// mbarrier with a transaction count) that thread 0 issues kRawStages chunks
-// ahead, so the global-memory latency overlaps the conversion and the MMAs.
-// Needs 16-byte aligned lines and p * d * 2 a multiple of 16.
+// Same sums (the kernel above is the route for unaligned lines), with the
+// line's 64-pixel chunks brought into a kRawStages-stage ring in shared memory
+// by bulk asynchronous copies (cp.async.bulk, completing on an mbarrier with a
+// transaction count) issued kRawStages chunks ahead, so the global-memory
+// latency overlaps the conversion and the MMAs.  Needs 16-byte aligned lines
+// and p * d * 2 a multiple of 16.
 // Roles: warps 0-7 convert the chunks into the bf16 tiles and drain the
 // accumulators; warp 8's lane 0 issues each chunk's MMAs and the bulk copies,
-// so that the converters go on with the next chunk while the MMAs are issued
-// (with one thread of warp 0 issuing them, its warp and then the whole CTA at
-// the next barrier waited for it).  Each converter's (band, 8-pixel group)
-// items are the same in every chunk and are worked out once.
+// so that the converters go on with the next chunk while the MMAs are issued.
+// Each converter's items are the same in every chunk and are worked out once;
+// for even d an item is two bands of an 8-pixel group (one 32-bit read per
+// pixel, the bf16 values from one bf16x2 subtraction per pair).  Per 16
+// pixels two MMAs of N = 256 (A = the H or the L tile, B = the H and L tiles
+// together, which lie next to each other) fill four accumulators, HH | HL and
+// LH | LL, over the 512 TMEM columns; the drain adds HL + LH as integers.
 // split > 1 (a line or a few pushed alone): CTA b takes only the chunks
 // b % split, b % split + split, ... of line b / split and adds its sums into
 // S1 and S2 (zeroed by the launcher) with 64-bit integer atomics; integer
