@@ -161,6 +161,12 @@ int route_format(int route) {
   return route == 2 ? 2 : route == 3 ? 1 : 3;
 }
 
+int least_priority() {
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  return least;
+}
+
 // chain of a stream in the step's graph: 0 above 128 dimensions, else 1
 int chain_of(const BStream& e) { return e.d > 128 ? 0 : 1; }
 
@@ -319,15 +325,22 @@ void enqueue_step(erx_batch* b, cudaStream_t st) {
 erx_status capture(erx_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec), b->exec = nullptr;
   if (b->graph) cudaGraphDestroy(b->graph), b->graph = nullptr;
+  // chain 0 is captured from a stream of the greatest priority, chain 1 from
+  // one of the least, and the graph keeps each node's priority: whenever SMs
+  // free up, the waiting CTAs of the long chain are placed first
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
   cudaStream_t cs = nullptr;
-  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return ERX_ECUDA;
+  if (cudaStreamCreateWithPriority(&cs, cudaStreamNonBlocking, greatest) != cudaSuccess)
+    return ERX_ECUDA;
   erx_status s = ERX_OK;
   if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     s = ERX_ECUDA;
   } else {
     enqueue_step(b, cs);
     if (cudaStreamEndCapture(cs, &b->graph) != cudaSuccess ||
-        cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+        cudaGraphInstantiateWithFlags(&b->exec, b->graph,
+                                      cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess)
       s = ERX_ECUDA;
   }
   cudaStreamDestroy(cs);
@@ -480,7 +493,8 @@ erx_status erx_batch_create(int32_t n, const erx_config* cfgs, void* cuda_stream
     if (s == ERX_OK) s = build_step_items(b, std::move(st_items), std::move(ema_items));
     if (s == ERX_OK) s = build_chol_items(b);
     if (s == ERX_OK &&
-        (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        (cudaStreamCreateWithPriority(&b->side, cudaStreamNonBlocking, least_priority()) !=
+             cudaSuccess ||
          cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
          cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess))
       s = ERX_ECUDA;

@@ -51,12 +51,16 @@ struct erx_ctx {
   double* imc_mprev = nullptr;   // IMC: per-line deltas, constants and chunk sums of a block
   float2* L2 = nullptr;          // FP64E: the blocked factor and mu_t as hi/lo floats
   float2* mu2 = nullptr;
-  // pushes of several blocks: block b+1's statistics, update and factor (stream A,
-  // the context's stream) overlap block b's score (stream B); the buffers that
-  // pass from A to B have one copy per slot (b & 1)
+  // pushes of several blocks: block b+1's statistics, update and factor (stream A)
+  // overlap block b's score (stream B); the buffers that pass from A to B have
+  // one copy per slot (b & 1).  Stream A, the chain every block waits on, has
+  // the greatest priority and B the least, so that SMs freed by the scores go
+  // to the statistics, EMA and factor kernels first; both fork from and join
+  // back into the context's stream.
   bool overlap = false;
-  cudaStream_t sB = nullptr;
-  cudaEvent_t ev_fac[2] = {}, ev_fin[2] = {}, ev_join = nullptr;
+  cudaStream_t sA = nullptr, sB = nullptr;
+  cudaEvent_t ev_fac[2] = {}, ev_fin[2] = {}, ev_join = nullptr, ev_fork = nullptr,
+              ev_joinA = nullptr;
   double* mu_t_s[2] = {};
   double* Linv_s[2] = {};
   float* Linv32_s[2] = {};
@@ -127,8 +131,10 @@ void free_all(erx_ctx* c) {
   if (c->h_out) cudaFreeHost(c->h_out);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   for (cudaEvent_t* e : {&c->ev_start, &c->ev_stats, &c->ev_scored, &c->ev_ready, &c->ev_fac[0],
-                        &c->ev_fac[1], &c->ev_fin[0], &c->ev_fin[1], &c->ev_join})
+                        &c->ev_fac[1], &c->ev_fin[0], &c->ev_fin[1], &c->ev_join, &c->ev_fork,
+                        &c->ev_joinA})
     if (*e) cudaEventDestroy(*e), *e = nullptr;
+  if (c->sA) cudaStreamDestroy(c->sA), c->sA = nullptr;
   if (c->sB) cudaStreamDestroy(c->sB), c->sB = nullptr;
   if (c->side) cudaStreamDestroy(c->side), c->side = nullptr;
   if (c->audit) erx_destroy(c->audit), c->audit = nullptr;
@@ -721,8 +727,13 @@ erx_status erx_create(const erx_config* cfg, void* cuda_stream, erx_ctx** out) {
     if (s == ERX_OK) s = dalloc(c, &c->mu_t_s[1], (size_t)T * d);
     if (s == ERX_OK) s = dalloc(c, &c->Linv_s[1], (size_t)T * P);
     if (s == ERX_OK && !c->fp64) s = dalloc(c, &c->Linv32_s[1], (size_t)T * P);
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (s == ERX_OK &&
-        (cudaStreamCreateWithFlags(&c->sB, cudaStreamNonBlocking) != cudaSuccess ||
+        (cudaStreamCreateWithPriority(&c->sA, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+         cudaStreamCreateWithPriority(&c->sB, cudaStreamNonBlocking, least) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&c->ev_joinA, cudaEventDisableTiming) != cudaSuccess ||
          cudaEventCreateWithFlags(&c->ev_fac[0], cudaEventDisableTiming) != cudaSuccess ||
          cudaEventCreateWithFlags(&c->ev_fac[1], cudaEventDisableTiming) != cudaSuccess ||
          cudaEventCreateWithFlags(&c->ev_fin[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -801,27 +812,39 @@ erx_status erx_push_lines(erx_ctx* c, const void* lines, int64_t n, int64_t stri
     return run_line_pipelined(c, lines, stride, delta, dn, mask, det);
   pipeline_join(c);
   const bool two = c->overlap && n > c->T;
-  for (int64_t b = 0; b < n; b += c->T) {
+  cudaStream_t user = c->stream;
+  if (two) {
+    // the blocks' stream A work runs on the internal stream of the greatest
+    // priority, after what the context's stream holds
+    cudaEventRecord(c->ev_fork, user);
+    cudaStreamWaitEvent(c->sA, c->ev_fork, 0);
+    c->stream = c->sA;
+  }
+  erx_status s = ERX_OK;
+  for (int64_t b = 0; b < n && s == ERX_OK; b += c->T) {
     const int64_t m = std::min<int64_t>(c->T, n - b);
     const char* x = (const char*)lines + b * stride_bytes;
-    erx_status s = run_block(c, x, m, stride, (char*)delta + (size_t)b * c->W * ss,
-                             dn ? (char*)dn + (size_t)b * c->W * ss : nullptr,
-                             mask ? mask + (size_t)b * c->W : nullptr, det ? det + b : nullptr,
-                             two ? (int)((b / c->T) & 1) : -1);
-    if (s != ERX_OK) return s;
+    s = run_block(c, x, m, stride, (char*)delta + (size_t)b * c->W * ss,
+                  dn ? (char*)dn + (size_t)b * c->W * ss : nullptr,
+                  mask ? mask + (size_t)b * c->W : nullptr, det ? det + b : nullptr,
+                  two ? (int)((b / c->T) & 1) : -1);
   }
   if (two) {
-    // the context's stream waits for the last scores; slot 0's buffers are the
-    // ones the single-stream path uses
+    // the context's stream waits for both streams' last work; slot 0's buffers
+    // are the ones the single-stream path uses
+    c->stream = user;
+    cudaEventRecord(c->ev_joinA, c->sA);
+    cudaStreamWaitEvent(user, c->ev_joinA, 0);
     cudaEventRecord(c->ev_join, c->sB);
-    cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    cudaStreamWaitEvent(user, c->ev_join, 0);
     c->mu_t = c->mu_t_s[0];
     c->Linv = c->Linv_s[0];
     c->Linv32 = c->Linv32_s[0];
     c->Z = c->Z_s[0];
-    const erx_status s = check_cuda(c, cudaGetLastError());
-    if (s != ERX_OK) return s;
+    const erx_status js = check_cuda(c, cudaGetLastError());
+    if (s == ERX_OK) s = js;
   }
+  if (s != ERX_OK) return s;
   return pipeline_refresh(c);
 }
 
