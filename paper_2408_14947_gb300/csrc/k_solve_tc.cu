@@ -8,8 +8,9 @@
 // meets rows j >= k0 of X (X is zero above its diagonal), so one MMA of
 // N = dK - k0 per K step accumulates into TMEM columns k0 .. dK-1 (pixel p is
 // TMEM lane p).  Two stage buffers: while the MMAs of chunk c run, the threads
-// stage chunk c+1 (R from registers loaded one chunk ahead, X from L2), and one
-// thread issues the MMAs and commits them to the stage's mbarrier.  Operand
+// stage chunk c+1 (R from registers loaded one chunk ahead, X from L2 with all
+// of a thread's loads issued before the stage's wait), and one thread issues
+// the MMAs and commits them to the stage's mbarrier.  Operand
 // tiles are K-major, no swizzle.  r is formed as (x - mu_hi) - mu_lo with mu
 // split into two floats; TF32 operands are rounded to nearest (cvt.rna).
 // 3xTF32 (FMT 3) splits each operand v as hi = tf32(v), lo = tf32(v - hi) and
@@ -64,6 +65,7 @@ __device__ __forceinline__ void pack16(const float* v, uint4& hi, uint4& lo) {
 }
 
 __host__ __device__ inline int tc_dk(int d) { return (d + kB - 1) / kB * kB; }
+constexpr int kTcDKMax = (kMaxDim + kB - 1) / kB * kB;   // 224
 // TMEM columns: the smallest power of two >= dK (at least 32)
 __host__ __device__ inline uint32_t tc_cols(int d) {
   const int dk = tc_dk(d);
@@ -110,8 +112,10 @@ __device__ __forceinline__ void load_chunk(const InT* __restrict__ xp, bool vali
 
 // Pixels tile*128 .. +127 of one line (x, pixel stride ps) with mu (d) and the
 // FP32 inverse factor Xg (packed lower); delta: the line's W scores; `line` is
-// reported on a timeout.  FMT 1: BF16, 2: TF32, 3: 3xTF32.
-template <typename InT, int FMT, bool VEC>
+// reported on a timeout.  FMT 1: BF16, 2: TF32, 3: 3xTF32.  DKM: the largest
+// dK the instance takes (128 or 224); it sizes the registers that hold a
+// thread's share of an X chunk, so that d <= 128 keeps four CTAs per SM.
+template <typename InT, int FMT, bool VEC, int DKM>
 __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps, int W, int d,
                                               const double* __restrict__ mu,
                                               const float* __restrict__ Xg,
@@ -124,6 +128,8 @@ __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps,
   constexpr int NT = FMT == 3 ? 2 : 1;
   constexpr uint32_t SBO = (kB / CK) * 128u;
   constexpr int FK = FMT == 1 ? 1 : 2;
+  // 16-byte groups of an X chunk per thread at the largest dK
+  constexpr int kXIt = (DKM * (kB / CK) + kPix - 1) / kPix;
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tslot;
@@ -168,6 +174,21 @@ __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps,
     unsigned char* Xl = Xh + x_bytes;                   // FMT 3 only
     float nxt[kB];
     if (kc + 1 < nK) load_chunk<InT, VEC>(xp, valid, k0 + kB, d, nxt);
+    // rows j = k0 .. dK-1 of X, columns k0 .. k0+31 (zero above the diagonal and
+    // beyond d): all of this thread's loads from L2 are issued here, before the
+    // stage's wait, and packed after it
+    const int nrows = dK - k0;
+    const int ne = nrows * (kB / CK);
+    float xv[kXIt][CK];
+#pragma unroll
+    for (int it = 0; it < kXIt; ++it) {
+      const int e = tid + it * kPix;
+      const int j = k0 + e / (kB / CK), kb = k0 + (e % (kB / CK)) * CK;
+      const float* Xj = Xg + (int64_t)j * (j + 1) / 2;
+#pragma unroll
+      for (int u = 0; u < CK; ++u)
+        xv[it][u] = (e < ne && j < d && kb + u <= j) ? __ldg(Xj + kb + u) : 0.f;
+    }
     if (kc >= 2) {
       const bool w_ok = tc::mbar_wait(&mbar[b], (uint32_t)((kc - 2) >> 1) & 1u, kWaitLimit);
       if (__syncthreads_or(!w_ok)) {
@@ -189,21 +210,17 @@ __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps,
       *reinterpret_cast<uint4*>(Rh + off(p, g * CK)) = hi;
       if constexpr (FMT == 3) *reinterpret_cast<uint4*>(Rl + off(p, g * CK)) = lo;
     }
-    // rows j = k0 .. dK-1 of X, columns k0 .. k0+31 (zero above the diagonal and beyond d)
-    const int nrows = dK - k0;
-    for (int e = tid; e < nrows * (kB / CK); e += kPix) {
-      const int jj = e / (kB / CK), kg = e % (kB / CK), j = k0 + jj;
-      const float* Xj = Xg + (int64_t)j * (j + 1) / 2;
-      float v[CK];
+    // the X chunk
 #pragma unroll
-      for (int u = 0; u < CK; ++u) {
-        const int k = k0 + kg * CK + u;
-        v[u] = (j < d && k <= j) ? __ldg(Xj + k) : 0.f;
+    for (int it = 0; it < kXIt; ++it) {
+      const int e = tid + it * kPix;
+      if (e < ne) {
+        const int jj = e / (kB / CK), kg = e % (kB / CK);
+        uint4 hi, lo;
+        pack16<FMT>(xv[it], hi, lo);
+        *reinterpret_cast<uint4*>(Xh + off(jj, kg * CK)) = hi;
+        if constexpr (FMT == 3) *reinterpret_cast<uint4*>(Xl + off(jj, kg * CK)) = lo;
       }
-      uint4 hi, lo;
-      pack16<FMT>(v, hi, lo);
-      *reinterpret_cast<uint4*>(Xh + off(jj, kg * CK)) = hi;
-      if constexpr (FMT == 3) *reinterpret_cast<uint4*>(Xl + off(jj, kg * CK)) = lo;
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -275,30 +292,30 @@ __device__ __forceinline__ void solve_tc_body(const InT* __restrict__ x, int ps,
   if (warp == 0) tc::tmem_free(tmem, ncols);
 }
 
-template <typename InT, int FMT, bool VEC>
-__global__ void __launch_bounds__(kPix) solve_tc_kernel(
+template <typename InT, int FMT, bool VEC, int DKM>
+__global__ void __launch_bounds__(kPix, DKM <= 128 ? 4 : 1) solve_tc_kernel(
     const InT* __restrict__ X, int64_t line_stride, int ps, int W, int d,
     const double* __restrict__ mu_t, const float* __restrict__ Lf32, float* __restrict__ delta,
     unsigned long long* __restrict__ err, int64_t t0) {
   const int t = blockIdx.y;
-  solve_tc_body<InT, FMT, VEC>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
+  solve_tc_body<InT, FMT, VEC, DKM>(X + (int64_t)t * line_stride, ps, W, d, mu_t + (int64_t)t * d,
                                Lf32 + (int64_t)t * packed_size(d), delta + (int64_t)t * W, err,
                                t0 + t, blockIdx.x);
 }
 
 // Batched form: one CTA per (stream, 128-pixel tile) item.
-template <int FMT>
-__global__ void __launch_bounds__(kPix) b_solve_tc_kernel(const BStream* __restrict__ S,
-                                                          const BItem* __restrict__ items,
-                                                          unsigned long long* __restrict__ err) {
+template <int FMT, int DKM>
+__global__ void __launch_bounds__(kPix, DKM <= 128 ? 4 : 1) b_solve_tc_kernel(
+    const BStream* __restrict__ S, const BItem* __restrict__ items,
+    unsigned long long* __restrict__ err) {
   const BItem it = items[blockIdx.x];
   const BStream& s = S[it.s];
   if (((uintptr_t)s.x % 16) == 0 && (s.d % 4) == 0)
-    solve_tc_body<float, FMT, true>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta, err,
-                                    it.s, it.tile);
+    solve_tc_body<float, FMT, true, DKM>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta,
+                                         err, it.s, it.tile);
   else
-    solve_tc_body<float, FMT, false>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta, err,
-                                     it.s, it.tile);
+    solve_tc_body<float, FMT, false, DKM>(s.x, s.d, s.W, s.d, s.mu_t, s.Lf32, (float*)s.delta,
+                                          err, it.s, it.tile);
 }
 
 // Dynamic shared memory of one CTA: two stages, raised where needed so that no
@@ -327,22 +344,22 @@ cudaError_t configure_solve_tc_kernels() {
   const int m1 = most(1), m2 = most(2), m3 = most(3);
 #define ERX_CFG(K, M) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, M)
-#define ERX_CFG_T(IT)                                  \
-  ERX_CFG((solve_tc_kernel<IT, 1, false>), m1);        \
-  ERX_CFG((solve_tc_kernel<IT, 2, false>), m2);        \
-  ERX_CFG((solve_tc_kernel<IT, 3, false>), m3);
-  ERX_CFG_T(uint16_t)
-  ERX_CFG_T(float)
-  ERX_CFG_T(double)
-  ERX_CFG((solve_tc_kernel<uint16_t, 1, true>), m1);
-  ERX_CFG((solve_tc_kernel<uint16_t, 2, true>), m2);
-  ERX_CFG((solve_tc_kernel<uint16_t, 3, true>), m3);
-  ERX_CFG((solve_tc_kernel<float, 1, true>), m1);
-  ERX_CFG((solve_tc_kernel<float, 2, true>), m2);
-  ERX_CFG((solve_tc_kernel<float, 3, true>), m3);
-  ERX_CFG((b_solve_tc_kernel<1>), m1);
-  ERX_CFG((b_solve_tc_kernel<2>), m2);
-  ERX_CFG((b_solve_tc_kernel<3>), m3);
+#define ERX_CFG_T(IT, V, K)                            \
+  ERX_CFG((solve_tc_kernel<IT, 1, V, K>), m1);         \
+  ERX_CFG((solve_tc_kernel<IT, 2, V, K>), m2);         \
+  ERX_CFG((solve_tc_kernel<IT, 3, V, K>), m3);
+#define ERX_CFG_K(K)                                   \
+  ERX_CFG_T(uint16_t, false, K)                        \
+  ERX_CFG_T(float, false, K)                           \
+  ERX_CFG_T(double, false, K)                          \
+  ERX_CFG_T(uint16_t, true, K)                         \
+  ERX_CFG_T(float, true, K)                            \
+  ERX_CFG((b_solve_tc_kernel<1, K>), m1);              \
+  ERX_CFG((b_solve_tc_kernel<2, K>), m2);              \
+  ERX_CFG((b_solve_tc_kernel<3, K>), m3);
+  ERX_CFG_K(128)
+  ERX_CFG_K(kTcDKMax)
+#undef ERX_CFG_K
 #undef ERX_CFG_T
 #undef ERX_CFG
   return e;
@@ -351,9 +368,18 @@ cudaError_t configure_solve_tc_kernels() {
 void launch_batch_solve_tc(int fmt, const BStream* S, const BItem* items, int n_items, int dmax,
                            unsigned long long* err, cudaStream_t st) {
   const size_t sm = launch_smem(dmax, fmt);
-  if (fmt == 1) b_solve_tc_kernel<1><<<n_items, kPix, sm, st>>>(S, items, err);
-  else if (fmt == 2) b_solve_tc_kernel<2><<<n_items, kPix, sm, st>>>(S, items, err);
-  else b_solve_tc_kernel<3><<<n_items, kPix, sm, st>>>(S, items, err);
+#define ERX_B(F, K) b_solve_tc_kernel<F, K><<<n_items, kPix, sm, st>>>(S, items, err)
+#define ERX_BK(K)                 \
+  if (fmt == 1) ERX_B(1, K);      \
+  else if (fmt == 2) ERX_B(2, K); \
+  else ERX_B(3, K);
+  if (tc_dk(dmax) <= 128) {
+    ERX_BK(128)
+  } else {
+    ERX_BK(kTcDKMax)
+  }
+#undef ERX_BK
+#undef ERX_B
 }
 
 void launch_solve_tc(int fmt, int in_type, const void* x, int64_t line_stride, int ps, int W,
@@ -367,22 +393,29 @@ void launch_solve_tc(int fmt, int in_type, const void* x, int64_t line_stride, i
                    (line_stride % 4) == 0 && (d % 4) == 0;
   const bool vec16 = in_type == 0 && ((uintptr_t)x % 8) == 0 && (ps % 4) == 0 &&
                      (line_stride % 4) == 0 && (d % 4) == 0;
-#define ERX_L(IT, F, V)                                                                  \
-  solve_tc_kernel<IT, F, V><<<grid, kPix, sm, st>>>((const IT*)x, line_stride, ps, W, d, \
-                                                    mu_t, Lf32, delta, err, t0)
-#define ERX_LF(F)                          \
-  if (vec16) ERX_L(uint16_t, F, true);     \
-  else if (in_type == 0) ERX_L(uint16_t, F, false); \
-  else if (vec) ERX_L(float, F, true);     \
-  else if (in_type == 1) ERX_L(float, F, false); \
-  else ERX_L(double, F, false);
-  if (fmt == 1) {
-    ERX_LF(1)
-  } else if (fmt == 2) {
-    ERX_LF(2)
-  } else {
-    ERX_LF(3)
+#define ERX_L(IT, F, V, K)                                                             \
+  solve_tc_kernel<IT, F, V, K><<<grid, kPix, sm, st>>>((const IT*)x, line_stride, ps, W, d, \
+                                                       mu_t, Lf32, delta, err, t0)
+#define ERX_LF(F, K)                                   \
+  if (vec16) ERX_L(uint16_t, F, true, K);              \
+  else if (in_type == 0) ERX_L(uint16_t, F, false, K); \
+  else if (vec) ERX_L(float, F, true, K);              \
+  else if (in_type == 1) ERX_L(float, F, false, K);    \
+  else ERX_L(double, F, false, K);
+#define ERX_LK(K)           \
+  if (fmt == 1) {           \
+    ERX_LF(1, K)            \
+  } else if (fmt == 2) {    \
+    ERX_LF(2, K)            \
+  } else {                  \
+    ERX_LF(3, K)            \
   }
+  if (tc_dk(d) <= 128) {
+    ERX_LK(128)
+  } else {
+    ERX_LK(kTcDKMax)
+  }
+#undef ERX_LK
 #undef ERX_LF
 #undef ERX_L
 }
