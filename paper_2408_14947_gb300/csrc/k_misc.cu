@@ -361,15 +361,22 @@ __global__ void __launch_bounds__(128) imc_pass_c(EmaSrc s, int T, int64_t t0, i
 }
 
 // ---- S6: line-by-line normalisation (Sec. III-E) -------------------------
-__device__ double block_sum(double v, double* sh) {
+// Sum of v over the block: a shuffle tree per warp, then the warps' sums added
+// in warp order by thread 0 alone (the result is valid in thread 0 only).  An
+// FP64 warp instruction costs this part's SM about 19 cycles of its FP64 pipe
+// however few lanes it uses, so the tail of the reduction, the division, the
+// square root and the reciprocal run once per line, not once per warp.
+__device__ double block_sum0(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) sh[w] = v;
   __syncthreads();
   double tot = 0.0;
-  const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) tot += sh[i];
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) tot += sh[i];
+  }
   return tot;
 }
 
@@ -380,16 +387,25 @@ __device__ __forceinline__ void normalise_body(const ST* __restrict__ dl, int W,
                                                ST* __restrict__ dn, uint8_t* __restrict__ mask,
                                                uint8_t* __restrict__ detecting) {
   __shared__ double sh[32];
+  __shared__ double bc[2];   // the line's mean and 1 / sigma, from thread 0
   double s = 0.0;
   for (int i = threadIdx.x; i < W; i += blockDim.x) s += to_d(dl[i]);
-  const double mean = block_sum(s, sh) / (double)W;
+  const double ts = block_sum0(s, sh);
+  if (threadIdx.x == 0) bc[0] = ts / (double)W;
+  __syncthreads();
+  const double mean = bc[0];
   double v = 0.0;
   for (int i = threadIdx.x; i < W; i += blockDim.x) {
     const double e = __dsub_rn(to_d(dl[i]), mean);
     v = __fma_rn(e, e, v);
   }
-  const double sd = sqrt(block_sum(v, sh) / (double)W);
-  const double rsd = sd > 0.0 ? 1.0 / sd : 0.0;   // one division per line, not per pixel
+  const double tv = block_sum0(v, sh);
+  if (threadIdx.x == 0) {
+    const double sd = sqrt(tv / (double)W);
+    bc[1] = sd > 0.0 ? 1.0 / sd : 0.0;   // one division per line, not per pixel
+  }
+  __syncthreads();
+  const double rsd = bc[1];
   for (int i = threadIdx.x; i < W; i += blockDim.x) {
     const double z = (to_d(dl[i]) - mean) * rsd;
     if (dn) dn[i] = (ST)z;
