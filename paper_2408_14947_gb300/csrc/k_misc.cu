@@ -169,17 +169,26 @@ __global__ void __launch_bounds__(128) ema_pass_b(int64_t n, int T, int G, doubl
   double s = *st;
   double bp = 1.0;                       // (1-a)^kEmaChunk
   for (int i = 0; i < kEmaChunk; ++i) bp *= beta;
-  for (int g = 0; g < G; ++g) {
-    Cin[(int64_t)g * n + q] = s;
-    const int tb = g * kEmaChunk, te = min(T, tb + kEmaChunk);
-    const bool has_init = (t0 + tb <= 0) && (t0 + te > 0);
-    double w = bp;
-    if (te - tb != kEmaChunk) {
-      w = 1.0;
-      for (int i = tb; i < te; ++i) w *= beta;
+  // the chunk aggregates are loaded kEmaPre at a time ahead of the chain, which
+  // then waits on no load
+  for (int g8 = 0; g8 < G; g8 += kEmaPre) {
+    double ev[kEmaPre];
+#pragma unroll
+    for (int j = 0; j < kEmaPre; ++j) ev[j] = g8 + j < G ? E[(int64_t)(g8 + j) * n + q] : 0.0;
+#pragma unroll
+    for (int j = 0; j < kEmaPre; ++j) {
+      const int g = g8 + j;
+      if (g >= G) break;
+      Cin[(int64_t)g * n + q] = s;
+      const int tb = g * kEmaChunk, te = min(T, tb + kEmaChunk);
+      const bool has_init = (t0 + tb <= 0) && (t0 + te > 0);
+      double w = bp;
+      if (te - tb != kEmaChunk) {
+        w = 1.0;
+        for (int i = tb; i < te; ++i) w *= beta;
+      }
+      s = has_init ? ev[j] : __dadd_rn(__dmul_rn(w, s), ev[j]);
     }
-    const double e = E[(int64_t)g * n + q];
-    s = has_init ? e : __dadd_rn(__dmul_rn(w, s), e);
   }
   *st = s;
 }
